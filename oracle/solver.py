@@ -1,0 +1,168 @@
+"""Algorithm 1 (PCG), the subset weighted mean and the Levenberg-Marquardt step.
+
+* ``pcg``: Algorithm 1 (Sec. 3.3) step by step, in the paper's notation
+  (b, M^-1, x, u, g, r, z, p, alpha, beta). The preconditioner is the Jacobi
+  M^-1 = 1 / diag(J^T J), or a given positive diagonal D in its place.
+* ``combine``: Eq. combine-pcg (Sec. 3.3), Delta = sum_i M_i Delta_i / sum_k M_k.
+* ``lm_step``: Eq. norm-eq for the direction, Eq. tr-update for rho and the
+  damping update, with gamma = 1 (no line search).
+
+Readings where the paper is silent (stated again in the design doc):
+  - the loop "for i = 0 to n_iters" runs n_iters times after the initial product;
+  - M^-1_k = 0 where diag_k <= 1e-30 (parameters the subset never sees);
+  - the break test compares ||r||^2 with break_rel2 * ||b||^2 (0 disables it);
+  - a step is accepted when rho > 1e-5 and the predicted decrease is positive;
+    lambda is multiplied by 1 - (2 rho - 1)^3 (accepted) or 2 (rejected), then
+    clamped to [lambda_min, lambda_max];
+  - the predicted decrease uses every subset's J_i and F_i at the old parameters.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import jacobian as jac
+
+
+@dataclass
+class PCGStats:
+    iters: int = 0
+    rel_residual: float = 0.0        # ||r|| / ||b|| (recursive r)
+    breakdown: bool = False
+    history: list = field(default_factory=list)   # ||r||^2 after each iteration
+
+
+def jacobi_inverse(diag: np.ndarray) -> np.ndarray:
+    return np.where(diag > 1e-30, 1.0 / np.where(diag > 1e-30, diag, 1.0), 0.0)
+
+
+def pcg(apply_JTJ, b: np.ndarray, M: np.ndarray, lam: float, n_iters: int = 8,
+        break_rel2: float = 0.0, Minv: np.ndarray | None = None, x_star=None):
+    """Algorithm 1. apply_JTJ(v) returns J^T J v. Returns (x, stats).
+
+    If x_star is given, stats.history also records nothing extra; it is only
+    accepted for symmetry with callers that track errors themselves.
+    """
+    if Minv is None:
+        Minv = jacobi_inverse(M)
+    st = PCGStats()
+    bb = float(np.vdot(b, b))
+    x = Minv * b                                   # x0 = M^-1 b
+    g = apply_JTJ(x)                               # u0 = J x0; g0 = J^T u0
+    r = b - (g + lam * M * x)                      # r0 = b - (g0 + lambda M x0)
+    z = Minv * r                                   # z0 = M^-1 r0
+    p = z.copy()                                   # p0 = z0
+    rz = float(np.vdot(r, z))
+    for i in range(n_iters):
+        g = apply_JTJ(p)                           # u_i = J p_i; g_i = J^T u_i
+        g = g + lam * M * p                        # g_i += lambda M p_i
+        pg = float(np.vdot(p, g))
+        if not np.isfinite(pg) or pg <= 0.0:
+            st.breakdown = True
+            break
+        alpha = rz / pg                            # alpha_i = r^T z / p^T g
+        x = x + alpha * p
+        r = r - alpha * g
+        z = Minv * r
+        rz_new = float(np.vdot(r, z))
+        beta = rz_new / rz if rz != 0.0 else 0.0
+        p = z + beta * p
+        rz = rz_new
+        st.iters = i + 1
+        rr = float(np.vdot(r, r))
+        st.history.append(rr)
+        if break_rel2 > 0.0 and rr < break_rel2 * bb:
+            break
+    st.rel_residual = float(np.sqrt(np.vdot(r, r) / bb)) if bb > 0 else 0.0
+    return x, st
+
+
+def combine(deltas: list, diags: list) -> np.ndarray:
+    """Eq. combine-pcg: elementwise weighted mean with weights M_i = diag(J_i^T J_i)."""
+    num = np.zeros_like(deltas[0])
+    den = np.zeros_like(diags[0])
+    for d, m in zip(deltas, diags):
+        num += m * d
+        den += m
+    return np.where(den > 0.0, num / np.where(den > 0.0, den, 1.0), 0.0)
+
+
+@dataclass
+class SubsetSystem:
+    cams: list
+    lin: list
+    F: np.ndarray
+    cost: float
+    b: np.ndarray
+    M: np.ndarray
+
+
+def build_subset(params: np.ndarray, cams: list, targets_flat: np.ndarray, smooth=False) -> SubsetSystem:
+    """buildCache + diagJTJ of Algorithm 1: F, b = -J^T F and M = diag(J^T J) for one subset."""
+    lin = jac.linearise(params, cams, smooth)
+    img = np.concatenate([vl.ras.image.ravel() for vl in lin])
+    F = jac.residual(img, targets_flat)
+    N = params.shape[0]
+    b = -jac.apply_JT(lin, F, N)
+    M = jac.jacobi_diag(lin, N)
+    return SubsetSystem(cams, lin, F, jac.cost(F), b, M)
+
+
+def solve_subset(sys_: SubsetSystem, lam: float, n_iters: int, break_rel2: float = 0.0, Minv=None):
+    N = sys_.b.shape[0]
+    n_res = sys_.F.shape[0]
+    A = lambda v: jac.apply_JT(sys_.lin, jac.apply_J(sys_.lin, v, n_res), N)
+    return pcg(A, sys_.b, sys_.M, lam, n_iters, break_rel2, Minv)
+
+
+@dataclass
+class LMResult:
+    params: np.ndarray
+    lam: float
+    accepted: bool
+    rho: float
+    cost: float
+    cost_new: float
+    pred: float
+    delta: np.ndarray
+    pcg: list
+
+
+def lm_step(params: np.ndarray, subsets: list, targets: list, lam: float, n_iters: int = 8,
+            lambda_min: float = 1e-4, lambda_max: float = 1e4, break_rel2: float = 0.0,
+            smooth=False, precond=None) -> LMResult:
+    """One LM iteration over image subsets (Sec. 3.2 and Eq. combine-pcg).
+
+    subsets: list of camera lists; targets: list of flat target vectors (one per subset).
+    precond: optional callable (SubsetSystem) -> D replacing M^-1 in Algorithm 1.
+    """
+    systems = [build_subset(params, cams, tg, smooth) for cams, tg in zip(subsets, targets)]
+    deltas, stats = [], []
+    for s in systems:
+        Minv = precond(s) if precond is not None else None
+        d, st = solve_subset(s, lam, n_iters, break_rel2, Minv)
+        deltas.append(d)
+        stats.append(st)
+    delta = combine(deltas, [s.M for s in systems])
+    cost0 = sum(s.cost for s in systems)
+    pred = 0.0
+    for s in systems:
+        u = jac.apply_J(s.lin, delta, s.F.shape[0]) + s.F
+        pred += float(np.dot(u, u))
+    new = params + delta
+    cost1 = 0.0
+    for cams, tg in zip(subsets, targets):
+        F1 = jac.render(new, cams, smooth) - tg
+        cost1 += float(np.dot(F1, F1))
+    den = cost0 - pred
+    rho = (cost0 - cost1) / den if den > 0 else -np.inf
+    accepted = bool(den > 0 and rho > 1e-5)
+    if accepted:
+        lam = lam * (1.0 - (2.0 * rho - 1.0) ** 3)
+        out = new
+    else:
+        lam = lam * 2.0
+        out = params
+    lam = float(min(max(lam, lambda_min), lambda_max))
+    return LMResult(out, lam, accepted, float(rho), cost0, cost1, pred, delta, stats)
