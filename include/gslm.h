@@ -1,0 +1,213 @@
+/*
+ * gslm.h - C ABI of the GB300 (sm_103a) Levenberg-Marquardt / PCG hot path for
+ * 3D Gaussian Splatting, after 3DGS-LM (arXiv 2409.12892).
+ *
+ * What the calls compute (paper sections in brackets):
+ *   gslm_render        images of the splatted scene [Sec. 3.1, Eq. alpha-blending]
+ *   gslm_build_cache   residual F = c - C, cost ||F||^2, the per-(pixel, splat)
+ *                      gradient cache and b = -J^T F [Sec. 3.3 "buildCache",
+ *                      "sortCacheByGaussians"; Algorithm 1, first two lines]
+ *   gslm_apply_J       u = J p  [Sec. A, Eq. apply-j]
+ *   gslm_apply_JT      g = J^T u  [Sec. A, Eq. apply-jt]
+ *   gslm_jacobi_diag   M = diag(J^T J)  [Sec. A, Eq. diag-jtj]
+ *   gslm_pcg_solve     Algorithm 1 on (J^T J + lambda M) x = b  [Sec. 3.3]
+ *   gslm_combine_*     weighted mean of subset directions [Eq. combine-pcg]
+ *   gslm_lm_step       one LM iteration over image subsets [Sec. 3.2,
+ *                      Eq. norm-eq, Eq. tr-update, Eq. combine-pcg]
+ *
+ * Conventions
+ *   - Every array pointer is a DEVICE pointer unless its comment says "host".
+ *     Arrays passed in are owned by the caller; the library never frees them.
+ *   - The library owns gslm_ctx and gslm_cache objects and the device memory
+ *     behind them (allocated with cudaMallocAsync on the context's stream).
+ *   - All work is enqueued on the context's CUDA stream. Outputs are valid
+ *     once that stream has been synchronised. gslm_build_cache synchronises
+ *     once (to size the cache); gslm_lm_step synchronises to fill its stats;
+ *     gslm_pcg_solve synchronises only when stats is non-NULL.
+ *   - Errors are returned as gslm_status codes; nothing throws across the
+ *     ABI; gslm_last_error() gives a message for the last failure on a
+ *     context. The library never traps on the device.
+ *
+ * Layouts
+ *   - Gaussian parameters and every parameter-space vector (b, p, g, x, M,
+ *     preconditioner, Delta): structure of arrays, float32 [59][ld], element
+ *     (k, i) at offset k*ld + i for parameter k of Gaussian i; ld >= N and a
+ *     multiple of 4. Parameter order per Gaussian: position (3), log-scale (3),
+ *     quaternion w,x,y,z (4, not normalised), opacity logit (1), SH (48, index
+ *     3*coeff + channel, coeff l-major, degree <= 3). This is the paper's
+ *     per-attribute layout q (Sec. A, "Design of applyJ and diagJTJ").
+ *   - Residual-space vectors (targets, F, u, images): float32, the views of a
+ *     call concatenated in order, each view row-major [H][W][3].
+ */
+#ifndef GSLM_H
+#define GSLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GSLM_OK = 0,
+  GSLM_E_INVALID = -1,        /* bad argument (null pointer, size, layout) */
+  GSLM_E_OOM = -2,            /* device allocation failed or budget exceeded */
+  GSLM_E_CUDA = -3,           /* a CUDA runtime call failed */
+  GSLM_E_CACHE_OVERFLOW = -4, /* the cache would exceed options.mem_budget */
+  GSLM_E_TIMEOUT = -5,        /* a bounded device wait ran out */
+  GSLM_E_NUMERIC = -6,        /* non-finite value where one is not allowed */
+  GSLM_W_PCG_BREAKDOWN = 1    /* PCG stopped early: p^T g <= 0 or not finite */
+} gslm_status;
+
+typedef enum { GSLM_CACHE_FP32 = 0, GSLM_CACHE_BF16 = 1, GSLM_CACHE_FP16S = 2 } gslm_cache_fmt;
+
+/* A posed pinhole camera. World point X maps to camera point R X + t (OpenCV
+ * axes: x right, y down, z forward) and to pixel (fx x/z + cx, fy y/z + cy).
+ * Pixel (px, py) has its centre at (px + 0.5, py + 0.5). */
+typedef struct {
+  float R[9];          /* row-major world -> camera rotation */
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} gslm_camera;
+
+typedef struct {
+  int32_t cache_fmt;   /* gslm_cache_fmt */
+  int32_t n_iters;     /* PCG loop iterations after the initial product (paper: 8) */
+  float break_rel2;    /* stop when ||r||^2 < break_rel2 ||b||^2 (paper: 0.01); 0 = never */
+  float lambda_min;    /* LM damping clamp (paper: 1e-4 .. 1e4) */
+  float lambda_max;
+  int32_t smooth;      /* test mode: no alpha clamp/skip, no T stop, no SH clamp, no tile culling */
+  size_t mem_budget;   /* bytes a cache may take; 0 = no limit */
+  int32_t group;       /* lanes per cache segment in the apply kernels (0 = default) */
+  int32_t profile;     /* 1: gslm_lm_step records CUDA events per phase (ms_phase in its stats) */
+  int32_t reserved[6];
+} gslm_options;
+
+typedef struct gslm_ctx gslm_ctx;
+typedef struct gslm_cache gslm_cache;
+
+typedef struct {
+  int64_t entries;       /* (pixel, splat) cache entries */
+  int64_t segments;      /* non-empty (tile, splat) segments */
+  int64_t splats;        /* visible (view, Gaussian) splats */
+  int64_t active_splats; /* splats with at least one entry */
+  int64_t keys;          /* tile keys sorted while building */
+  int64_t bytes;         /* device bytes held by the cache */
+  int64_t pixels;        /* residual pixels covered (sum of W*H over the views) */
+  int32_t views;
+  int32_t cache_fmt;
+} gslm_cache_info;
+
+typedef struct {
+  int32_t iters;         /* loop iterations run */
+  int32_t breakdown;     /* 1 if p^T g <= 0 or non-finite stopped the loop */
+  double rr;             /* ||r||^2 of the recursive residual at exit */
+  double bb;             /* ||b||^2 */
+} gslm_pcg_stats;
+
+typedef struct {
+  float lambda;          /* in: damping for this step; out: updated damping */
+  int32_t step;          /* in/out: LM step counter (incremented) */
+} gslm_lm_state;
+
+typedef struct {
+  double cost;           /* ||F(x)||^2 over all subsets' views */
+  double cost_new;       /* ||F(x + Delta)||^2 */
+  double predicted;      /* sum_i ||J_i Delta + F_i||^2 */
+  double rho;            /* Eq. tr-update */
+  int32_t accepted;
+  int32_t pcg_iters;     /* summed over subsets */
+  int64_t cache_entries; /* summed over subsets */
+  int64_t cache_bytes;
+  double ms_total;       /* device time of the step (CUDA events) */
+  /* With options.profile: device ms per phase, summed over the step:
+   * [0] cache build, [1] Jacobi diagonal, [2] tangent (dy/dx) p, [3] apply_J tile
+   * kernel, [4] apply_JT tile kernel, [5] adjoint (dy/dx)^T ybar, [6] PCG vector
+   * kernels, [7] rho evaluation (J Delta and the trial render). */
+  double ms_phase[8];
+  int32_t n_pairs;       /* J p + J^T u pairs executed (initial product + PCG iterations) */
+  int32_t pad;
+  /* Algorithmic bytes of those pairs: per pair on a cache with E entries of B_e
+   * payload bytes, P pixels, N Gaussians and S active splats:
+   * 2 E (B_e + 1) + 24 P + 472 N + 192 S. */
+  double pair_bytes;
+} gslm_lm_stats;
+
+/* Default options: FP32 cache, 8 iterations, break 0.01, lambda in [1e-4, 1e4]. */
+void gslm_default_options(gslm_options* opt);
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+gslm_status gslm_create(const gslm_options* opt, void* cuda_stream, gslm_ctx** out);
+void gslm_destroy(gslm_ctx* ctx);
+const char* gslm_last_error(const gslm_ctx* ctx);
+/* Replace the context's options (e.g. to switch cache format). */
+gslm_status gslm_set_options(gslm_ctx* ctx, const gslm_options* opt);
+
+/* Render the V views [Sec. 3.1, Eq. alpha-blending].
+ * params: [59][ld]; cams: host array of V cameras; img: [sum W*H][3].
+ * If targets is non-NULL, also writes cost[0] = ||img - targets||^2 (cost: host
+ * double*, may be NULL). */
+gslm_status gslm_render(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld,
+                        const gslm_camera* cams, int32_t V, float* img,
+                        const float* targets, double* cost);
+
+/* Build the gradient cache of one image subset [Sec. 3.3, Algorithm 1 lines 1-2].
+ * Writes F = img - targets into F (may be NULL), b = -J^T F into b ([59][ld], may be
+ * NULL) and cost ||F||^2 into *cost (host, may be NULL). The cache holds its
+ * own device copy of params, so the caller may change or free params afterwards.
+ * Returns GSLM_E_CACHE_OVERFLOW (and no cache) if options.mem_budget is exceeded. */
+gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld,
+                             const gslm_camera* cams, int32_t V, const float* targets,
+                             gslm_cache** cache, float* F, float* b, double* cost);
+gslm_status gslm_cache_stats(const gslm_cache* cache, gslm_cache_info* info);
+void gslm_cache_free(gslm_cache* cache);
+
+/* u = J p [Eq. apply-j]. p: [59][ld]; u: [pixels][3]. */
+gslm_status gslm_apply_J(gslm_ctx* ctx, const gslm_cache* cache, const float* p, float* u);
+/* g = J^T u [Eq. apply-jt]. u: [pixels][3]; g: [59][ld]. */
+gslm_status gslm_apply_JT(gslm_ctx* ctx, const gslm_cache* cache, const float* u, float* g);
+/* M = diag(J^T J) [Eq. diag-jtj]. diag: [59][ld]. */
+gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* cache, float* diag);
+
+/* Algorithm 1 [Sec. 3.3]: x ~ (J^T J + lambda M)^-1 b with M = diag (given),
+ * preconditioner M^-1 = 1/M (0 where M <= 1e-30) or, if precond is non-NULL,
+ * the given positive diagonal D ([59][ld]) in its place. x: [59][ld] output.
+ * stats: host pointer or NULL (NULL: no synchronisation). Returns
+ * GSLM_W_PCG_BREAKDOWN if the loop stopped on p^T g <= 0. */
+gslm_status gslm_pcg_solve(gslm_ctx* ctx, const gslm_cache* cache, const float* b,
+                           const float* diag, const float* precond, float lambda,
+                           float* x, gslm_pcg_stats* stats);
+
+/* Eq. combine-pcg, accumulated subset by subset:
+ * gslm_combine_accumulate: num += M_i * Delta_i, den += M_i;
+ * gslm_combine_finish:     Delta = num / den (0 where den == 0). All [59][ld]. */
+gslm_status gslm_combine_accumulate(gslm_ctx* ctx, int64_t N, int64_t ld, const float* delta_i,
+                                    const float* diag_i, float* num, float* den);
+gslm_status gslm_combine_finish(gslm_ctx* ctx, int64_t N, int64_t ld, const float* num,
+                                const float* den, float* delta);
+
+/* One LM step [Sec. 3.2]: for each of the n_b subsets build the cache, the
+ * Jacobi diagonal and the PCG direction; combine [Eq. combine-pcg]; evaluate
+ * rho [Eq. tr-update] with gamma = 1; on acceptance (rho > 1e-5) params +=
+ * Delta in place, else params are unchanged; lambda is updated and clamped.
+ * cams: host array of all cameras; targets: [sum over all cams W*H][3] in camera
+ * order; subset_views: host, concatenated camera indices of the subsets;
+ * subset_off: host, n_b + 1 offsets into subset_views. precond: optional
+ * per-subset preconditioners (host array of n_b device pointers, or NULL). */
+gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld,
+                         const gslm_camera* cams, int32_t n_cams, const float* targets,
+                         const int32_t* subset_views, const int32_t* subset_off, int32_t n_b,
+                         const float* const* precond, gslm_lm_state* state, gslm_lm_stats* stats);
+
+/* Library version string. */
+const char* gslm_version(void);
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t gslm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSLM_H */

@@ -38,6 +38,9 @@ class Projection:
     raw_rgb: np.ndarray      # (S, 3) SH(dir) + 0.5 before the clamp
     rect_margin: np.ndarray  # (S,) relative distance of the rect/radius decisions to a flip
     depth_raw: np.ndarray    # (N,) camera-space z of every Gaussian
+    rect_flip: np.ndarray = None  # (S,) a radius or tile-rect decision lies within float32 reach
+    rect_outer: np.ndarray = None  # (S, 4) union of the rects float32 rounding could produce
+    rect_inner: np.ndarray = None  # (S, 4) their intersection
 
 
 def camera_center(cam) -> np.ndarray:
@@ -72,7 +75,8 @@ def project(params: np.ndarray, cam, smooth: bool = False, want_jac: bool = True
             n=N, visible=cat("visible"),
             idx=np.concatenate([p.idx + o for p, o in zip(parts, offs)]),
             y=cat("y"), jac=cat("jac"), depth=cat("depth"), radius=cat("radius"), rect=cat("rect"),
-            raw_rgb=cat("raw_rgb"), rect_margin=cat("rect_margin"), depth_raw=cat("depth_raw"))
+            raw_rgb=cat("raw_rgb"), rect_margin=cat("rect_margin"), depth_raw=cat("depth_raw"),
+            rect_flip=cat("rect_flip"), rect_outer=cat("rect_outer"), rect_inner=cat("rect_inner"))
     return _project(P, cam, smooth, want_jac)
 
 
@@ -175,12 +179,46 @@ def _project(P: np.ndarray, cam, smooth: bool, want_jac: bool) -> Projection:
         y1[:] = tiles_y
     rect = np.stack([x0, y0, x1, y1], axis=1)
 
-    # relative margins of the integer decisions (radius ceil, rect floors)
+    # margins of the integer decisions (radius ceil, rect floors), relative; and
+    # the rects float32 arithmetic could produce instead: a radius within 1e-5
+    # (relative) of an integer may round to its neighbour, a rect edge within
+    # 1e-3 px of a tile edge may floor to the neighbouring tile.
     frac = lambda v: np.abs(v - np.round(v))
     m = frac(r_real) / np.maximum(r_real, 1e-30)
     for e in ex:
         m = np.minimum(m, frac(e) / np.maximum(np.abs(e), 1.0))
     m = np.minimum(m, np.abs(tz.v - cv.NEAR) / cv.NEAR)
+
+    def rect_of(rad, shift=(0, 0, 0, 0)):
+        e = [(yv[:, 0] - rad) / cv.TILE, (yv[:, 1] - rad) / cv.TILE,
+             (yv[:, 0] + rad) / cv.TILE, (yv[:, 1] + rad) / cv.TILE]
+        lim = (tiles_x, tiles_y, tiles_x, tiles_y)
+        out = []
+        for i in range(4):
+            f = np.floor(e[i]) + (1 if i >= 2 else 0) + shift[i]
+            out.append(np.clip(f, 0, lim[i]).astype(np.int64))
+        return np.stack(out, axis=1)
+
+    alts = [rect]
+    near_r = frac(r_real) < 1e-5 * np.maximum(r_real, 1.0)
+    r_alt = np.where(r_real - np.floor(r_real) < 0.5, radius - 1, radius + 1)
+    alts.append(np.where(near_r[:, None], rect_of(r_alt), rect))
+    for i, e in enumerate(ex):
+        near = frac(e) * cv.TILE < 1e-3
+        step = np.where(e - np.floor(e) < 0.5, -1, 1)
+        shift_v = [0, 0, 0, 0]
+        alt = rect.copy()
+        for sgn in (-1, 1):
+            shift_v[i] = sgn
+            cand = rect_of(radius, tuple(shift_v))
+            alt = np.where(((step == sgn) & near)[:, None], cand, alt)
+        alts.append(alt)
+    A_ = np.stack(alts)
+    r_outer = np.concatenate([A_[:, :, 0:2].min(0), A_[:, :, 2:4].max(0)], axis=1)
+    r_inner = np.concatenate([A_[:, :, 0:2].max(0), A_[:, :, 2:4].min(0)], axis=1)
+    if smooth:
+        r_outer, r_inner = rect, rect
+    flip = np.any(r_outer != r_inner, axis=1) | (np.abs(tz.v - cv.NEAR) < 1e-5)
 
     ok = (det.v > 0) & (x1 > x0) & (y1 > y0)
     sel = np.nonzero(ok)[0]
@@ -190,5 +228,5 @@ def _project(P: np.ndarray, cam, smooth: bool, want_jac: bool) -> Projection:
         n=N, visible=visible, idx=idx[sel], y=yv[sel], jac=jac[sel] if want_jac else jac,
         depth=tz.v[sel], radius=radius[sel].astype(np.int64), rect=rect[sel],
         raw_rgb=np.stack([q.v for q in rgb_raw], axis=1)[sel], rect_margin=m[sel],
-        depth_raw=tz_all,
+        depth_raw=tz_all, rect_flip=flip[sel], rect_outer=r_outer[sel], rect_inner=r_inner[sel],
     )

@@ -35,8 +35,9 @@ class ViewRaster:
     rec_clamped: np.ndarray  # (R,) True where alpha hit ALPHA_MAX
     rec_dcda: np.ndarray     # (R, 3) dc/dalpha
     rec_d: np.ndarray        # (R, 2) pixel centre minus splat mean
-    margin: np.ndarray       # (H*W,) smallest relative distance of a decision to its threshold
+    margin: np.ndarray       # (H*W,) smallest relative distance of an alpha/T decision to its threshold
     n_contrib: np.ndarray    # (H*W,) contributing splats per pixel
+    flip: np.ndarray = None  # (H*W,) a depth-order or tile-rect decision within float32 reach touches the pixel
 
 
 def blend_order(proj: Projection) -> np.ndarray:
@@ -50,13 +51,14 @@ def rasterize(proj: Projection, cam, smooth: bool = False) -> ViewRaster:
     tiles_x, tiles_y = (W + T_ - 1) // T_, (H + T_ - 1) // T_
     image = np.zeros((H, W, 3))
     margin = np.full(H * W, np.inf)
+    flip = np.zeros(H * W, bool)
     n_contrib = np.zeros(H * W, np.int64)
     recs = {k: [] for k in ("pix", "splat", "T", "alpha", "G", "clamped", "dcda", "d")}
     order = blend_order(proj)
     rect = proj.rect
     y = proj.y
     depth32 = proj.depth.astype(np.float32).astype(np.float64)
-    rect_small = proj.rect_margin < 1e-3
+    rect_flip = proj.rect_flip if proj.rect_flip is not None else np.zeros(proj.idx.shape[0], bool)
 
     for ty in range(tiles_y):
         for tx in range(tiles_x):
@@ -68,13 +70,18 @@ def rasterize(proj: Projection, cam, smooth: bool = False) -> ViewRaster:
             py = gy.ravel() + 0.5
             r = rect[order]
             sel = order[(r[:, 0] <= tx) & (tx < r[:, 2]) & (r[:, 1] <= ty) & (ty < r[:, 3])]
-            # rect decisions near a flip: mark tiles on or just outside the rect boundary
-            if not smooth:
-                ext = (r[:, 0] - 1 <= tx) & (tx <= r[:, 2]) & (r[:, 1] - 1 <= ty) & (ty <= r[:, 3])
-                inner = (r[:, 0] < tx) & (tx < r[:, 2] - 1) & (r[:, 1] < ty) & (ty < r[:, 3] - 1)
-                ring = order[ext & ~inner & rect_small[order]]
-                if ring.size:
-                    margin[pix] = np.minimum(margin[pix], proj.rect_margin[ring].min())
+            # a rect decision near a flip can add or drop the splat in the tiles
+            # between its inner and outer rects: flag the pixels it would reach
+            if not smooth and rect_flip.any():
+                ro, ri = proj.rect_outer[order], proj.rect_inner[order]
+                in_o = (ro[:, 0] <= tx) & (tx < ro[:, 2]) & (ro[:, 1] <= ty) & (ty < ro[:, 3])
+                in_i = (ri[:, 0] <= tx) & (tx < ri[:, 2]) & (ri[:, 1] <= ty) & (ty < ri[:, 3])
+                ring = order[in_o & ~in_i & rect_flip[order]]
+                for s_ in ring:
+                    yr = y[s_]
+                    ddx, ddy = px - yr[0], py - yr[1]
+                    ar = yr[5] * np.exp(-0.5 * (yr[2] * ddx * ddx + yr[4] * ddy * ddy) - yr[3] * ddx * ddy)
+                    flip[pix] |= ar >= cv.ALPHA_MIN * (1.0 - 1e-3)
             L = sel.shape[0]
             if L == 0:
                 continue
@@ -112,12 +119,13 @@ def rasterize(proj: Projection, cam, smooth: bool = False) -> ViewRaster:
                 m_stop = np.where(valid, np.abs(Tbef * (1.0 - alpha) - cv.T_MIN) / cv.T_MIN, np.inf)
                 m = np.minimum(np.minimum(m_skip, m_clamp), m_stop)
                 m = np.where(seen, m, np.inf).min(axis=1)
-                # depth-order ties between consecutive splats of the list
+                margin[pix] = np.minimum(margin[pix], m)
+                # depth-order near-ties (float32 depths within 2e-6 relative) between
+                # consecutive splats that both reach the pixel
                 if L > 1:
                     dd = np.abs(np.diff(depth32[sel])) / np.maximum(depth32[sel][:-1], 1e-30)
                     both = valid[:, :-1] & valid[:, 1:] & seen[:, 1:]
-                    m = np.minimum(m, np.where(both, dd[None, :], np.inf).min(axis=1))
-                margin[pix] = np.minimum(margin[pix], m)
+                    flip[pix] |= (both & (dd[None, :] < 2e-6)).any(axis=1)
             w = np.where(contrib, alpha * Tbef, 0.0)              # dc/dc_s = alpha_s T_s
             rgb = ys_[:, 6:9]
             wc = w[:, :, None] * rgb[None, :, :]                  # (P, L, 3)
@@ -144,5 +152,5 @@ def rasterize(proj: Projection, cam, smooth: bool = False) -> ViewRaster:
         W, H, image,
         cat("pix", (0,)).astype(np.int64), cat("splat", (0,)).astype(np.int64), cat("T", (0,)),
         cat("alpha", (0,)), cat("G", (0,)), cat("clamped", (0,)).astype(bool), cat("dcda", (0, 3)),
-        cat("d", (0, 2)), margin, n_contrib,
+        cat("d", (0, 2)), margin, n_contrib, flip,
     )

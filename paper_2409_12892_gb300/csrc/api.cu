@@ -1,0 +1,883 @@
+// C ABI of libgslm (include/gslm.h): contexts, caches and the host-side order
+// of the device work of Algorithm 1 and of one LM step (Sec. 3.2, 3.3).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace gslm;
+
+namespace gslm {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace gslm
+
+namespace {
+
+// Stream-ordered device buffer.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p != nullptr) cudaFreeAsync(p, st);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t alloc(size_t n, cudaStream_t s) {
+    release();
+    st = s;
+    if (n == 0) n = 16;
+    const cudaError_t e = cudaMallocAsync(&p, n, s);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = n;
+    return cudaSuccess;
+  }
+  cudaError_t ensure(size_t n, cudaStream_t s) {
+    if (p != nullptr && bytes >= n) return cudaSuccess;
+    return alloc(n, s);
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace
+
+// Per-phase CUDA-event timing of one LM step (options.profile).
+struct PhaseTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  std::vector<cudaEvent_t> pool;
+  int open_phase = -1;
+  cudaEvent_t open_ev = nullptr;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Opens a phase unless one is already open (nested calls are attributed to
+  // the outer phase); returns whether end() must close it.
+  bool begin(int phase) {
+    if (!on || open_phase >= 0) return false;
+    open_phase = phase;
+    open_ev = get();
+    cudaEventRecord(open_ev, st);
+    return true;
+  }
+  void end(bool opened) {
+    if (!opened) return;
+    cudaEvent_t e = get();
+    cudaEventRecord(e, st);
+    marks.push_back({open_phase, {open_ev, e}});
+    open_phase = -1;
+  }
+  // Sums elapsed ms per phase (after the stream has been synchronised).
+  void collect(double* ms, int n) {
+    for (auto& m : marks) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, m.second.first, m.second.second) == cudaSuccess && m.first < n) ms[m.first] += t;
+      pool.push_back(m.second.first);
+      pool.push_back(m.second.second);
+    }
+    marks.clear();
+  }
+  ~PhaseTimer() {
+    for (auto& m : marks) {
+      cudaEventDestroy(m.second.first);
+      cudaEventDestroy(m.second.second);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+enum { PH_BUILD = 0, PH_DIAG, PH_TANGENT, PH_APPLY_J, PH_APPLY_JT, PH_VJP, PH_VEC, PH_RHO };
+
+struct gslm_ctx {
+  gslm_options opt;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  std::string err;
+  PhaseTimer timer;
+  // scratch reused across calls
+  Buf ydot, seg_ybar, seg_q, u, partials, scalars, reduce_out;
+  Buf r, z, p, g, minv;
+  Buf lm_num, lm_den, lm_delta, lm_trial, lm_x, lm_b, lm_M, lm_tgt, lm_img;
+};
+
+struct gslm_cache {
+  gslm_ctx* ctx = nullptr;
+  const float* params = nullptr;
+  int N = 0;
+  long long ld = 0;
+  int V = 0;
+  int smooth = 0;
+  int fmt = 0;
+  int n_tiles = 0;
+  long long n_pix = 0;
+  long long n_vis = 0, n_keys = 0, n_seg = 0, n_entries = 0, n_active = 0;
+  double cost = 0.0;
+  std::vector<DevCam> hcams;
+  Buf cams, rec, slot_active, tile_seg_off, seg_entry_off, seg_slot, payload, seg_scale, pixoff;
+  Buf slot_seg_start, slot_seg_end, slot_seg_list, F, own_params;
+
+  CacheView view() const {
+    CacheView cv;
+    cv.cams = cams.as<DevCam>();
+    cv.V = V;
+    cv.n_tiles = n_tiles;
+    cv.n_pix = n_pix;
+    cv.N = N;
+    cv.n_slots = (long long)N * V;
+    cv.rec = rec.as<SplatRec>();
+    cv.tile_seg_off = tile_seg_off.as<uint32_t>();
+    cv.seg_entry_off = seg_entry_off.as<unsigned long long>();
+    cv.seg_slot = seg_slot.as<uint32_t>();
+    cv.payload = payload.p;
+    cv.seg_scale = seg_scale.as<float>();
+    cv.pixoff = pixoff.as<uint8_t>();
+    cv.slot_seg_start = slot_seg_start.as<uint32_t>();
+    cv.slot_seg_end = slot_seg_end.as<uint32_t>();
+    cv.slot_seg_list = slot_seg_list.as<uint32_t>();
+    cv.slot_active = slot_active.as<uint8_t>();
+    cv.n_seg = n_seg;
+    cv.n_entries = n_entries;
+    cv.fmt = fmt;
+    cv.skip = nullptr;
+    return cv;
+  }
+  size_t device_bytes() const {
+    return cams.bytes + rec.bytes + slot_active.bytes + tile_seg_off.bytes + seg_entry_off.bytes + seg_slot.bytes +
+           payload.bytes + seg_scale.bytes + pixoff.bytes + slot_seg_start.bytes + slot_seg_end.bytes +
+           slot_seg_list.bytes + F.bytes + own_params.bytes;
+  }
+};
+
+namespace {
+
+gslm_status fail(gslm_ctx* c, gslm_status s, const std::string& msg) {
+  if (c != nullptr) c->err = msg;
+  return s;
+}
+
+gslm_status cuda_fail(gslm_ctx* c, cudaError_t e, const char* where) {
+  const gslm_status s = (e == cudaErrorMemoryAllocation) ? GSLM_E_OOM : GSLM_E_CUDA;
+  cudaGetLastError();
+  return fail(c, s, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                                  \
+  do {                                                            \
+    const cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr);      \
+  } while (0)
+
+#define CKS(expr)                                                 \
+  do {                                                            \
+    const gslm_status s_ = (expr);                                \
+    if (s_ != GSLM_OK) return s_;                                 \
+  } while (0)
+
+int bits_for(unsigned long long n) {
+  int b = 0;
+  while (b < 64 && (1ull << b) < n) ++b;
+  return b;
+}
+
+size_t payload_bytes(int fmt) { return fmt == GSLM_CACHE_FP32 ? 16 : 8; }
+
+// Cameras of a call with their tile/pixel offsets.
+gslm_status make_cams(gslm_ctx* ctx, const gslm_camera* cams, int V, std::vector<DevCam>& out, int& n_tiles,
+                      long long& n_pix) {
+  out.resize(V);
+  long long toff = 0, poff = 0;
+  for (int v = 0; v < V; ++v) {
+    const gslm_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * kTile || c.height > 65535 * kTile)
+      return fail(ctx, GSLM_E_INVALID, "camera size out of range");
+    DevCam& d = out[v];
+    std::memcpy(d.R, c.R, sizeof(d.R));
+    std::memcpy(d.t, c.t, sizeof(d.t));
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    for (int i = 0; i < 3; ++i)
+      d.campos[i] = -(c.R[0 * 3 + i] * c.t[0] + c.R[1 * 3 + i] * c.t[1] + c.R[2 * 3 + i] * c.t[2]);
+    d.W = c.width;
+    d.H = c.height;
+    d.tiles_x = (c.width + kTile - 1) / kTile;
+    d.tiles_y = (c.height + kTile - 1) / kTile;
+    d.tile_off = (int)toff;
+    d.pad = 0;
+    d.pix_off = poff;
+    toff += (long long)d.tiles_x * d.tiles_y;
+    poff += (long long)c.width * c.height;
+    if (toff >= (1ll << 31)) return fail(ctx, GSLM_E_INVALID, "too many tiles");
+  }
+  n_tiles = (int)toff;
+  n_pix = poff;
+  return GSLM_OK;
+}
+
+gslm_status check_vec_args(gslm_ctx* ctx, long long N, long long ld) {
+  if (ctx == nullptr) return GSLM_E_INVALID;
+  if (N <= 0 || N >= (1ll << 31)) return fail(ctx, GSLM_E_INVALID, "N out of range");
+  if (ld < N || (ld & 3) != 0) return fail(ctx, GSLM_E_INVALID, "ld must be >= N and a multiple of 4");
+  return GSLM_OK;
+}
+
+// Projection, depth sort, tile keys and tile ranges of a call (shared by render
+// and build_cache). Leaves the per-tile splat lists in (tile_start, tile_end,
+// tile_vals) and the splats in rec.
+struct Binning {
+  Buf cams, rec, ntiles, rect, depth, flags, pos, vis, keys_a, vals_a, keys_b, vals_b, sort_tmp, key_off;
+  Buf tile_start, tile_end, scan_tmp;
+  uint32_t* tile_vals = nullptr;
+  uint32_t* tile_keys = nullptr;
+  long long n_vis = 0, n_keys = 0;
+};
+
+gslm_status bin_splats(gslm_ctx* ctx, const float* params, int N, long long ld, const std::vector<DevCam>& hc,
+                       int n_tiles, int smooth, Binning& B) {
+  cudaStream_t st = ctx->st;
+  const int V = (int)hc.size();
+  const long long S = (long long)N * V;
+  if (S >= (1ll << 32) - 1) return fail(ctx, GSLM_E_INVALID, "views x Gaussians exceeds 2^32 splats");
+  CK(B.cams.alloc(sizeof(DevCam) * V, st));
+  CK(cudaMemcpyAsync(B.cams.p, hc.data(), sizeof(DevCam) * V, cudaMemcpyHostToDevice, st));
+  CK(B.rec.alloc(sizeof(SplatRec) * S, st));
+  CK(B.ntiles.alloc(sizeof(uint32_t) * S, st));
+  CK(B.rect.alloc(sizeof(uint2) * S, st));
+  CK(B.depth.alloc(sizeof(uint32_t) * S, st));
+  CK(launch_project(params, N, ld, B.cams.as<DevCam>(), V, smooth, B.rec.as<SplatRec>(), B.ntiles.as<uint32_t>(),
+                    B.rect.as<uint2>(), B.depth.as<uint32_t>(), st));
+  // visible splats, compacted in slot order
+  CK(B.flags.alloc(sizeof(uint32_t) * S, st));
+  CK(B.pos.alloc(sizeof(uint32_t) * (S + 1), st));
+  CK(B.scan_tmp.alloc(std::max(scan_temp_bytes(S), scan_temp_bytes(n_tiles + 1)), st));
+  CK(launch_flags(B.ntiles.as<uint32_t>(), S, B.flags.as<uint32_t>(), st));
+  CK(exclusive_scan_u32(B.flags.as<uint32_t>(), B.pos.as<uint32_t>(), S, B.scan_tmp.p, st));
+  uint32_t nvis = 0;
+  CK(cudaMemcpyAsync(&nvis, B.pos.as<uint32_t>() + S, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  B.n_vis = nvis;
+  const long long nv = std::max<long long>(B.n_vis, 1);
+  CK(B.vis.alloc(sizeof(uint32_t) * nv, st));
+  CK(launch_compact_flags(B.ntiles.as<uint32_t>(), B.pos.as<uint32_t>(), S, B.vis.as<uint32_t>(), st));
+  // depth order (stable: ties keep the Gaussian order)
+  CK(B.keys_a.alloc(sizeof(uint32_t) * nv, st));
+  CK(B.keys_b.alloc(sizeof(uint32_t) * nv, st));
+  CK(B.vals_b.alloc(sizeof(uint32_t) * nv, st));
+  CK(launch_gather_u32(B.depth.as<uint32_t>(), B.vis.as<uint32_t>(), B.n_vis, B.keys_a.as<uint32_t>(), st));
+  CK(B.sort_tmp.alloc(radix_temp_bytes(nv), st));
+  uint32_t *dk = nullptr, *dv = nullptr;
+  CK(radix_sort_pairs(B.keys_a.as<uint32_t>(), B.vis.as<uint32_t>(), B.keys_b.as<uint32_t>(),
+                      B.vals_b.as<uint32_t>(), B.n_vis, 32, B.sort_tmp.p, &dk, &dv, st));
+  // tiles per sorted splat -> key offsets
+  CK(launch_gather_u32(B.ntiles.as<uint32_t>(), dv, B.n_vis, dk, st));
+  CK(B.key_off.alloc(sizeof(unsigned long long) * (nv + 1), st));
+  CK(B.scan_tmp.ensure(scan_temp_bytes(nv + 1), st));
+  CK(exclusive_scan_u64(dk, B.key_off.as<unsigned long long>(), B.n_vis, B.scan_tmp.p, st));
+  unsigned long long nkeys = 0;
+  CK(cudaMemcpyAsync(&nkeys, B.key_off.as<unsigned long long>() + B.n_vis, sizeof(nkeys), cudaMemcpyDeviceToHost,
+                     st));
+  CK(cudaStreamSynchronize(st));
+  if (nkeys >= (1ull << 32) - 1) return fail(ctx, GSLM_E_CACHE_OVERFLOW, "more than 2^32 tile keys");
+  B.n_keys = (long long)nkeys;
+  const long long nk = std::max<long long>(B.n_keys, 1);
+  // the depth-sorted slot list must survive the key emission: keep it in vals_b or vis
+  Buf sorted_slots;
+  CK(sorted_slots.alloc(sizeof(uint32_t) * nv, st));
+  CK(cudaMemcpyAsync(sorted_slots.p, dv, sizeof(uint32_t) * B.n_vis, cudaMemcpyDeviceToDevice, st));
+  B.keys_a.release();
+  B.keys_b.release();
+  B.vals_b.release();
+  B.vis.release();
+  CK(B.keys_a.alloc(sizeof(uint32_t) * nk, st));
+  CK(B.vals_a.alloc(sizeof(uint32_t) * nk, st));
+  CK(B.keys_b.alloc(sizeof(uint32_t) * nk, st));
+  CK(B.vals_b.alloc(sizeof(uint32_t) * nk, st));
+  CK(launch_emit_keys(sorted_slots.as<uint32_t>(), B.n_vis, B.rect.as<uint2>(), B.cams.as<DevCam>(), V, N,
+                      B.key_off.as<unsigned long long>(), B.keys_a.as<uint32_t>(), B.vals_a.as<uint32_t>(), st));
+  CK(B.sort_tmp.ensure(radix_temp_bytes(nk), st));
+  CK(radix_sort_pairs(B.keys_a.as<uint32_t>(), B.vals_a.as<uint32_t>(), B.keys_b.as<uint32_t>(),
+                      B.vals_b.as<uint32_t>(), B.n_keys, bits_for((unsigned long long)n_tiles), B.sort_tmp.p,
+                      &B.tile_keys, &B.tile_vals, st));
+  CK(B.tile_start.alloc(sizeof(uint32_t) * (n_tiles + 1), st));
+  CK(B.tile_end.alloc(sizeof(uint32_t) * (n_tiles + 1), st));
+  CK(cudaMemsetAsync(B.tile_start.p, 0, sizeof(uint32_t) * (n_tiles + 1), st));
+  CK(cudaMemsetAsync(B.tile_end.p, 0, sizeof(uint32_t) * (n_tiles + 1), st));
+  CK(launch_ranges(B.tile_keys, B.n_keys, B.tile_start.as<uint32_t>(), B.tile_end.as<uint32_t>(), st));
+  B.ntiles.release();
+  B.depth.release();
+  B.flags.release();
+  B.pos.release();
+  B.key_off.release();
+  B.sort_tmp.release();
+  return GSLM_OK;
+}
+
+gslm_status reduce_to_host(gslm_ctx* ctx, const double* partials, int n, double* host) {
+  cudaStream_t st = ctx->st;
+  CK(ctx->reduce_out.ensure(sizeof(double), st));
+  CK(launch_reduce_partials(partials, n, ctx->reduce_out.as<double>(), st));
+  CK(cudaMemcpyAsync(host, ctx->reduce_out.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GSLM_OK;
+}
+
+// J p through the cache: per-Gaussian tangent, then the tile kernel.
+gslm_status do_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float* u, const float* z_beta,
+                       float* p_out, const PcgScalars* sc, const float* Fadd, double* sq_partials) {
+  cudaStream_t st = ctx->st;
+  const long long S = (long long)c->N * c->V;
+  CK(ctx->ydot.ensure(sizeof(float) * 12 * std::max<long long>(S, 1), st));
+  bool t = ctx->timer.begin(PH_TANGENT);
+  CK(launch_tangent(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_active.as<uint8_t>(), p,
+                    ctx->ydot.as<float>(), z_beta, p_out, sc, st));
+  CacheView cv = c->view();
+  cv.skip = sc != nullptr ? &sc->done : nullptr;
+  ctx->timer.end(t);
+  t = ctx->timer.begin(PH_APPLY_J);
+  CK(launch_apply_J(cv, ctx->ydot.as<float>(), Fadd, u, sq_partials, ctx->opt.group, st));
+  ctx->timer.end(t);
+  return GSLM_OK;
+}
+
+gslm_status do_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, float* g, float scale, const float* p,
+                        const float* M, float lambda, double* partials, const PcgScalars* sc) {
+  cudaStream_t st = ctx->st;
+  CK(ctx->seg_ybar.ensure(sizeof(float) * 12 * std::max<long long>(c->n_seg, 1), st));
+  CacheView cv = c->view();
+  cv.skip = sc != nullptr ? &sc->done : nullptr;
+  bool t = ctx->timer.begin(PH_APPLY_JT);
+  CK(launch_apply_JT(cv, u, ctx->seg_ybar.as<float>(), ctx->opt.group, st));
+  ctx->timer.end(t);
+  t = ctx->timer.begin(PH_VJP);
+  CK(launch_vjp(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
+                c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), ctx->seg_ybar.as<float>(), scale, g,
+                p, M, lambda, partials, sc, st));
+  ctx->timer.end(t);
+  return GSLM_OK;
+}
+
+gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, const float* diag, const float* D,
+                        float lambda, float* x) {
+  cudaStream_t st = ctx->st;
+  const int N = c->N;
+  const long long ld = c->ld;
+  const size_t vb = sizeof(float) * kNP * (size_t)ld;
+  CK(ctx->r.ensure(vb, st));
+  CK(ctx->z.ensure(vb, st));
+  CK(ctx->p.ensure(vb, st));
+  CK(ctx->g.ensure(vb, st));
+  CK(ctx->minv.ensure(vb, st));
+  CK(ctx->u.ensure(sizeof(float) * 3 * std::max<long long>(c->n_pix, 1), st));
+  const int nvec = pcg_blocks(N), nvjp = vjp_blocks(N);
+  CK(ctx->partials.ensure(sizeof(double) * 2 * std::max(nvec, nvjp), st));
+  CK(ctx->scalars.ensure(sizeof(PcgScalars), st));
+  PcgScalars* sc = ctx->scalars.as<PcgScalars>();
+  double* part = ctx->partials.as<double>();
+  float *r = ctx->r.as<float>(), *z = ctx->z.as<float>(), *p = ctx->p.as<float>(), *g = ctx->g.as<float>();
+  float* Minv = ctx->minv.as<float>();
+  float* u = ctx->u.as<float>();
+  // x0 = M^-1 b
+  bool t = ctx->timer.begin(PH_VEC);
+  CK(launch_pcg_init(0, ld, N, b, diag, D, x, Minv, part, st));
+  CK(launch_pcg_scalars(sc, part, nvec, 0, ctx->opt.break_rel2, st));
+  ctx->timer.end(t);
+  // u0 = J x0; g0 = J^T u0; r0 = b - (g0 + lambda M x0); z0 = M^-1 r0; p0 = z0
+  CKS(do_apply_J(ctx, c, x, u, nullptr, nullptr, nullptr, nullptr, nullptr));
+  CKS(do_apply_JT(ctx, c, u, g, 1.f, nullptr, nullptr, 0.f, nullptr, nullptr));
+  t = ctx->timer.begin(PH_VEC);
+  CK(launch_pcg_residual0(N, ld, b, g, diag, x, lambda, Minv, r, z, p, part, st));
+  CK(launch_pcg_scalars(sc, part, nvec, 1, ctx->opt.break_rel2, st));
+  ctx->timer.end(t);
+  for (int it = 0; it < ctx->opt.n_iters; ++it) {
+    // p_i = z_i + beta p_{i-1} (fused), u_i = J p_i
+    CKS(do_apply_J(ctx, c, p, u, it > 0 ? z : nullptr, it > 0 ? p : nullptr, sc, nullptr, nullptr));
+    // g_i = J^T u_i + lambda M p_i, p^T g
+    CKS(do_apply_JT(ctx, c, u, g, 1.f, p, diag, lambda, part, sc));
+    t = ctx->timer.begin(PH_VEC);
+    CK(launch_pcg_scalars(sc, part, nvjp, 2, ctx->opt.break_rel2, st));
+    CK(launch_pcg_update(N, ld, sc, p, g, Minv, x, r, z, part, st));
+    CK(launch_pcg_scalars(sc, part, nvec, 3, ctx->opt.break_rel2, st));
+    ctx->timer.end(t);
+  }
+  return GSLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gslm_version(void) { return "gslm 0.1 (sm_103a)"; }
+
+int64_t gslm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+void gslm_default_options(gslm_options* o) {
+  if (o == nullptr) return;
+  std::memset(o, 0, sizeof(*o));
+  o->cache_fmt = GSLM_CACHE_FP32;
+  o->n_iters = 8;
+  o->break_rel2 = 0.01f;
+  o->lambda_min = 1e-4f;
+  o->lambda_max = 1e4f;
+  o->smooth = 0;
+  o->mem_budget = 0;
+  o->group = 32;
+}
+
+static gslm_status validate_opts(const gslm_options* o) {
+  if (o->cache_fmt < 0 || o->cache_fmt > 2) return GSLM_E_INVALID;
+  if (o->n_iters < 0 || o->n_iters > 100000) return GSLM_E_INVALID;
+  if (!(o->lambda_min > 0.f) || !(o->lambda_max >= o->lambda_min)) return GSLM_E_INVALID;
+  if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
+  return GSLM_OK;
+}
+
+gslm_status gslm_create(const gslm_options* opt, void* stream, gslm_ctx** out) {
+  if (out == nullptr) return GSLM_E_INVALID;
+  *out = nullptr;
+  gslm_options o;
+  if (opt != nullptr) o = *opt;
+  else gslm_default_options(&o);
+  if (o.group == 0) o.group = 32;
+  if (validate_opts(&o) != GSLM_OK) return GSLM_E_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GSLM_E_CUDA;
+  }
+  gslm_ctx* c = new gslm_ctx();
+  c->opt = o;
+  c->st = static_cast<cudaStream_t>(stream);
+  c->device = dev;
+  *out = c;
+  return GSLM_OK;
+}
+
+void gslm_destroy(gslm_ctx* ctx) {
+  if (ctx == nullptr) return;
+  cudaStreamSynchronize(ctx->st);
+  delete ctx;
+}
+
+const char* gslm_last_error(const gslm_ctx* ctx) { return ctx == nullptr ? "null context" : ctx->err.c_str(); }
+
+gslm_status gslm_set_options(gslm_ctx* ctx, const gslm_options* opt) {
+  if (ctx == nullptr || opt == nullptr) return GSLM_E_INVALID;
+  gslm_options o = *opt;
+  if (o.group == 0) o.group = 32;
+  if (validate_opts(&o) != GSLM_OK) return fail(ctx, GSLM_E_INVALID, "invalid options");
+  ctx->opt = o;
+  return GSLM_OK;
+}
+
+gslm_status gslm_render(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld, const gslm_camera* cams,
+                        int32_t V, float* img, const float* targets, double* cost) {
+  CKS(check_vec_args(ctx, N, ld));
+  if (params == nullptr || cams == nullptr || img == nullptr || V <= 0)
+    return fail(ctx, GSLM_E_INVALID, "render: null argument or V <= 0");
+  std::vector<DevCam> hc;
+  int n_tiles = 0;
+  long long n_pix = 0;
+  CKS(make_cams(ctx, cams, V, hc, n_tiles, n_pix));
+  Binning B;
+  CKS(bin_splats(ctx, params, (int)N, ld, hc, n_tiles, ctx->opt.smooth, B));
+  Buf partials;
+  CK(partials.alloc(sizeof(double) * n_tiles, ctx->st));
+  CK(launch_raster_count(B.cams.as<DevCam>(), V, n_tiles, B.tile_start.as<uint32_t>(), B.tile_end.as<uint32_t>(),
+                         B.tile_vals, B.rec.as<SplatRec>(), ctx->opt.smooth, targets, img, nullptr,
+                         targets != nullptr ? partials.as<double>() : nullptr, nullptr, nullptr, ctx->st));
+  if (targets != nullptr && cost != nullptr) CKS(reduce_to_host(ctx, partials.as<double>(), n_tiles, cost));
+  return GSLM_OK;
+}
+
+gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld, const gslm_camera* cams,
+                             int32_t V, const float* targets, gslm_cache** out, float* F, float* b, double* cost) {
+  CKS(check_vec_args(ctx, N, ld));
+  if (out == nullptr) return fail(ctx, GSLM_E_INVALID, "build_cache: null cache pointer");
+  *out = nullptr;
+  if (params == nullptr || cams == nullptr || targets == nullptr || V <= 0)
+    return fail(ctx, GSLM_E_INVALID, "build_cache: null argument or V <= 0");
+  cudaStream_t st = ctx->st;
+  gslm_cache* c = new gslm_cache();
+  struct Guard {
+    gslm_cache*& c;
+    ~Guard() { delete c; }
+  } guard{c};
+  c->ctx = ctx;
+  c->N = (int)N;
+  c->ld = ld;
+  c->V = V;
+  c->smooth = ctx->opt.smooth;
+  c->fmt = ctx->opt.cache_fmt;
+  CKS(make_cams(ctx, cams, V, c->hcams, c->n_tiles, c->n_pix));
+  // The cache keeps its own copy of the parameters it linearises around.
+  CK(c->own_params.alloc(sizeof(float) * kNP * (size_t)ld, st));
+  CK(cudaMemcpyAsync(c->own_params.p, params, sizeof(float) * kNP * (size_t)ld, cudaMemcpyDeviceToDevice, st));
+  c->params = c->own_params.as<float>();
+  params = c->params;
+  const int n_tiles = c->n_tiles;
+  const long long S = (long long)N * V;
+  Binning B;
+  CKS(bin_splats(ctx, params, (int)N, ld, c->hcams, n_tiles, c->smooth, B));
+  c->n_vis = B.n_vis;
+  c->n_keys = B.n_keys;
+  // blend + count entries and segments per tile
+  Buf img, cost_part, tile_entries, tile_segs, tile_entry_off;
+  CK(img.alloc(sizeof(float) * 3 * c->n_pix, st));
+  CK(c->F.alloc(sizeof(float) * 3 * c->n_pix, st));
+  CK(cost_part.alloc(sizeof(double) * n_tiles, st));
+  CK(tile_entries.alloc(sizeof(uint32_t) * (n_tiles + 1), st));
+  CK(tile_segs.alloc(sizeof(uint32_t) * (n_tiles + 1), st));
+  CK(launch_raster_count(B.cams.as<DevCam>(), V, n_tiles, B.tile_start.as<uint32_t>(), B.tile_end.as<uint32_t>(),
+                         B.tile_vals, B.rec.as<SplatRec>(), c->smooth, targets, img.as<float>(), c->F.as<float>(),
+                         cost_part.as<double>(), tile_entries.as<uint32_t>(), tile_segs.as<uint32_t>(), st));
+  CK(tile_entry_off.alloc(sizeof(unsigned long long) * (n_tiles + 1), st));
+  CK(c->tile_seg_off.alloc(sizeof(uint32_t) * (n_tiles + 1), st));
+  CK(B.scan_tmp.ensure(scan_temp_bytes(n_tiles + 1), st));
+  CK(exclusive_scan_u64(tile_entries.as<uint32_t>(), tile_entry_off.as<unsigned long long>(), n_tiles,
+                        B.scan_tmp.p, st));
+  CK(exclusive_scan_u32(tile_segs.as<uint32_t>(), c->tile_seg_off.as<uint32_t>(), n_tiles, B.scan_tmp.p, st));
+  unsigned long long E = 0;
+  uint32_t nseg = 0;
+  CK(cudaMemcpyAsync(&E, tile_entry_off.as<unsigned long long>() + n_tiles, sizeof(E), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&nseg, c->tile_seg_off.as<uint32_t>() + n_tiles, sizeof(nseg), cudaMemcpyDeviceToHost, st));
+  CKS(reduce_to_host(ctx, cost_part.as<double>(), n_tiles, &c->cost));
+  c->n_entries = (long long)E;
+  c->n_seg = nseg;
+  const size_t need = E * (payload_bytes(c->fmt) + 1) + (size_t)nseg * (8 + 4 + 4 + 4 * (c->fmt == 2)) +
+                      (size_t)S * (sizeof(SplatRec) + 1 + 8);
+  if (ctx->opt.mem_budget != 0 && need > ctx->opt.mem_budget) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg), "cache needs %zu bytes (%llu entries), budget %zu", need, E,
+                  ctx->opt.mem_budget);
+    return fail(ctx, GSLM_E_CACHE_OVERFLOW, msg);
+  }
+  const long long ns = std::max<long long>(nseg, 1);
+  CK(c->payload.alloc(payload_bytes(c->fmt) * std::max<unsigned long long>(E, 1), st));
+  CK(c->pixoff.alloc(std::max<unsigned long long>(E, 1), st));
+  CK(c->seg_entry_off.alloc(sizeof(unsigned long long) * (ns + 1), st));
+  CK(c->seg_slot.alloc(sizeof(uint32_t) * ns, st));
+  if (c->fmt == GSLM_CACHE_FP16S) CK(c->seg_scale.alloc(sizeof(float) * ns, st));
+  CK(c->slot_active.alloc(std::max<long long>(S, 1), st));
+  CK(cudaMemsetAsync(c->slot_active.p, 0, std::max<long long>(S, 1), st));
+  Buf errflag;
+  CK(errflag.alloc(sizeof(int), st));
+  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
+  CK(launch_raster_write(B.cams.as<DevCam>(), V, n_tiles, B.tile_start.as<uint32_t>(), B.tile_end.as<uint32_t>(),
+                         B.tile_vals, B.rec.as<SplatRec>(), c->smooth, img.as<float>(),
+                         tile_entry_off.as<unsigned long long>(), c->tile_seg_off.as<uint32_t>(), c->fmt,
+                         c->payload.p, c->seg_scale.as<float>(), c->pixoff.as<uint8_t>(),
+                         c->seg_entry_off.as<unsigned long long>(), c->seg_slot.as<uint32_t>(),
+                         c->slot_active.as<uint8_t>(), errflag.as<int>(), st));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr != 0) {
+    char msg[96];
+    std::snprintf(msg, sizeof(msg), "cache write disagreed with the counting pass (flags %d)", herr);
+    return fail(ctx, GSLM_E_NUMERIC, msg);
+  }
+  CK(cudaMemcpyAsync(c->seg_entry_off.as<unsigned long long>() + nseg, &E, sizeof(E), cudaMemcpyHostToDevice, st));
+  // segments ordered by splat (the paper's sortCacheByGaussians, on segments)
+  {
+    Buf ka, va, kb, vb, tmp;
+    CK(ka.alloc(sizeof(uint32_t) * ns, st));
+    CK(va.alloc(sizeof(uint32_t) * ns, st));
+    CK(kb.alloc(sizeof(uint32_t) * ns, st));
+    CK(vb.alloc(sizeof(uint32_t) * ns, st));
+    CK(tmp.alloc(radix_temp_bytes(ns), st));
+    CK(cudaMemcpyAsync(ka.p, c->seg_slot.p, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
+    CK(launch_iota_u32(va.as<uint32_t>(), nseg, st));
+    uint32_t *sk = nullptr, *sv = nullptr;
+    CK(radix_sort_pairs(ka.as<uint32_t>(), va.as<uint32_t>(), kb.as<uint32_t>(), vb.as<uint32_t>(), nseg,
+                        bits_for((unsigned long long)S), tmp.p, &sk, &sv, st));
+    CK(c->slot_seg_start.alloc(sizeof(uint32_t) * std::max<long long>(S, 1), st));
+    CK(c->slot_seg_end.alloc(sizeof(uint32_t) * std::max<long long>(S, 1), st));
+    CK(cudaMemsetAsync(c->slot_seg_start.p, 0, sizeof(uint32_t) * std::max<long long>(S, 1), st));
+    CK(cudaMemsetAsync(c->slot_seg_end.p, 0, sizeof(uint32_t) * std::max<long long>(S, 1), st));
+    CK(launch_ranges(sk, nseg, c->slot_seg_start.as<uint32_t>(), c->slot_seg_end.as<uint32_t>(), st));
+    CK(c->slot_seg_list.alloc(sizeof(uint32_t) * ns, st));
+    CK(cudaMemcpyAsync(c->slot_seg_list.p, sv, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
+  }
+  {
+    Buf cnt;
+    CK(cnt.alloc(sizeof(unsigned long long), st));
+    CK(launch_count_nonzero_u8(c->slot_active.as<uint8_t>(), S, cnt.as<unsigned long long>(), st));
+    unsigned long long na = 0;
+    CK(cudaMemcpyAsync(&na, cnt.p, sizeof(na), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->n_active = (long long)na;
+  }
+  // keep the splats and cameras; drop the binning buffers
+  c->rec.p = B.rec.p;
+  c->rec.bytes = B.rec.bytes;
+  c->rec.st = st;
+  B.rec.p = nullptr;
+  c->cams.p = B.cams.p;
+  c->cams.bytes = B.cams.bytes;
+  c->cams.st = st;
+  B.cams.p = nullptr;
+  // b = -J^T F
+  if (b != nullptr) CKS(do_apply_JT(ctx, c, c->F.as<float>(), b, -1.f, nullptr, nullptr, 0.f, nullptr, nullptr));
+  if (F != nullptr)
+    CK(cudaMemcpyAsync(F, c->F.p, sizeof(float) * 3 * c->n_pix, cudaMemcpyDeviceToDevice, st));
+  if (cost != nullptr) *cost = c->cost;
+  *out = c;
+  c = nullptr;   // release from the guard
+  return GSLM_OK;
+}
+
+gslm_status gslm_cache_stats(const gslm_cache* c, gslm_cache_info* info) {
+  if (c == nullptr || info == nullptr) return GSLM_E_INVALID;
+  info->entries = c->n_entries;
+  info->segments = c->n_seg;
+  info->splats = c->n_vis;
+  info->keys = c->n_keys;
+  info->bytes = (int64_t)c->device_bytes();
+  info->pixels = c->n_pix;
+  info->views = c->V;
+  info->cache_fmt = c->fmt;
+  info->active_splats = c->n_active;
+  return GSLM_OK;
+}
+
+void gslm_cache_free(gslm_cache* c) { delete c; }
+
+gslm_status gslm_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float* u) {
+  if (ctx == nullptr || c == nullptr || p == nullptr || u == nullptr) return fail(ctx, GSLM_E_INVALID, "apply_J: null");
+  return do_apply_J(ctx, c, p, u, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+gslm_status gslm_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, float* g) {
+  if (ctx == nullptr || c == nullptr || u == nullptr || g == nullptr) return fail(ctx, GSLM_E_INVALID, "apply_JT: null");
+  return do_apply_JT(ctx, c, u, g, 1.f, nullptr, nullptr, 0.f, nullptr, nullptr);
+}
+
+gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* c, float* diag) {
+  if (ctx == nullptr || c == nullptr || diag == nullptr) return fail(ctx, GSLM_E_INVALID, "jacobi_diag: null");
+  cudaStream_t st = ctx->st;
+  CK(ctx->seg_q.ensure(sizeof(float) * 40 * std::max<long long>(c->n_seg, 1), st));
+  CK(launch_diag_entries(c->view(), ctx->seg_q.as<float>(), st));
+  CK(launch_diag(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
+                 c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), ctx->seg_q.as<float>(), diag, st));
+  return GSLM_OK;
+}
+
+gslm_status gslm_pcg_solve(gslm_ctx* ctx, const gslm_cache* c, const float* b, const float* diag, const float* D,
+                           float lambda, float* x, gslm_pcg_stats* stats) {
+  if (ctx == nullptr || c == nullptr || b == nullptr || diag == nullptr || x == nullptr)
+    return fail(ctx, GSLM_E_INVALID, "pcg_solve: null");
+  CKS(pcg_enqueue(ctx, c, b, diag, D, lambda, x));
+  if (stats != nullptr) {
+    PcgScalars h;
+    CK(cudaMemcpyAsync(&h, ctx->scalars.p, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    stats->iters = h.iters;
+    stats->breakdown = h.breakdown;
+    stats->rr = h.rr;
+    stats->bb = h.bb;
+    if (h.breakdown) return GSLM_W_PCG_BREAKDOWN;
+  }
+  return GSLM_OK;
+}
+
+gslm_status gslm_combine_accumulate(gslm_ctx* ctx, int64_t N, int64_t ld, const float* d, const float* m, float* num,
+                                    float* den) {
+  CKS(check_vec_args(ctx, N, ld));
+  if (d == nullptr || m == nullptr || num == nullptr || den == nullptr) return fail(ctx, GSLM_E_INVALID, "combine: null");
+  CK(launch_combine_acc((int)N, ld, d, m, num, den, ctx->st));
+  return GSLM_OK;
+}
+
+gslm_status gslm_combine_finish(gslm_ctx* ctx, int64_t N, int64_t ld, const float* num, const float* den,
+                                float* delta) {
+  CKS(check_vec_args(ctx, N, ld));
+  if (num == nullptr || den == nullptr || delta == nullptr) return fail(ctx, GSLM_E_INVALID, "combine: null");
+  CK(launch_combine_finish((int)N, ld, num, den, delta, ctx->st));
+  return GSLM_OK;
+}
+
+gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, const gslm_camera* cams,
+                         int32_t n_cams, const float* targets, const int32_t* subset_views,
+                         const int32_t* subset_off, int32_t n_b, const float* const* precond, gslm_lm_state* state,
+                         gslm_lm_stats* stats) {
+  CKS(check_vec_args(ctx, N, ld));
+  if (params == nullptr || cams == nullptr || targets == nullptr || subset_views == nullptr ||
+      subset_off == nullptr || n_b <= 0 || state == nullptr)
+    return fail(ctx, GSLM_E_INVALID, "lm_step: null argument");
+  cudaStream_t st = ctx->st;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+  CK(cudaEventRecord(ev0, st));
+  // camera pixel offsets inside `targets`
+  std::vector<long long> cam_pix(n_cams + 1, 0);
+  for (int i = 0; i < n_cams; ++i) cam_pix[i + 1] = cam_pix[i] + (long long)cams[i].width * cams[i].height;
+  const size_t vb = sizeof(float) * kNP * (size_t)ld;
+  CK(ctx->lm_num.ensure(vb, st));
+  CK(ctx->lm_den.ensure(vb, st));
+  CK(ctx->lm_delta.ensure(vb, st));
+  CK(ctx->lm_trial.ensure(vb, st));
+  CK(ctx->lm_x.ensure(vb, st));
+  CK(ctx->lm_b.ensure(vb, st));
+  CK(ctx->lm_M.ensure(vb, st));
+  CK(cudaMemsetAsync(ctx->lm_num.p, 0, vb, st));
+  CK(cudaMemsetAsync(ctx->lm_den.p, 0, vb, st));
+  std::vector<gslm_cache*> caches(n_b, nullptr);
+  struct CacheGuard {
+    std::vector<gslm_cache*>& v;
+    ~CacheGuard() {
+      for (auto* c : v) delete c;
+    }
+  } cg{caches};
+  std::vector<std::vector<gslm_camera>> scams(n_b);
+  std::vector<Buf> stg(n_b);
+  double cost0 = 0.0, pair_bytes = 0.0;
+  int pcg_iters = 0, n_pairs = 0;
+  ctx->timer.on = ctx->opt.profile != 0;
+  ctx->timer.st = st;
+  struct TimerOff {
+    PhaseTimer& t;
+    ~TimerOff() { t.on = false; t.open_phase = -1; }
+  } toff{ctx->timer};
+  long long entries = 0, bytes = 0;
+  const float lambda = state->lambda;
+  for (int i = 0; i < n_b; ++i) {
+    const int a = subset_off[i], e = subset_off[i + 1];
+    if (e <= a) return fail(ctx, GSLM_E_INVALID, "lm_step: empty subset");
+    long long pix = 0;
+    for (int k = a; k < e; ++k) {
+      const int v = subset_views[k];
+      if (v < 0 || v >= n_cams) return fail(ctx, GSLM_E_INVALID, "lm_step: bad camera index");
+      scams[i].push_back(cams[v]);
+      pix += (long long)cams[v].width * cams[v].height;
+    }
+    CK(stg[i].alloc(sizeof(float) * 3 * pix, st));
+    long long o = 0;
+    for (int k = a; k < e; ++k) {
+      const int v = subset_views[k];
+      const long long np = cam_pix[v + 1] - cam_pix[v];
+      CK(cudaMemcpyAsync(stg[i].as<float>() + 3 * o, targets + 3 * cam_pix[v], sizeof(float) * 3 * np,
+                         cudaMemcpyDeviceToDevice, st));
+      o += np;
+    }
+    double ci = 0.0;
+    bool t = ctx->timer.begin(PH_BUILD);
+    CKS(gslm_build_cache(ctx, params, N, ld, scams[i].data(), (int)scams[i].size(), stg[i].as<float>(), &caches[i],
+                         nullptr, ctx->lm_b.as<float>(), &ci));
+    ctx->timer.end(t);
+    cost0 += ci;
+    entries += caches[i]->n_entries;
+    bytes += (long long)caches[i]->device_bytes();
+    t = ctx->timer.begin(PH_DIAG);
+    CKS(gslm_jacobi_diag(ctx, caches[i], ctx->lm_M.as<float>()));
+    ctx->timer.end(t);
+    const float* D = precond != nullptr ? precond[i] : nullptr;
+    CKS(pcg_enqueue(ctx, caches[i], ctx->lm_b.as<float>(), ctx->lm_M.as<float>(), D, lambda, ctx->lm_x.as<float>()));
+    PcgScalars h;
+    CK(cudaMemcpyAsync(&h, ctx->scalars.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(launch_combine_acc((int)N, ld, ctx->lm_x.as<float>(), ctx->lm_M.as<float>(), ctx->lm_num.as<float>(),
+                          ctx->lm_den.as<float>(), st));
+    CK(cudaStreamSynchronize(st));
+    pcg_iters += h.iters;
+    const gslm_cache* c = caches[i];
+    n_pairs += 1 + h.iters;
+    pair_bytes += (1.0 + h.iters) * (2.0 * (double)c->n_entries * (double)(payload_bytes(c->fmt) + 1) +
+                                     24.0 * (double)c->n_pix + 472.0 * (double)N + 192.0 * (double)c->n_active);
+  }
+  CK(launch_combine_finish((int)N, ld, ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), ctx->lm_delta.as<float>(),
+                           st));
+  // predicted: sum_i ||J_i Delta + F_i||^2
+  bool trho = ctx->timer.begin(PH_RHO);
+  double pred = 0.0;
+  for (int i = 0; i < n_b; ++i) {
+    gslm_cache* c = caches[i];
+    CK(ctx->partials.ensure(sizeof(double) * std::max(c->n_tiles, 1), st));
+    CKS(do_apply_J(ctx, c, ctx->lm_delta.as<float>(), nullptr, nullptr, nullptr, nullptr, c->F.as<float>(),
+                   ctx->partials.as<double>()));
+    double pi = 0.0;
+    CKS(reduce_to_host(ctx, ctx->partials.as<double>(), c->n_tiles, &pi));
+    pred += pi;
+  }
+  // actual: ||F(x + Delta)||^2 over the same views
+  CK(launch_axpy_params((int)N, ld, params, ctx->lm_delta.as<float>(), ctx->lm_trial.as<float>(), st));
+  double cost1 = 0.0;
+  for (int i = 0; i < n_b; ++i) {
+    CK(ctx->lm_img.ensure(sizeof(float) * 3 * caches[i]->n_pix, st));
+    double ci = 0.0;
+    CKS(gslm_render(ctx, ctx->lm_trial.as<float>(), N, ld, scams[i].data(), (int)scams[i].size(),
+                    ctx->lm_img.as<float>(), stg[i].as<float>(), &ci));
+    cost1 += ci;
+  }
+  ctx->timer.end(trho);
+  const double den = cost0 - pred;
+  const double rho = den > 0.0 ? (cost0 - cost1) / den : -INFINITY;
+  const bool accept = den > 0.0 && rho > 1e-5;
+  double lam = state->lambda;
+  if (accept) {
+    CK(cudaMemcpyAsync(params, ctx->lm_trial.p, vb, cudaMemcpyDeviceToDevice, st));
+    lam *= 1.0 - std::pow(2.0 * rho - 1.0, 3.0);
+  } else {
+    lam *= 2.0;
+  }
+  lam = std::min<double>(std::max<double>(lam, ctx->opt.lambda_min), ctx->opt.lambda_max);
+  state->lambda = (float)lam;
+  state->step += 1;
+  CK(cudaEventRecord(ev1, st));
+  CK(cudaEventSynchronize(ev1));
+  if (stats != nullptr) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    stats->cost = cost0;
+    stats->cost_new = cost1;
+    stats->predicted = pred;
+    stats->rho = rho;
+    stats->accepted = accept ? 1 : 0;
+    stats->pcg_iters = pcg_iters;
+    stats->cache_entries = entries;
+    stats->cache_bytes = bytes;
+    stats->ms_total = ms;
+    for (int k = 0; k < 8; ++k) stats->ms_phase[k] = 0.0;
+    ctx->timer.collect(stats->ms_phase, 8);
+    stats->n_pairs = n_pairs;
+    stats->pad = 0;
+    stats->pair_bytes = pair_bytes;
+  } else {
+    double dummy[8] = {0};
+    ctx->timer.collect(dummy, 8);
+  }
+  return GSLM_OK;
+}
+
+}  // extern "C"

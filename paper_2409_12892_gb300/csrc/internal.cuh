@@ -1,0 +1,184 @@
+// Internal declarations shared by the CUDA translation units of libgslm.
+// Everything here is private to the library; the public ABI is include/gslm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "gslm.h"
+
+namespace gslm {
+
+// Rasterizer constants. The paper (Sec. 3.1) uses the 3DGS rasterizer without
+// stating its constants; these are the values this library adopts.
+constexpr int kTile = 16;                   // 16 x 16 pixel tiles
+constexpr int kTilePix = kTile * kTile;     // one thread per pixel in the tile kernels
+constexpr float kDilation = 0.3f;           // added to the 2D covariance diagonal
+constexpr float kNear = 0.2f;               // visible only if camera-space z > kNear
+constexpr float kRadiusSigmas = 3.0f;       // splat radius in standard deviations
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kShOffset = 0.5f;
+constexpr int kNP = 59;                     // parameters per Gaussian
+
+// Camera of one view of a call, with the view's place in the call's tile and
+// pixel index spaces.
+struct DevCam {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float campos[3];          // camera centre in world coordinates, -R^T t
+  int W, H;
+  int tiles_x, tiles_y;
+  int tile_off;             // first tile of this view in the call's tile numbering
+  int pad;
+  long long pix_off;        // first pixel of this view in the call's residual vector
+};
+
+// Projected splat as read by the blending and apply kernels.
+//   a = (mu_x, mu_y, conic A, conic B), b = (conic C, opacity, depth, 0),
+//   c = (r, g, b, 0)
+struct SplatRec {
+  float4 a, b, c;
+};
+
+// Device-side scalars of one PCG solve (Algorithm 1).
+struct PcgScalars {
+  double bb;        // ||b||^2
+  double rz;        // r^T z of the current iterate
+  double rz_new;
+  double pg;        // p^T g
+  double rr;        // ||r||^2
+  double alpha, beta;
+  int done;         // set when the break test fires or on breakdown
+  int iters;
+  int breakdown;
+  int pad;
+};
+
+// Everything the apply kernels need about one cache (device pointers).
+struct CacheView {
+  const DevCam* cams;
+  int V;
+  int n_tiles;
+  long long n_pix;                 // pixels over all views
+  int N;                           // Gaussians
+  long long n_slots;               // V * N
+  const SplatRec* rec;             // [n_slots]
+  const uint32_t* tile_seg_off;    // [n_tiles + 1]
+  const unsigned long long* seg_entry_off;  // [n_seg + 1]
+  const uint32_t* seg_slot;        // [n_seg]
+  const void* payload;             // [E] float4 (FP32) or 4 x 16-bit
+  const float* seg_scale;          // [n_seg] (FP16S only)
+  const uint8_t* pixoff;           // [E] pixel index inside the tile (row-major 16 x 16)
+  const uint32_t* slot_seg_start;  // [n_slots] segments of a slot, as a range of slot_seg_list
+  const uint32_t* slot_seg_end;
+  const uint32_t* slot_seg_list;   // [n_seg] segment ids ordered by slot
+  const uint8_t* slot_active;      // [n_slots]
+  long long n_seg;
+  long long n_entries;
+  int fmt;
+  const int* skip;                 // if non-null and *skip != 0 the kernels do nothing (PCG finished)
+};
+
+// Counts kernel launches of this library (reported by gslm_kernel_launches).
+void note_launch();
+
+// ----------------------------------------------------------------------------
+// Launchers (each defined in the .cu file that holds the kernel).
+// All return cudaGetLastError() of the launch.
+
+// project.cu
+cudaError_t launch_project(const float* params, int N, long long ld, const DevCam* cams, int V,
+                           int smooth, SplatRec* rec, uint32_t* ntiles, uint2* rect,
+                           uint32_t* depth_key, cudaStream_t st);
+cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCam* cams, int V,
+                           int smooth, const uint8_t* slot_active, const float* p,
+                           float* ydot, const float* z_beta, float* p_out,
+                           const PcgScalars* sc, cudaStream_t st);
+cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V,
+                       int smooth, const uint32_t* slot_seg_start, const uint32_t* slot_seg_end,
+                       const uint32_t* slot_seg_list, const float* seg_ybar, float scale,
+                       float* g, const float* p, const float* M, float lambda,
+                       double* dot_partials, const PcgScalars* sc, cudaStream_t st);
+cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V,
+                        int smooth, const uint32_t* slot_seg_start, const uint32_t* slot_seg_end,
+                        const uint32_t* slot_seg_list, const float* seg_q, float* diag,
+                        cudaStream_t st);
+int vjp_blocks(int N);
+
+// sort.cu
+size_t scan_temp_bytes(long long n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, void* temp,
+                               cudaStream_t st);   // out[n] = total
+cudaError_t exclusive_scan_u64(const uint32_t* in, unsigned long long* out, long long n,
+                               void* temp, cudaStream_t st);   // out[n] = total
+size_t radix_temp_bytes(long long n);
+// Stable LSD sort of (key, value) pairs on the low `bits` bits of the key. The
+// sorted result ends in (keys_out, vals_out); the *_tmp buffers are scratch.
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                             uint32_t* vals_tmp, long long n, int bits, void* temp,
+                             uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st);
+cudaError_t launch_flags(const uint32_t* counts, long long n, uint32_t* flags, cudaStream_t st);
+cudaError_t launch_compact_flags(const uint32_t* counts, const uint32_t* pos, long long n,
+                                 uint32_t* list, cudaStream_t st);
+cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, long long n,
+                              uint32_t* dst, cudaStream_t st);
+cudaError_t launch_iota_u32(uint32_t* dst, long long n, cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t* sorted_keys, long long n, uint32_t* start,
+                          uint32_t* end, cudaStream_t st);
+
+// raster.cu
+cudaError_t launch_emit_keys(const uint32_t* sorted_slots, long long n_vis, const uint2* rect,
+                             const DevCam* cams, int V, int N, const unsigned long long* key_off,
+                             uint32_t* tile_keys, uint32_t* tile_vals, cudaStream_t st);
+// Blend every tile. mode 0: render only; mode 1: also count entries/segments.
+cudaError_t launch_raster_count(const DevCam* cams, int V, int n_tiles, const uint32_t* tile_start,
+                                const uint32_t* tile_end, const uint32_t* tile_vals,
+                                const SplatRec* rec, int smooth, const float* targets,
+                                float* img, float* F, double* cost_partials, uint32_t* tile_entries,
+                                uint32_t* tile_segs, cudaStream_t st);
+cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const uint32_t* tile_start,
+                                const uint32_t* tile_end, const uint32_t* tile_vals,
+                                const SplatRec* rec, int smooth, const float* img,
+                                const unsigned long long* tile_entry_off,
+                                const uint32_t* tile_seg_off, int fmt, void* payload,
+                                float* seg_scale, uint8_t* pixoff,
+                                unsigned long long* seg_entry_off, uint32_t* seg_slot,
+                                uint8_t* slot_active, int* err, cudaStream_t st);
+
+// apply.cu
+cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add,
+                           float* u, double* sq_partials, int group, cudaStream_t st);
+cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar, int group,
+                            cudaStream_t st);
+cudaError_t launch_diag_entries(const CacheView& cv, float* seg_q, cudaStream_t st);
+int apply_J_partials(const CacheView& cv);
+
+// pcg.cu
+cudaError_t launch_reduce_partials(const double* partials, int n, double* out, cudaStream_t st);
+cudaError_t launch_pcg_init(long long n59, long long ld, int N, const float* b, const float* M,
+                            const float* D, float* x, float* Minv_out, double* partials,
+                            cudaStream_t st);
+cudaError_t launch_pcg_residual0(int N, long long ld, const float* b, const float* g,
+                                 const float* M, const float* x, float lambda, const float* Minv,
+                                 float* r, float* z, float* p, double* partials, cudaStream_t st);
+cudaError_t launch_pcg_scalars(PcgScalars* sc, const double* partials, int n_partials, int stage,
+                               float break_rel2, cudaStream_t st);
+cudaError_t launch_pcg_update(int N, long long ld, const PcgScalars* sc, const float* p,
+                              const float* g, const float* Minv, float* x, float* r, float* z,
+                              double* partials, cudaStream_t st);
+int pcg_blocks(int N);
+cudaError_t launch_combine_acc(int N, long long ld, const float* delta, const float* diag,
+                               float* num, float* den, cudaStream_t st);
+cudaError_t launch_combine_finish(int N, long long ld, const float* num, const float* den,
+                                  float* delta, cudaStream_t st);
+cudaError_t launch_axpy_params(int N, long long ld, const float* x, const float* d, float* out,
+                               cudaStream_t st);
+cudaError_t launch_neg_copy(long long n, const float* src, float* dst, cudaStream_t st);
+cudaError_t launch_count_nonzero_u8(const uint8_t* v, long long n, unsigned long long* out, cudaStream_t st);
+
+}  // namespace gslm

@@ -1,0 +1,281 @@
+// Vector operations of Algorithm 1 (Sec. 3.3; the paper runs these in
+// PyTorch), the subset weighted mean (Eq. combine-pcg) and small helpers.
+//
+// Vectors are [59][ld] float32. Dot products are accumulated in float64: each
+// block writes one partial, and a one-block kernel reduces the partials in a
+// fixed order and updates the device-side scalars (alpha, beta, the break
+// test), so a whole solve runs without host synchronisation.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace gslm {
+namespace {
+
+constexpr int kBS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+__device__ __forceinline__ int part_index() { return blockIdx.y * gridDim.x + blockIdx.x; }
+
+__global__ void k_pcg_init(int N, long long ld, const float* __restrict__ b, const float* __restrict__ M,
+                           const float* __restrict__ D, float* __restrict__ x, float* __restrict__ Minv,
+                           double* __restrict__ partials) {
+  __shared__ double red[kBS / 32];
+  const int i = blockIdx.x * kBS + threadIdx.x;
+  const long long o = (long long)blockIdx.y * ld + i;
+  double bb = 0.0;
+  if (i < N) {
+    float mi;
+    if (D != nullptr) {
+      mi = D[o];
+    } else {
+      const float m = M[o];
+      mi = m > 1e-30f ? 1.f / m : 0.f;
+    }
+    Minv[o] = mi;
+    const float bv = b[o];
+    x[o] = mi * bv;
+    bb = (double)bv * bv;
+  }
+  const double s = block_sum(bb, red);
+  if (threadIdx.x == 0) partials[part_index()] = s;
+}
+
+__global__ void k_pcg_residual0(int N, long long ld, const float* __restrict__ b, const float* __restrict__ g,
+                                const float* __restrict__ M, const float* __restrict__ x, float lambda,
+                                const float* __restrict__ Minv, float* __restrict__ r, float* __restrict__ z,
+                                float* __restrict__ p, double* __restrict__ partials) {
+  __shared__ double red[kBS / 32];
+  const int i = blockIdx.x * kBS + threadIdx.x;
+  const long long o = (long long)blockIdx.y * ld + i;
+  double rz = 0.0;
+  if (i < N) {
+    const float rv = b[o] - (g[o] + lambda * M[o] * x[o]);
+    const float zv = Minv[o] * rv;
+    r[o] = rv;
+    z[o] = zv;
+    p[o] = zv;
+    rz = (double)rv * zv;
+  }
+  const double s = block_sum(rz, red);
+  if (threadIdx.x == 0) partials[part_index()] = s;
+}
+
+__global__ void k_pcg_update(int N, long long ld, const PcgScalars* __restrict__ sc, const float* __restrict__ p,
+                             const float* __restrict__ g, const float* __restrict__ Minv, float* __restrict__ x,
+                             float* __restrict__ r, float* __restrict__ z, double* __restrict__ partials) {
+  __shared__ double red[kBS / 32];
+  if (sc->done) return;
+  const int i = blockIdx.x * kBS + threadIdx.x;
+  const long long o = (long long)blockIdx.y * ld + i;
+  const float alpha = (float)sc->alpha;
+  double rz = 0.0, rr = 0.0;
+  if (i < N) {
+    x[o] = x[o] + alpha * p[o];
+    const float rv = r[o] - alpha * g[o];
+    const float zv = Minv[o] * rv;
+    r[o] = rv;
+    z[o] = zv;
+    rz = (double)rv * zv;
+    rr = (double)rv * rv;
+  }
+  const double s0 = block_sum(rz, red);
+  __syncthreads();
+  const double s1 = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    partials[2 * part_index()] = s0;
+    partials[2 * part_index() + 1] = s1;
+  }
+}
+
+// stage 0: ||b||^2 (resets the solve state); 1: r^T z; 2: p^T g -> alpha;
+// 3: (r^T z, ||r||^2) -> beta and the break test.
+__global__ void k_pcg_scalars(PcgScalars* __restrict__ sc, const double* __restrict__ partials, int n, int stage,
+                              float break_rel2) {
+  __shared__ double red[kBS / 32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < n; i += kBS) {
+    if (stage == 3) {
+      s0 += partials[2 * i];
+      s1 += partials[2 * i + 1];
+    } else {
+      s0 += partials[i];
+    }
+  }
+  const double t0 = block_sum(s0, red);
+  __syncthreads();
+  const double t1 = block_sum(s1, red);
+  if (threadIdx.x != 0) return;
+  switch (stage) {
+    case 0:
+      sc->bb = t0;
+      sc->done = 0;
+      sc->iters = 0;
+      sc->breakdown = 0;
+      sc->alpha = 0.0;
+      sc->beta = 0.0;
+      sc->rr = t0;
+      break;
+    case 1:
+      sc->rz = t0;
+      break;
+    case 2:
+      if (sc->done) break;
+      sc->pg = t0;
+      if (!(t0 > 0.0) || !isfinite(t0)) {
+        sc->done = 1;
+        sc->breakdown = 1;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = sc->rz / t0;
+      }
+      break;
+    default:
+      if (sc->done) break;
+      sc->beta = sc->rz != 0.0 ? t0 / sc->rz : 0.0;
+      sc->rz = t0;
+      sc->rr = t1;
+      sc->iters += 1;
+      if (break_rel2 > 0.f && t1 < (double)break_rel2 * sc->bb) sc->done = 1;
+      break;
+  }
+}
+
+__global__ void k_reduce(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  __shared__ double red[kBS / 32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kBS) s += partials[i];
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) *out = t;
+}
+
+__global__ void k_combine_acc(int N, long long ld, const float* __restrict__ d, const float* __restrict__ m,
+                              float* __restrict__ num, float* __restrict__ den) {
+  const int i = blockIdx.x * kBS + threadIdx.x;
+  if (i >= N) return;
+  const long long o = (long long)blockIdx.y * ld + i;
+  const float mv = m[o];
+  num[o] += mv * d[o];
+  den[o] += mv;
+}
+
+__global__ void k_combine_finish(int N, long long ld, const float* __restrict__ num, const float* __restrict__ den,
+                                 float* __restrict__ d) {
+  const int i = blockIdx.x * kBS + threadIdx.x;
+  if (i >= N) return;
+  const long long o = (long long)blockIdx.y * ld + i;
+  const float dv = den[o];
+  d[o] = dv > 0.f ? num[o] / dv : 0.f;
+}
+
+__global__ void k_axpy(int N, long long ld, const float* __restrict__ x, const float* __restrict__ d,
+                       float* __restrict__ out) {
+  const int i = blockIdx.x * kBS + threadIdx.x;
+  if (i >= N) return;
+  const long long o = (long long)blockIdx.y * ld + i;
+  out[o] = x[o] + d[o];
+}
+
+__global__ void k_neg(long long n, const float* __restrict__ s, float* __restrict__ d) {
+  const long long i = (long long)blockIdx.x * kBS + threadIdx.x;
+  if (i < n) d[i] = -s[i];
+}
+
+__global__ void k_count_nonzero(const uint8_t* __restrict__ v, long long n, unsigned long long* __restrict__ out) {
+  __shared__ unsigned int red[kBS / 32];
+  unsigned int c = 0;
+  for (long long i = (long long)blockIdx.x * kBS + threadIdx.x; i < n; i += (long long)gridDim.x * kBS) c += v[i] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int w = 0; w < kBS / 32; ++w) s += red[w];
+    atomicAdd(out, s);
+  }
+}
+
+dim3 vec_grid(int N) { return dim3((unsigned)((N + kBS - 1) / kBS), kNP); }
+
+}  // namespace
+
+int pcg_blocks(int N) { return ((N + kBS - 1) / kBS) * kNP; }
+
+cudaError_t launch_reduce_partials(const double* partials, int n, double* out, cudaStream_t st) {
+  { k_reduce<<<1, kBS, 0, st>>>(partials, n, out); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_init(long long n59, long long ld, int N, const float* b, const float* M, const float* D,
+                            float* x, float* Minv, double* partials, cudaStream_t st) {
+  (void)n59;
+  if (N <= 0) return cudaSuccess;
+  { k_pcg_init<<<vec_grid(N), kBS, 0, st>>>(N, ld, b, M, D, x, Minv, partials); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_residual0(int N, long long ld, const float* b, const float* g, const float* M, const float* x,
+                                 float lambda, const float* Minv, float* r, float* z, float* p, double* partials,
+                                 cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  { k_pcg_residual0<<<vec_grid(N), kBS, 0, st>>>(N, ld, b, g, M, x, lambda, Minv, r, z, p, partials); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_scalars(PcgScalars* sc, const double* partials, int n_partials, int stage, float break_rel2,
+                               cudaStream_t st) {
+  { k_pcg_scalars<<<1, kBS, 0, st>>>(sc, partials, n_partials, stage, break_rel2); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update(int N, long long ld, const PcgScalars* sc, const float* p, const float* g,
+                              const float* Minv, float* x, float* r, float* z, double* partials, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  { k_pcg_update<<<vec_grid(N), kBS, 0, st>>>(N, ld, sc, p, g, Minv, x, r, z, partials); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_acc(int N, long long ld, const float* delta, const float* diag, float* num, float* den,
+                               cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  { k_combine_acc<<<vec_grid(N), kBS, 0, st>>>(N, ld, delta, diag, num, den); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_finish(int N, long long ld, const float* num, const float* den, float* delta,
+                                  cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  { k_combine_finish<<<vec_grid(N), kBS, 0, st>>>(N, ld, num, den, delta); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_params(int N, long long ld, const float* x, const float* d, float* out, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  { k_axpy<<<vec_grid(N), kBS, 0, st>>>(N, ld, x, d, out); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_neg_copy(long long n, const float* src, float* dst, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { k_neg<<<(unsigned)((n + kBS - 1) / kBS), kBS, 0, st>>>(n, src, dst); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_nonzero_u8(const uint8_t* v, long long n, unsigned long long* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || n <= 0) return e;
+  const long long blocks = std::min<long long>((n + kBS - 1) / kBS, 4096);
+  { k_count_nonzero<<<(unsigned)blocks, kBS, 0, st>>>(v, n, out); note_launch(); }
+  return cudaGetLastError();
+}
+
+}  // namespace gslm

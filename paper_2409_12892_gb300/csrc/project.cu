@@ -1,0 +1,703 @@
+// Gaussian -> splat projection and the per-Gaussian factor dy/dx of the chain
+// rule in Eq. backward-pass (Sec. 3.3): forward (k_project), its tangent
+// (k_tangent: ydot = (dy/dx) p, used by J p) and its adjoint (k_vjp:
+// (dy/dx)^T ybar, used by J^T u), plus the diag(J^T J) finalisation (k_diag).
+//
+// The per-Gaussian kernels keep one thread per Gaussian and loop over the views
+// of the cache, so each Gaussian's 59 parameters and 59 vector entries are read
+// once per call (coalesced, structure-of-arrays) and the per-view results are
+// summed in registers: this is the paper's applyJT_p2/p3 and the "sortX" it
+// needs before applyJ (Sec. A), replaced by one pass in the [59][ld] layout.
+//
+// Splat attributes y (9): mean (mx, my), conic (A, B, C) = inverse of the 2D
+// covariance [[a, b], [b, c]], opacity o, colour (r, g, b).
+#include "internal.cuh"
+
+namespace gslm {
+namespace {
+
+// Real spherical harmonics, degree <= 3, with the Condon-Shortley phase
+// (sign (-1)^m); normalisation constants are the closed forms
+// 1/(2 sqrt(pi)), sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4,
+// sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kY1 = 0.48860251190291992f;
+constexpr float kY2a = 1.09254843059207907f;
+constexpr float kY2b = 0.31539156525252001f;
+constexpr float kY2c = 0.54627421529603953f;
+constexpr float kY3a = 0.59004358992664352f;
+constexpr float kY3b = 2.89061144264055405f;
+constexpr float kY3c = 0.45704579946446572f;
+constexpr float kY3d = 0.37317633259011540f;
+constexpr float kY3e = 1.44530572132027702f;
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = kY0;
+  Y[1] = -kY1 * y;
+  Y[2] = kY1 * z;
+  Y[3] = -kY1 * x;
+  Y[4] = kY2a * x * y;
+  Y[5] = -kY2a * y * z;
+  Y[6] = kY2b * (2.f * zz - xx - yy);
+  Y[7] = -kY2a * x * z;
+  Y[8] = kY2c * (xx - yy);
+  Y[9] = -kY3a * y * (3.f * xx - yy);
+  Y[10] = kY3b * x * y * z;
+  Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+  Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+  Y[14] = kY3e * z * (xx - yy);
+  Y[15] = -kY3a * x * (xx - 3.f * yy);
+}
+
+// g = sum_k w_k grad Y_k(x, y, z), the polynomial gradient (no re-normalisation).
+__device__ __forceinline__ void sh_grad(float x, float y, float z, const float w[16], float g[3]) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  gy += -kY1 * w[1];
+  gz += kY1 * w[2];
+  gx += -kY1 * w[3];
+  gx += kY2a * y * w[4];            gy += kY2a * x * w[4];
+  gy += -kY2a * z * w[5];           gz += -kY2a * y * w[5];
+  gx += -2.f * kY2b * x * w[6];     gy += -2.f * kY2b * y * w[6];     gz += 4.f * kY2b * z * w[6];
+  gx += -kY2a * z * w[7];           gz += -kY2a * x * w[7];
+  gx += 2.f * kY2c * x * w[8];      gy += -2.f * kY2c * y * w[8];
+  gx += -kY3a * 6.f * x * y * w[9]; gy += -kY3a * (3.f * xx - 3.f * yy) * w[9];
+  gx += kY3b * y * z * w[10];       gy += kY3b * x * z * w[10];       gz += kY3b * x * y * w[10];
+  gx += kY3c * 2.f * x * y * w[11];
+  gy += -kY3c * (4.f * zz - xx - 3.f * yy) * w[11];
+  gz += -kY3c * 8.f * y * z * w[11];
+  gx += -kY3d * 6.f * x * z * w[12];
+  gy += -kY3d * 6.f * y * z * w[12];
+  gz += kY3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+  gx += -kY3c * (4.f * zz - 3.f * xx - yy) * w[13];
+  gy += kY3c * 2.f * x * y * w[13];
+  gz += -kY3c * 8.f * x * z * w[13];
+  gx += kY3e * 2.f * x * z * w[14]; gy += -kY3e * 2.f * y * z * w[14]; gz += kY3e * (xx - yy) * w[14];
+  gx += -kY3a * (3.f * xx - 3.f * yy) * w[15];
+  gy += kY3a * 6.f * x * y * w[15];
+  g[0] = gx;
+  g[1] = gy;
+  g[2] = gz;
+}
+
+// View-independent state of one Gaussian.
+struct GaussGeo {
+  float mu[3];
+  float qn[4];
+  float qinv;      // 1 / |q|
+  float R[9];      // rotation of the normalised quaternion, row-major
+  float S[3];      // exp(log-scale)
+  float M[9];      // R diag(S)
+  float Sig[6];    // 3D covariance M M^T: xx, xy, xz, yy, yz, zz
+  float o;         // opacity
+};
+
+__device__ __forceinline__ float sym(const float s[6], int i, int j) {
+  // index of (i, j) in xx, xy, xz, yy, yz, zz
+  const int a = i < j ? i : j, b = i < j ? j : i;
+  const int idx = a == 0 ? b : (a == 1 ? 2 + b : 5);
+  return s[idx];
+}
+
+__device__ __forceinline__ void gauss_geo(const float* __restrict__ P, long long ld, int g, GaussGeo& G) {
+  G.mu[0] = P[0 * ld + g];
+  G.mu[1] = P[1 * ld + g];
+  G.mu[2] = P[2 * ld + g];
+  const float q0 = P[6 * ld + g], q1 = P[7 * ld + g], q2 = P[8 * ld + g], q3 = P[9 * ld + g];
+  const float len = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  G.qinv = 1.f / len;
+  const float w = q0 * G.qinv, x = q1 * G.qinv, y = q2 * G.qinv, z = q3 * G.qinv;
+  G.qn[0] = w; G.qn[1] = x; G.qn[2] = y; G.qn[3] = z;
+  G.R[0] = 1.f - 2.f * (y * y + z * z); G.R[1] = 2.f * (x * y - w * z); G.R[2] = 2.f * (x * z + w * y);
+  G.R[3] = 2.f * (x * y + w * z); G.R[4] = 1.f - 2.f * (x * x + z * z); G.R[5] = 2.f * (y * z - w * x);
+  G.R[6] = 2.f * (x * z - w * y); G.R[7] = 2.f * (y * z + w * x); G.R[8] = 1.f - 2.f * (x * x + y * y);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) G.S[j] = expf(P[(3 + j) * ld + g]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G.M[i * 3 + j] = G.R[i * 3 + j] * G.S[j];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      G.Sig[k++] = G.M[i * 3 + 0] * G.M[j * 3 + 0] + G.M[i * 3 + 1] * G.M[j * 3 + 1] +
+                   G.M[i * 3 + 2] * G.M[j * 3 + 2];
+    }
+  G.o = 1.f / (1.f + expf(-P[10 * ld + g]));
+}
+
+// Per-view state of one splat.
+struct ViewGeo {
+  float tc[3];
+  float iz;
+  float T0[3], T1[3];      // T = Jp W (2 x 3)
+  float ST0[3], ST1[3];    // Sigma T0^T, Sigma T1^T
+  float a, b, c;           // 2D covariance incl. dilation
+  float A, B, C;           // conic
+  float det;
+  float mx, my;
+  float dir[3];
+  float inv_dlen;
+};
+
+__device__ __forceinline__ void view_geo(const GaussGeo& G, const DevCam& cam, ViewGeo& V) {
+  const float* W = cam.R;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    V.tc[i] = W[i * 3 + 0] * G.mu[0] + W[i * 3 + 1] * G.mu[1] + W[i * 3 + 2] * G.mu[2] + cam.t[i];
+  V.iz = 1.f / V.tc[2];
+  const float iz2 = V.iz * V.iz;
+  const float J00 = cam.fx * V.iz, J02 = -cam.fx * V.tc[0] * iz2;
+  const float J11 = cam.fy * V.iz, J12 = -cam.fy * V.tc[1] * iz2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    V.T0[k] = J00 * W[0 * 3 + k] + J02 * W[2 * 3 + k];
+    V.T1[k] = J11 * W[1 * 3 + k] + J12 * W[2 * 3 + k];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    V.ST0[i] = sym(G.Sig, i, 0) * V.T0[0] + sym(G.Sig, i, 1) * V.T0[1] + sym(G.Sig, i, 2) * V.T0[2];
+    V.ST1[i] = sym(G.Sig, i, 0) * V.T1[0] + sym(G.Sig, i, 1) * V.T1[1] + sym(G.Sig, i, 2) * V.T1[2];
+  }
+  V.a = V.T0[0] * V.ST0[0] + V.T0[1] * V.ST0[1] + V.T0[2] * V.ST0[2] + kDilation;
+  V.b = V.T0[0] * V.ST1[0] + V.T0[1] * V.ST1[1] + V.T0[2] * V.ST1[2];
+  V.c = V.T1[0] * V.ST1[0] + V.T1[1] * V.ST1[1] + V.T1[2] * V.ST1[2] + kDilation;
+  V.det = V.a * V.c - V.b * V.b;
+  const float inv = 1.f / V.det;
+  V.A = V.c * inv;
+  V.B = -V.b * inv;
+  V.C = V.a * inv;
+  V.mx = cam.fx * V.tc[0] * V.iz + cam.cx;
+  V.my = cam.fy * V.tc[1] * V.iz + cam.cy;
+  const float d0 = G.mu[0] - cam.campos[0], d1 = G.mu[1] - cam.campos[1], d2 = G.mu[2] - cam.campos[2];
+  const float dl = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  V.inv_dlen = 1.f / dl;
+  V.dir[0] = d0 * V.inv_dlen;
+  V.dir[1] = d1 * V.inv_dlen;
+  V.dir[2] = d2 * V.inv_dlen;
+}
+
+// d(R(qn)) for a tangent qdn of the normalised quaternion.
+__device__ __forceinline__ void rot_tangent(const float qn[4], const float qd[4], float Rd[9]) {
+  const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+  const float dw = qd[0], dx = qd[1], dy = qd[2], dz = qd[3];
+  Rd[0] = -4.f * (y * dy + z * dz);
+  Rd[1] = 2.f * (dx * y + x * dy - dw * z - w * dz);
+  Rd[2] = 2.f * (dx * z + x * dz + dw * y + w * dy);
+  Rd[3] = 2.f * (dx * y + x * dy + dw * z + w * dz);
+  Rd[4] = -4.f * (x * dx + z * dz);
+  Rd[5] = 2.f * (dy * z + y * dz - dw * x - w * dx);
+  Rd[6] = 2.f * (dx * z + x * dz - dw * y - w * dy);
+  Rd[7] = 2.f * (dy * z + y * dz + dw * x + w * dx);
+  Rd[8] = -4.f * (x * dx + y * dy);
+}
+
+// Tangent of the 3D covariance for parameter tangents (ds, dq).
+__device__ __forceinline__ void sigma_tangent(const GaussGeo& G, const float ds[3], const float dq[4],
+                                              float Sd[6]) {
+  const float qdot = G.qn[0] * dq[0] + G.qn[1] * dq[1] + G.qn[2] * dq[2] + G.qn[3] * dq[3];
+  float qnd[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) qnd[i] = (dq[i] - G.qn[i] * qdot) * G.qinv;
+  float Rd[9];
+  rot_tangent(G.qn, qnd, Rd);
+  float Md[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Md[i * 3 + j] = Rd[i * 3 + j] * G.S[j] + G.R[i * 3 + j] * G.S[j] * ds[j];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      Sd[k++] = Md[i * 3 + 0] * G.M[j * 3 + 0] + Md[i * 3 + 1] * G.M[j * 3 + 1] + Md[i * 3 + 2] * G.M[j * 3 + 2] +
+                G.M[i * 3 + 0] * Md[j * 3 + 0] + G.M[i * 3 + 1] * Md[j * 3 + 1] + G.M[i * 3 + 2] * Md[j * 3 + 2];
+    }
+}
+
+// Geometric part of ydot: (mx, my, A, B, C) tangents for mean tangent mud and
+// covariance tangent Sd.
+__device__ __forceinline__ void geo_tangent(const ViewGeo& V, const DevCam& cam, const float mud[3],
+                                            const float Sd[6], float yd[5]) {
+  const float* W = cam.R;
+  float td[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) td[i] = W[i * 3 + 0] * mud[0] + W[i * 3 + 1] * mud[1] + W[i * 3 + 2] * mud[2];
+  const float iz = V.iz, iz2 = iz * iz, iz3 = iz2 * iz;
+  yd[0] = cam.fx * (td[0] * iz - V.tc[0] * iz2 * td[2]);
+  yd[1] = cam.fy * (td[1] * iz - V.tc[1] * iz2 * td[2]);
+  const float J00d = -cam.fx * iz2 * td[2];
+  const float J02d = -cam.fx * (td[0] * iz2 - 2.f * V.tc[0] * iz3 * td[2]);
+  const float J11d = -cam.fy * iz2 * td[2];
+  const float J12d = -cam.fy * (td[1] * iz2 - 2.f * V.tc[1] * iz3 * td[2]);
+  float T0d[3], T1d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T0d[k] = J00d * W[0 * 3 + k] + J02d * W[2 * 3 + k];
+    T1d[k] = J11d * W[1 * 3 + k] + J12d * W[2 * 3 + k];
+  }
+  // T0 Sd T0^T etc.
+  float SdT0[3], SdT1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    SdT0[i] = sym(Sd, i, 0) * V.T0[0] + sym(Sd, i, 1) * V.T0[1] + sym(Sd, i, 2) * V.T0[2];
+    SdT1[i] = sym(Sd, i, 0) * V.T1[0] + sym(Sd, i, 1) * V.T1[1] + sym(Sd, i, 2) * V.T1[2];
+  }
+  const float ad = 2.f * (T0d[0] * V.ST0[0] + T0d[1] * V.ST0[1] + T0d[2] * V.ST0[2]) +
+                   (V.T0[0] * SdT0[0] + V.T0[1] * SdT0[1] + V.T0[2] * SdT0[2]);
+  const float bd = (T0d[0] * V.ST1[0] + T0d[1] * V.ST1[1] + T0d[2] * V.ST1[2]) +
+                   (T1d[0] * V.ST0[0] + T1d[1] * V.ST0[1] + T1d[2] * V.ST0[2]) +
+                   (V.T0[0] * SdT1[0] + V.T0[1] * SdT1[1] + V.T0[2] * SdT1[2]);
+  const float cd = 2.f * (T1d[0] * V.ST1[0] + T1d[1] * V.ST1[1] + T1d[2] * V.ST1[2]) +
+                   (V.T1[0] * SdT1[0] + V.T1[1] * SdT1[1] + V.T1[2] * SdT1[2]);
+  const float A = V.A, B = V.B, C = V.C;
+  yd[2] = -(A * A * ad + 2.f * A * B * bd + B * B * cd);
+  yd[3] = -(A * B * ad + (A * C + B * B) * bd + B * C * cd);
+  yd[4] = -(B * B * ad + 2.f * B * C * bd + C * C * cd);
+}
+
+__device__ __forceinline__ long long n_slots(int N, int V) { return (long long)N * V; }
+
+__global__ void k_project(const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams,
+                          int V, int smooth, SplatRec* __restrict__ rec, uint32_t* __restrict__ ntiles,
+                          uint2* __restrict__ rect, uint32_t* __restrict__ depth_key) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots(N, V)) return;
+  const int v = (int)(s / N);
+  const int g = (int)(s - (long long)v * N);
+  const DevCam& cam = cams[v];
+  const float tz = cam.R[6] * P[0 * ld + g] + cam.R[7] * P[1 * ld + g] + cam.R[8] * P[2 * ld + g] + cam.t[2];
+  ntiles[s] = 0;
+  depth_key[s] = 0xffffffffu;
+  if (!(tz > kNear)) return;
+  GaussGeo G;
+  gauss_geo(P, ld, g, G);
+  ViewGeo VG;
+  view_geo(G, cam, VG);
+  if (!(VG.det > 0.f) || !isfinite(VG.A) || !isfinite(VG.mx) || !isfinite(VG.my)) return;
+  const float mid = 0.5f * (VG.a + VG.c);
+  const float disc = fmaxf(0.25f * (VG.a - VG.c) * (VG.a - VG.c) + VG.b * VG.b, 0.f);
+  const float lam = mid + sqrtf(disc);
+  const float r = ceilf(kRadiusSigmas * sqrtf(lam));
+  int x0, y0, x1, y1;
+  if (smooth) {
+    x0 = 0; y0 = 0; x1 = cam.tiles_x; y1 = cam.tiles_y;
+  } else {
+    const float inv = 1.f / kTile;
+    x0 = (int)fminf(fmaxf(floorf((VG.mx - r) * inv), 0.f), (float)cam.tiles_x);
+    y0 = (int)fminf(fmaxf(floorf((VG.my - r) * inv), 0.f), (float)cam.tiles_y);
+    x1 = (int)fminf(fmaxf(floorf((VG.mx + r) * inv) + 1.f, 0.f), (float)cam.tiles_x);
+    y1 = (int)fminf(fmaxf(floorf((VG.my + r) * inv) + 1.f, 0.f), (float)cam.tiles_y);
+  }
+  if (x1 <= x0 || y1 <= y0) return;
+  float Y[16];
+  sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
+  float rgb[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += Y[k] * P[(11 + 3 * k + ch) * ld + g];
+    acc += kShOffset;
+    rgb[ch] = smooth ? acc : fmaxf(acc, 0.f);
+  }
+  SplatRec R;
+  R.a = make_float4(VG.mx, VG.my, VG.A, VG.B);
+  R.b = make_float4(VG.C, G.o, VG.tc[2], 0.f);
+  R.c = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+  rec[s] = R;
+  ntiles[s] = (uint32_t)((x1 - x0) * (y1 - y0));
+  rect[s] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+  depth_key[s] = __float_as_uint(VG.tc[2]);
+}
+
+// ydot[slot] = (dy/dx) p for every active slot of every Gaussian. With z_beta
+// given, first p = z + beta p (Algorithm 1's last vector update, fused), and the
+// new p is written back to p_out.
+__global__ void __launch_bounds__(128) k_tangent(
+    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+    const uint8_t* __restrict__ slot_active, const float* __restrict__ pin, float* __restrict__ ydot,
+    const float* __restrict__ zb, float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  if (sc != nullptr && sc->done) return;
+  float pd[kNP];
+  if (zb != nullptr) {
+    const float beta = (float)sc->beta;
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) {
+      const float v = zb[k * ld + g] + beta * pin[k * ld + g];
+      pd[k] = v;
+      pout[k * ld + g] = v;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) pd[k] = pin[k * ld + g];
+  }
+  bool any = false;
+  for (int v = 0; v < V; ++v) any |= slot_active[(long long)v * N + g] != 0;
+  if (!any) return;
+  GaussGeo G;
+  gauss_geo(P, ld, g, G);
+  float Sd[6];
+  sigma_tangent(G, pd + 3, pd + 6, Sd);
+  const float od = G.o * (1.f - G.o) * pd[10];
+  for (int v = 0; v < V; ++v) {
+    const long long slot = (long long)v * N + g;
+    if (!slot_active[slot]) continue;
+    const DevCam& cam = cams[v];
+    ViewGeo VG;
+    view_geo(G, cam, VG);
+    float yd[5];
+    geo_tangent(VG, cam, pd, Sd, yd);
+    float Y[16];
+    sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
+    const float mdot = VG.dir[0] * pd[0] + VG.dir[1] * pd[1] + VG.dir[2] * pd[2];
+    float dd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dd[i] = (pd[i] - VG.dir[i] * mdot) * VG.inv_dlen;
+    float rgbd[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float w[16];
+      float raw = kShOffset, acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        w[k] = P[(11 + 3 * k + ch) * ld + g];
+        raw += Y[k] * w[k];
+        acc += Y[k] * pd[11 + 3 * k + ch];
+      }
+      float gr[3];
+      sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], w, gr);
+      acc += gr[0] * dd[0] + gr[1] * dd[1] + gr[2] * dd[2];
+      rgbd[ch] = (!smooth && raw < 0.f) ? 0.f : acc;
+    }
+    float4* out = reinterpret_cast<float4*>(ydot + slot * 12);
+    out[0] = make_float4(yd[0], yd[1], yd[2], yd[3]);
+    out[1] = make_float4(yd[4], od, rgbd[0], rgbd[1]);
+    out[2] = make_float4(rgbd[2], 0.f, 0.f, 0.f);
+  }
+}
+
+// g = scale * (dy/dx)^T ybar summed over the views; ybar of a slot is the sum
+// of its segments' partial sums. Epilogue (M != null): g += lambda M p and a
+// per-block float64 partial of p^T g.
+__global__ void __launch_bounds__(128) k_vjp(
+    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+    const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
+    const uint32_t* __restrict__ s_list, const float* __restrict__ seg_ybar, float scale,
+    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
+    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool skip = (sc != nullptr && sc->done);
+  double local = 0.0;
+  if (g < N && !skip) {
+    float mub[3] = {0.f, 0.f, 0.f};
+    float GS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float ob = 0.f;
+    float shb[48];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) shb[k] = 0.f;
+    bool any = false;
+    GaussGeo G;
+    for (int v = 0; v < V; ++v) {
+      const long long slot = (long long)v * N + g;
+      const uint32_t a = s_start[slot], b = s_end[slot];
+      if (a == b) continue;
+      if (!any) {
+        gauss_geo(P, ld, g, G);
+        any = true;
+      }
+      float yb[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) yb[i] = 0.f;
+      for (uint32_t j = a; j < b; ++j) {
+        const float4* s4 = reinterpret_cast<const float4*>(seg_ybar + (size_t)s_list[j] * 12);
+        const float4 u0 = s4[0], u1 = s4[1], u2 = s4[2];
+        yb[0] += u0.x; yb[1] += u0.y; yb[2] += u0.z; yb[3] += u0.w;
+        yb[4] += u1.x; yb[5] += u1.y; yb[6] += u1.z; yb[7] += u1.w; yb[8] += u2.x;
+      }
+      const DevCam& cam = cams[v];
+      ViewGeo VG;
+      view_geo(G, cam, VG);
+      // colour -> SH coefficients and view direction
+      float Y[16];
+      sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
+      float wsum[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float raw = kShOffset;
+        float shv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          shv[k] = P[(11 + 3 * k + ch) * ld + g];
+          raw += Y[k] * shv[k];
+        }
+        const float rb = (!smooth && raw < 0.f) ? 0.f : yb[6 + ch];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          shb[3 * k + ch] += Y[k] * rb;
+          wsum[k] += rb * shv[k];
+        }
+      }
+      float db[3];
+      sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], wsum, db);
+      const float dd = VG.dir[0] * db[0] + VG.dir[1] * db[1] + VG.dir[2] * db[2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) mub[i] += (db[i] - VG.dir[i] * dd) * VG.inv_dlen;
+      ob += yb[5];
+      // conic -> 2D covariance
+      const float A = VG.A, B = VG.B, C = VG.C;
+      const float ab = -(A * A * yb[2] + A * B * yb[3] + B * B * yb[4]);
+      const float bb = -(2.f * A * B * yb[2] + (A * C + B * B) * yb[3] + 2.f * B * C * yb[4]);
+      const float cb = -(B * B * yb[2] + B * C * yb[3] + C * C * yb[4]);
+      // 2D covariance -> 3D covariance (symmetric full-matrix gradient) and T
+      {
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = i; j < 3; ++j) {
+            GS[k++] += ab * VG.T0[i] * VG.T0[j] + 0.5f * bb * (VG.T0[i] * VG.T1[j] + VG.T1[i] * VG.T0[j]) +
+                       cb * VG.T1[i] * VG.T1[j];
+          }
+      }
+      float T0b[3], T1b[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        T0b[i] = 2.f * ab * VG.ST0[i] + bb * VG.ST1[i];
+        T1b[i] = bb * VG.ST0[i] + 2.f * cb * VG.ST1[i];
+      }
+      const float* W = cam.R;
+      const float J00b = T0b[0] * W[0] + T0b[1] * W[1] + T0b[2] * W[2];
+      const float J02b = T0b[0] * W[6] + T0b[1] * W[7] + T0b[2] * W[8];
+      const float J11b = T1b[0] * W[3] + T1b[1] * W[4] + T1b[2] * W[5];
+      const float J12b = T1b[0] * W[6] + T1b[1] * W[7] + T1b[2] * W[8];
+      const float iz = VG.iz, iz2 = iz * iz, iz3 = iz2 * iz;
+      const float tx = VG.tc[0], ty = VG.tc[1];
+      float tb[3];
+      tb[0] = -cam.fx * iz2 * J02b + cam.fx * iz * yb[0];
+      tb[1] = -cam.fy * iz2 * J12b + cam.fy * iz * yb[1];
+      tb[2] = -cam.fx * iz2 * J00b + 2.f * cam.fx * tx * iz3 * J02b - cam.fy * iz2 * J11b +
+              2.f * cam.fy * ty * iz3 * J12b - cam.fx * tx * iz2 * yb[0] - cam.fy * ty * iz2 * yb[1];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) mub[i] += W[0 * 3 + i] * tb[0] + W[1 * 3 + i] * tb[1] + W[2 * 3 + i] * tb[2];
+    }
+    float out[kNP];
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) out[k] = 0.f;
+    if (any) {
+      out[0] = mub[0]; out[1] = mub[1]; out[2] = mub[2];
+      // 3D covariance -> M = R diag(S): Mb = 2 GS M
+      float Mb[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          Mb[i * 3 + j] = 2.f * (sym(GS, i, 0) * G.M[0 * 3 + j] + sym(GS, i, 1) * G.M[1 * 3 + j] +
+                                 sym(GS, i, 2) * G.M[2 * 3 + j]);
+      float Rb[9];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        float sbar = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          Rb[i * 3 + j] = Mb[i * 3 + j] * G.S[j];
+          sbar += Mb[i * 3 + j] * G.R[i * 3 + j];
+        }
+        out[3 + j] = sbar * G.S[j];
+      }
+      const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
+      float qb[4];
+      qb[0] = 2.f * (-Rb[1] * z + Rb[2] * y + Rb[3] * z - Rb[5] * x - Rb[6] * y + Rb[7] * x);
+      qb[1] = -4.f * x * (Rb[4] + Rb[8]) + 2.f * (Rb[1] * y + Rb[2] * z + Rb[3] * y - Rb[5] * w + Rb[6] * z + Rb[7] * w);
+      qb[2] = -4.f * y * (Rb[0] + Rb[8]) + 2.f * (Rb[1] * x + Rb[2] * w + Rb[3] * x + Rb[5] * z - Rb[6] * w + Rb[7] * z);
+      qb[3] = -4.f * z * (Rb[0] + Rb[4]) + 2.f * (-Rb[1] * w + Rb[2] * x + Rb[3] * w + Rb[5] * y + Rb[6] * x + Rb[7] * y);
+      const float qd = G.qn[0] * qb[0] + G.qn[1] * qb[1] + G.qn[2] * qb[2] + G.qn[3] * qb[3];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) out[6 + i] = (qb[i] - G.qn[i] * qd) * G.qinv;
+      out[10] = ob * G.o * (1.f - G.o);
+#pragma unroll
+      for (int k = 0; k < 48; ++k) out[11 + k] = shb[k];
+    }
+    if (Mdiag != nullptr) {
+#pragma unroll
+      for (int k = 0; k < kNP; ++k) {
+        const float pk = p[k * ld + g];
+        const float gk = scale * out[k] + lambda * Mdiag[k * ld + g] * pk;
+        gout[k * ld + g] = gk;
+        local += (double)pk * (double)gk;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kNP; ++k) gout[k * ld + g] = scale * out[k];
+    }
+  }
+  if (partials != nullptr) {
+    // block reduction of the float64 partial dot
+    __shared__ double red[4];
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      partials[blockIdx.x] = s;
+    }
+  }
+}
+
+// diag(J^T J) for every Gaussian: sum over views of v_k^T Q v_k, where v_k is
+// column k of dy/dx and Q (per slot) is the sum over its cache entries and
+// channels of (dc/dy)^T (dc/dy), stored as 21 geo-geo + 18 geo-rgb + 1 rgb values.
+__global__ void __launch_bounds__(128) k_diag(
+    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+    const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
+    const uint32_t* __restrict__ s_list, const float* __restrict__ seg_q, float* __restrict__ dout) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  float d[kNP];
+#pragma unroll
+  for (int k = 0; k < kNP; ++k) d[k] = 0.f;
+  bool any = false;
+  GaussGeo G;
+  for (int v = 0; v < V; ++v) {
+    const long long slot = (long long)v * N + g;
+    const uint32_t a = s_start[slot], b = s_end[slot];
+    if (a == b) continue;
+    if (!any) {
+      gauss_geo(P, ld, g, G);
+      any = true;
+    }
+    float Q[40];
+#pragma unroll
+    for (int i = 0; i < 40; ++i) Q[i] = 0.f;
+    for (uint32_t j = a; j < b; ++j) {
+      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)s_list[j] * 40);
+#pragma unroll
+      for (int i = 0; i < 10; ++i) {
+        const float4 t = q4[i];
+        Q[4 * i + 0] += t.x; Q[4 * i + 1] += t.y; Q[4 * i + 2] += t.z; Q[4 * i + 3] += t.w;
+      }
+    }
+    const DevCam& cam = cams[v];
+    ViewGeo VG;
+    view_geo(G, cam, VG);
+    float Y[16];
+    sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
+    bool live[3];
+    float grad[3][3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float w[16];
+      float raw = kShOffset;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        w[k] = P[(11 + 3 * k + ch) * ld + g];
+        raw += Y[k] * w[k];
+      }
+      live[ch] = smooth || raw >= 0.f;
+      sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], w, grad[ch]);
+    }
+    const float D = Q[39];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch)
+        if (live[ch]) d[11 + 3 * k + ch] += D * Y[k] * Y[k];
+    // the 11 geometric parameters: unit tangents
+#pragma unroll 1
+    for (int k = 0; k < 11; ++k) {
+      float mud[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+      float od = 0.f;
+      if (k < 3) mud[k] = 1.f;
+      else if (k < 6) ds[k - 3] = 1.f;
+      else if (k < 10) dq[k - 6] = 1.f;
+      else od = G.o * (1.f - G.o);
+      float Sd[6];
+      sigma_tangent(G, ds, dq, Sd);
+      float yv[9];
+      geo_tangent(VG, cam, mud, Sd, yv);
+      yv[5] = od;
+      if (k < 3) {
+        const float md = VG.dir[k];
+        float dd[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dd[i] = ((i == k ? 1.f : 0.f) - VG.dir[i] * md) * VG.inv_dlen;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+          yv[6 + ch] = live[ch] ? grad[ch][0] * dd[0] + grad[ch][1] * dd[1] + grad[ch][2] * dd[2] : 0.f;
+      } else {
+        yv[6] = yv[7] = yv[8] = 0.f;
+      }
+      // v^T Q v with Q = [[Qgg, X], [X^T, D I]]
+      float acc = 0.f;
+      int idx = 0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) {
+          const float q = Q[idx++];
+          acc += (i == j ? 1.f : 2.f) * q * yv[i] * yv[j];
+        }
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc += 2.f * Q[21 + i * 3 + c] * yv[i] * yv[6 + c];
+      acc += D * (yv[6] * yv[6] + yv[7] * yv[7] + yv[8] * yv[8]);
+      d[k] += acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kNP; ++k) dout[k * ld + g] = d[k];
+}
+
+}  // namespace
+
+cudaError_t launch_project(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
+                           SplatRec* rec, uint32_t* ntiles, uint2* rect, uint32_t* depth_key, cudaStream_t st) {
+  const long long n = (long long)N * V;
+  if (n == 0) return cudaSuccess;
+  const int bs = 256;
+  { k_project<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(params, N, ld, cams, V, smooth, rec, ntiles, rect,
+                                                          depth_key); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
+                           const uint8_t* slot_active, const float* p, float* ydot, const float* z_beta,
+                           float* p_out, const PcgScalars* sc, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  { k_tangent<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, slot_active, p, ydot, z_beta,
+                                             p_out, sc); note_launch(); }
+  return cudaGetLastError();
+}
+
+int vjp_blocks(int N) { return (N + 127) / 128; }
+
+cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
+                       const uint32_t* s_start, const uint32_t* s_end, const uint32_t* s_list,
+                       const float* seg_ybar, float scale, float* g, const float* p, const float* M, float lambda,
+                       double* partials, const PcgScalars* sc, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, seg_ybar, scale,
+                                       g, p, M, lambda, partials, sc); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
+                        const uint32_t* s_start, const uint32_t* s_end, const uint32_t* s_list,
+                        const float* seg_q, float* diag, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  { k_diag<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, seg_q, diag); note_launch(); }
+  return cudaGetLastError();
+}
+
+}  // namespace gslm

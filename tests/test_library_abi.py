@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every entry point include/gslm.h declares (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gslm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(gslm_[A-Za-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2409_12892_gb300 import build
+    try:
+        return build.build()
+    except RuntimeError as e:   # no nvcc: cannot check the library here
+        pytest.skip(str(e))
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_functions()
+    for n in ["gslm_build_cache", "gslm_apply_J", "gslm_apply_JT", "gslm_jacobi_diag", "gslm_pcg_solve",
+              "gslm_lm_step", "gslm_render", "gslm_combine_accumulate", "gslm_combine_finish"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    for n in declared_functions():
+        assert re.search(rf"\bT {n}$", out, flags=re.M), n
+
+
+def test_binding_names_match_the_abi(lib_path):
+    from paper_2409_12892_gb300 import gslm
+    assert set(gslm.exported_symbols()) <= set(declared_functions())
+    for n in ["render", "build_cache", "apply_J", "apply_JT", "jacobi_diag", "pcg_solve", "combine_accumulate",
+              "combine_finish", "lm_step"]:
+        assert hasattr(gslm.Context, n)
+
+
+def test_version_and_default_options_without_gpu(lib_path):
+    from paper_2409_12892_gb300 import gslm
+    lib = gslm.load_library(lib_path)
+    assert lib.gslm_version().startswith(b"gslm")
+    opt = gslm.Options()
+    lib.gslm_default_options(ctypes.byref(opt))
+    assert opt.n_iters == 8 and abs(opt.break_rel2 - 0.01) < 1e-9 and opt.cache_fmt == 0
+    assert abs(opt.lambda_min - 1e-4) < 1e-10 and abs(opt.lambda_max - 1e4) < 1e-3
