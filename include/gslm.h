@@ -172,9 +172,11 @@ gslm_status gslm_apply_JT(gslm_ctx* ctx, const gslm_cache* cache, const float* u
 /* M = diag(J^T J) [Eq. diag-jtj]. diag: [59][ld]. */
 gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* cache, float* diag);
 
-/* Algorithm 1 [Sec. 3.3]: x ~ (J^T J + lambda M)^-1 b with M = diag (given),
- * preconditioner M^-1 = 1/M (0 where M <= 1e-30) or, if precond is non-NULL,
- * the given positive diagonal D ([59][ld]) in its place. x: [59][ld] output.
+/* Algorithm 1 [Sec. 3.3]: x ~ (J^T J + lambda M)^-1 b with M = diag(J^T J) as
+ * given, clamped to [1e-6, 1e32] (the LM diagonal bounds of Ceres, whose LM the
+ * paper follows) both in the damping term and in the Jacobi preconditioner
+ * M^-1 = 1/M; if precond is non-NULL, the given positive diagonal D ([59][ld])
+ * replaces M^-1. x: [59][ld] output.
  * stats: host pointer or NULL (NULL: no synchronisation). Returns
  * GSLM_W_PCG_BREAKDOWN if the loop stopped on p^T g <= 0. */
 gslm_status gslm_pcg_solve(gslm_ctx* ctx, const gslm_cache* cache, const float* b,

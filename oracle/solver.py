@@ -9,7 +9,11 @@
 
 Readings where the paper is silent (stated again in the design doc):
   - the loop "for i = 0 to n_iters" runs n_iters times after the initial product;
-  - M^-1_k = 0 where diag_k <= 1e-30 (parameters the subset never sees);
+  - the LM update follows Ceres (Sec. 3.2), whose Levenberg-Marquardt strategy
+    clamps the diagonal diag(J^T J) to [1e-6, 1e32] before using it; the
+    clamped diagonal is used as the Jacobi preconditioner and in the damping
+    term lambda * M, while the subset weights of Eq. combine-pcg keep the raw
+    diagonal (they come from the derivation in Sec. B);
   - the break test compares ||r||^2 with break_rel2 * ||b||^2 (0 disables it);
   - a step is accepted when rho > 1e-5 and the predicted decrease is positive;
     lambda is multiplied by 1 - (2 rho - 1)^3 (accepted) or 2 (rejected), then
@@ -33,19 +37,26 @@ class PCGStats:
     history: list = field(default_factory=list)   # ||r||^2 after each iteration
 
 
+DIAG_MIN, DIAG_MAX = 1e-6, 1e32
+
+
+def clamp_diag(diag: np.ndarray) -> np.ndarray:
+    """diag(J^T J) clamped to [DIAG_MIN, DIAG_MAX] (Ceres' LM diagonal bounds)."""
+    return np.clip(diag, DIAG_MIN, DIAG_MAX)
+
+
 def jacobi_inverse(diag: np.ndarray) -> np.ndarray:
-    return np.where(diag > 1e-30, 1.0 / np.where(diag > 1e-30, diag, 1.0), 0.0)
+    """M^-1 of Algorithm 1 from the clamped diagonal."""
+    return 1.0 / clamp_diag(diag)
 
 
 def pcg(apply_JTJ, b: np.ndarray, M: np.ndarray, lam: float, n_iters: int = 8,
-        break_rel2: float = 0.0, Minv: np.ndarray | None = None, x_star=None):
-    """Algorithm 1. apply_JTJ(v) returns J^T J v. Returns (x, stats).
-
-    If x_star is given, stats.history also records nothing extra; it is only
-    accepted for symmetry with callers that track errors themselves.
-    """
+        break_rel2: float = 0.0, Minv: np.ndarray | None = None):
+    """Algorithm 1. apply_JTJ(v) returns J^T J v; M is the raw diag(J^T J), clamped
+    here for the preconditioner and the damping. Returns (x, stats)."""
     if Minv is None:
         Minv = jacobi_inverse(M)
+    M = clamp_diag(M)
     st = PCGStats()
     bb = float(np.vdot(b, b))
     x = Minv * b                                   # x0 = M^-1 b

@@ -836,8 +836,15 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   for (int i = 0; i < n_b; ++i) {
     CK(ctx->lm_img.ensure(sizeof(float) * 3 * caches[i]->n_pix, st));
     double ci = 0.0;
-    CKS(gslm_render(ctx, ctx->lm_trial.as<float>(), N, ld, scams[i].data(), (int)scams[i].size(),
-                    ctx->lm_img.as<float>(), stg[i].as<float>(), &ci));
+    const gslm_status rs = gslm_render(ctx, ctx->lm_trial.as<float>(), N, ld, scams[i].data(),
+                                       (int)scams[i].size(), ctx->lm_img.as<float>(), stg[i].as<float>(), &ci);
+    if (rs == GSLM_E_CACHE_OVERFLOW) {
+      // the trial parameters project to more tile keys than a render can hold:
+      // the step is rejected like any step that does not decrease the cost
+      cost1 = INFINITY;
+      break;
+    }
+    CKS(rs);
     cost1 += ci;
   }
   ctx->timer.end(trho);

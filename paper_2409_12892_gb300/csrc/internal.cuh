@@ -23,6 +23,12 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr float kShOffset = 0.5f;
 constexpr int kNP = 59;                     // parameters per Gaussian
+// Bounds applied to diag(J^T J) where it serves as the Jacobi preconditioner and
+// as the LM damping term (the Levenberg-Marquardt diagonal bounds of Ceres, whose
+// LM implementation the paper follows, Sec. 3.2). Subset weights use the raw diagonal.
+constexpr float kDiagMin = 1e-6f;
+constexpr float kDiagMax = 1e32f;
+__host__ __device__ __forceinline__ float clamp_diag(float m) { return fminf(fmaxf(m, kDiagMin), kDiagMax); }
 
 // Camera of one view of a call, with the view's place in the call's tile and
 // pixel index spaces.

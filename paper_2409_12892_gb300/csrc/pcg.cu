@@ -38,8 +38,7 @@ __global__ void k_pcg_init(int N, long long ld, const float* __restrict__ b, con
     if (D != nullptr) {
       mi = D[o];
     } else {
-      const float m = M[o];
-      mi = m > 1e-30f ? 1.f / m : 0.f;
+      mi = 1.f / clamp_diag(M[o]);
     }
     Minv[o] = mi;
     const float bv = b[o];
@@ -59,7 +58,7 @@ __global__ void k_pcg_residual0(int N, long long ld, const float* __restrict__ b
   const long long o = (long long)blockIdx.y * ld + i;
   double rz = 0.0;
   if (i < N) {
-    const float rv = b[o] - (g[o] + lambda * M[o] * x[o]);
+    const float rv = b[o] - (g[o] + lambda * clamp_diag(M[o]) * x[o]);
     const float zv = Minv[o] * rv;
     r[o] = rv;
     z[o] = zv;

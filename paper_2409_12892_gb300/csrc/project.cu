@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(128) k_vjp(
 #pragma unroll
       for (int k = 0; k < kNP; ++k) {
         const float pk = p[k * ld + g];
-        const float gk = scale * out[k] + lambda * Mdiag[k * ld + g] * pk;
+        const float gk = scale * out[k] + lambda * clamp_diag(Mdiag[k * ld + g]) * pk;
         gout[k * ld + g] = gk;
         local += (double)pk * (double)gk;
       }

@@ -272,8 +272,8 @@ def test_pcg_equals_dense_cholesky_solve():
     lam = 1e-3
     x, st = solver.solve_subset(sys_, lam, n_iters=600)
     Jx = J.explicit_J(sys_.lin, J.n_residuals(cams), P.shape[0]).toarray()
-    obs = sys_.M.ravel() > 1e-30
-    A = (Jx.T @ Jx + lam * np.diag(sys_.M.ravel()))[np.ix_(obs, obs)]
+    obs = sys_.M.ravel() > 0.0
+    A = (Jx.T @ Jx + lam * np.diag(solver.clamp_diag(sys_.M.ravel())))[np.ix_(obs, obs)]
     L = np.linalg.cholesky(A)
     ref = np.zeros(P.size)
     ref[obs] = np.linalg.solve(L.T, np.linalg.solve(L, sys_.b.ravel()[obs]))
@@ -287,7 +287,7 @@ def test_pcg_energy_norm_error_decreases():
     sys_ = solver.build_subset(P, cams, tg)
     lam = 1e-2
     Jx = J.explicit_J(sys_.lin, J.n_residuals(cams), P.shape[0]).toarray()
-    A = Jx.T @ Jx + lam * np.diag(sys_.M.ravel())
+    A = Jx.T @ Jx + lam * np.diag(solver.clamp_diag(sys_.M.ravel()))
     xs = np.linalg.lstsq(A, sys_.b.ravel(), rcond=None)[0]
     errs = []
     for n in range(0, 12):
@@ -301,7 +301,7 @@ def test_pcg_energy_norm_error_decreases():
 def test_pcg_first_iteration_by_hand():
     """One iteration of Algorithm 1 written out on a 2x2 SPD system."""
     A0 = np.array([[4.0, 1.0], [1.0, 3.0]])
-    M = np.diag(A0).copy()
+    M = np.diag(A0).copy()          # inside the clamp range, so clamping changes nothing
     b = np.array([1.0, 2.0])
     lam = 0.5
     x, _ = solver.pcg(lambda v: A0 @ v, b, M, lam, n_iters=1)
@@ -316,6 +316,15 @@ def test_pcg_first_iteration_by_hand():
 
 
 # ----------------------------------------------------------------------------- weighted mean
+def test_diag_clamp_bounds_the_jacobi_step():
+    """A barely observed parameter (diag 1e-17) no longer gets x0 = b / diag ~ 1e7."""
+    M = np.array([1e-17, 2.0, 0.0])
+    b = np.array([1e-10, 1.0, 0.0])
+    x, _ = solver.pcg(lambda v: M * v, b, M, 1e-3, n_iters=0)
+    np.testing.assert_allclose(x, [1e-4, 0.5, 0.0])
+    np.testing.assert_allclose(solver.clamp_diag(np.array([1e-9, 5.0, 1e40])), [1e-6, 5.0, 1e32])
+
+
 def test_combine_single_subset_is_identity():
     rng = np.random.default_rng(0)
     d = rng.standard_normal((7, 59))
