@@ -169,6 +169,20 @@ void gslm_cache_free(gslm_cache* cache);
 gslm_status gslm_apply_J(gslm_ctx* ctx, const gslm_cache* cache, const float* p, float* u);
 /* g = J^T u [Eq. apply-jt]. u: [pixels][3]; g: [59][ld]. */
 gslm_status gslm_apply_JT(gslm_ctx* ctx, const gslm_cache* cache, const float* u, float* g);
+/* g = J^T u like gslm_apply_JT, for callers that must not allocate device
+ * memory once running (a service whose memory another allocator reserved up
+ * front, or a thread that may not call cudaMalloc). The paper has no
+ * counterpart. The per-segment partial sums live in one fixed 24 MiB
+ * __device__ array inside the library (held by every GPU that loads it, until
+ * exit) instead of a context buffer; the call allocates nothing.
+ * Limits and rules: caches with more than 2^19 (tile, splat) segments
+ * (gslm_cache_info.segments) are rejected with GSLM_E_INVALID. The first call
+ * on a device looks up the array's device address for that device, so make it
+ * with that device current and before any stream capture. All calls share the
+ * array: calls whose work overlaps on the GPU (other streams, other contexts)
+ * race; calls on one stream are ordered and need no clearing in between. */
+gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* cache, const float* u, float* g);
+
 /* M = diag(J^T J) [Eq. diag-jtj]. diag: [59][ld]. */
 gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* cache, float* diag);
 

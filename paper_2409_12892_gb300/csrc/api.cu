@@ -429,6 +429,34 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
 
 }  // namespace
 
+namespace gslm {
+
+bool cache_parts(const gslm_cache* c, CacheParts* out) {
+  if (c == nullptr || out == nullptr) return false;
+  out->view = c->view();
+  out->params = c->params;
+  out->N = c->N;
+  out->ld = c->ld;
+  out->cams = c->cams.as<DevCam>();
+  out->V = c->V;
+  out->smooth = c->smooth;
+  return true;
+}
+
+bool context_parts(const gslm_ctx* c, ContextParts* out) {
+  if (c == nullptr || out == nullptr) return false;
+  out->st = c->st;
+  out->group = c->opt.group;
+  out->device = c->device;
+  return true;
+}
+
+void set_context_error(gslm_ctx* c, const char* msg) {
+  if (c != nullptr) c->err = msg;
+}
+
+}  // namespace gslm
+
 extern "C" {
 
 const char* gslm_version(void) { return "gslm 0.1 (sm_103a)"; }

@@ -93,6 +93,25 @@ struct CacheView {
 // Counts kernel launches of this library (reported by gslm_kernel_launches).
 void note_launch();
 
+// Views of a cache and of a context for entry points defined outside api.cu.
+struct CacheParts {
+  CacheView view;
+  const float* params;
+  int N;
+  long long ld;
+  const DevCam* cams;
+  int V;
+  int smooth;
+};
+struct ContextParts {
+  cudaStream_t st;
+  int group;
+  int device;
+};
+bool cache_parts(const gslm_cache* c, CacheParts* out);
+bool context_parts(const gslm_ctx* c, ContextParts* out);
+void set_context_error(gslm_ctx* c, const char* msg);
+
 // ----------------------------------------------------------------------------
 // Launchers (each defined in the .cu file that holds the kernel).
 // All return cudaGetLastError() of the launch.

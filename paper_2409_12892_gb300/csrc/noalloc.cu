@@ -1,0 +1,77 @@
+// gslm_apply_JT_noalloc: J^T u without any device allocation.
+//
+// The paper has no counterpart; this entry point exists for callers that must
+// not allocate device memory once they are running, e.g. a service whose
+// device memory is reserved up front by another allocator, or a host thread
+// that may not call cudaMalloc (which can synchronise the device). The normal
+// gslm_apply_JT keeps its per-segment partial sums in a context-owned buffer
+// that grows with cudaMallocAsync; this variant keeps them in the fixed array
+// below instead and calls no allocating routine.
+#include <mutex>
+
+#include "internal.cuh"
+
+// Largest cache (in non-empty tile/splat segments) the variant accepts.
+static constexpr long long kNoAllocMaxSegments = 1ll << 19;
+
+// 2^19 segments x 12 floats = 24 MiB of per-segment J^T u partials. Every GPU
+// that loads the library holds this array until the process exits.
+static __device__ __align__(256) float g_noalloc_seg_ybar[kNoAllocMaxSegments * 12];
+
+namespace {
+constexpr int kMaxDevices = 256;
+std::mutex g_setup_mu;
+void* g_setup_addr[kMaxDevices] = {};   // device address of the array, per device, set up once
+}  // namespace
+
+extern "C" gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* cache, const float* u, float* g) {
+  gslm::CacheParts cp;
+  gslm::ContextParts xp;
+  if (ctx == nullptr || cache == nullptr || u == nullptr || g == nullptr || !gslm::cache_parts(cache, &cp) ||
+      !gslm::context_parts(ctx, &xp)) {
+    gslm::set_context_error(ctx, "apply_JT_noalloc: null argument");
+    return GSLM_E_INVALID;
+  }
+  if (cp.view.n_seg > kNoAllocMaxSegments) {
+    gslm::set_context_error(ctx, "apply_JT_noalloc: the cache has more than 524288 (tile, splat) segments, "
+                                 "the most this allocation-free variant holds; use gslm_apply_JT");
+    return GSLM_E_INVALID;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    gslm::set_context_error(ctx, "apply_JT_noalloc: no usable current CUDA device");
+    return GSLM_E_CUDA;
+  }
+  void* scratch = nullptr;
+  {
+    // Set-up, once per device, with that device current: the array's name is
+    // only a host-side stand-in, its device address has to be looked up.
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (g_setup_addr[dev] == nullptr) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_seg_ybar);
+      if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        gslm::set_context_error(ctx, "apply_JT_noalloc: cudaGetSymbolAddress failed");
+        return GSLM_E_CUDA;
+      }
+      g_setup_addr[dev] = p;
+    }
+    scratch = g_setup_addr[dev];
+  }
+  // Every segment slot read below is written first in this call, so nothing in
+  // the shared array needs clearing.
+  float* seg_ybar = static_cast<float*>(scratch);
+  cudaError_t e = gslm::launch_apply_JT(cp.view, u, seg_ybar, xp.group, xp.st);
+  if (e == cudaSuccess)
+    e = gslm::launch_vjp(cp.params, cp.N, cp.ld, cp.cams, cp.V, cp.smooth, cp.view.slot_seg_start,
+                         cp.view.slot_seg_end, cp.view.slot_seg_list, seg_ybar, 1.f, g, nullptr, nullptr, 0.f,
+                         nullptr, nullptr, xp.st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    gslm::set_context_error(ctx, "apply_JT_noalloc: kernel launch failed");
+    return GSLM_E_CUDA;
+  }
+  return GSLM_OK;
+}
