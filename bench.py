@@ -47,6 +47,9 @@ def parse_args(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--group", type=int, default=32)
+    ap.add_argument("--subsets", type=int, default=0,
+                    help="override: number of image subsets per LM step (profiling-sized cases)")
+    ap.add_argument("--views", type=int, default=0, help="override: views per subset (profiling-sized cases)")
     return ap.parse_args(argv)
 
 
@@ -145,13 +148,24 @@ def load_peaks() -> dict:
 
 
 # ----------------------------------------------------------------------------- workload
-def build_workload(name: str, device):
+def workload(args):
+    """The named workload, with the subset shape optionally overridden."""
+    import dataclasses
+    import synth
+    wl = synth.WORKLOADS[args.workload]
+    if args.subsets or args.views:
+        ns = args.subsets or len(wl.subset_sizes)
+        nv = args.views or wl.subset_sizes[0]
+        wl = dataclasses.replace(wl, subset_sizes=[nv] * ns)
+    return wl
+
+
+def build_workload(wl, device):
     """Scene, cameras and GPU-rendered targets (perturbed copy + pixel noise), resident in HBM."""
     import numpy as np
     import torch
     import synth
     import paper_2409_12892_gb300 as g
-    wl = synth.WORKLOADS[name]
     P = synth.make_gaussians(wl)
     cams = synth.make_cameras(wl)
     pert = g.to_soa(synth.perturbed_copy(wl, P), device=device)
@@ -368,8 +382,7 @@ def run_reference(args):
 
 
 def workload_config(args, form: str) -> dict:
-    import synth
-    wl = synth.WORKLOADS[args.workload]
+    wl = workload(args)
     return {
         "workload": (f"{wl.name}: {wl.n_gaussians} Gaussians ({wl.n_clusters} clusters), {wl.n_cameras} cameras "
                      f"{wl.resolutions[0][0]}x{wl.resolutions[0][1]}, {len(wl.subset_sizes)} subsets x "
@@ -413,7 +426,8 @@ def run_ours(args):
     barrier(dist)
     g.load_library()
     peak = load_peaks()
-    wl, P, cams, targets = build_workload(args.workload, dev)
+    wl = workload(args)
+    wl, P, cams, targets = build_workload(wl, dev)
     N = P.shape[0]
     ld = g.padded_ld(N)
     result = {}
@@ -428,7 +442,8 @@ def run_ours(args):
         ms, stats, launches, clk = run_steps(g, ctx, params, N, cams, targets, wl, args.steps, args.warmup, dist,
                                              clocks)
         ms = max_over_ranks(ms, dist, dev)
-        result[form] = {"ms": ms, "stats": stats, "launches": launches, "clocks": clk, "fmt": fmt}
+        result[form] = {"ms": ms, "stats": stats, "launches": launches, "clocks": clk, "fmt": fmt,
+                        "autotune": ctx.autotune_info()}
         if form == "chosen" and not args.skip_e2e:
             e2e_ms, h2d, d2h = run_e2e(g, ctx, P, N, ld, cams, targets, wl, args.steps, args.warmup, dist)
             result["e2e"] = {"value": max_over_ranks(e2e_ms, dist, dev), "unit": "ms", "h2d_bytes_per_step": h2d,
@@ -452,14 +467,18 @@ def run_ours(args):
         "gpu_launches": ch["launches"] // max(args.steps, 1),
         "gpu_launches_total": ch["launches"],
         "phase_ms": summarize_phases(stats),
+        "autotune": ch["autotune"],
         "lm": {"accepted": [int(s.accepted) for s in stats], "rho": [s.rho for s in stats],
                "cost": [s.cost for s in stats], "cost_new": [s.cost_new for s in stats],
                "predicted": [s.predicted for s in stats], "pcg_iters": [s.pcg_iters for s in stats],
-               "cache_entries": E_step, "cache_gb": statistics.mean(s.cache_bytes for s in stats) / 1e9},
+               "cache_entries": E_step, "cache_gb": statistics.mean(s.cache_bytes for s in stats) / 1e9,
+               "cache_segments": statistics.mean(s.cache_segments for s in stats),
+               "active_splats": statistics.mean(s.active_splats for s in stats)},
     }
     if "plain" in result:
         pl = result["plain"]
         line["plain_fp32"] = {"ms_per_step": pl["ms"], "roofline": pair_roofline(pl["stats"], peak),
+                              "autotune": pl["autotune"],
                               "phase_ms": summarize_phases(pl["stats"]),
                               "cache_gb": statistics.mean(s.cache_bytes for s in pl["stats"]) / 1e9}
         line["speedup_vs_plain"] = pl["ms"] / ch["ms"]

@@ -80,9 +80,11 @@ typedef struct {
   float lambda_max;
   int32_t smooth;      /* test mode: no alpha clamp/skip, no T stop, no SH clamp, no tile culling */
   size_t mem_budget;   /* bytes a cache may take; 0 = no limit */
-  int32_t group;       /* lanes per cache segment in the apply kernels (0 = default) */
+  int32_t group;       /* reserved: lanes per cache segment in the apply kernels (0 or 32) */
   int32_t profile;     /* 1: gslm_lm_step records CUDA events per phase (ms_phase in its stats) */
-  int32_t reserved[6];
+  int32_t autotune;    /* 1 (default): on first use per cache format, time every apply kernel
+                          variant once on the real cache and keep the fastest; 0: fixed variant */
+  int32_t reserved[5];
 } gslm_options;
 
 typedef struct gslm_ctx gslm_ctx;
@@ -133,6 +135,8 @@ typedef struct {
    * payload bytes, P pixels, N Gaussians and S active splats:
    * 2 E (B_e + 1) + 24 P + 472 N + 192 S. */
   double pair_bytes;
+  int64_t cache_segments; /* non-empty (tile, splat) segments, summed over subsets */
+  int64_t active_splats;  /* splats with at least one cache entry, summed over subsets */
 } gslm_lm_stats;
 
 /* Default options: FP32 cache, 8 iterations, break 0.01, lambda in [1e-4, 1e4]. */
@@ -222,6 +226,10 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld,
 const char* gslm_version(void);
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t gslm_kernel_launches(void);
+/* Kernel variants the autotuner chose on this context: out[0..2] apply_J and
+ * out[3..5] apply_JT for the FP32, BF16 and FP16S caches (-1 = not tuned yet);
+ * ms[0..5] (may be NULL) the time of the chosen variant when it was tuned. */
+gslm_status gslm_autotune_info(const gslm_ctx* ctx, int32_t out[6], float ms[6]);
 
 #ifdef __cplusplus
 }

@@ -118,6 +118,10 @@ struct gslm_ctx {
   int device = 0;
   std::string err;
   PhaseTimer timer;
+  int var_J[3] = {-1, -1, -1};      // autotuned apply kernel variants per cache format
+  int var_JT[3] = {-1, -1, -1};
+  float ms_J[3] = {0.f, 0.f, 0.f};
+  float ms_JT[3] = {0.f, 0.f, 0.f};
   // scratch reused across calls
   Buf ydot, seg_ybar, seg_q, u, partials, scalars, reduce_out;
   Buf r, z, p, g, minv;
@@ -137,8 +141,8 @@ struct gslm_cache {
   long long n_vis = 0, n_keys = 0, n_seg = 0, n_entries = 0, n_active = 0;
   double cost = 0.0;
   std::vector<DevCam> hcams;
-  Buf cams, rec, slot_active, tile_seg_off, seg_entry_off, seg_slot, payload, seg_scale, pixoff;
-  Buf slot_seg_start, slot_seg_end, slot_seg_list, F, own_params;
+  Buf cams, rec, slot_active, tile_seg_off, seg_entry_off, seg_slot, seg_rec, payload, seg_scale, pixoff;
+  Buf slot_seg_start, slot_seg_end, slot_seg_list, F, own_params, vmask;
 
   CacheView view() const {
     CacheView cv;
@@ -152,6 +156,7 @@ struct gslm_cache {
     cv.tile_seg_off = tile_seg_off.as<uint32_t>();
     cv.seg_entry_off = seg_entry_off.as<unsigned long long>();
     cv.seg_slot = seg_slot.as<uint32_t>();
+    cv.seg_rec = seg_rec.as<SegRec>();
     cv.payload = payload.p;
     cv.seg_scale = seg_scale.as<float>();
     cv.pixoff = pixoff.as<uint8_t>();
@@ -159,6 +164,7 @@ struct gslm_cache {
     cv.slot_seg_end = slot_seg_end.as<uint32_t>();
     cv.slot_seg_list = slot_seg_list.as<uint32_t>();
     cv.slot_active = slot_active.as<uint8_t>();
+    cv.vmask = vmask.as<unsigned long long>();
     cv.n_seg = n_seg;
     cv.n_entries = n_entries;
     cv.fmt = fmt;
@@ -167,8 +173,9 @@ struct gslm_cache {
   }
   size_t device_bytes() const {
     return cams.bytes + rec.bytes + slot_active.bytes + tile_seg_off.bytes + seg_entry_off.bytes + seg_slot.bytes +
+           seg_rec.bytes +
            payload.bytes + seg_scale.bytes + pixoff.bytes + slot_seg_start.bytes + slot_seg_end.bytes +
-           slot_seg_list.bytes + F.bytes + own_params.bytes;
+           slot_seg_list.bytes + F.bytes + own_params.bytes + vmask.bytes;
   }
 };
 
@@ -346,6 +353,46 @@ gslm_status reduce_to_host(gslm_ctx* ctx, const double* partials, int n, double*
   return GSLM_OK;
 }
 
+constexpr int kDefaultVariant = 2;
+
+// Autotuner: times every kernel variant once on the caller's real inputs (all
+// variants compute the same result, so the last one run leaves valid outputs)
+// and returns the fastest. Runs synchronously, once per context and cache format.
+template <class F>
+gslm_status tune_variant(gslm_ctx* ctx, F&& launch, int* chosen, float* chosen_ms) {
+  cudaStream_t st = ctx->st;
+  const int n = apply_variants();
+  std::vector<cudaEvent_t> ev(n + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  struct Ev {
+    std::vector<cudaEvent_t>& v;
+    ~Ev() {
+      for (auto e : v) cudaEventDestroy(e);
+    }
+  } evg{ev};
+  CK(cudaEventRecord(ev[0], st));
+  for (int v = 0; v < n; ++v) {
+    CK(launch(v));
+    CK(cudaEventRecord(ev[v + 1], st));
+  }
+  CK(cudaEventSynchronize(ev[n]));
+  int best = kDefaultVariant;
+  float best_ms = 1e30f;
+  for (int v = 0; v < n; ++v) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ev[v], ev[v + 1]));
+    if (t < best_ms) {
+      best_ms = t;
+      best = v;
+    }
+  }
+  // run the chosen variant last so that its result is the one left behind
+  CK(launch(best));
+  *chosen = best;
+  *chosen_ms = best_ms;
+  return GSLM_OK;
+}
+
 // J p through the cache: per-Gaussian tangent, then the tile kernel.
 gslm_status do_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float* u, const float* z_beta,
                        float* p_out, const PcgScalars* sc, const float* Fadd, double* sq_partials) {
@@ -353,13 +400,21 @@ gslm_status do_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float
   const long long S = (long long)c->N * c->V;
   CK(ctx->ydot.ensure(sizeof(float) * 12 * std::max<long long>(S, 1), st));
   bool t = ctx->timer.begin(PH_TANGENT);
-  CK(launch_tangent(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_active.as<uint8_t>(), p,
+  CK(launch_tangent(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_active.as<uint8_t>(),
+                    c->vmask.as<unsigned long long>(), p,
                     ctx->ydot.as<float>(), z_beta, p_out, sc, st));
   CacheView cv = c->view();
   cv.skip = sc != nullptr ? &sc->done : nullptr;
   ctx->timer.end(t);
   t = ctx->timer.begin(PH_APPLY_J);
-  CK(launch_apply_J(cv, ctx->ydot.as<float>(), Fadd, u, sq_partials, ctx->opt.group, st));
+  int& var = ctx->var_J[c->fmt];
+  if (var < 0 && ctx->opt.autotune) {
+    const float* yd = ctx->ydot.as<float>();
+    CKS(tune_variant(ctx, [&](int v) { return launch_apply_J(cv, yd, Fadd, u, sq_partials, v, st); }, &var,
+                     &ctx->ms_J[c->fmt]));
+  } else {
+    CK(launch_apply_J(cv, ctx->ydot.as<float>(), Fadd, u, sq_partials, var < 0 ? kDefaultVariant : var, st));
+  }
   ctx->timer.end(t);
   return GSLM_OK;
 }
@@ -371,11 +426,18 @@ gslm_status do_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, floa
   CacheView cv = c->view();
   cv.skip = sc != nullptr ? &sc->done : nullptr;
   bool t = ctx->timer.begin(PH_APPLY_JT);
-  CK(launch_apply_JT(cv, u, ctx->seg_ybar.as<float>(), ctx->opt.group, st));
+  int& var = ctx->var_JT[c->fmt];
+  float* sy = ctx->seg_ybar.as<float>();
+  if (var < 0 && ctx->opt.autotune) {
+    CKS(tune_variant(ctx, [&](int v) { return launch_apply_JT(cv, u, sy, v, st); }, &var, &ctx->ms_JT[c->fmt]));
+  } else {
+    CK(launch_apply_JT(cv, u, sy, var < 0 ? kDefaultVariant : var, st));
+  }
   ctx->timer.end(t);
   t = ctx->timer.begin(PH_VJP);
   CK(launch_vjp(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
-                c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), ctx->seg_ybar.as<float>(), scale, g,
+                c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), c->vmask.as<unsigned long long>(),
+                ctx->seg_ybar.as<float>(), scale, g,
                 p, M, lambda, partials, sc, st));
   ctx->timer.end(t);
   return GSLM_OK;
@@ -443,10 +505,10 @@ bool cache_parts(const gslm_cache* c, CacheParts* out) {
   return true;
 }
 
-bool context_parts(const gslm_ctx* c, ContextParts* out) {
-  if (c == nullptr || out == nullptr) return false;
+bool context_parts(const gslm_ctx* c, int cache_fmt, ContextParts* out) {
+  if (c == nullptr || out == nullptr || cache_fmt < 0 || cache_fmt > 2) return false;
   out->st = c->st;
-  out->group = c->opt.group;
+  out->variant_JT = c->var_JT[cache_fmt] >= 0 ? c->var_JT[cache_fmt] : kDefaultVariant;
   out->device = c->device;
   return true;
 }
@@ -463,6 +525,19 @@ const char* gslm_version(void) { return "gslm 0.1 (sm_103a)"; }
 
 int64_t gslm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+gslm_status gslm_autotune_info(const gslm_ctx* ctx, int32_t out[6], float ms[6]) {
+  if (ctx == nullptr || out == nullptr) return GSLM_E_INVALID;
+  for (int f = 0; f < 3; ++f) {
+    out[f] = ctx->var_J[f];
+    out[3 + f] = ctx->var_JT[f];
+    if (ms != nullptr) {
+      ms[f] = ctx->ms_J[f];
+      ms[3 + f] = ctx->ms_JT[f];
+    }
+  }
+  return GSLM_OK;
+}
+
 void gslm_default_options(gslm_options* o) {
   if (o == nullptr) return;
   std::memset(o, 0, sizeof(*o));
@@ -474,6 +549,8 @@ void gslm_default_options(gslm_options* o) {
   o->smooth = 0;
   o->mem_budget = 0;
   o->group = 32;
+  o->profile = 0;
+  o->autotune = 1;
 }
 
 static gslm_status validate_opts(const gslm_options* o) {
@@ -596,7 +673,7 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
   CKS(reduce_to_host(ctx, cost_part.as<double>(), n_tiles, &c->cost));
   c->n_entries = (long long)E;
   c->n_seg = nseg;
-  const size_t need = E * (payload_bytes(c->fmt) + 1) + (size_t)nseg * (8 + 4 + 4 + 4 * (c->fmt == 2)) +
+  const size_t need = E * (payload_bytes(c->fmt) + 1) + (size_t)nseg * (8 + 4 + 4 + 48 + 4 * (c->fmt == 2)) +
                       (size_t)S * (sizeof(SplatRec) + 1 + 8);
   if (ctx->opt.mem_budget != 0 && need > ctx->opt.mem_budget) {
     char msg[160];
@@ -609,6 +686,7 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
   CK(c->pixoff.alloc(std::max<unsigned long long>(E, 1), st));
   CK(c->seg_entry_off.alloc(sizeof(unsigned long long) * (ns + 1), st));
   CK(c->seg_slot.alloc(sizeof(uint32_t) * ns, st));
+  CK(c->seg_rec.alloc(sizeof(SegRec) * ns, st));
   if (c->fmt == GSLM_CACHE_FP16S) CK(c->seg_scale.alloc(sizeof(float) * ns, st));
   CK(c->slot_active.alloc(std::max<long long>(S, 1), st));
   CK(cudaMemsetAsync(c->slot_active.p, 0, std::max<long long>(S, 1), st));
@@ -620,7 +698,7 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
                          tile_entry_off.as<unsigned long long>(), c->tile_seg_off.as<uint32_t>(), c->fmt,
                          c->payload.p, c->seg_scale.as<float>(), c->pixoff.as<uint8_t>(),
                          c->seg_entry_off.as<unsigned long long>(), c->seg_slot.as<uint32_t>(),
-                         c->slot_active.as<uint8_t>(), errflag.as<int>(), st));
+                         c->seg_rec.as<SegRec>(), c->slot_active.as<uint8_t>(), errflag.as<int>(), st));
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -650,6 +728,10 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
     CK(launch_ranges(sk, nseg, c->slot_seg_start.as<uint32_t>(), c->slot_seg_end.as<uint32_t>(), st));
     CK(c->slot_seg_list.alloc(sizeof(uint32_t) * ns, st));
     CK(cudaMemcpyAsync(c->slot_seg_list.p, sv, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
+  }
+  if (V <= 64) {
+    CK(c->vmask.alloc(sizeof(unsigned long long) * (size_t)N, st));
+    CK(launch_view_mask(c->slot_active.as<uint8_t>(), (int)N, V, c->vmask.as<unsigned long long>(), st));
   }
   {
     Buf cnt;
@@ -711,7 +793,8 @@ gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* c, float* diag) {
   CK(ctx->seg_q.ensure(sizeof(float) * 40 * std::max<long long>(c->n_seg, 1), st));
   CK(launch_diag_entries(c->view(), ctx->seg_q.as<float>(), st));
   CK(launch_diag(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
-                 c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), ctx->seg_q.as<float>(), diag, st));
+                 c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), c->vmask.as<unsigned long long>(),
+                 ctx->seg_q.as<float>(), diag, st));
   return GSLM_OK;
 }
 
@@ -793,6 +876,7 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   std::vector<Buf> stg(n_b);
   double cost0 = 0.0, pair_bytes = 0.0;
   int pcg_iters = 0, n_pairs = 0;
+  long long segs = 0, actives = 0;
   ctx->timer.on = ctx->opt.profile != 0;
   ctx->timer.st = st;
   struct TimerOff {
@@ -827,6 +911,8 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     ctx->timer.end(t);
     cost0 += ci;
     entries += caches[i]->n_entries;
+    segs += caches[i]->n_seg;
+    actives += caches[i]->n_active;
     bytes += (long long)caches[i]->device_bytes();
     t = ctx->timer.begin(PH_DIAG);
     CKS(gslm_jacobi_diag(ctx, caches[i], ctx->lm_M.as<float>()));
@@ -908,6 +994,8 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     stats->n_pairs = n_pairs;
     stats->pad = 0;
     stats->pair_bytes = pair_bytes;
+    stats->cache_segments = segs;
+    stats->active_splats = actives;
   } else {
     double dummy[8] = {0};
     ctx->timer.collect(dummy, 8);

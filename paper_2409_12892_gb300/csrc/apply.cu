@@ -60,51 +60,174 @@ __device__ __forceinline__ unsigned group_mask() {
   return ((1u << G) - 1u) << (lane & ~(G - 1));
 }
 
-template <int G, int kFmt>
-__global__ void __launch_bounds__(kTilePix) k_apply_J(CacheView cv, const float* __restrict__ ydot,
-                                                      const float* __restrict__ Fadd, float* __restrict__ u,
-                                                      double* __restrict__ sq_partials) {
-  __shared__ float su[3 * kTilePix];
-  __shared__ double dred[kTilePix / 32];
+// ---------------------------------------------------------------------------
+// Work distribution of both tile kernels: the warps of a tile's CTA take the
+// tile's segments one at a time from a shared counter (long and short segments
+// balance), read a segment's 48-byte record with one broadcast load, and stream
+// its entries with every lane keeping U loads in flight. The record (and for
+// J p the splat tangent) of the segment after next is fetched while the
+// current one streams, so the record latency stays off the critical path.
+constexpr int kWarps = kTilePix / 32;
+
+// Shared-memory index of pixel p of colour plane ch, padded by one word every
+// 32 pixels (two tile rows) to spread a segment's pixels over more banks.
+__device__ __forceinline__ int upad(int ch, int p) { return ch * (kTilePix + kTilePix / 32) + p + (p >> 5); }
+
+__device__ __forceinline__ SegRec load_rec(const SegRec* __restrict__ r) {
+  const uint4* q = reinterpret_cast<const uint4*>(r);
+  const uint4 a = q[0], b = q[1], c = q[2];
+  SegRec s;
+  s.e0 = ((unsigned long long)a.y << 32) | a.x;
+  s.e1 = ((unsigned long long)a.w << 32) | a.z;
+  s.slot = b.x;
+  s.mx = __uint_as_float(b.y);
+  s.my = __uint_as_float(b.z);
+  s.A = __uint_as_float(b.w);
+  s.B = __uint_as_float(c.x);
+  s.C = __uint_as_float(c.y);
+  s.io = __uint_as_float(c.z);
+  s.scale = __uint_as_float(c.w);
+  return s;
+}
+
+__device__ __forceinline__ uint32_t grab(unsigned int* counter) {
+  uint32_t k = 0;
+  if ((threadIdx.x & 31) == 0) k = atomicAdd(counter, 1u);
+  return __shfl_sync(kFull, k, 0);
+}
+
+// Raw payload as loaded (float4 for FP32, two 32-bit words for the 16-bit
+// formats), decoded only when used so that U loads stay cheap in registers.
+template <int kFmt>
+struct Raw {
+  using T = uint2;
+};
+template <>
+struct Raw<GSLM_CACHE_FP32> {
+  using T = float4;
+};
+
+template <int kFmt>
+__device__ __forceinline__ typename Raw<kFmt>::T load_raw(const void* __restrict__ payload, unsigned long long e) {
+  return __ldcs(reinterpret_cast<const typename Raw<kFmt>::T*>(payload) + e);
+}
+
+template <int kFmt>
+__device__ __forceinline__ float4 decode(const typename Raw<kFmt>::T& r, float scale) {
+  if constexpr (kFmt == GSLM_CACHE_FP32) {
+    return r;
+  } else if constexpr (kFmt == GSLM_CACHE_BF16) {
+    const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+    const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+  } else {
+    const float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    return make_float4(fa.x * scale, fa.y * scale, fb.x * scale, fb.y * scale);
+  }
+}
+
+struct Tangent {
+  float dmx, dmy, dA, dB, dC, od, dr, dg, db;
+};
+
+__device__ __forceinline__ Tangent load_tangent(const float* __restrict__ ydot, uint32_t slot, float io) {
+  const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)slot * 12);
+  const float4 y0 = yd[0], y1 = yd[1], y2 = yd[2];
+  Tangent t;
+  t.dmx = y0.x;
+  t.dmy = y0.y;
+  t.dA = y0.z;
+  t.dB = y0.w;
+  t.dC = y1.x;
+  t.od = y1.y * io;
+  t.dr = y1.z;
+  t.dg = y1.w;
+  t.db = y2.x;
+  return t;
+}
+
+template <int kFmt, int U, int kMinBlocks>
+__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, const float* __restrict__ ydot,
+                                                                  const float* __restrict__ Fadd,
+                                                                  float* __restrict__ u,
+                                                                  double* __restrict__ sq_partials) {
+  __shared__ float su[3 * (kTilePix + kTilePix / 32)];
+  __shared__ float2 sxy[kTilePix];   // tile-local pixel coordinates (x, y) of pixel p
+  __shared__ double dred[kWarps];
+  __shared__ unsigned int next_seg;
   if (cv.skip != nullptr && *cv.skip) return;
+  sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
   const int tile = blockIdx.x;
   const int v = find_view(cv.cams, cv.V, tile);
   const DevCam& cam = cv.cams[v];
   const int lt = tile - cam.tile_off;
   const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
-  const float ox = tx * kTile + 0.5f, oy = ty * kTile + 0.5f;
-  for (int i = threadIdx.x; i < 3 * kTilePix; i += kTilePix) su[i] = 0.f;
+  for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
+  if (threadIdx.x == 0) next_seg = 0;
   __syncthreads();
-  const uint32_t g0 = cv.tile_seg_off[tile], g1 = cv.tile_seg_off[tile + 1];
-  const int gid = threadIdx.x / G, gl = threadIdx.x % G;
-  constexpr int kGroups = kTilePix / G;
-  for (uint32_t seg = g0 + gid; seg < g1; seg += kGroups) {
-    const uint32_t slot = cv.seg_slot[seg];
-    const unsigned long long e0 = cv.seg_entry_off[seg], e1 = cv.seg_entry_off[seg + 1];
-    const float4 ra = cv.rec[slot].a;
-    const float2 rb = *reinterpret_cast<const float2*>(&cv.rec[slot].b);
-    const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)slot * 12);
-    const float4 y0 = yd[0], y1 = yd[1], y2 = yd[2];
-    const float mx = ra.x - ox, my = ra.y - oy, A = ra.z, B = ra.w, C = rb.x;
-    const float od = y1.y / rb.y;
-    const float scale = kFmt == GSLM_CACHE_FP16S ? cv.seg_scale[seg] : 1.f;
-    for (unsigned long long e = e0 + gl; e < e1; e += G) {
-      const float4 pe = load_entry<kFmt>(cv.payload, e, scale);
-      const int p = cv.pixoff[e];
-      const float dx = (float)(p & (kTile - 1)) - mx, dy = (float)(p / kTile) - my;
-      const float q = (A * dx + B * dy) * y0.x + (B * dx + C * dy) * y0.y -
-                      0.5f * dx * dx * y0.z - dx * dy * y0.w - 0.5f * dy * dy * y1.x + od;
-      atomicAdd(&su[p], pe.x * y1.z + pe.y * q);
-      atomicAdd(&su[kTilePix + p], pe.x * y1.w + pe.z * q);
-      atomicAdd(&su[2 * kTilePix + p], pe.x * y2.x + pe.w * q);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t g0 = cv.tile_seg_off[tile];
+  const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
+  uint32_t k = grab(&next_seg);
+  SegRec cur, nxt;
+  Tangent t;
+  if (k < n) {
+    cur = load_rec(cv.seg_rec + g0 + k);
+    t = load_tangent(ydot, cur.slot, cur.io);
+  }
+  uint32_t kn = grab(&next_seg);
+  if (kn < n) nxt = load_rec(cv.seg_rec + g0 + kn);
+  while (k < n) {
+    // prefetch: the record after next, and the next segment's tangent
+    const uint32_t kn2 = grab(&next_seg);
+    SegRec nxt2;
+    if (kn2 < n) nxt2 = load_rec(cv.seg_rec + g0 + kn2);
+    Tangent tn;
+    if (kn < n) tn = load_tangent(ydot, nxt.slot, nxt.io);
+    {
+      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + cur.e0;
+      const uint8_t* po = cv.pixoff + cur.e0;
+      const uint32_t len = (uint32_t)(cur.e1 - cur.e0);
+      for (uint32_t i = lane; i < len; i += 32 * U) {
+        typename Raw<kFmt>::T raw[U];
+        int pp[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          if (i + 32 * j < len) {
+            raw[j] = __ldcs(pl + i + 32 * j);
+            pp[j] = po[i + 32 * j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          if (i + 32 * j < len) {
+            const int p = pp[j];
+            const float4 pe = decode<kFmt>(raw[j], cur.scale);
+            const float2 c = sxy[p];
+            const float dx = c.x - cur.mx, dy = c.y - cur.my;
+            const float q = (cur.A * dx + cur.B * dy) * t.dmx + (cur.B * dx + cur.C * dy) * t.dmy -
+                            0.5f * dx * dx * t.dA - dx * dy * t.dB - 0.5f * dy * dy * t.dC + t.od;
+            atomicAdd(&su[upad(0, p)], pe.x * t.dr + pe.y * q);
+            atomicAdd(&su[upad(1, p)], pe.x * t.dg + pe.z * q);
+            atomicAdd(&su[upad(2, p)], pe.x * t.db + pe.w * q);
+          }
+        }
+      }
     }
+    k = kn;
+    cur = nxt;
+    t = tn;
+    kn = kn2;
+    nxt = nxt2;
   }
   __syncthreads();
   const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
   double local = 0.0;
   if (x < cam.W && y < cam.H) {
     const long long pix = cam.pix_off + (long long)y * cam.W + x;
-    const float u0 = su[threadIdx.x], u1 = su[kTilePix + threadIdx.x], u2 = su[2 * kTilePix + threadIdx.x];
+    const int p = threadIdx.x;
+    const float u0 = su[upad(0, p)], u1 = su[upad(1, p)], u2 = su[upad(2, p)];
     if (u != nullptr) {
       u[pix * 3 + 0] = u0;
       u[pix * 3 + 1] = u1;
@@ -118,89 +241,135 @@ __global__ void __launch_bounds__(kTilePix) k_apply_J(CacheView cv, const float*
   }
   if (sq_partials != nullptr) {
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
-    if ((threadIdx.x & 31) == 0) dred[threadIdx.x >> 5] = local;
+    if (lane == 0) dred[warp] = local;
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int w = 0; w < kTilePix / 32; ++w) s += dred[w];
+      for (int w = 0; w < kWarps; ++w) s += dred[w];
       sq_partials[tile] = s;
     }
   }
 }
 
-template <int G, int kFmt>
-__global__ void __launch_bounds__(kTilePix) k_apply_JT(CacheView cv, const float* __restrict__ u,
-                                                       float* __restrict__ seg_ybar) {
-  __shared__ float su[3 * kTilePix];
+// One step of a recursive-halving reduction: lanes whose `upper` bit is set keep
+// the upper half of their N values, the others the lower half; each kept value
+// gains the partner lane's matching value.
+template <int N>
+__device__ __forceinline__ void halve(float (&v)[16], bool upper, int o) {
+#pragma unroll
+  for (int k = 0; k < N / 2; ++k) {
+    const float send = upper ? v[k] : v[k + N / 2];
+    const float keep = upper ? v[k + N / 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(kFull, send, o);
+  }
+}
+
+// Sums 16 values over the 32 lanes of the warp (16 shuffles instead of the 80
+// of a butterfly per value). Lanes 0, 2, ..., 30 then hold the sum of value
+// index lane / 2 in v[0] (odd lanes hold the same sums).
+__device__ __forceinline__ void warp_sum16(float (&v)[16], int lane) {
+  halve<16>(v, lane & 16, 16);
+  halve<8>(v, lane & 8, 8);
+  halve<4>(v, lane & 4, 4);
+  halve<2>(v, lane & 2, 2);
+  v[0] += __shfl_xor_sync(kFull, v[0], 1);
+}
+
+template <int kFmt, int U, int kMinBlocks>
+__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv, const float* __restrict__ u,
+                                                                   float* __restrict__ seg_ybar) {
+  __shared__ float4 su4[kTilePix];
+  __shared__ float2 sxy[kTilePix];
+  __shared__ unsigned int next_seg;
   if (cv.skip != nullptr && *cv.skip) return;
   const int tile = blockIdx.x;
-  const uint32_t g0 = cv.tile_seg_off[tile], g1 = cv.tile_seg_off[tile + 1];
-  if (g0 == g1) return;
+  const uint32_t g0 = cv.tile_seg_off[tile];
+  const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
+  if (n == 0) return;
   const int v = find_view(cv.cams, cv.V, tile);
   const DevCam& cam = cv.cams[v];
   const int lt = tile - cam.tile_off;
   const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
-  const float ox = tx * kTile + 0.5f, oy = ty * kTile + 0.5f;
   {
     const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
-    float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
     if (x < cam.W && y < cam.H) {
       const long long pix = cam.pix_off + (long long)y * cam.W + x;
-      u0 = u[pix * 3 + 0];
-      u1 = u[pix * 3 + 1];
-      u2 = u[pix * 3 + 2];
+      uv = make_float4(u[pix * 3 + 0], u[pix * 3 + 1], u[pix * 3 + 2], 0.f);
     }
-    su[threadIdx.x] = u0;
-    su[kTilePix + threadIdx.x] = u1;
-    su[2 * kTilePix + threadIdx.x] = u2;
+    su4[threadIdx.x] = uv;
+    sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
   }
+  if (threadIdx.x == 0) next_seg = 0;
   __syncthreads();
-  const int gid = threadIdx.x / G, gl = threadIdx.x % G;
-  constexpr int kGroups = kTilePix / G;
-  const unsigned gm = group_mask<G>();
-  for (uint32_t seg = g0 + gid; seg < g1; seg += kGroups) {
-    const uint32_t slot = cv.seg_slot[seg];
-    const unsigned long long e0 = cv.seg_entry_off[seg], e1 = cv.seg_entry_off[seg + 1];
-    const float4 ra = cv.rec[slot].a;
-    const float2 rb = *reinterpret_cast<const float2*>(&cv.rec[slot].b);
-    const float mx = ra.x - ox, my = ra.y - oy, A = ra.z, B = ra.w, C = rb.x;
-    const float scale = kFmt == GSLM_CACHE_FP16S ? cv.seg_scale[seg] : 1.f;
-    // sums of s, s*dx, s*dy, s*dx^2, s*dx*dy, s*dy^2 and w*u_ch
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, r0 = 0.f, r1 = 0.f, r2 = 0.f;
-    for (unsigned long long e = e0 + gl; e < e1; e += G) {
-      const float4 pe = load_entry<kFmt>(cv.payload, e, scale);
-      const int p = cv.pixoff[e];
-      const float dx = (float)(p & (kTile - 1)) - mx, dy = (float)(p / kTile) - my;
-      const float u0 = su[p], u1 = su[kTilePix + p], u2 = su[2 * kTilePix + p];
-      const float s = pe.y * u0 + pe.z * u1 + pe.w * u2;
-      a0 += s;
-      a1 += s * dx;
-      a2 += s * dy;
-      a3 += s * dx * dx;
-      a4 += s * dx * dy;
-      a5 += s * dy * dy;
-      r0 += pe.x * u0;
-      r1 += pe.x * u1;
-      r2 += pe.x * u2;
-    }
+  const int lane = threadIdx.x & 31;
+  uint32_t k = grab(&next_seg);
+  SegRec cur;
+  if (k < n) cur = load_rec(cv.seg_rec + g0 + k);
+  while (k < n) {
+    const uint32_t kn = grab(&next_seg);
+    SegRec nxt;
+    if (kn < n) nxt = load_rec(cv.seg_rec + g0 + kn);
+    // moments of s = h . u over the segment's pixels (tile-local offsets from
+    // the splat mean), and sums of w u; the conic is applied once per segment
+    float a[16];
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(gm, a0, o);
-      a1 += __shfl_xor_sync(gm, a1, o);
-      a2 += __shfl_xor_sync(gm, a2, o);
-      a3 += __shfl_xor_sync(gm, a3, o);
-      a4 += __shfl_xor_sync(gm, a4, o);
-      a5 += __shfl_xor_sync(gm, a5, o);
-      r0 += __shfl_xor_sync(gm, r0, o);
-      r1 += __shfl_xor_sync(gm, r1, o);
-      r2 += __shfl_xor_sync(gm, r2, o);
+    for (int i = 0; i < 16; ++i) a[i] = 0.f;
+    {
+      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + cur.e0;
+      const uint8_t* po = cv.pixoff + cur.e0;
+      const uint32_t len = (uint32_t)(cur.e1 - cur.e0);
+      for (uint32_t i = lane; i < len; i += 32 * U) {
+        typename Raw<kFmt>::T raw[U];
+        int pp[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          if (i + 32 * j < len) {
+            raw[j] = __ldcs(pl + i + 32 * j);
+            pp[j] = po[i + 32 * j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          if (i + 32 * j < len) {
+            const int p = pp[j];
+            const float4 pej = decode<kFmt>(raw[j], cur.scale);
+            const float4 uv = su4[p];
+            const float2 c = sxy[p];
+            const float dx = c.x - cur.mx, dy = c.y - cur.my;
+            const float sv = pej.y * uv.x + pej.z * uv.y + pej.w * uv.z;
+            const float t1 = sv * dx, t2 = sv * dy;
+            a[0] += sv;
+            a[1] += t1;
+            a[2] += t2;
+            a[3] += t1 * dx;
+            a[4] += t1 * dy;
+            a[5] += t2 * dy;
+            a[6] += pej.x * uv.x;
+            a[7] += pej.x * uv.y;
+            a[8] += pej.x * uv.z;
+          }
+        }
+      }
     }
-    if (gl == 0) {
-      float4* out = reinterpret_cast<float4*>(seg_ybar + (size_t)seg * 12);
-      out[0] = make_float4(A * a1 + B * a2, B * a1 + C * a2, -0.5f * a3, -a4);
-      out[1] = make_float4(-0.5f * a5, a0 / rb.y, r0, r1);
-      out[2] = make_float4(r2, 0.f, 0.f, 0.f);
+    warp_sum16(a, lane);
+    // lane 2i holds moment i: m0 = sum s, m1 = sum s dx, m2 = sum s dy,
+    // m3 = sum s dx^2, m4 = sum s dx dy, m5 = sum s dy^2, m6..m8 = sum w u
+    float m[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m[i] = __shfl_sync(kFull, a[0], 2 * i);
+    if (lane < 9) {
+      float val = m[lane < 9 ? lane : 0];
+      if (lane == 0) val = cur.A * m[1] + cur.B * m[2];
+      else if (lane == 1) val = cur.B * m[1] + cur.C * m[2];
+      else if (lane == 2) val = -0.5f * m[3];
+      else if (lane == 3) val = -m[4];
+      else if (lane == 4) val = -0.5f * m[5];
+      else if (lane == 5) val = m[0] * cur.io;
+      seg_ybar[(size_t)(g0 + k) * 12 + lane] = val;
     }
+    k = kn;
+    cur = nxt;
   }
 }
 
@@ -261,44 +430,62 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
   }
 }
 
-template <int G>
-cudaError_t apply_J_g(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq,
-                      cudaStream_t st) {
-  if (cv.fmt == GSLM_CACHE_FP32) { k_apply_J<G, GSLM_CACHE_FP32><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq); note_launch(); }
-  else if (cv.fmt == GSLM_CACHE_BF16) { k_apply_J<G, GSLM_CACHE_BF16><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq); note_launch(); }
-  else { k_apply_J<G, GSLM_CACHE_FP16S><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq); note_launch(); }
+// Variants: entries each lane keeps in flight (U) and the minimum number of
+// resident 256-thread blocks per SM the registers must allow.
+template <int kFmt, int U, int B>
+cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
+  k_apply_J<kFmt, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
+  note_launch();
   return cudaGetLastError();
 }
 
-template <int G>
-cudaError_t apply_JT_g(const CacheView& cv, const float* u, float* seg_ybar, cudaStream_t st) {
-  if (cv.fmt == GSLM_CACHE_FP32) { k_apply_JT<G, GSLM_CACHE_FP32><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar); note_launch(); }
-  else if (cv.fmt == GSLM_CACHE_BF16) { k_apply_JT<G, GSLM_CACHE_BF16><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar); note_launch(); }
-  else { k_apply_JT<G, GSLM_CACHE_FP16S><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar); note_launch(); }
+template <int kFmt, int U, int B>
+cudaError_t run_JT(const CacheView& cv, const float* u, float* seg_ybar, cudaStream_t st) {
+  k_apply_JT<kFmt, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar);
+  note_launch();
   return cudaGetLastError();
+}
+
+template <int kFmt>
+cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot, const float* F_add, float* u,
+                            double* sq, cudaStream_t st) {
+  switch (variant) {
+    case 0: return run_J<kFmt, 1, 6>(cv, ydot, F_add, u, sq, st);
+    case 1: return run_J<kFmt, 2, 5>(cv, ydot, F_add, u, sq, st);
+    case 2: return run_J<kFmt, 4, 4>(cv, ydot, F_add, u, sq, st);
+    default: return run_J<kFmt, 8, 3>(cv, ydot, F_add, u, sq, st);
+  }
+}
+
+template <int kFmt>
+cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, float* seg_ybar, cudaStream_t st) {
+  switch (variant) {
+    case 0: return run_JT<kFmt, 1, 6>(cv, u, seg_ybar, st);
+    case 1: return run_JT<kFmt, 2, 5>(cv, u, seg_ybar, st);
+    case 2: return run_JT<kFmt, 4, 4>(cv, u, seg_ybar, st);
+    default: return run_JT<kFmt, 8, 3>(cv, u, seg_ybar, st);
+  }
 }
 
 }  // namespace
 
 int apply_J_partials(const CacheView& cv) { return cv.n_tiles; }
 
+int apply_variants() { return 4; }
+
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add, float* u,
-                           double* sq_partials, int group, cudaStream_t st) {
+                           double* sq_partials, int variant, cudaStream_t st) {
   if (cv.n_tiles <= 0) return cudaSuccess;
-  switch (group) {
-    case 8: return apply_J_g<8>(cv, ydot, F_add, u, sq_partials, st);
-    case 16: return apply_J_g<16>(cv, ydot, F_add, u, sq_partials, st);
-    default: return apply_J_g<32>(cv, ydot, F_add, u, sq_partials, st);
-  }
+  if (cv.fmt == GSLM_CACHE_FP32) return apply_J_variant<GSLM_CACHE_FP32>(variant, cv, ydot, F_add, u, sq_partials, st);
+  if (cv.fmt == GSLM_CACHE_BF16) return apply_J_variant<GSLM_CACHE_BF16>(variant, cv, ydot, F_add, u, sq_partials, st);
+  return apply_J_variant<GSLM_CACHE_FP16S>(variant, cv, ydot, F_add, u, sq_partials, st);
 }
 
-cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar, int group, cudaStream_t st) {
+cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar, int variant, cudaStream_t st) {
   if (cv.n_tiles <= 0) return cudaSuccess;
-  switch (group) {
-    case 8: return apply_JT_g<8>(cv, u, seg_ybar, st);
-    case 16: return apply_JT_g<16>(cv, u, seg_ybar, st);
-    default: return apply_JT_g<32>(cv, u, seg_ybar, st);
-  }
+  if (cv.fmt == GSLM_CACHE_FP32) return apply_JT_variant<GSLM_CACHE_FP32>(variant, cv, u, seg_ybar, st);
+  if (cv.fmt == GSLM_CACHE_BF16) return apply_JT_variant<GSLM_CACHE_BF16>(variant, cv, u, seg_ybar, st);
+  return apply_JT_variant<GSLM_CACHE_FP16S>(variant, cv, u, seg_ybar, st);
 }
 
 cudaError_t launch_diag_entries(const CacheView& cv, float* seg_q, cudaStream_t st) {

@@ -51,6 +51,19 @@ struct SplatRec {
   float4 a, b, c;
 };
 
+// One non-empty (tile, splat) segment of the cache, as the apply kernels read
+// it: a single 48-byte broadcast load gives everything a warp needs to walk the
+// segment's entries.
+struct SegRec {
+  unsigned long long e0, e1;  // entry range [e0, e1)
+  uint32_t slot;              // splat (view * N + Gaussian)
+  float mx, my;               // 2D mean relative to the centre of the tile's first pixel
+  float A, B, C;              // conic
+  float io;                   // 1 / opacity
+  float scale;                // FP16S payload scale (1 for the other formats)
+};
+static_assert(sizeof(SegRec) == 48, "SegRec is three 16-byte words");
+
 // Device-side scalars of one PCG solve (Algorithm 1).
 struct PcgScalars {
   double bb;        // ||b||^2
@@ -77,6 +90,7 @@ struct CacheView {
   const uint32_t* tile_seg_off;    // [n_tiles + 1]
   const unsigned long long* seg_entry_off;  // [n_seg + 1]
   const uint32_t* seg_slot;        // [n_seg]
+  const SegRec* seg_rec;           // [n_seg]
   const void* payload;             // [E] float4 (FP32) or 4 x 16-bit
   const float* seg_scale;          // [n_seg] (FP16S only)
   const uint8_t* pixoff;           // [E] pixel index inside the tile (row-major 16 x 16)
@@ -84,6 +98,7 @@ struct CacheView {
   const uint32_t* slot_seg_end;
   const uint32_t* slot_seg_list;   // [n_seg] segment ids ordered by slot
   const uint8_t* slot_active;      // [n_slots]
+  const unsigned long long* vmask; // [N] active views per Gaussian (null when V > 64)
   long long n_seg;
   long long n_entries;
   int fmt;
@@ -105,11 +120,11 @@ struct CacheParts {
 };
 struct ContextParts {
   cudaStream_t st;
-  int group;
+  int variant_JT;   // apply_JT kernel variant for the cache format asked about
   int device;
 };
 bool cache_parts(const gslm_cache* c, CacheParts* out);
-bool context_parts(const gslm_ctx* c, ContextParts* out);
+bool context_parts(const gslm_ctx* c, int cache_fmt, ContextParts* out);
 void set_context_error(gslm_ctx* c, const char* msg);
 
 // ----------------------------------------------------------------------------
@@ -120,19 +135,23 @@ void set_context_error(gslm_ctx* c, const char* msg);
 cudaError_t launch_project(const float* params, int N, long long ld, const DevCam* cams, int V,
                            int smooth, SplatRec* rec, uint32_t* ntiles, uint2* rect,
                            uint32_t* depth_key, cudaStream_t st);
+cudaError_t launch_view_mask(const uint8_t* slot_active, int N, int V, unsigned long long* vmask,
+                             cudaStream_t st);
+// vmask (per Gaussian, bit v = view v has cache entries) may be null, and must
+// be null when V > 64; the kernels then visit every view.
 cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCam* cams, int V,
-                           int smooth, const uint8_t* slot_active, const float* p,
-                           float* ydot, const float* z_beta, float* p_out,
+                           int smooth, const uint8_t* slot_active, const unsigned long long* vmask,
+                           const float* p, float* ydot, const float* z_beta, float* p_out,
                            const PcgScalars* sc, cudaStream_t st);
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V,
                        int smooth, const uint32_t* slot_seg_start, const uint32_t* slot_seg_end,
-                       const uint32_t* slot_seg_list, const float* seg_ybar, float scale,
-                       float* g, const float* p, const float* M, float lambda,
-                       double* dot_partials, const PcgScalars* sc, cudaStream_t st);
+                       const uint32_t* slot_seg_list, const unsigned long long* vmask,
+                       const float* seg_ybar, float scale, float* g, const float* p, const float* M,
+                       float lambda, double* dot_partials, const PcgScalars* sc, cudaStream_t st);
 cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V,
                         int smooth, const uint32_t* slot_seg_start, const uint32_t* slot_seg_end,
-                        const uint32_t* slot_seg_list, const float* seg_q, float* diag,
-                        cudaStream_t st);
+                        const uint32_t* slot_seg_list, const unsigned long long* vmask,
+                        const float* seg_q, float* diag, cudaStream_t st);
 int vjp_blocks(int N);
 
 // sort.cu
@@ -172,13 +191,15 @@ cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const ui
                                 const unsigned long long* tile_entry_off,
                                 const uint32_t* tile_seg_off, int fmt, void* payload,
                                 float* seg_scale, uint8_t* pixoff,
-                                unsigned long long* seg_entry_off, uint32_t* seg_slot,
+                                unsigned long long* seg_entry_off, uint32_t* seg_slot, SegRec* seg_rec,
                                 uint8_t* slot_active, int* err, cudaStream_t st);
 
-// apply.cu
+// apply.cu. `variant` selects one of apply_variants() kernel configurations
+// (entries in flight per lane and register budget); all compute the same result.
+int apply_variants();
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add,
-                           float* u, double* sq_partials, int group, cudaStream_t st);
-cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar, int group,
+                           float* u, double* sq_partials, int variant, cudaStream_t st);
+cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar, int variant,
                             cudaStream_t st);
 cudaError_t launch_diag_entries(const CacheView& cv, float* seg_q, cudaStream_t st);
 int apply_J_partials(const CacheView& cv);

@@ -28,7 +28,7 @@ extern "C" gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* ca
   gslm::CacheParts cp;
   gslm::ContextParts xp;
   if (ctx == nullptr || cache == nullptr || u == nullptr || g == nullptr || !gslm::cache_parts(cache, &cp) ||
-      !gslm::context_parts(ctx, &xp)) {
+      !gslm::context_parts(ctx, cp.view.fmt, &xp)) {
     gslm::set_context_error(ctx, "apply_JT_noalloc: null argument");
     return GSLM_E_INVALID;
   }
@@ -63,11 +63,11 @@ extern "C" gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* ca
   // Every segment slot read below is written first in this call, so nothing in
   // the shared array needs clearing.
   float* seg_ybar = static_cast<float*>(scratch);
-  cudaError_t e = gslm::launch_apply_JT(cp.view, u, seg_ybar, xp.group, xp.st);
+  cudaError_t e = gslm::launch_apply_JT(cp.view, u, seg_ybar, xp.variant_JT, xp.st);
   if (e == cudaSuccess)
     e = gslm::launch_vjp(cp.params, cp.N, cp.ld, cp.cams, cp.V, cp.smooth, cp.view.slot_seg_start,
-                         cp.view.slot_seg_end, cp.view.slot_seg_list, seg_ybar, 1.f, g, nullptr, nullptr, 0.f,
-                         nullptr, nullptr, xp.st);
+                         cp.view.slot_seg_end, cp.view.slot_seg_list, cp.view.vmask, seg_ybar, 1.f, g, nullptr,
+                         nullptr, 0.f, nullptr, nullptr, xp.st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     gslm::set_context_error(ctx, "apply_JT_noalloc: kernel launch failed");

@@ -24,29 +24,29 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-__device__ __forceinline__ int part_index() { return blockIdx.y * gridDim.x + blockIdx.x; }
+// The vector kernels stride over Gaussians with a bounded grid (at most
+// kVecBlocks blocks) and loop over the 59 parameter rows, so each block writes
+// one float64 partial and the scalar kernel reduces at most kVecBlocks of them.
+constexpr int kVecBlocks = 2432;   // 16 blocks of 256 threads per SM on 152 SMs
 
 __global__ void k_pcg_init(int N, long long ld, const float* __restrict__ b, const float* __restrict__ M,
                            const float* __restrict__ D, float* __restrict__ x, float* __restrict__ Minv,
                            double* __restrict__ partials) {
   __shared__ double red[kBS / 32];
-  const int i = blockIdx.x * kBS + threadIdx.x;
-  const long long o = (long long)blockIdx.y * ld + i;
   double bb = 0.0;
-  if (i < N) {
-    float mi;
-    if (D != nullptr) {
-      mi = D[o];
-    } else {
-      mi = 1.f / clamp_diag(M[o]);
+  for (int i = blockIdx.x * kBS + threadIdx.x; i < N; i += gridDim.x * kBS) {
+#pragma unroll 4
+    for (int k = 0; k < kNP; ++k) {
+      const long long o = (long long)k * ld + i;
+      const float mi = D != nullptr ? D[o] : 1.f / clamp_diag(M[o]);
+      Minv[o] = mi;
+      const float bv = b[o];
+      x[o] = mi * bv;
+      bb += (double)bv * bv;
     }
-    Minv[o] = mi;
-    const float bv = b[o];
-    x[o] = mi * bv;
-    bb = (double)bv * bv;
   }
   const double s = block_sum(bb, red);
-  if (threadIdx.x == 0) partials[part_index()] = s;
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void k_pcg_residual0(int N, long long ld, const float* __restrict__ b, const float* __restrict__ g,
@@ -54,19 +54,21 @@ __global__ void k_pcg_residual0(int N, long long ld, const float* __restrict__ b
                                 const float* __restrict__ Minv, float* __restrict__ r, float* __restrict__ z,
                                 float* __restrict__ p, double* __restrict__ partials) {
   __shared__ double red[kBS / 32];
-  const int i = blockIdx.x * kBS + threadIdx.x;
-  const long long o = (long long)blockIdx.y * ld + i;
   double rz = 0.0;
-  if (i < N) {
-    const float rv = b[o] - (g[o] + lambda * clamp_diag(M[o]) * x[o]);
-    const float zv = Minv[o] * rv;
-    r[o] = rv;
-    z[o] = zv;
-    p[o] = zv;
-    rz = (double)rv * zv;
+  for (int i = blockIdx.x * kBS + threadIdx.x; i < N; i += gridDim.x * kBS) {
+#pragma unroll 4
+    for (int k = 0; k < kNP; ++k) {
+      const long long o = (long long)k * ld + i;
+      const float rv = b[o] - (g[o] + lambda * clamp_diag(M[o]) * x[o]);
+      const float zv = Minv[o] * rv;
+      r[o] = rv;
+      z[o] = zv;
+      p[o] = zv;
+      rz += (double)rv * zv;
+    }
   }
   const double s = block_sum(rz, red);
-  if (threadIdx.x == 0) partials[part_index()] = s;
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void k_pcg_update(int N, long long ld, const PcgScalars* __restrict__ sc, const float* __restrict__ p,
@@ -74,25 +76,27 @@ __global__ void k_pcg_update(int N, long long ld, const PcgScalars* __restrict__
                              float* __restrict__ r, float* __restrict__ z, double* __restrict__ partials) {
   __shared__ double red[kBS / 32];
   if (sc->done) return;
-  const int i = blockIdx.x * kBS + threadIdx.x;
-  const long long o = (long long)blockIdx.y * ld + i;
   const float alpha = (float)sc->alpha;
   double rz = 0.0, rr = 0.0;
-  if (i < N) {
-    x[o] = x[o] + alpha * p[o];
-    const float rv = r[o] - alpha * g[o];
-    const float zv = Minv[o] * rv;
-    r[o] = rv;
-    z[o] = zv;
-    rz = (double)rv * zv;
-    rr = (double)rv * rv;
+  for (int i = blockIdx.x * kBS + threadIdx.x; i < N; i += gridDim.x * kBS) {
+#pragma unroll 4
+    for (int k = 0; k < kNP; ++k) {
+      const long long o = (long long)k * ld + i;
+      x[o] = x[o] + alpha * p[o];
+      const float rv = r[o] - alpha * g[o];
+      const float zv = Minv[o] * rv;
+      r[o] = rv;
+      z[o] = zv;
+      rz += (double)rv * zv;
+      rr += (double)rv * rv;
+    }
   }
   const double s0 = block_sum(rz, red);
   __syncthreads();
   const double s1 = block_sum(rr, red);
   if (threadIdx.x == 0) {
-    partials[2 * part_index()] = s0;
-    partials[2 * part_index() + 1] = s1;
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
   }
 }
 
@@ -207,7 +211,7 @@ dim3 vec_grid(int N) { return dim3((unsigned)((N + kBS - 1) / kBS), kNP); }
 
 }  // namespace
 
-int pcg_blocks(int N) { return ((N + kBS - 1) / kBS) * kNP; }
+int pcg_blocks(int N) { return std::max(1, std::min((N + kBS - 1) / kBS, kVecBlocks)); }
 
 cudaError_t launch_reduce_partials(const double* partials, int n, double* out, cudaStream_t st) {
   { k_reduce<<<1, kBS, 0, st>>>(partials, n, out); note_launch(); }
@@ -218,7 +222,7 @@ cudaError_t launch_pcg_init(long long n59, long long ld, int N, const float* b, 
                             float* x, float* Minv, double* partials, cudaStream_t st) {
   (void)n59;
   if (N <= 0) return cudaSuccess;
-  { k_pcg_init<<<vec_grid(N), kBS, 0, st>>>(N, ld, b, M, D, x, Minv, partials); note_launch(); }
+  { k_pcg_init<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, b, M, D, x, Minv, partials); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -226,7 +230,7 @@ cudaError_t launch_pcg_residual0(int N, long long ld, const float* b, const floa
                                  float lambda, const float* Minv, float* r, float* z, float* p, double* partials,
                                  cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  { k_pcg_residual0<<<vec_grid(N), kBS, 0, st>>>(N, ld, b, g, M, x, lambda, Minv, r, z, p, partials); note_launch(); }
+  { k_pcg_residual0<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, b, g, M, x, lambda, Minv, r, z, p, partials); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -239,7 +243,7 @@ cudaError_t launch_pcg_scalars(PcgScalars* sc, const double* partials, int n_par
 cudaError_t launch_pcg_update(int N, long long ld, const PcgScalars* sc, const float* p, const float* g,
                               const float* Minv, float* x, float* r, float* z, double* partials, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  { k_pcg_update<<<vec_grid(N), kBS, 0, st>>>(N, ld, sc, p, g, Minv, x, r, z, partials); note_launch(); }
+  { k_pcg_update<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, sc, p, g, Minv, x, r, z, partials); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -263,6 +263,27 @@ __device__ __forceinline__ void geo_tangent(const ViewGeo& V, const DevCam& cam,
 
 __device__ __forceinline__ long long n_slots(int N, int V) { return (long long)N * V; }
 
+// Iteration over the views of one Gaussian: with a view mask (bit v set when the
+// splat of view v has cache entries; only for V <= 64) the set bits in
+// ascending order, otherwise every view. `mm` holds the bits not yet visited.
+__device__ __forceinline__ int next_view(bool use_mask, unsigned long long& mm, int v, int V) {
+  if (!use_mask) return v + 1;
+  if (mm == 0) return V;
+  const int b = __ffsll((long long)mm) - 1;
+  mm &= mm - 1;
+  return b;
+}
+
+__global__ void k_view_mask(const uint8_t* __restrict__ slot_active, int N, int V,
+                            unsigned long long* __restrict__ vmask) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  unsigned long long m = 0;
+  for (int v = 0; v < V && v < 64; ++v)
+    if (slot_active[(long long)v * N + g]) m |= 1ull << v;
+  vmask[g] = m;
+}
+
 __global__ void k_project(const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams,
                           int V, int smooth, SplatRec* __restrict__ rec, uint32_t* __restrict__ ntiles,
                           uint2* __restrict__ rect, uint32_t* __restrict__ depth_key) {
@@ -321,8 +342,9 @@ __global__ void k_project(const float* __restrict__ P, int N, long long ld, cons
 // new p is written back to p_out.
 __global__ void __launch_bounds__(128) k_tangent(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
-    const uint8_t* __restrict__ slot_active, const float* __restrict__ pin, float* __restrict__ ydot,
-    const float* __restrict__ zb, float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
+    const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
+    const float* __restrict__ pin, float* __restrict__ ydot, const float* __restrict__ zb,
+    float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   if (sc != nullptr && sc->done) return;
@@ -339,15 +361,21 @@ __global__ void __launch_bounds__(128) k_tangent(
 #pragma unroll
     for (int k = 0; k < kNP; ++k) pd[k] = pin[k * ld + g];
   }
-  bool any = false;
-  for (int v = 0; v < V; ++v) any |= slot_active[(long long)v * N + g] != 0;
-  if (!any) return;
+  const bool use_mask = vmask != nullptr;
+  unsigned long long mm = use_mask ? vmask[g] : 0ull;
+  if (use_mask) {
+    if (mm == 0) return;
+  } else {
+    bool any = false;
+    for (int v = 0; v < V; ++v) any |= slot_active[(long long)v * N + g] != 0;
+    if (!any) return;
+  }
   GaussGeo G;
   gauss_geo(P, ld, g, G);
   float Sd[6];
   sigma_tangent(G, pd + 3, pd + 6, Sd);
   const float od = G.o * (1.f - G.o) * pd[10];
-  for (int v = 0; v < V; ++v) {
+  for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
     const long long slot = (long long)v * N + g;
     if (!slot_active[slot]) continue;
     const DevCam& cam = cams[v];
@@ -390,9 +418,10 @@ __global__ void __launch_bounds__(128) k_tangent(
 __global__ void __launch_bounds__(128) k_vjp(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const uint32_t* __restrict__ s_list, const float* __restrict__ seg_ybar, float scale,
-    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
-    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
+    const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ vmask,
+    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
+    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
+    const PcgScalars* __restrict__ sc) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const bool skip = (sc != nullptr && sc->done);
   double local = 0.0;
@@ -405,7 +434,9 @@ __global__ void __launch_bounds__(128) k_vjp(
     for (int k = 0; k < 48; ++k) shb[k] = 0.f;
     bool any = false;
     GaussGeo G;
-    for (int v = 0; v < V; ++v) {
+    const bool use_mask = vmask != nullptr;
+    unsigned long long mm = use_mask ? vmask[g] : 0ull;
+    for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
       const long long slot = (long long)v * N + g;
       const uint32_t a = s_start[slot], b = s_end[slot];
       if (a == b) continue;
@@ -560,7 +591,8 @@ __global__ void __launch_bounds__(128) k_vjp(
 __global__ void __launch_bounds__(128) k_diag(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const uint32_t* __restrict__ s_list, const float* __restrict__ seg_q, float* __restrict__ dout) {
+    const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ vmask,
+    const float* __restrict__ seg_q, float* __restrict__ dout) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   float d[kNP];
@@ -568,7 +600,9 @@ __global__ void __launch_bounds__(128) k_diag(
   for (int k = 0; k < kNP; ++k) d[k] = 0.f;
   bool any = false;
   GaussGeo G;
-  for (int v = 0; v < V; ++v) {
+  const bool use_mask = vmask != nullptr;
+  unsigned long long mm = use_mask ? vmask[g] : 0ull;
+  for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
     const long long slot = (long long)v * N + g;
     const uint32_t a = s_start[slot], b = s_end[slot];
     if (a == b) continue;
@@ -671,12 +705,19 @@ cudaError_t launch_project(const float* params, int N, long long ld, const DevCa
   return cudaGetLastError();
 }
 
-cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
-                           const uint8_t* slot_active, const float* p, float* ydot, const float* z_beta,
-                           float* p_out, const PcgScalars* sc, cudaStream_t st) {
+cudaError_t launch_view_mask(const uint8_t* slot_active, int N, int V, unsigned long long* vmask,
+                             cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_tangent<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, slot_active, p, ydot, z_beta,
-                                             p_out, sc); note_launch(); }
+  { k_view_mask<<<(N + 255) / 256, 256, 0, st>>>(slot_active, N, V, vmask); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
+                           const uint8_t* slot_active, const unsigned long long* vmask, const float* p,
+                           float* ydot, const float* z_beta, float* p_out, const PcgScalars* sc, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  { k_tangent<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, slot_active, vmask, p, ydot,
+                                             z_beta, p_out, sc); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -684,19 +725,21 @@ int vjp_blocks(int N) { return (N + 127) / 128; }
 
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
                        const uint32_t* s_start, const uint32_t* s_end, const uint32_t* s_list,
-                       const float* seg_ybar, float scale, float* g, const float* p, const float* M, float lambda,
-                       double* partials, const PcgScalars* sc, cudaStream_t st) {
+                       const unsigned long long* vmask, const float* seg_ybar, float scale, float* g,
+                       const float* p, const float* M, float lambda, double* partials, const PcgScalars* sc,
+                       cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, seg_ybar, scale,
-                                       g, p, M, lambda, partials, sc); note_launch(); }
+  { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, vmask, seg_ybar,
+                                       scale, g, p, M, lambda, partials, sc); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
                         const uint32_t* s_start, const uint32_t* s_end, const uint32_t* s_list,
-                        const float* seg_q, float* diag, cudaStream_t st) {
+                        const unsigned long long* vmask, const float* seg_q, float* diag, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_diag<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, seg_q, diag); note_launch(); }
+  { k_diag<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, vmask, seg_q,
+                                            diag); note_launch(); }
   return cudaGetLastError();
 }
 

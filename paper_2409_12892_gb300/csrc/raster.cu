@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
     int smooth, const float* __restrict__ img, const unsigned long long* __restrict__ tile_entry_off,
     const uint32_t* __restrict__ tile_seg_off, void* __restrict__ payload, float* __restrict__ seg_scale,
     uint8_t* __restrict__ pixoff, unsigned long long* __restrict__ seg_entry_off,
-    uint32_t* __restrict__ seg_slot, uint8_t* __restrict__ slot_active, int* __restrict__ err) {
+    uint32_t* __restrict__ seg_slot, SegRec* __restrict__ seg_rec, uint8_t* __restrict__ slot_active,
+    int* __restrict__ err) {
   __shared__ float4 sA[kTilePix];
   __shared__ float2 sB[kTilePix];
   __shared__ float4 sC[kTilePix];
@@ -331,6 +332,20 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
             seg_entry_off[sidx] = ebase + erun + excl;
             slot_active[slot] = 1;
             segidx[j] = (int)sidx;
+            const float4 a = sA[sub + j];
+            const float2 bb = sB[sub + j];
+            SegRec r;
+            r.e0 = ebase + erun + excl;
+            r.e1 = r.e0 + cj;
+            r.slot = slot;
+            r.mx = a.x - (ts.x0 + 0.5f);
+            r.my = a.y - (ts.y0 + 0.5f);
+            r.A = a.z;
+            r.B = a.w;
+            r.C = bb.x;
+            r.io = 1.f / bb.y;
+            r.scale = 1.f;
+            seg_rec[sidx] = r;
           } else {
             atomicOr(err, 2);
           }
@@ -365,8 +380,10 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
           Tq = transmit(Tq, alpha);
         }
         __syncthreads();
-        if (threadIdx.x < 32 && segidx[threadIdx.x] >= 0)
+        if (threadIdx.x < 32 && segidx[threadIdx.x] >= 0) {
           seg_scale[segidx[threadIdx.x]] = __uint_as_float(segmax[threadIdx.x]);
+          seg_rec[segidx[threadIdx.x]].scale = __uint_as_float(segmax[threadIdx.x]);
+        }
       }
       for (int j = 0; j < m; ++j) {
         if (!((mask >> j) & 1u)) continue;
@@ -436,13 +453,13 @@ cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const ui
                                 int smooth, const float* img, const unsigned long long* tile_entry_off,
                                 const uint32_t* tile_seg_off, int fmt, void* payload, float* seg_scale,
                                 uint8_t* pixoff, unsigned long long* seg_entry_off, uint32_t* seg_slot,
-                                uint8_t* slot_active, int* err, cudaStream_t st) {
+                                SegRec* seg_rec, uint8_t* slot_active, int* err, cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
 #define GSLM_WRITE(F)                                                                                         \
   do {                                                                                                        \
     k_raster_write<F><<<n_tiles, kTilePix, 0, st>>>(cams, V, tile_start, tile_end, tile_vals, rec, smooth, img, \
                                                     tile_entry_off, tile_seg_off, payload, seg_scale, pixoff,   \
-                                                    seg_entry_off, seg_slot, slot_active, err);                 \
+                                                    seg_entry_off, seg_slot, seg_rec, slot_active, err);        \
     note_launch();                                                                                            \
   } while (0)
   if (fmt == GSLM_CACHE_FP32) GSLM_WRITE(GSLM_CACHE_FP32);

@@ -143,11 +143,19 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, long long n, int
   for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[(long long)d * nblocks + blockIdx.x] = h[d];
 }
 
+// Stable scatter of one 4096-item block. Items are ranked per digit with warp
+// match (stable within a warp), then per warp prefix (stable across warps); the
+// block is first reordered by digit in shared memory and then written out, so
+// each digit's run goes to global memory with coalesced stores.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, long long n, int shift, int nblocks,
     const uint32_t* __restrict__ offs, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
   __shared__ uint32_t wcnt[kSortWarps][kRadix];
   __shared__ uint32_t goff[kRadix];
+  __shared__ uint32_t lstart[kRadix];
+  __shared__ uint32_t wsum[kSortWarps];
+  __shared__ uint32_t skeys[kSortTile];
+  __shared__ uint32_t svals[kSortTile];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
 #pragma unroll
@@ -156,7 +164,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
-  const long long wbase = (long long)blockIdx.x * kSortTile + (long long)warp * (kSortRounds * 32);
+  const long long bbase = (long long)blockIdx.x * kSortTile;
+  const long long wbase = bbase + (long long)warp * (kSortRounds * 32);
   uint32_t kk[kSortRounds], vv[kSortRounds], rk[kSortRounds];
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
@@ -177,7 +186,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     __syncwarp();
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+  // per digit: warp prefixes, and the block's count of the digit
+  uint32_t cnt = 0;
+  {
+    const int d = threadIdx.x;   // kSortThreads == kRadix
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
@@ -185,17 +197,40 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
       wcnt[w][d] = run;
       run += c;
     }
+    cnt = run;
   }
+  // exclusive scan of the digit counts over the block (digit = thread)
+  uint32_t inc = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
   __syncthreads();
+  uint32_t woff = 0;
+  for (int w = 0; w < warp; ++w) woff += wsum[w];
+  lstart[threadIdx.x] = woff + inc - cnt;
+  __syncthreads();
+  // reorder by digit in shared memory
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const long long i = wbase + r * 32 + lane;
     if (i < n) {
       const uint32_t d = (kk[r] >> shift) & (kRadix - 1);
-      const uint32_t pos = goff[d] + wcnt[warp][d] + rk[r];
-      keys_out[pos] = kk[r];
-      vals_out[pos] = vv[r];
+      const uint32_t lp = lstart[d] + wcnt[warp][d] + rk[r];
+      skeys[lp] = kk[r];
+      svals[lp] = vv[r];
     }
+  }
+  __syncthreads();
+  const long long rem = n - bbase;
+  const int valid = rem < kSortTile ? (int)rem : kSortTile;
+  for (int t = threadIdx.x; t < valid; t += kSortThreads) {
+    const uint32_t key = skeys[t];
+    const uint32_t d = (key >> shift) & (kRadix - 1);
+    const uint32_t pos = goff[d] + (uint32_t)t - lstart[d];
+    keys_out[pos] = key;
+    vals_out[pos] = svals[t];
   }
 }
 

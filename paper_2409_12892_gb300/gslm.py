@@ -47,7 +47,8 @@ class Camera(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("cache_fmt", c_int32), ("n_iters", c_int32), ("break_rel2", c_float),
                 ("lambda_min", c_float), ("lambda_max", c_float), ("smooth", c_int32),
-                ("mem_budget", c_size_t), ("group", c_int32), ("profile", c_int32), ("reserved", c_int32 * 6)]
+                ("mem_budget", c_size_t), ("group", c_int32), ("profile", c_int32), ("autotune", c_int32),
+                ("reserved", c_int32 * 5)]
 
 
 class CacheInfo(ctypes.Structure):
@@ -68,7 +69,8 @@ class LMStats(ctypes.Structure):
     _fields_ = [("cost", c_double), ("cost_new", c_double), ("predicted", c_double), ("rho", c_double),
                 ("accepted", c_int32), ("pcg_iters", c_int32), ("cache_entries", c_int64),
                 ("cache_bytes", c_int64), ("ms_total", c_double), ("ms_phase", c_double * 8),
-                ("n_pairs", c_int32), ("pad", c_int32), ("pair_bytes", c_double)]
+                ("n_pairs", c_int32), ("pad", c_int32), ("pair_bytes", c_double), ("cache_segments", c_int64),
+                ("active_splats", c_int64)]
 
 
 _lib = None
@@ -103,6 +105,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gslm_lm_step": (c_int32, [P, P, c_int64, c_int64, P, c_int32, P, P, P, c_int32, P, P, P]),
         "gslm_version": (ctypes.c_char_p, []),
         "gslm_kernel_launches": (c_int64, []),
+        "gslm_autotune_info": (c_int32, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -120,7 +123,7 @@ def exported_symbols() -> list:
     return ["gslm_default_options", "gslm_create", "gslm_destroy", "gslm_last_error", "gslm_set_options",
             "gslm_render", "gslm_build_cache", "gslm_cache_stats", "gslm_cache_free", "gslm_apply_J",
             "gslm_apply_JT", "gslm_jacobi_diag", "gslm_pcg_solve", "gslm_combine_accumulate",
-            "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches"]
+            "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches", "gslm_autotune_info"]
 
 
 # ----------------------------------------------------------------------------- marshalling helpers
@@ -199,7 +202,7 @@ class Context:
     """A libgslm context on the current CUDA device and torch's current stream."""
 
     def __init__(self, cache_fmt="fp32", n_iters=8, break_rel2=0.01, lambda_min=1e-4, lambda_max=1e4,
-                 smooth=False, mem_budget=0, group=32, profile=False, stream=None):
+                 smooth=False, mem_budget=0, group=32, profile=False, autotune=True, stream=None):
         self.lib = load_library()
         opt = Options()
         self.lib.gslm_default_options(ctypes.byref(opt))
@@ -208,6 +211,7 @@ class Context:
         opt.lambda_min, opt.lambda_max = float(lambda_min), float(lambda_max)
         opt.smooth, opt.mem_budget, opt.group = int(bool(smooth)), int(mem_budget), int(group)
         opt.profile = int(bool(profile))
+        opt.autotune = int(bool(autotune))
         self.opt = opt
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
@@ -233,6 +237,13 @@ class Context:
             msg = self.lib.gslm_last_error(self.h).decode(errors="replace") if self.h else ""
             raise GslmError(s, msg)
         return s
+
+    def autotune_info(self) -> dict:
+        """Kernel variants the autotuner chose: {'apply_J': [fp32, bf16, fp16s], 'apply_JT': [...]}."""
+        out = (c_int32 * 6)()
+        ms = (c_float * 6)()
+        self._check(self.lib.gslm_autotune_info(self.h, out, ms))
+        return {"apply_J": list(out[0:3]), "apply_JT": list(out[3:6]), "ms_J": list(ms[0:3]), "ms_JT": list(ms[3:6])}
 
     def set_options(self, **kw):
         for k, v in kw.items():
