@@ -1,0 +1,170 @@
+"""Learned diagonal preconditioner: the per-Gaussian MLP, in float64.
+
+The paper uses the Jacobi preconditioner M^-1 = 1 / diag(J^T J) (Sec. 3.3,
+Algorithm 1). This module is the oracle for the learned replacement: a small
+per-Gaussian network whose softplus output gives a positive diagonal D, so that
+z = D r keeps PCG on a symmetric positive definite system. The paper has no
+such network; the reading below is this project's (stated in the design doc):
+
+  features phi (64) per Gaussian, from one image subset's linear system:
+      log(M_k + 1e-12), k = 0..58    the subset's diag(J^T J)
+      log-scale (3), opacity sigmoid(logit) (1)
+      log(1 + entries)               cache entries that touch the Gaussian
+  standardised with a per-feature mean and standard deviation;
+  network  h1 = GELU(W1 phi + b1), h2 = GELU(W2 h1 + b2), o = W3 h2 + b3
+           (64 -> 64 -> 64 -> 59, exact GELU x Phi(x))
+  output   c = softplus(o), D_k = c_k / clamp(M_k)   (clamp as for Jacobi)
+  init     W3 = 0, b3 = log(e - 1): c = 1, i.e. D = the Jacobi preconditioner
+  loss     sum_k M_k (D_k b_k - x*_k)^2 / sum_k M_k x*_k^2 over all Gaussians,
+           x* the Jacobi-PCG solution of the subset system at ||r|| / ||b|| <= 1e-3:
+           the diagonally weighted error of the warm start x0 = D b
+  training Adam (beta1 0.9, beta2 0.999, eps 1e-8)
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+from scipy.special import erf
+
+from .solver import clamp_diag
+
+N_IN, N_HID, N_OUT = 64, 64, 59
+B3_INIT = math.log(math.e - 1.0)        # softplus(B3_INIT) = 1
+
+
+@dataclass
+class MLP:
+    W1: np.ndarray   # (64, 64)  out x in
+    b1: np.ndarray   # (64,)
+    W2: np.ndarray   # (64, 64)
+    b2: np.ndarray   # (64,)
+    W3: np.ndarray   # (59, 64)
+    b3: np.ndarray   # (59,)
+
+    def params(self):
+        return [self.W1, self.b1, self.W2, self.b2, self.W3, self.b3]
+
+    def flat(self) -> np.ndarray:
+        return np.concatenate([p.ravel() for p in self.params()])
+
+    @staticmethod
+    def from_flat(v: np.ndarray) -> "MLP":
+        shapes = [(N_HID, N_IN), (N_HID,), (N_HID, N_HID), (N_HID,), (N_OUT, N_HID), (N_OUT,)]
+        out, o = [], 0
+        for s in shapes:
+            n = int(np.prod(s))
+            out.append(np.asarray(v[o:o + n], np.float64).reshape(s).copy())
+            o += n
+        return MLP(*out)
+
+
+N_WEIGHTS = N_HID * N_IN + N_HID + N_HID * N_HID + N_HID + N_OUT * N_HID + N_OUT
+
+
+def init_mlp(seed: int, scale: float = 0.5) -> MLP:
+    """Hidden layers ~ N(0, scale^2 / fan_in); output layer zero with bias log(e - 1)."""
+    rng = np.random.default_rng([seed, 11])
+    W1 = rng.standard_normal((N_HID, N_IN)) * (scale / math.sqrt(N_IN))
+    W2 = rng.standard_normal((N_HID, N_HID)) * (scale / math.sqrt(N_HID))
+    return MLP(W1, np.zeros(N_HID), W2, np.zeros(N_HID), np.zeros((N_OUT, N_HID)), np.full(N_OUT, B3_INIT))
+
+
+def features(M: np.ndarray, params: np.ndarray, entries: np.ndarray) -> np.ndarray:
+    """phi (N, 64) from diag(J^T J) (N, 59), the parameters (N, 59) and entries per Gaussian (N,)."""
+    P = np.asarray(params, np.float64)
+    return np.concatenate([
+        np.log(np.asarray(M, np.float64) + 1e-12),
+        P[:, 3:6],
+        (1.0 / (1.0 + np.exp(-P[:, 10])))[:, None],
+        np.log1p(np.asarray(entries, np.float64))[:, None],
+    ], axis=1)
+
+
+def standardizer(phi: np.ndarray):
+    """Per-feature mean and standard deviation (std floored at 1e-6)."""
+    mu = phi.mean(axis=0)
+    sd = np.maximum(phi.std(axis=0), 1e-6)
+    return mu, sd
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
+
+
+def gelu_grad(x):
+    return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+
+
+def softplus(x):
+    return np.logaddexp(0.0, x)
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def forward(net: MLP, phi_hat: np.ndarray):
+    """Returns (a1, h1, a2, h2, o) for standardised features (N, 64)."""
+    a1 = phi_hat @ net.W1.T + net.b1
+    h1 = gelu(a1)
+    a2 = h1 @ net.W2.T + net.b2
+    h2 = gelu(a2)
+    o = h2 @ net.W3.T + net.b3
+    return a1, h1, a2, h2, o
+
+
+def precond_diag(net: MLP, phi_hat: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """D (N, 59) = softplus(o) / clamp(M)."""
+    o = forward(net, phi_hat)[-1]
+    return softplus(o) / clamp_diag(M)
+
+
+def loss_and_grad(net: MLP, phi_hat: np.ndarray, M: np.ndarray, b: np.ndarray, xstar: np.ndarray):
+    """The M-weighted warm-start loss and its gradient (list matching net.params())."""
+    a1, h1, a2, h2, o = forward(net, phi_hat)
+    Mc = clamp_diag(M)
+    D = softplus(o) / Mc
+    err = D * b - xstar
+    norm = float(np.sum(M * xstar * xstar))
+    norm = norm if norm > 0 else 1.0
+    L = float(np.sum(M * err * err)) / norm
+    dD = 2.0 * M * err * b / norm
+    do = dD / Mc * sigmoid(o)
+    gW3 = do.T @ h2
+    gb3 = do.sum(axis=0)
+    dh2 = do @ net.W3
+    da2 = dh2 * gelu_grad(a2)
+    gW2 = da2.T @ h1
+    gb2 = da2.sum(axis=0)
+    dh1 = da2 @ net.W2
+    da1 = dh1 * gelu_grad(a1)
+    gW1 = da1.T @ phi_hat
+    gb1 = da1.sum(axis=0)
+    return L, [gW1, gb1, gW2, gb2, gW3, gb3]
+
+
+@dataclass
+class Adam:
+    lr: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    t: int = 0
+    m: list = None
+    v: list = None
+
+    def step(self, net: MLP, grads: list) -> None:
+        if self.m is None:
+            self.m = [np.zeros_like(g) for g in grads]
+            self.v = [np.zeros_like(g) for g in grads]
+        self.t += 1
+        for p, g, m, v in zip(net.params(), grads, self.m, self.v):
+            m *= self.beta1
+            m += (1 - self.beta1) * g
+            v *= self.beta2
+            v += (1 - self.beta2) * g * g
+            mh = m / (1 - self.beta1 ** self.t)
+            vh = v / (1 - self.beta2 ** self.t)
+            p -= self.lr * mh / (np.sqrt(vh) + self.eps)

@@ -458,3 +458,63 @@ def _swap_mean_axes(orig):
 @pytest.mark.parametrize("mistake", [_drop_behind_term, _flip_conic_cross_sign, _swap_mean_axes])
 def test_planted_mistakes_are_caught(mistake):
     assert _fd_pin_fails(_patched(J, "dc_dy", mistake))
+
+
+# ----------------------------------------------------------------------------- learned preconditioner MLP
+def _mlp_case(seed=0, n=40):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    net = mlp.init_mlp(seed)
+    net.W3 = rng.standard_normal(net.W3.shape) * 0.1          # leave the Jacobi start for the FD check
+    net.b3 = net.b3 + rng.standard_normal(net.b3.shape) * 0.1
+    phi = rng.standard_normal((n, 64))
+    M = np.exp(rng.normal(-4, 2, (n, 59)))
+    b = rng.standard_normal((n, 59)) * M
+    xs = rng.standard_normal((n, 59)) * 0.5
+    return mlp, net, phi, M, b, xs
+
+
+def test_mlp_activations_closed_forms():
+    from oracle import mlp
+    assert abs(mlp.softplus(0.0) - math.log(2.0)) < 1e-15
+    assert abs(mlp.softplus(mlp.B3_INIT) - 1.0) < 1e-15
+    assert mlp.gelu(0.0) == 0.0 and abs(mlp.gelu_grad(0.0) - 0.5) < 1e-15
+    x = np.array([-3.0, -0.5, 0.7, 2.5])
+    phi = 0.5 * (1 + np.array([math.erf(v / math.sqrt(2)) for v in x]))
+    np.testing.assert_allclose(mlp.gelu(x), x * phi, rtol=1e-15)
+
+
+def test_mlp_starts_at_the_jacobi_preconditioner():
+    from oracle import mlp
+    net = mlp.init_mlp(3)
+    rng = np.random.default_rng(1)
+    M = np.exp(rng.normal(-3, 3, (25, 59)))
+    D = mlp.precond_diag(net, rng.standard_normal((25, 64)), M)
+    np.testing.assert_allclose(D, solver.jacobi_inverse(M), rtol=1e-14)
+
+
+def test_mlp_gradient_matches_central_differences():
+    mlp, net, phi, M, b, xs = _mlp_case()
+    L, grads = mlp.loss_and_grad(net, phi, M, b, xs)
+    g = np.concatenate([x.ravel() for x in grads])
+    v = net.flat()
+    rng = np.random.default_rng(5)
+    for i in rng.choice(v.size, 120, replace=False):
+        h = 1e-6 * max(1.0, abs(v[i]))
+        vp, vm = v.copy(), v.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd = (mlp.loss_and_grad(mlp.MLP.from_flat(vp), phi, M, b, xs)[0]
+              - mlp.loss_and_grad(mlp.MLP.from_flat(vm), phi, M, b, xs)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), i
+
+
+def test_mlp_adam_reduces_the_loss():
+    mlp, net, phi, M, b, xs = _mlp_case(2, 200)
+    xs = 0.3 * b / solver.clamp_diag(M)           # a target a diagonal scaling can reach
+    opt = mlp.Adam(lr=1e-2)
+    L0 = mlp.loss_and_grad(net, phi, M, b, xs)[0]
+    for _ in range(200):
+        L, g = mlp.loss_and_grad(net, phi, M, b, xs)
+        opt.step(net, g)
+    assert L < 0.1 * L0
