@@ -15,10 +15,16 @@ such network; the reading below is this project's (stated in the design doc):
            (64 -> 64 -> 64 -> 59, exact GELU x Phi(x))
   output   c = softplus(o), D_k = c_k / clamp(M_k)   (clamp as for Jacobi)
   init     W3 = 0, b3 = log(e - 1): c = 1, i.e. D = the Jacobi preconditioner
-  loss     sum_k M_k (D_k b_k - x*_k)^2 / sum_k M_k x*_k^2 over all Gaussians,
-           x* the Jacobi-PCG solution of the subset system at ||r|| / ||b|| <= 1e-3:
-           the diagonally weighted error of the warm start x0 = D b
+  loss     L = 1/2 log(||r_K||^2 / ||b||^2): the relative residual after K
+           iterations of Algorithm 1 run with D in place of M^-1 (x0 = D b,
+           z = D r) on the subset system A = J^T J + lambda clamp(M); its
+           gradient in D is the reverse mode of those K iterations
+           (unrolled_loss_and_grad), then the network's own reverse mode
   training Adam (beta1 0.9, beta2 0.999, eps 1e-8)
+
+A warm-start loss (fit D b to the converged solution) was tried first and
+rejected: it drives many entries of D towards zero, and PCG with that D no
+longer converges.
 """
 from __future__ import annotations
 
@@ -121,28 +127,113 @@ def precond_diag(net: MLP, phi_hat: np.ndarray, M: np.ndarray) -> np.ndarray:
     return softplus(o) / clamp_diag(M)
 
 
-def loss_and_grad(net: MLP, phi_hat: np.ndarray, M: np.ndarray, b: np.ndarray, xstar: np.ndarray):
-    """The M-weighted warm-start loss and its gradient (list matching net.params())."""
+def backward(net: MLP, phi_hat: np.ndarray, M: np.ndarray, dD: np.ndarray):
+    """Weight gradients (list matching net.params()) for an upstream gradient dL/dD (N, 59)."""
     a1, h1, a2, h2, o = forward(net, phi_hat)
-    Mc = clamp_diag(M)
-    D = softplus(o) / Mc
-    err = D * b - xstar
-    norm = float(np.sum(M * xstar * xstar))
-    norm = norm if norm > 0 else 1.0
-    L = float(np.sum(M * err * err)) / norm
-    dD = 2.0 * M * err * b / norm
-    do = dD / Mc * sigmoid(o)
+    do = dD / clamp_diag(M) * sigmoid(o)           # D = softplus(o) / clamp(M)
     gW3 = do.T @ h2
     gb3 = do.sum(axis=0)
-    dh2 = do @ net.W3
-    da2 = dh2 * gelu_grad(a2)
+    da2 = (do @ net.W3) * gelu_grad(a2)
     gW2 = da2.T @ h1
     gb2 = da2.sum(axis=0)
-    dh1 = da2 @ net.W2
-    da1 = dh1 * gelu_grad(a1)
+    da1 = (da2 @ net.W2) * gelu_grad(a1)
     gW1 = da1.T @ phi_hat
     gb1 = da1.sum(axis=0)
-    return L, [gW1, gb1, gW2, gb2, gW3, gb3]
+    return [gW1, gb1, gW2, gb2, gW3, gb3]
+
+
+@dataclass
+class Tape:
+    """Forward values of the unrolled iterations kept for the reverse pass."""
+    r: list          # r_0 .. r_K
+    p: list          # p_0 .. p_{K-1}
+    g: list          # g_i = A p_i
+    rho: list        # rho_i = r_i . z_i, i = 0 .. K
+    pg: list         # p_i . g_i
+    alpha: list
+    beta: list
+
+
+def unrolled_pcg(apply_A, b: np.ndarray, d: np.ndarray, K: int):
+    """K iterations of Algorithm 1 with the diagonal d as preconditioner:
+    x0 = d b, r0 = b - A x0, z = d r, p0 = z0, then alpha = rho / p.Ap,
+    r -= alpha A p, beta = rho_new / rho, p = z + beta p. Returns (x_K, tape)."""
+    x = d * b
+    r = b - apply_A(x)
+    z = d * r
+    p = z.copy()
+    tp = Tape([r], [], [], [float(np.vdot(r, z))], [], [], [])
+    for _ in range(K):
+        g = apply_A(p)
+        pg = float(np.vdot(p, g))
+        alpha = tp.rho[-1] / pg
+        x = x + alpha * p
+        r = r - alpha * g
+        z = d * r
+        rho = float(np.vdot(r, z))
+        beta = rho / tp.rho[-1]
+        tp.p.append(p)
+        tp.g.append(g)
+        tp.pg.append(pg)
+        tp.alpha.append(alpha)
+        tp.beta.append(beta)
+        tp.r.append(r)
+        tp.rho.append(rho)
+        p = z + beta * p
+    return x, tp
+
+
+def unrolled_loss_and_grad(apply_A, b: np.ndarray, d: np.ndarray, K: int):
+    """L = 1/2 log(||r_K||^2 / ||b||^2) of unrolled_pcg and dL/dd, by reverse mode
+    through the iterations (A symmetric, so the adjoint of g = A p is pbar += A gbar)."""
+    _, tp = unrolled_pcg(apply_A, b, d, K)
+    rK = tp.r[K]
+    rr = float(np.vdot(rK, rK))
+    L = 0.5 * math.log(rr / float(np.vdot(b, b)))
+    dbar = np.zeros_like(d)
+    rbar = rK / rr                                  # dL/dr_K
+    pbar = np.zeros_like(d)                         # adjoint of p_{i+1}
+    rhobar = [0.0] * (K + 1)
+    for i in range(K - 1, -1, -1):
+        r1, z1 = tp.r[i + 1], d * tp.r[i + 1]
+        # p_{i+1} = z_{i+1} + beta_i p_i
+        zbar = pbar.copy()
+        betabar = float(np.vdot(pbar, tp.p[i]))
+        pbar_i = tp.beta[i] * pbar
+        # beta_i = rho_{i+1} / rho_i
+        rhobar[i + 1] += betabar / tp.rho[i]
+        rhobar[i] -= betabar * tp.rho[i + 1] / tp.rho[i] ** 2
+        # rho_{i+1} = r_{i+1} . z_{i+1};  z_{i+1} = d r_{i+1}
+        rbar = rbar + rhobar[i + 1] * z1
+        zbar = zbar + rhobar[i + 1] * r1
+        rbar = rbar + d * zbar
+        dbar += r1 * zbar
+        # r_{i+1} = r_i - alpha_i g_i
+        alphabar = -float(np.vdot(rbar, tp.g[i]))
+        gbar = -tp.alpha[i] * rbar
+        # alpha_i = rho_i / (p_i . g_i)
+        rhobar[i] += alphabar / tp.pg[i]
+        pgbar = -alphabar * tp.rho[i] / tp.pg[i] ** 2
+        # pg_i = p_i . g_i;  g_i = A p_i
+        pbar_i = pbar_i + pgbar * tp.g[i]
+        gbar = gbar + pgbar * tp.p[i]
+        pbar = pbar_i + apply_A(gbar)
+        # rbar now holds dL/dr_i (r_{i+1} depends on r_i with unit weight)
+    # p_0 = z_0, rho_0 = r_0 . z_0, z_0 = d r_0
+    r0 = tp.r[0]
+    zbar = pbar + rhobar[0] * r0
+    rbar = rbar + rhobar[0] * (d * r0) + d * zbar
+    dbar += r0 * zbar
+    # r_0 = b - A x_0, x_0 = d b
+    dbar += b * (-apply_A(rbar))
+    return L, dbar
+
+
+def loss_and_grad(net: MLP, phi_hat: np.ndarray, M: np.ndarray, apply_A, b: np.ndarray, K: int):
+    """Unrolled-PCG loss of the network's D on one system and its weight gradients."""
+    D = precond_diag(net, phi_hat, M)
+    L, dD = unrolled_loss_and_grad(apply_A, b, D, K)
+    return L, backward(net, phi_hat, M, dD)
 
 
 @dataclass

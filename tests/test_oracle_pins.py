@@ -461,17 +461,21 @@ def test_planted_mistakes_are_caught(mistake):
 
 
 # ----------------------------------------------------------------------------- learned preconditioner MLP
-def _mlp_case(seed=0, n=40):
+def _mlp_case(seed=0, n=4):
+    """A random network off its Jacobi start and a random SPD system over n Gaussians."""
     from oracle import mlp
     rng = np.random.default_rng(seed)
     net = mlp.init_mlp(seed)
-    net.W3 = rng.standard_normal(net.W3.shape) * 0.1          # leave the Jacobi start for the FD check
+    net.W3 = rng.standard_normal(net.W3.shape) * 0.1
     net.b3 = net.b3 + rng.standard_normal(net.b3.shape) * 0.1
     phi = rng.standard_normal((n, 64))
-    M = np.exp(rng.normal(-4, 2, (n, 59)))
-    b = rng.standard_normal((n, 59)) * M
-    xs = rng.standard_normal((n, 59)) * 0.5
-    return mlp, net, phi, M, b, xs
+    m = n * 59
+    B = rng.standard_normal((2 * m, m)) * np.exp(rng.normal(0.0, 1.0, m))
+    A = B.T @ B / (2 * m) + 0.05 * np.eye(m)
+    M = np.diag(A).reshape(n, 59).copy()
+    b = rng.standard_normal((n, 59))
+    apply_A = lambda v: (A @ v.ravel()).reshape(v.shape)
+    return mlp, net, phi, M, b, apply_A, A
 
 
 def test_mlp_activations_closed_forms():
@@ -493,28 +497,105 @@ def test_mlp_starts_at_the_jacobi_preconditioner():
     np.testing.assert_allclose(D, solver.jacobi_inverse(M), rtol=1e-14)
 
 
-def test_mlp_gradient_matches_central_differences():
-    mlp, net, phi, M, b, xs = _mlp_case()
-    L, grads = mlp.loss_and_grad(net, phi, M, b, xs)
-    g = np.concatenate([x.ravel() for x in grads])
+def test_unrolled_pcg_reaches_the_exact_solution_in_n_steps():
+    # conjugate gradients terminate in at most n steps in exact arithmetic
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    n = 14
+    B = rng.standard_normal((30, n))
+    A = B.T @ B + 0.5 * np.eye(n)
+    b = rng.standard_normal(n)
+    d = np.exp(rng.normal(0.0, 0.5, n)) / np.diag(A)
+    x, tp = mlp.unrolled_pcg(lambda v: A @ v, b, d, n)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(tp.r[n], b - A @ x, atol=1e-9)
+
+
+def test_unrolled_pcg_matches_algorithm_1_with_the_same_diagonal():
+    from oracle import mlp
+    rng = np.random.default_rng(6)
+    n, lam = 40, 0.3
+    J_ = rng.standard_normal((70, n)) * np.exp(rng.normal(0.0, 1.0, n))
+    JTJ = J_.T @ J_
+    Mraw = np.diag(JTJ).copy()
+    b = rng.standard_normal(n)
+    d = np.exp(rng.normal(0.0, 0.3, n)) / solver.clamp_diag(Mraw)
+    x1, _ = solver.pcg(lambda v: JTJ @ v, b, Mraw, lam, n_iters=6, Minv=d)
+    x2, _ = mlp.unrolled_pcg(lambda v: JTJ @ v + lam * solver.clamp_diag(Mraw) * v, b, d, 6)
+    np.testing.assert_allclose(x2, x1, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("K", [1, 3, 8])
+def test_unrolled_pcg_adjoint_matches_central_differences(K):
+    from oracle import mlp
+    rng = np.random.default_rng(K)
+    n = 30
+    B = rng.standard_normal((60, n)) * np.exp(rng.standard_normal(n))
+    A = B.T @ B + 0.1 * np.eye(n)
+    b = rng.standard_normal(n)
+    d = np.exp(rng.standard_normal(n)) / np.diag(A)
+    L, g = mlp.unrolled_loss_and_grad(lambda v: A @ v, b, d, K)
+    _, tp = mlp.unrolled_pcg(lambda v: A @ v, b, d, K)
+    assert abs(L - 0.5 * math.log(np.dot(tp.r[K], tp.r[K]) / np.dot(b, b))) < 1e-14
+    for k in range(n):
+        h = 1e-6 * d[k]
+        e = np.zeros(n)
+        e[k] = h
+        fd = (mlp.unrolled_loss_and_grad(lambda v: A @ v, b, d + e, K)[0]
+              - mlp.unrolled_loss_and_grad(lambda v: A @ v, b, d - e, K)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-5 * np.abs(g).max(), (k, fd, g[k])
+
+
+def test_mlp_backward_matches_central_differences():
+    mlp, net, phi, M, b, _, _ = _mlp_case(0, 40)
+    W = np.random.default_rng(9).standard_normal(M.shape)   # f(net) = sum W * D(net)
+    g = np.concatenate([x.ravel() for x in mlp.backward(net, phi, M, W)])
     v = net.flat()
+    f = lambda w: float(np.sum(W * mlp.precond_diag(mlp.MLP.from_flat(w), phi, M)))
     rng = np.random.default_rng(5)
-    for i in rng.choice(v.size, 120, replace=False):
+    for i in rng.choice(v.size, 150, replace=False):
         h = 1e-6 * max(1.0, abs(v[i]))
         vp, vm = v.copy(), v.copy()
         vp[i] += h
         vm[i] -= h
-        fd = (mlp.loss_and_grad(mlp.MLP.from_flat(vp), phi, M, b, xs)[0]
-              - mlp.loss_and_grad(mlp.MLP.from_flat(vm), phi, M, b, xs)[0]) / (2 * h)
+        fd = (f(vp) - f(vm)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), i
 
 
-def test_mlp_adam_reduces_the_loss():
-    mlp, net, phi, M, b, xs = _mlp_case(2, 200)
-    xs = 0.3 * b / solver.clamp_diag(M)           # a target a diagonal scaling can reach
-    opt = mlp.Adam(lr=1e-2)
-    L0 = mlp.loss_and_grad(net, phi, M, b, xs)[0]
-    for _ in range(200):
-        L, g = mlp.loss_and_grad(net, phi, M, b, xs)
+def test_mlp_loss_gradient_matches_central_differences():
+    mlp, net, phi, M, b, apply_A, _ = _mlp_case(1, 3)
+    L, grads = mlp.loss_and_grad(net, phi, M, apply_A, b, 5)
+    g = np.concatenate([x.ravel() for x in grads])
+    v = net.flat()
+    rng = np.random.default_rng(7)
+    for i in rng.choice(v.size, 60, replace=False):
+        h = 1e-6 * max(1.0, abs(v[i]))
+        vp, vm = v.copy(), v.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd = (mlp.loss_and_grad(mlp.MLP.from_flat(vp), phi, M, apply_A, b, 5)[0]
+              - mlp.loss_and_grad(mlp.MLP.from_flat(vm), phi, M, apply_A, b, 5)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * max(1e-3, np.abs(g).max()), i
+
+
+def test_adam_first_step_moves_each_weight_by_the_learning_rate():
+    # after one step m_hat = g and v_hat = g^2, so every weight moves by lr * g / (|g| + eps)
+    from oracle import mlp
+    net = mlp.init_mlp(2)
+    rng = np.random.default_rng(3)
+    grads = [rng.standard_normal(p.shape) for p in net.params()]
+    before = net.flat()
+    mlp.Adam(lr=0.01, eps=0.0).step(net, grads)
+    np.testing.assert_allclose(net.flat() - before, -0.01 * np.sign(np.concatenate([g.ravel() for g in grads])),
+                               rtol=1e-12)
+
+
+def test_mlp_training_lowers_the_unrolled_residual():
+    mlp, net, phi, M, b, apply_A, _ = _mlp_case(2, 3)
+    net = mlp.init_mlp(2)
+    opt = mlp.Adam(lr=3e-3)
+    L0 = mlp.loss_and_grad(net, phi, M, apply_A, b, 6)[0]
+    for _ in range(60):
+        L, g = mlp.loss_and_grad(net, phi, M, apply_A, b, 6)
         opt.step(net, g)
-    assert L < 0.1 * L0
+    assert L < L0 - 0.1
