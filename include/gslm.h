@@ -222,6 +222,71 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld,
                          const int32_t* subset_views, const int32_t* subset_off, int32_t n_b,
                          const float* const* precond, gslm_lm_state* state, gslm_lm_stats* stats);
 
+/* ---------------------------------------------------------------------------
+ * Learned diagonal preconditioner. The paper has no counterpart: it uses the
+ * Jacobi preconditioner M^-1 of Algorithm 1. This is a per-Gaussian network
+ * whose output scales that preconditioner entry by entry:
+ *   phi (64 features per Gaussian): log(M_k + 1e-12) for the 59 entries of the
+ *     subset's diag(J^T J), the 3 log-scales, sigmoid(opacity logit) and
+ *     log(1 + cache entries of the Gaussian), standardised with a stored
+ *     per-feature mean and standard deviation;
+ *   h1 = GELU(W1 phi + b1), h2 = GELU(W2 h1 + b2), o = W3 h2 + b3
+ *     (64 -> 64 -> 64 -> 59, GELU(x) = x Phi(x));
+ *   D_k = softplus(o_k) / clamp(M_k), used as D in gslm_pcg_solve.
+ * Training minimises L = 1/2 log(||r_K||^2 / ||b||^2), the relative residual
+ * after K iterations of Algorithm 1 run with D (x0 = D b, z = D r), by reverse
+ * mode through those iterations and then through the network, with Adam.
+ * Weights: float32 vector of gslm_precond_weight_count() values in the order
+ * W1 (64 x 64, row = output), b1, W2 (64 x 64), b2, W3 (59 x 64), b3.
+ * Feature arrays phi: device, float32 [N][64] row-major. */
+typedef struct gslm_precond gslm_precond;
+
+/* 12,155: the number of network weights. */
+int32_t gslm_precond_weight_count(void);
+
+/* Creates a network on ctx's device and stream. weights (host, or NULL):
+ * initial weights; NULL starts at the Jacobi preconditioner (W3 = 0,
+ * b3 = log(e - 1), so D = 1/clamp(M)) with W1, W2 ~ N(0, 0.25/64) drawn from
+ * SplitMix64(seed) by Box-Muller. mean, std (host [64], or NULL for 0 and 1):
+ * the standardisation. Adam state starts at zero. */
+gslm_status gslm_precond_create(gslm_ctx* ctx, const float* weights, const float* mean, const float* std,
+                                uint64_t seed, gslm_precond** out);
+void gslm_precond_free(gslm_precond* pc);
+/* Host copies of the weights / standardisation (any pointer may be NULL). Synchronises. */
+gslm_status gslm_precond_get(const gslm_precond* pc, float* weights, float* mean, float* std);
+/* Replaces the weights and/or the standardisation from host arrays (NULL = keep). */
+gslm_status gslm_precond_set(gslm_precond* pc, const float* weights, const float* mean, const float* std);
+
+/* Features phi [N][64] of a cache's system; diag = its diag(J^T J) [59][ld]. */
+gslm_status gslm_precond_features(gslm_ctx* ctx, const gslm_cache* cache, const float* diag, float* phi);
+/* Sets the standardisation to the per-feature mean and standard deviation
+ * (floored at 1e-6) of phi [N][64]. Synchronises. */
+gslm_status gslm_precond_fit_standardizer(gslm_precond* pc, const float* phi, int64_t N);
+/* D [59][ld] = softplus(o) / clamp(diag) for features phi [N][64]. */
+gslm_status gslm_precond_apply(gslm_precond* pc, const float* phi, int64_t N, int64_t ld, const float* diag,
+                               float* D);
+/* Weight gradient for an upstream gradient dD = dL/dD [59][ld]; added to
+ * grad (device, [weight_count]) when accumulate != 0, written otherwise. */
+gslm_status gslm_precond_backward(gslm_precond* pc, const float* phi, int64_t N, int64_t ld, const float* diag,
+                                  const float* dD, float* grad, int32_t accumulate);
+/* The unrolled loss for a given diagonal D on the cache's system
+ * A = J^T J + lambda clamp(diag) with right-hand side b: *loss (host) = L and
+ * dD (may be NULL) = dL/dD [59][ld]. K >= 1 iterations. Synchronises. Uses
+ * about (3K + 8) vectors of [59][ld] floats of device memory. */
+gslm_status gslm_precond_unrolled_grad(gslm_ctx* ctx, const gslm_cache* cache, const float* b, const float* diag,
+                                       float lambda, const float* D, int32_t K, double* loss, float* dD);
+/* One training contribution: D from the network, the unrolled loss and its
+ * weight gradient, added (scaled by weight) to the network's own gradient
+ * accumulator. *loss (host, may be NULL) = L. Synchronises. */
+gslm_status gslm_precond_accumulate(gslm_precond* pc, const gslm_cache* cache, const float* phi, const float* b,
+                                    const float* diag, float lambda, int32_t K, float weight, double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the accumulated
+ * gradient, which is then cleared. */
+gslm_status gslm_precond_adam(gslm_precond* pc, float lr);
+/* Makes gslm_lm_step use the network for every subset that gets no explicit
+ * preconditioner (NULL restores Jacobi). The network must outlive its use. */
+gslm_status gslm_set_precond(gslm_ctx* ctx, gslm_precond* pc);
+
 /* Library version string. */
 const char* gslm_version(void);
 /* Number of CUDA kernels this library has launched in this process. */

@@ -3,5 +3,5 @@
 The compute path lives in ``libgslm.so`` (hand-written CUDA, C ABI in
 ``include/gslm.h``); ``gslm`` is its thin Python binding.
 """
-from .gslm import (Cache, Context, GslmError, load_library, padded_ld, to_soa, from_soa,  # noqa: F401
+from .gslm import (Cache, Context, GslmError, Precond, load_library, padded_ld, to_soa, from_soa,  # noqa: F401
                    make_cameras, n_pixels, exported_symbols, kernel_launches, LIB_PATH)

@@ -17,45 +17,6 @@ static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace gslm
 
-namespace {
-
-// Stream-ordered device buffer.
-struct Buf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  cudaStream_t st = nullptr;
-  Buf() = default;
-  Buf(const Buf&) = delete;
-  Buf& operator=(const Buf&) = delete;
-  ~Buf() { release(); }
-  void release() {
-    if (p != nullptr) cudaFreeAsync(p, st);
-    p = nullptr;
-    bytes = 0;
-  }
-  cudaError_t alloc(size_t n, cudaStream_t s) {
-    release();
-    st = s;
-    if (n == 0) n = 16;
-    const cudaError_t e = cudaMallocAsync(&p, n, s);
-    if (e != cudaSuccess) {
-      p = nullptr;
-      return e;
-    }
-    bytes = n;
-    return cudaSuccess;
-  }
-  cudaError_t ensure(size_t n, cudaStream_t s) {
-    if (p != nullptr && bytes >= n) return cudaSuccess;
-    return alloc(n, s);
-  }
-  template <class T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
-
-}  // namespace
 
 // Per-phase CUDA-event timing of one LM step (options.profile).
 struct PhaseTimer {
@@ -125,7 +86,8 @@ struct gslm_ctx {
   // scratch reused across calls
   Buf ydot, seg_ybar, seg_q, u, partials, scalars, reduce_out;
   Buf r, z, p, g, minv;
-  Buf lm_num, lm_den, lm_delta, lm_trial, lm_x, lm_b, lm_M, lm_tgt, lm_img;
+  Buf lm_num, lm_den, lm_delta, lm_trial, lm_x, lm_b, lm_M, lm_tgt, lm_img, lm_D;
+  gslm_precond* pc = nullptr;       // learned preconditioner used by lm_step, if set
 };
 
 struct gslm_cache {
@@ -517,6 +479,15 @@ void set_context_error(gslm_ctx* c, const char* msg) {
   if (c != nullptr) c->err = msg;
 }
 
+cudaStream_t context_stream(const gslm_ctx* c) { return c->st; }
+
+gslm_status apply_A(gslm_ctx* ctx, const gslm_cache* c, const float* v, const float* M, float lambda, float* out) {
+  CK(ctx->u.ensure(sizeof(float) * 3 * std::max<long long>(c->n_pix, 1), ctx->st));
+  CKS(do_apply_J(ctx, c, v, ctx->u.as<float>(), nullptr, nullptr, nullptr, nullptr, nullptr));
+  CKS(do_apply_JT(ctx, c, ctx->u.as<float>(), out, 1.f, v, M, lambda, nullptr, nullptr));
+  return GSLM_OK;
+}
+
 }  // namespace gslm
 
 extern "C" {
@@ -832,6 +803,12 @@ gslm_status gslm_combine_finish(gslm_ctx* ctx, int64_t N, int64_t ld, const floa
   return GSLM_OK;
 }
 
+gslm_status gslm_set_precond(gslm_ctx* ctx, gslm_precond* pc) {
+  if (ctx == nullptr) return GSLM_E_INVALID;
+  ctx->pc = pc;
+  return GSLM_OK;
+}
+
 gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, const gslm_camera* cams,
                          int32_t n_cams, const float* targets, const int32_t* subset_views,
                          const int32_t* subset_off, int32_t n_b, const float* const* precond, gslm_lm_state* state,
@@ -918,6 +895,11 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     CKS(gslm_jacobi_diag(ctx, caches[i], ctx->lm_M.as<float>()));
     ctx->timer.end(t);
     const float* D = precond != nullptr ? precond[i] : nullptr;
+    if (D == nullptr && ctx->pc != nullptr) {
+      CK(ctx->lm_D.ensure(vb, st));
+      CKS(precond_for_cache(ctx->pc, ctx, caches[i], ctx->lm_M.as<float>(), ctx->lm_D.as<float>()));
+      D = ctx->lm_D.as<float>();
+    }
     CKS(pcg_enqueue(ctx, caches[i], ctx->lm_b.as<float>(), ctx->lm_M.as<float>(), D, lambda, ctx->lm_x.as<float>()));
     PcgScalars h;
     CK(cudaMemcpyAsync(&h, ctx->scalars.p, sizeof(h), cudaMemcpyDeviceToHost, st));

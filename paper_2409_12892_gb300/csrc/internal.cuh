@@ -30,6 +30,43 @@ constexpr float kDiagMin = 1e-6f;
 constexpr float kDiagMax = 1e32f;
 __host__ __device__ __forceinline__ float clamp_diag(float m) { return fminf(fmaxf(m, kDiagMin), kDiagMax); }
 
+// Stream-ordered device buffer.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p != nullptr) cudaFreeAsync(p, st);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t alloc(size_t n, cudaStream_t s) {
+    release();
+    st = s;
+    if (n == 0) n = 16;
+    const cudaError_t e = cudaMallocAsync(&p, n, s);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = n;
+    return cudaSuccess;
+  }
+  cudaError_t ensure(size_t n, cudaStream_t s) {
+    if (p != nullptr && bytes >= n) return cudaSuccess;
+    return alloc(n, s);
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+
 // Camera of one view of a call, with the view's place in the call's tile and
 // pixel index spaces.
 struct DevCam {
@@ -124,6 +161,11 @@ struct ContextParts {
   int device;
 };
 bool cache_parts(const gslm_cache* c, CacheParts* out);
+// out = (J^T J + lambda clamp(M)) v through the cache (api.cu).
+gslm_status apply_A(gslm_ctx* ctx, const gslm_cache* c, const float* v, const float* M, float lambda, float* out);
+cudaStream_t context_stream(const gslm_ctx* c);
+// D = the learned preconditioner of a cache's system with diagonal M (precond.cu).
+gslm_status precond_for_cache(gslm_precond* pc, gslm_ctx* ctx, const gslm_cache* c, const float* M, float* D);
 bool context_parts(const gslm_ctx* c, int cache_fmt, ContextParts* out);
 void set_context_error(gslm_ctx* c, const char* msg);
 

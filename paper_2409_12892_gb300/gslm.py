@@ -106,6 +106,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gslm_version": (ctypes.c_char_p, []),
         "gslm_kernel_launches": (c_int64, []),
         "gslm_autotune_info": (c_int32, [P, P, P]),
+        "gslm_apply_JT_noalloc": (c_int32, [P, P, P, P]),
+        "gslm_precond_weight_count": (c_int32, []),
+        "gslm_precond_create": (c_int32, [P, P, P, P, ctypes.c_uint64, P]),
+        "gslm_precond_free": (None, [P]),
+        "gslm_precond_get": (c_int32, [P, P, P, P]),
+        "gslm_precond_set": (c_int32, [P, P, P, P]),
+        "gslm_precond_features": (c_int32, [P, P, P, P]),
+        "gslm_precond_fit_standardizer": (c_int32, [P, P, c_int64]),
+        "gslm_precond_apply": (c_int32, [P, P, c_int64, c_int64, P, P]),
+        "gslm_precond_backward": (c_int32, [P, P, c_int64, c_int64, P, P, P, c_int32]),
+        "gslm_precond_unrolled_grad": (c_int32, [P, P, P, P, c_float, P, c_int32, P, P]),
+        "gslm_precond_accumulate": (c_int32, [P, P, P, P, P, c_float, c_int32, c_float, P]),
+        "gslm_precond_adam": (c_int32, [P, c_float]),
+        "gslm_set_precond": (c_int32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -123,7 +137,11 @@ def exported_symbols() -> list:
     return ["gslm_default_options", "gslm_create", "gslm_destroy", "gslm_last_error", "gslm_set_options",
             "gslm_render", "gslm_build_cache", "gslm_cache_stats", "gslm_cache_free", "gslm_apply_J",
             "gslm_apply_JT", "gslm_jacobi_diag", "gslm_pcg_solve", "gslm_combine_accumulate",
-            "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches", "gslm_autotune_info"]
+            "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches", "gslm_autotune_info",
+            "gslm_apply_JT_noalloc", "gslm_precond_weight_count", "gslm_precond_create", "gslm_precond_free",
+            "gslm_precond_get", "gslm_precond_set", "gslm_precond_features", "gslm_precond_fit_standardizer",
+            "gslm_precond_apply", "gslm_precond_backward", "gslm_precond_unrolled_grad",
+            "gslm_precond_accumulate", "gslm_precond_adam", "gslm_set_precond"]
 
 
 # ----------------------------------------------------------------------------- marshalling helpers
@@ -311,6 +329,25 @@ class Context:
     def combine_finish(self, n: int, num, den, delta):
         self._check(self.lib.gslm_combine_finish(self.h, n, num.shape[1], _ptr(num), _ptr(den), _ptr(delta)))
 
+    def precond_features(self, cache: Cache, diag, phi=None):
+        """Features [N][64] of the learned preconditioner for a cache's system."""
+        if phi is None:
+            phi = torch.empty((cache.n, 64), dtype=torch.float32, device=diag.device)
+        self._check(self.lib.gslm_precond_features(self.h, ctypes.c_void_p(cache.handle), _ptr(diag), _ptr(phi)))
+        return phi
+
+    def unrolled_grad(self, cache: Cache, b, diag, lam: float, D, K: int, want_grad=True):
+        """(L, dL/dD) of the K-iteration unrolled PCG residual for the diagonal D."""
+        loss = c_double(0.0)
+        dD = torch.zeros_like(D) if want_grad else None
+        self._check(self.lib.gslm_precond_unrolled_grad(self.h, ctypes.c_void_p(cache.handle), _ptr(b), _ptr(diag),
+                                                        float(lam), _ptr(D), int(K), ctypes.byref(loss), _ptr(dD)))
+        return loss.value, dD
+
+    def set_precond(self, pc: "Precond | None"):
+        """lm_step uses the network for subsets without an explicit preconditioner (None: Jacobi)."""
+        self._check(self.lib.gslm_set_precond(self.h, ctypes.c_void_p(pc.h if pc is not None else None)))
+
     def lm_step(self, params, n: int, cams, targets, subsets, lam: float, step: int = 0, precond=None):
         """One LM step. subsets: list of lists of camera indices. Returns (LMState, LMStats)."""
         ca = make_cameras(cams)
@@ -327,3 +364,79 @@ class Context:
                                           views, offs, len(subsets), pre, ctypes.byref(state),
                                           ctypes.byref(stats)))
         return state, stats
+
+
+def _host_f32(a, n: int):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, np.float32).ravel())
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+class Precond:
+    """The learned diagonal preconditioner (gslm_precond_*) on a context's device and stream."""
+
+    def __init__(self, ctx: Context, weights=None, mean=None, std=None, seed: int = 0):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.n_weights = int(self.lib.gslm_precond_weight_count())
+        w, m, s = _host_f32(weights, self.n_weights), _host_f32(mean, 64), _host_f32(std, 64)
+        h = ctypes.c_void_p()
+        f = lambda a: a.ctypes.data_as(c_void_p) if a is not None else None
+        ctx._check(self.lib.gslm_precond_create(ctx.h, f(w), f(m), f(s), ctypes.c_uint64(seed), ctypes.byref(h)))
+        self.h = h.value
+
+    def free(self):
+        if self.h:
+            self.lib.gslm_precond_free(ctypes.c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def get(self):
+        """(weights, mean, std) as float32 numpy arrays."""
+        w, m, s = np.empty(self.n_weights, np.float32), np.empty(64, np.float32), np.empty(64, np.float32)
+        self.ctx._check(self.lib.gslm_precond_get(ctypes.c_void_p(self.h), w.ctypes.data_as(c_void_p),
+                                                  m.ctypes.data_as(c_void_p), s.ctypes.data_as(c_void_p)))
+        return w, m, s
+
+    def set(self, weights=None, mean=None, std=None):
+        w, m, s = _host_f32(weights, self.n_weights), _host_f32(mean, 64), _host_f32(std, 64)
+        f = lambda a: a.ctypes.data_as(c_void_p) if a is not None else None
+        self.ctx._check(self.lib.gslm_precond_set(ctypes.c_void_p(self.h), f(w), f(m), f(s)))
+
+    def fit_standardizer(self, phi):
+        self.ctx._check(self.lib.gslm_precond_fit_standardizer(ctypes.c_void_p(self.h), _ptr(phi), phi.shape[0]))
+
+    def apply(self, phi, diag, D=None):
+        """D [59][ld] = softplus(net(phi)) / clamp(diag)."""
+        if D is None:
+            D = torch.zeros_like(diag)
+        self.ctx._check(self.lib.gslm_precond_apply(ctypes.c_void_p(self.h), _ptr(phi), phi.shape[0], diag.shape[1],
+                                                    _ptr(diag), _ptr(D)))
+        return D
+
+    def backward(self, phi, diag, dD, grad=None, accumulate=False):
+        """Weight gradient for the upstream dL/dD."""
+        if grad is None:
+            grad = torch.zeros(self.n_weights, dtype=torch.float32, device=diag.device)
+        self.ctx._check(self.lib.gslm_precond_backward(ctypes.c_void_p(self.h), _ptr(phi), phi.shape[0],
+                                                       diag.shape[1], _ptr(diag), _ptr(dD), _ptr(grad),
+                                                       int(bool(accumulate))))
+        return grad
+
+    def accumulate(self, cache: Cache, phi, b, diag, lam: float, K: int, weight: float = 1.0) -> float:
+        """Adds weight * dL/dweights of the unrolled loss on one system; returns L."""
+        loss = c_double(0.0)
+        self.ctx._check(self.lib.gslm_precond_accumulate(ctypes.c_void_p(self.h), ctypes.c_void_p(cache.handle),
+                                                         _ptr(phi), _ptr(b), _ptr(diag), float(lam), int(K),
+                                                         float(weight), ctypes.byref(loss)))
+        return loss.value
+
+    def adam(self, lr: float):
+        self.ctx._check(self.lib.gslm_precond_adam(ctypes.c_void_p(self.h), float(lr)))

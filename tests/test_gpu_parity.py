@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI (GPU only).
 
-Tolerances (stated by the task for the plain FP32 path):
+Tolerances of the plain FP32 path:
     rendered pixels   1e-5 absolute (pixels with a decision within 1e-5 of its threshold excluded)
     J p, J^T u        1e-4 relative L2
     PCG x             1e-3 relative L2 after a fixed number of iterations

@@ -1,0 +1,219 @@
+"""The learned diagonal preconditioner on the GPU against the oracle network (GPU only).
+
+Features, the network's D and weight gradient, and the reverse mode of the
+unrolled PCG residual are compared with oracle/mlp.py on the same inputs; a
+network trained on the GPU must then need fewer PCG iterations than Jacobi to
+reach a relative residual of 1e-3 on image subsets it was not trained on.
+"""
+import numpy as np
+import pytest
+
+import synth
+from common import N_PARAMS, rel_l2, tiny_case
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_12892_gb300 import build
+    build.build()
+    import paper_2409_12892_gb300 as g
+    return g
+
+
+def _soa(lib, a, ld):
+    """[N][59] float64 -> [59][ld] float32 CUDA tensor (zero pad)."""
+    out = np.zeros((N_PARAMS, ld), np.float32)
+    out[:, :a.shape[0]] = a.T
+    return torch.from_numpy(out).cuda()
+
+
+def _random_net(seed):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    net = mlp.init_mlp(seed)
+    net.W3 = rng.standard_normal(net.W3.shape) * 0.2
+    net.b3 = net.b3 + rng.standard_normal(net.b3.shape) * 0.2
+    return net
+
+
+def test_precond_weight_count_matches_the_oracle(lib):
+    from oracle import mlp
+    assert int(lib.load_library().gslm_precond_weight_count()) == mlp.N_WEIGHTS
+
+
+def test_precond_features_match_the_oracle(lib):
+    from oracle import jacobian as J, mlp
+    wl, P, cams, tgt = tiny_case()
+    N = P.shape[0]
+    lin = J.linearise(P.astype(np.float64), cams)
+    M = J.jacobi_diag(lin, N)
+    entries = np.zeros(N)
+    for vl in lin:
+        entries += np.bincount(vl.gauss, minlength=N)
+    ref = mlp.features(M, P, entries)
+    ctx = lib.Context()
+    cache = ctx.build_cache(lib.to_soa(P), N, cams, torch.from_numpy(tgt).cuda().view(-1, 3))
+    phi = ctx.precond_features(cache, ctx.jacobi_diag(cache)).cpu().numpy().astype(np.float64)
+    assert cache.info().entries == int(entries.sum())
+    np.testing.assert_array_equal(np.round(np.expm1(phi[:, 63])), entries)
+    np.testing.assert_allclose(phi[:, 59:63], ref[:, 59:63], rtol=1e-6, atol=1e-6)
+    # log(M + 1e-12): M to the J^T u bound where it is well above the offset
+    big = M > 1e-8
+    np.testing.assert_allclose(phi[:, :59][big], ref[:, :59][big], atol=1e-3)
+    assert np.abs(phi[:, :59] - ref[:, :59]).max() < 0.05
+    cache.free()
+
+
+@pytest.mark.parametrize("N", [1, 1000])
+def test_precond_apply_and_backward_match_the_oracle_network(lib, N):
+    from oracle import mlp
+    rng = np.random.default_rng(N)
+    net = _random_net(N)
+    phi = rng.normal(0.5, 2.0, (N, 64))
+    mu, sd = (phi.mean(0), np.maximum(phi.std(0), 1e-6)) if N > 1 else (np.zeros(64), np.ones(64))
+    M = np.exp(rng.normal(-3.0, 3.0, (N, 59)))
+    dD = rng.standard_normal((N, 59)) * M
+    ld = lib.padded_ld(N)
+    ctx = lib.Context()
+    pc = lib.Precond(ctx, weights=net.flat(), mean=mu, std=sd)
+    phi_d = torch.from_numpy(phi.astype(np.float32)).cuda()
+    D = pc.apply(phi_d, _soa(lib, M, ld))
+    D_ref = mlp.precond_diag(net, (phi - mu) / sd, M)
+    Dg = D.cpu().numpy()[:, :N].T
+    np.testing.assert_allclose(Dg, D_ref, rtol=2e-5)
+    g = pc.backward(phi_d, _soa(lib, M, ld), _soa(lib, dD, ld)).cpu().numpy()
+    g_ref = np.concatenate([x.ravel() for x in mlp.backward(net, (phi - mu) / sd, M, dD)])
+    assert rel_l2(g, g_ref) < 1e-4
+    g2 = pc.backward(phi_d, _soa(lib, M, ld), _soa(lib, dD, ld), grad=torch.from_numpy(g).cuda(), accumulate=True)
+    assert rel_l2(g2.cpu().numpy(), 2 * g_ref) < 1e-4
+    w, m, s = pc.get()
+    np.testing.assert_array_equal(w, net.flat().astype(np.float32))
+    pc.free()
+
+
+def test_precond_fit_standardizer_matches_numpy(lib):
+    rng = np.random.default_rng(3)
+    phi = rng.normal(1.0, 3.0, (5003, 64)).astype(np.float32)
+    ctx = lib.Context()
+    pc = lib.Precond(ctx)
+    pc.fit_standardizer(torch.from_numpy(phi).cuda())
+    _, m, s = pc.get()
+    np.testing.assert_allclose(m, phi.astype(np.float64).mean(0), rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(s, phi.astype(np.float64).std(0), rtol=1e-5)
+
+
+def test_default_network_is_the_jacobi_preconditioner(lib):
+    rng = np.random.default_rng(5)
+    N = 777
+    ld = lib.padded_ld(N)
+    M = np.exp(rng.normal(-5.0, 4.0, (N, 59)))
+    ctx = lib.Context()
+    pc = lib.Precond(ctx, seed=11)
+    D = pc.apply(torch.from_numpy(rng.standard_normal((N, 64)).astype(np.float32)).cuda(), _soa(lib, M, ld))
+    from oracle import solver
+    np.testing.assert_allclose(D.cpu().numpy()[:, :N].T, solver.jacobi_inverse(M), rtol=2e-6)
+
+
+@pytest.mark.parametrize("K", [1, 4, 8])
+def test_unrolled_grad_matches_the_oracle(lib, K):
+    from oracle import jacobian as J, mlp, solver
+    wl, P, cams, tgt = tiny_case()
+    N = P.shape[0]
+    lam = 1e-3
+    sys_ = solver.build_subset(P.astype(np.float64), cams, tgt.astype(np.float64))
+    Mc = solver.clamp_diag(sys_.M)
+    n_res = sys_.F.shape[0]
+    apply_A = lambda v: J.apply_JT(sys_.lin, J.apply_J(sys_.lin, v, n_res), N) + lam * Mc * v
+    d = np.exp(np.random.default_rng(K).normal(0.0, 0.5, (N, 59))) / Mc
+    L_ref, g_ref = mlp.unrolled_loss_and_grad(apply_A, sys_.b, d, K)
+    ctx = lib.Context()
+    cache = ctx.build_cache(lib.to_soa(P), N, cams, torch.from_numpy(tgt).cuda().view(-1, 3))
+    ld = cache.ld
+    L, dD = ctx.unrolled_grad(cache, _soa(lib, sys_.b, ld), _soa(lib, sys_.M, ld), lam, _soa(lib, d, ld), K)
+    assert abs(L - L_ref) < 1e-3
+    assert rel_l2(dD.cpu().numpy()[:, :N].T, g_ref) < 1e-3
+    cache.free()
+
+
+def _scene(seed, n=400, views=8, W=64, H=64):
+    from oracle import jacobian as J
+    wl = synth.small_workload("precond", seed, n, views, W, H, cam_radius=4.0)
+    P = synth.make_gaussians(wl)
+    cams = synth.make_cameras(wl)
+    tgt = J.render(synth.perturbed_copy(wl, P).astype(np.float64), cams)
+    tgt = (tgt + synth.pixel_noise(wl, tgt.size)).astype(np.float32)
+    return P, cams, tgt
+
+
+def _systems(lib, ctx, seed, subsets):
+    P, cams, tgt = _scene(seed)
+    offs = np.concatenate([[0], np.cumsum([c.width * c.height * 3 for c in cams])])
+    out = []
+    for vs in subsets:
+        t = np.concatenate([tgt[offs[v]:offs[v + 1]] for v in vs])
+        sc = [cams[v] for v in vs]
+        cache = ctx.build_cache(lib.to_soa(P), P.shape[0], sc, torch.from_numpy(t).cuda().view(-1, 3))
+        diag = ctx.jacobi_diag(cache)
+        out.append((cache, diag, ctx.precond_features(cache, diag)))
+    return out
+
+
+def _iters_to(ctx, cache, diag, lam, D=None, tol=1e-3, cap=3000):
+    ctx.set_options(n_iters=cap, break_rel2=tol * tol)
+    _, st, _ = ctx.pcg_solve(cache, cache.b, diag, lam, precond=D)
+    assert st.rr < tol * tol * st.bb * 1.0001
+    return st.iters
+
+
+def test_learned_preconditioner_needs_fewer_pcg_iterations_than_jacobi(lib):
+    lam, K = 1e-3, 16
+    ctx = lib.Context()
+    train = _systems(lib, ctx, 77, [[0, 1, 2, 3], [4, 5, 6, 7]]) + _systems(lib, ctx, 78, [[0, 1, 2, 3], [4, 5, 6, 7]])
+    test = _systems(lib, ctx, 79, [[0, 2, 4, 6], [1, 3, 5, 7]])
+    pc = lib.Precond(ctx, seed=0)
+    pc.fit_standardizer(torch.cat([phi for _, _, phi in train]))
+    losses = []
+    for step in range(120):
+        L = sum(pc.accumulate(c, phi, c.b, diag, lam, K, weight=1.0 / len(train)) for c, diag, phi in train)
+        losses.append(L / len(train))
+        pc.adam(1e-3)
+    assert losses[-1] < losses[0] - 0.3
+    ratios = []
+    for c, diag, phi in test:
+        it_j = _iters_to(ctx, c, diag, lam)
+        it_l = _iters_to(ctx, c, diag, lam, D=pc.apply(phi, diag))
+        ratios.append(it_l / it_j)
+        print(f"held-out subset: Jacobi {it_j} iterations, learned {it_l}")
+    print(f"unrolled loss {losses[0]:.3f} -> {losses[-1]:.3f}")
+    assert max(ratios) < 0.95, ratios
+    ctx.set_options(n_iters=8, break_rel2=0.01)
+
+
+def test_lm_step_uses_the_network_set_on_the_context(lib):
+    P, cams, tgt = _scene(80, views=4)
+    N = P.shape[0]
+    ctx = lib.Context(n_iters=8, break_rel2=0.0)
+    pc = lib.Precond(ctx, weights=_random_net(4).flat())
+    tg = torch.from_numpy(tgt).cuda().view(-1, 3)
+    cache = ctx.build_cache(lib.to_soa(P), N, cams, tg)
+    diag = ctx.jacobi_diag(cache)
+    D = pc.apply(ctx.precond_features(cache, diag), diag)
+    cache.free()
+    p1, p2 = lib.to_soa(P), lib.to_soa(P)
+    _, s1 = ctx.lm_step(p1, N, cams, tg, [list(range(len(cams)))], 1e-3, precond=[D])
+    ctx.set_precond(pc)
+    _, s2 = ctx.lm_step(p2, N, cams, tg, [list(range(len(cams)))], 1e-3)
+    ctx.set_precond(None)
+    _, s3 = ctx.lm_step(lib.to_soa(P), N, cams, tg, [list(range(len(cams)))], 1e-3)
+    # J p sums per pixel in a nondeterministic order, so the directions agree up to
+    # float32 rounding; the trial render's blending decisions can flip on that
+    assert abs(s1.predicted - s2.predicted) <= 1e-5 * abs(s1.predicted)
+    assert abs(s1.cost_new - s2.cost_new) <= 1e-3 * abs(s1.cost_new)
+    assert abs(s3.predicted - s2.predicted) > 1e-3 * abs(s2.predicted)
+    assert torch.allclose(p1, p2, rtol=1e-4, atol=1e-6)
