@@ -11,6 +11,7 @@
  *   gslm_apply_JT      g = J^T u  [Sec. A, Eq. apply-jt]
  *   gslm_jacobi_diag   M = diag(J^T J)  [Sec. A, Eq. diag-jtj]
  *   gslm_pcg_solve     Algorithm 1 on (J^T J + lambda M) x = b  [Sec. 3.3]
+ *   gslm_pcg_solve_batch  the same for several image subsets in lock step
  *   gslm_combine_*     weighted mean of subset directions [Eq. combine-pcg]
  *   gslm_lm_step       one LM iteration over image subsets [Sec. 3.2,
  *                      Eq. norm-eq, Eq. tr-update, Eq. combine-pcg]
@@ -84,7 +85,12 @@ typedef struct {
   int32_t profile;     /* 1: gslm_lm_step records CUDA events per phase (ms_phase in its stats) */
   int32_t autotune;    /* 1 (default): on first use per cache format, time every apply kernel
                           variant once on the real cache and keep the fastest; 0: fixed variant */
-  int32_t reserved[5];
+  int32_t batch;       /* 1 (default): gslm_lm_step solves all subsets in lock step, one launch per
+                          phase over every subset (gslm_pcg_solve_batch); 0: one subset after another */
+  int32_t graph;       /* 1 (default): a batched solve is captured into one CUDA graph and launched
+                          once (after the first batched solve of a context, which also autotunes) */
+  int32_t batch_ctas;  /* resident CTAs per SM of the persistent batched tile kernels; 0 = autotune */
+  int32_t reserved[2];
 } gslm_options;
 
 typedef struct gslm_ctx gslm_ctx;
@@ -200,6 +206,22 @@ gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* cache, float* diag
 gslm_status gslm_pcg_solve(gslm_ctx* ctx, const gslm_cache* cache, const float* b,
                            const float* diag, const float* precond, float lambda,
                            float* x, gslm_pcg_stats* stats);
+
+/* Algorithm 1 for the systems of n_b image subsets of the same Gaussians at
+ * once [Sec. 3.2-3.3]: the solves advance in lock step and each phase (tangent,
+ * J p, J^T u, adjoint, vector update, scalars) is one launch over every
+ * subset; the tile kernels are persistent and take the tiles of all subsets
+ * from one queue, so subsets of uneven size share the GPU. Each subset's
+ * arithmetic is that of gslm_pcg_solve, with its own break test. With
+ * options.graph the solve is replayed from one captured CUDA graph.
+ * caches, b, diag, precond (may be NULL, or hold NULL entries: Jacobi), x:
+ * host arrays of n_b entries (device vectors [59][ld] as in gslm_pcg_solve).
+ * All caches must share N, ld, cache format and mode. stats: host array of n_b
+ * or NULL. Synchronises. Returns GSLM_W_PCG_BREAKDOWN if any subset broke down. */
+gslm_status gslm_pcg_solve_batch(gslm_ctx* ctx, const gslm_cache* const* caches, int32_t n_b,
+                                 const float* const* b, const float* const* diag,
+                                 const float* const* precond, float lambda, float* const* x,
+                                 gslm_pcg_stats* stats);
 
 /* Eq. combine-pcg, accumulated subset by subset:
  * gslm_combine_accumulate: num += M_i * Delta_i, den += M_i;

@@ -88,6 +88,18 @@ struct gslm_ctx {
   Buf r, z, p, g, minv;
   Buf lm_num, lm_den, lm_delta, lm_trial, lm_x, lm_b, lm_M, lm_tgt, lm_img, lm_D;
   gslm_precond* pc = nullptr;       // learned preconditioner used by lm_step, if set
+  // batched solves: stacked per-subset vectors and per-subset scratch
+  Buf bt_b, bt_M, bt_D, bt_x, bt_r, bt_z, bt_p, bt_g, bt_minv, bt_u, bt_ydot, bt_segy, bt_part, bt_sc, bt_queue;
+  int bvar_J[3] = {-1, -1, -1};     // autotuned (variant, CTAs per SM) of the persistent tile kernels
+  int bvar_JT[3] = {-1, -1, -1};
+  int bctas_J[3] = {0, 0, 0};
+  int bctas_JT[3] = {0, 0, 0};
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_st = nullptr;    // private stream the batched solve is captured on
+  ~gslm_ctx() {
+    if (graph_exec != nullptr) cudaGraphExecDestroy(graph_exec);
+    if (cap_st != nullptr) cudaStreamDestroy(cap_st);
+  }
 };
 
 struct gslm_cache {
@@ -451,6 +463,240 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
   return GSLM_OK;
 }
 
+
+// Candidates of the persistent tile kernels' autotuner: (variant, CTAs per SM).
+constexpr int kBatchCand = 8;
+inline int cand_variant(int c) { return c / 2; }
+inline int cand_ctas(int c) {
+  const int cap = 6 - c / 2;   // resident CTAs the variant's registers allow: 6, 5, 4, 3
+  return (c & 1) ? cap - 1 : cap;
+}
+
+// Times every candidate once (each computes the same result) and keeps the fastest.
+template <class F>
+gslm_status tune_batch(gslm_ctx* ctx, F&& launch, int* var, int* ctas) {
+  cudaStream_t st = ctx->st;
+  std::vector<cudaEvent_t> ev(kBatchCand + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  struct Ev {
+    std::vector<cudaEvent_t>& v;
+    ~Ev() {
+      for (auto e : v) cudaEventDestroy(e);
+    }
+  } evg{ev};
+  CK(cudaEventRecord(ev[0], st));
+  for (int c = 0; c < kBatchCand; ++c) {
+    CKS(launch(cand_variant(c), cand_ctas(c)));
+    CK(cudaEventRecord(ev[c + 1], st));
+  }
+  CK(cudaEventSynchronize(ev[kBatchCand]));
+  int best = 2 * kDefaultVariant;
+  float best_ms = 1e30f;
+  for (int c = 0; c < kBatchCand; ++c) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ev[c], ev[c + 1]));
+    if (t < best_ms) {
+      best_ms = t;
+      best = c;
+    }
+  }
+  *var = cand_variant(best);
+  *ctas = cand_ctas(best);
+  return GSLM_OK;
+}
+
+// Stacked layout of a batch of n subsets of the same Gaussians.
+struct BatchLayout {
+  int n = 0;
+  long long vs = 0;                 // floats per stacked vector
+  long long u_off[kMaxBatch + 1];   // floats
+  long long y_off[kMaxBatch + 1];   // floats (ydot)
+  long long s_off[kMaxBatch + 1];   // floats (segment adjoints)
+};
+
+gslm_status batch_layout(gslm_ctx* ctx, const gslm_cache* const* cs, int n, BatchLayout* L) {
+  if (n < 1 || n > kMaxBatch) return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: 1 to 16 subsets per batch");
+  const gslm_cache* c0 = cs[0];
+  L->n = n;
+  L->vs = (long long)kNP * c0->ld;
+  L->u_off[0] = L->y_off[0] = L->s_off[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    const gslm_cache* c = cs[i];
+    if (c == nullptr) return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: null cache");
+    if (c->N != c0->N || c->ld != c0->ld || c->fmt != c0->fmt || c->smooth != c0->smooth || c->params == nullptr)
+      return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: caches differ in N, ld, format or mode");
+    auto up = [](long long v) { return (v + 3) & ~3ll; };   // 16-byte aligned sub-buffers
+    L->u_off[i + 1] = L->u_off[i] + up(3 * std::max<long long>(c->n_pix, 1));
+    L->y_off[i + 1] = L->y_off[i] + up(12 * std::max<long long>((long long)c->N * c->V, 1));
+    L->s_off[i + 1] = L->s_off[i] + up(12 * std::max<long long>(c->n_seg, 1));
+  }
+  return GSLM_OK;
+}
+
+gslm_status batch_alloc(gslm_ctx* ctx, const BatchLayout& L) {
+  cudaStream_t st = ctx->st;
+  const size_t vb = sizeof(float) * (size_t)L.vs * L.n;
+  for (Buf* b : {&ctx->bt_b, &ctx->bt_M, &ctx->bt_D, &ctx->bt_x, &ctx->bt_r, &ctx->bt_z, &ctx->bt_p, &ctx->bt_g,
+                 &ctx->bt_minv})
+    CK(b->ensure(vb, st));
+  CK(ctx->bt_u.ensure(sizeof(float) * L.u_off[L.n], st));
+  CK(ctx->bt_ydot.ensure(sizeof(float) * L.y_off[L.n], st));
+  CK(ctx->bt_segy.ensure(sizeof(float) * L.s_off[L.n], st));
+  return GSLM_OK;
+}
+
+// Enqueues Algorithm 1 for a batch whose stacked b, M (raw diagonal) and
+// optional D are in ctx->bt_b, bt_M, bt_D (subset i uses D when bit i of
+// d_mask is set); x ends in ctx->bt_x, the scalars in ctx->bt_sc[i]. Nothing
+// here synchronises unless `tune` (first use: the tile kernels are autotuned).
+gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const BatchLayout& L, unsigned d_mask,
+                              float lambda, bool tune) {
+  cudaStream_t st = ctx->st;
+  const gslm_cache* c0 = cs[0];
+  const int n = L.n, N = c0->N, fmt = c0->fmt;
+  const long long ld = c0->ld, vs = L.vs;
+  const int nvec = pcg_blocks(N), nvjp = vjp_blocks(N);
+  PcgScalars* sc = ctx->bt_sc.as<PcgScalars>();
+  double* part = ctx->bt_part.as<double>();
+  float *b = ctx->bt_b.as<float>(), *M = ctx->bt_M.as<float>(), *D = ctx->bt_D.as<float>();
+  float *x = ctx->bt_x.as<float>(), *r = ctx->bt_r.as<float>(), *z = ctx->bt_z.as<float>();
+  float *p = ctx->bt_p.as<float>(), *g = ctx->bt_g.as<float>(), *Minv = ctx->bt_minv.as<float>();
+  GaussBatch gb;
+  TileBatch tb;
+  gb.n = tb.n = n;
+  tb.fmt = fmt;
+  tb.queue = ctx->bt_queue.as<unsigned int>();
+  long long tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const gslm_cache* c = cs[i];
+    SubsetRefs& R = gb.s[i];
+    R.cams = c->cams.as<DevCam>();
+    R.V = c->V;
+    R.slot_active = c->slot_active.as<uint8_t>();
+    R.vmask = c->vmask.as<unsigned long long>();
+    R.s_start = c->slot_seg_start.as<uint32_t>();
+    R.s_end = c->slot_seg_end.as<uint32_t>();
+    R.s_list = c->slot_seg_list.as<uint32_t>();
+    R.ydot = ctx->bt_ydot.as<float>() + L.y_off[i];
+    R.seg_ybar = ctx->bt_segy.as<float>() + L.s_off[i];
+    tiles += c->n_tiles;
+    tb.tile_end[i] = tiles;
+    tb.v[i] = c->view();
+    tb.ydot[i] = R.ydot;
+    tb.u[i] = ctx->bt_u.as<float>() + L.u_off[i];
+    tb.seg_ybar[i] = R.seg_ybar;
+  }
+  tb.total_tiles = tiles;
+  const float* params = c0->params;
+  const int smooth = c0->smooth;
+  int& vJ = ctx->bvar_J[fmt];
+  int& vJT = ctx->bvar_JT[fmt];
+  int& cJ = ctx->bctas_J[fmt];
+  int& cJT = ctx->bctas_JT[fmt];
+  auto runJ = [&](int var, int ctas) -> gslm_status {
+    CK(cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st));
+    CK(launch_apply_J_batch(tb, var, ctas, st));
+    return GSLM_OK;
+  };
+  auto runJT = [&](int var, int ctas) -> gslm_status {
+    CK(cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st));
+    CK(launch_apply_JT_batch(tb, var, ctas, st));
+    return GSLM_OK;
+  };
+  auto apply_pair = [&]() -> gslm_status {
+    bool t = ctx->timer.begin(PH_APPLY_J);
+    if (vJ < 0 && tune) {
+      CKS(tune_batch(ctx, runJ, &vJ, &cJ));
+    } else {
+      CKS(runJ(vJ < 0 ? kDefaultVariant : vJ, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : (cJ > 0 ? cJ : 4)));
+    }
+    ctx->timer.end(t);
+    t = ctx->timer.begin(PH_APPLY_JT);
+    if (vJT < 0 && tune) {
+      CKS(tune_batch(ctx, runJT, &vJT, &cJT));
+    } else {
+      CKS(runJT(vJT < 0 ? kDefaultVariant : vJT,
+                ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : (cJT > 0 ? cJT : 4)));
+    }
+    ctx->timer.end(t);
+    return GSLM_OK;
+  };
+  // x0 = M^-1 b
+  bool t = ctx->timer.begin(PH_VEC);
+  CK(launch_pcg_init_batch(n, N, ld, vs, b, M, D, d_mask, x, Minv, part, st));
+  CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 0, ctx->opt.break_rel2, st));
+  ctx->timer.end(t);
+  // u0 = J x0; g0 = J^T u0; r0 = b - (g0 + lambda M x0); z0 = M^-1 r0; p0 = z0
+  for (int i = 0; i < n; ++i) tb.v[i].skip = nullptr;
+  t = ctx->timer.begin(PH_TANGENT);
+  CK(launch_tangent_batch(params, N, ld, smooth, gb, x, vs, nullptr, nullptr, nullptr, st));
+  ctx->timer.end(t);
+  CKS(apply_pair());
+  t = ctx->timer.begin(PH_VJP);
+  CK(launch_vjp_batch(params, N, ld, smooth, gb, g, vs, nullptr, nullptr, 0.f, nullptr, nullptr, st));
+  ctx->timer.end(t);
+  t = ctx->timer.begin(PH_VEC);
+  CK(launch_pcg_residual0_batch(n, N, ld, vs, b, g, M, x, lambda, Minv, r, z, p, part, st));
+  CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 1, ctx->opt.break_rel2, st));
+  ctx->timer.end(t);
+  for (int i = 0; i < n; ++i) tb.v[i].skip = &sc[i].done;
+  for (int it = 0; it < ctx->opt.n_iters; ++it) {
+    t = ctx->timer.begin(PH_TANGENT);
+    CK(launch_tangent_batch(params, N, ld, smooth, gb, p, vs, it > 0 ? z : nullptr, it > 0 ? p : nullptr, sc, st));
+    ctx->timer.end(t);
+    CKS(apply_pair());
+    t = ctx->timer.begin(PH_VJP);
+    CK(launch_vjp_batch(params, N, ld, smooth, gb, g, vs, p, M, lambda, part, sc, st));
+    ctx->timer.end(t);
+    t = ctx->timer.begin(PH_VEC);
+    CK(launch_pcg_scalars_batch(n, sc, part, nvjp, nvjp, 2, ctx->opt.break_rel2, st));
+    CK(launch_pcg_update_batch(n, N, ld, vs, sc, p, g, Minv, x, r, z, part, st));
+    CK(launch_pcg_scalars_batch(n, sc, part, nvec, 2 * nvec, 3, ctx->opt.break_rel2, st));
+    ctx->timer.end(t);
+  }
+  return GSLM_OK;
+}
+
+// Runs a batch whose inputs are already stacked: directly the first time (it
+// autotunes), from one captured CUDA graph afterwards when options.graph is
+// set and no per-phase profile is wanted.
+gslm_status pcg_batch_run(gslm_ctx* ctx, const gslm_cache* const* cs, const BatchLayout& L, unsigned d_mask,
+                          float lambda) {
+  cudaStream_t st = ctx->st;
+  const int fmt = cs[0]->fmt;
+  const int N = cs[0]->N;
+  CK(ctx->bt_part.ensure(sizeof(double) * L.n * std::max(2 * pcg_blocks(N), vjp_blocks(N)), st));
+  CK(ctx->bt_sc.ensure(sizeof(PcgScalars) * L.n, st));
+  CK(ctx->bt_queue.ensure(sizeof(unsigned int), st));
+  const bool tuned = !ctx->opt.autotune || (ctx->bvar_J[fmt] >= 0 && ctx->bvar_JT[fmt] >= 0);
+  const bool use_graph = ctx->opt.graph && tuned && !ctx->timer.on;
+  if (!use_graph) return pcg_batch_enqueue(ctx, cs, L, d_mask, lambda, !tuned);
+  if (ctx->graph_exec != nullptr) {
+    CK(cudaGraphExecDestroy(ctx->graph_exec));
+    ctx->graph_exec = nullptr;
+  }
+  // Capture on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured); the graph is launched on the caller's.
+  if (ctx->cap_st == nullptr) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+  (void)device_sm_count();
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+  ctx->st = ctx->cap_st;
+  const gslm_status s = pcg_batch_enqueue(ctx, cs, L, d_mask, lambda, false);
+  ctx->st = st;
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap_st, &graph);
+  if (s != GSLM_OK) {
+    if (graph != nullptr) cudaGraphDestroy(graph);
+    return s;
+  }
+  CK(e);
+  const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(ei);
+  CK(cudaGraphLaunch(ctx->graph_exec, st));
+  return GSLM_OK;
+}
+
 }  // namespace
 
 namespace gslm {
@@ -522,6 +768,9 @@ void gslm_default_options(gslm_options* o) {
   o->group = 32;
   o->profile = 0;
   o->autotune = 1;
+  o->batch = 1;
+  o->graph = 1;
+  o->batch_ctas = 0;
 }
 
 static gslm_status validate_opts(const gslm_options* o) {
@@ -787,6 +1036,54 @@ gslm_status gslm_pcg_solve(gslm_ctx* ctx, const gslm_cache* c, const float* b, c
   return GSLM_OK;
 }
 
+gslm_status gslm_pcg_solve_batch(gslm_ctx* ctx, const gslm_cache* const* caches, int32_t n_b, const float* const* b,
+                                 const float* const* diag, const float* const* D, float lambda, float* const* x,
+                                 gslm_pcg_stats* stats) {
+  if (ctx == nullptr) return GSLM_E_INVALID;
+  if (caches == nullptr || b == nullptr || diag == nullptr || x == nullptr || n_b < 1)
+    return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: null argument or no subsets");
+  for (int i = 0; i < n_b; ++i)
+    if (caches[i] == nullptr || b[i] == nullptr || diag[i] == nullptr || x[i] == nullptr)
+      return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: null entry");
+  cudaStream_t st = ctx->st;
+  bool breakdown = false;
+  for (int g0 = 0; g0 < n_b; g0 += kMaxBatch) {
+    const int gn = std::min(kMaxBatch, n_b - g0);
+    BatchLayout L;
+    CKS(batch_layout(ctx, caches + g0, gn, &L));
+    if (caches[g0]->N != caches[0]->N || caches[g0]->ld != caches[0]->ld)
+      return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: caches differ in N or ld");
+    CKS(batch_alloc(ctx, L));
+    const size_t vb = sizeof(float) * (size_t)L.vs;
+    unsigned mask = 0;
+    for (int k = 0; k < gn; ++k) {
+      const int i = g0 + k;
+      CK(cudaMemcpyAsync(ctx->bt_b.as<float>() + k * L.vs, b[i], vb, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ctx->bt_M.as<float>() + k * L.vs, diag[i], vb, cudaMemcpyDeviceToDevice, st));
+      if (D != nullptr && D[i] != nullptr) {
+        CK(cudaMemcpyAsync(ctx->bt_D.as<float>() + k * L.vs, D[i], vb, cudaMemcpyDeviceToDevice, st));
+        mask |= 1u << k;
+      }
+    }
+    CKS(pcg_batch_run(ctx, caches + g0, L, mask, lambda));
+    for (int k = 0; k < gn; ++k)
+      CK(cudaMemcpyAsync(x[g0 + k], ctx->bt_x.as<float>() + k * L.vs, vb, cudaMemcpyDeviceToDevice, st));
+    std::vector<PcgScalars> h(gn);
+    CK(cudaMemcpyAsync(h.data(), ctx->bt_sc.p, sizeof(PcgScalars) * gn, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int k = 0; k < gn; ++k) {
+      breakdown |= h[k].breakdown != 0;
+      if (stats != nullptr) {
+        stats[g0 + k].iters = h[k].iters;
+        stats[g0 + k].breakdown = h[k].breakdown;
+        stats[g0 + k].rr = h[k].rr;
+        stats[g0 + k].bb = h[k].bb;
+      }
+    }
+  }
+  return breakdown ? GSLM_W_PCG_BREAKDOWN : GSLM_OK;
+}
+
 gslm_status gslm_combine_accumulate(gslm_ctx* ctx, int64_t N, int64_t ld, const float* d, const float* m, float* num,
                                     float* den) {
   CKS(check_vec_args(ctx, N, ld));
@@ -862,55 +1159,93 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   } toff{ctx->timer};
   long long entries = 0, bytes = 0;
   const float lambda = state->lambda;
-  for (int i = 0; i < n_b; ++i) {
-    const int a = subset_off[i], e = subset_off[i + 1];
-    if (e <= a) return fail(ctx, GSLM_E_INVALID, "lm_step: empty subset");
-    long long pix = 0;
-    for (int k = a; k < e; ++k) {
-      const int v = subset_views[k];
-      if (v < 0 || v >= n_cams) return fail(ctx, GSLM_E_INVALID, "lm_step: bad camera index");
-      scams[i].push_back(cams[v]);
-      pix += (long long)cams[v].width * cams[v].height;
+  const bool batched = ctx->opt.batch != 0;
+  const long long vsn = (long long)kNP * ld;
+  for (int g0 = 0; g0 < n_b; g0 += batched ? kMaxBatch : 1) {
+    const int gn = batched ? std::min(kMaxBatch, n_b - g0) : 1;
+    if (batched) {
+      CK(ctx->bt_b.ensure(vb * gn, st));
+      CK(ctx->bt_M.ensure(vb * gn, st));
+      CK(ctx->bt_D.ensure(vb * gn, st));
     }
-    CK(stg[i].alloc(sizeof(float) * 3 * pix, st));
-    long long o = 0;
-    for (int k = a; k < e; ++k) {
-      const int v = subset_views[k];
-      const long long np = cam_pix[v + 1] - cam_pix[v];
-      CK(cudaMemcpyAsync(stg[i].as<float>() + 3 * o, targets + 3 * cam_pix[v], sizeof(float) * 3 * np,
-                         cudaMemcpyDeviceToDevice, st));
-      o += np;
+    unsigned dmask = 0;
+    for (int k = 0; k < gn; ++k) {
+      const int i = g0 + k;
+      const int a = subset_off[i], e = subset_off[i + 1];
+      if (e <= a) return fail(ctx, GSLM_E_INVALID, "lm_step: empty subset");
+      long long pix = 0;
+      for (int q = a; q < e; ++q) {
+        const int v = subset_views[q];
+        if (v < 0 || v >= n_cams) return fail(ctx, GSLM_E_INVALID, "lm_step: bad camera index");
+        scams[i].push_back(cams[v]);
+        pix += (long long)cams[v].width * cams[v].height;
+      }
+      CK(stg[i].alloc(sizeof(float) * 3 * pix, st));
+      long long o = 0;
+      for (int q = a; q < e; ++q) {
+        const int v = subset_views[q];
+        const long long np = cam_pix[v + 1] - cam_pix[v];
+        CK(cudaMemcpyAsync(stg[i].as<float>() + 3 * o, targets + 3 * cam_pix[v], sizeof(float) * 3 * np,
+                           cudaMemcpyDeviceToDevice, st));
+        o += np;
+      }
+      float* bi = batched ? ctx->bt_b.as<float>() + k * vsn : ctx->lm_b.as<float>();
+      float* Mi = batched ? ctx->bt_M.as<float>() + k * vsn : ctx->lm_M.as<float>();
+      double ci = 0.0;
+      bool t = ctx->timer.begin(PH_BUILD);
+      CKS(gslm_build_cache(ctx, params, N, ld, scams[i].data(), (int)scams[i].size(), stg[i].as<float>(),
+                           &caches[i], nullptr, bi, &ci));
+      ctx->timer.end(t);
+      cost0 += ci;
+      entries += caches[i]->n_entries;
+      segs += caches[i]->n_seg;
+      actives += caches[i]->n_active;
+      bytes += (long long)caches[i]->device_bytes();
+      t = ctx->timer.begin(PH_DIAG);
+      CKS(gslm_jacobi_diag(ctx, caches[i], Mi));
+      ctx->timer.end(t);
+      const float* D = precond != nullptr ? precond[i] : nullptr;
+      float* Dslot = batched ? ctx->bt_D.as<float>() + k * vsn : nullptr;
+      if (D == nullptr && ctx->pc != nullptr) {
+        if (!batched) CK(ctx->lm_D.ensure(vb, st));
+        float* Dout = batched ? Dslot : ctx->lm_D.as<float>();
+        CKS(precond_for_cache(ctx->pc, ctx, caches[i], Mi, Dout));
+        D = Dout;
+      } else if (D != nullptr && batched) {
+        CK(cudaMemcpyAsync(Dslot, D, vb, cudaMemcpyDeviceToDevice, st));
+      }
+      if (D != nullptr) dmask |= 1u << k;
+      if (batched) continue;
+      CKS(pcg_enqueue(ctx, caches[i], bi, Mi, D, lambda, ctx->lm_x.as<float>()));
+      PcgScalars h;
+      CK(cudaMemcpyAsync(&h, ctx->scalars.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+      CK(launch_combine_acc((int)N, ld, ctx->lm_x.as<float>(), Mi, ctx->lm_num.as<float>(), ctx->lm_den.as<float>(),
+                            st));
+      CK(cudaStreamSynchronize(st));
+      pcg_iters += h.iters;
+      const gslm_cache* c = caches[i];
+      n_pairs += 1 + h.iters;
+      pair_bytes += (1.0 + h.iters) * (2.0 * (double)c->n_entries * (double)(payload_bytes(c->fmt) + 1) +
+                                       24.0 * (double)c->n_pix + 472.0 * (double)N + 192.0 * (double)c->n_active);
     }
-    double ci = 0.0;
-    bool t = ctx->timer.begin(PH_BUILD);
-    CKS(gslm_build_cache(ctx, params, N, ld, scams[i].data(), (int)scams[i].size(), stg[i].as<float>(), &caches[i],
-                         nullptr, ctx->lm_b.as<float>(), &ci));
-    ctx->timer.end(t);
-    cost0 += ci;
-    entries += caches[i]->n_entries;
-    segs += caches[i]->n_seg;
-    actives += caches[i]->n_active;
-    bytes += (long long)caches[i]->device_bytes();
-    t = ctx->timer.begin(PH_DIAG);
-    CKS(gslm_jacobi_diag(ctx, caches[i], ctx->lm_M.as<float>()));
-    ctx->timer.end(t);
-    const float* D = precond != nullptr ? precond[i] : nullptr;
-    if (D == nullptr && ctx->pc != nullptr) {
-      CK(ctx->lm_D.ensure(vb, st));
-      CKS(precond_for_cache(ctx->pc, ctx, caches[i], ctx->lm_M.as<float>(), ctx->lm_D.as<float>()));
-      D = ctx->lm_D.as<float>();
-    }
-    CKS(pcg_enqueue(ctx, caches[i], ctx->lm_b.as<float>(), ctx->lm_M.as<float>(), D, lambda, ctx->lm_x.as<float>()));
-    PcgScalars h;
-    CK(cudaMemcpyAsync(&h, ctx->scalars.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-    CK(launch_combine_acc((int)N, ld, ctx->lm_x.as<float>(), ctx->lm_M.as<float>(), ctx->lm_num.as<float>(),
-                          ctx->lm_den.as<float>(), st));
+    if (!batched) continue;
+    BatchLayout L;
+    CKS(batch_layout(ctx, caches.data() + g0, gn, &L));
+    CKS(batch_alloc(ctx, L));
+    CKS(pcg_batch_run(ctx, caches.data() + g0, L, dmask, lambda));
+    std::vector<PcgScalars> h(gn);
+    CK(cudaMemcpyAsync(h.data(), ctx->bt_sc.p, sizeof(PcgScalars) * gn, cudaMemcpyDeviceToHost, st));
+    for (int k = 0; k < gn; ++k)
+      CK(launch_combine_acc((int)N, ld, ctx->bt_x.as<float>() + k * vsn, ctx->bt_M.as<float>() + k * vsn,
+                            ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), st));
     CK(cudaStreamSynchronize(st));
-    pcg_iters += h.iters;
-    const gslm_cache* c = caches[i];
-    n_pairs += 1 + h.iters;
-    pair_bytes += (1.0 + h.iters) * (2.0 * (double)c->n_entries * (double)(payload_bytes(c->fmt) + 1) +
-                                     24.0 * (double)c->n_pix + 472.0 * (double)N + 192.0 * (double)c->n_active);
+    for (int k = 0; k < gn; ++k) {
+      const gslm_cache* c = caches[g0 + k];
+      pcg_iters += h[k].iters;
+      n_pairs += 1 + h[k].iters;
+      pair_bytes += (1.0 + h[k].iters) * (2.0 * (double)c->n_entries * (double)(payload_bytes(c->fmt) + 1) +
+                                          24.0 * (double)c->n_pix + 472.0 * (double)N + 192.0 * (double)c->n_active);
+    }
   }
   CK(launch_combine_finish((int)N, ld, ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), ctx->lm_delta.as<float>(),
                            st));

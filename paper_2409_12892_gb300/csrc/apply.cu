@@ -147,40 +147,32 @@ __device__ __forceinline__ Tangent load_tangent(const float* __restrict__ ydot, 
   return t;
 }
 
-template <int kFmt, int U, int kMinBlocks>
-__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, const float* __restrict__ ydot,
-                                                                  const float* __restrict__ Fadd,
-                                                                  float* __restrict__ u,
-                                                                  double* __restrict__ sq_partials) {
-  __shared__ float su[3 * (kTilePix + kTilePix / 32)];
-  __shared__ float2 sxy[kTilePix];   // tile-local pixel coordinates (x, y) of pixel p
-  __shared__ double dred[kWarps];
-  __shared__ unsigned int next_seg;
-  if (cv.skip != nullptr && *cv.skip) return;
-  sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
-  const int tile = blockIdx.x;
+// J p over one tile. su (u of the tile, padded planes) must be zero and
+// *next_seg zero on entry, sxy filled; the caller synchronises before.
+template <int kFmt, int U>
+__device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, const float* __restrict__ ydot,
+                                             const float* __restrict__ Fadd, float* __restrict__ u,
+                                             double* __restrict__ sq_partials, float* su, const float2* sxy,
+                                             double* dred, unsigned int* next_seg) {
   const int v = find_view(cv.cams, cv.V, tile);
   const DevCam& cam = cv.cams[v];
   const int lt = tile - cam.tile_off;
   const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
-  for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
-  if (threadIdx.x == 0) next_seg = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t g0 = cv.tile_seg_off[tile];
   const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
-  uint32_t k = grab(&next_seg);
+  uint32_t k = grab(next_seg);
   SegRec cur, nxt;
   Tangent t;
   if (k < n) {
     cur = load_rec(cv.seg_rec + g0 + k);
     t = load_tangent(ydot, cur.slot, cur.io);
   }
-  uint32_t kn = grab(&next_seg);
+  uint32_t kn = grab(next_seg);
   if (kn < n) nxt = load_rec(cv.seg_rec + g0 + kn);
   while (k < n) {
     // prefetch: the record after next, and the next segment's tangent
-    const uint32_t kn2 = grab(&next_seg);
+    const uint32_t kn2 = grab(next_seg);
     SegRec nxt2;
     if (kn2 < n) nxt2 = load_rec(cv.seg_rec + g0 + kn2);
     Tangent tn;
@@ -251,6 +243,57 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, 
   }
 }
 
+#define APPLY_J_SHARED                                   \
+  __shared__ float su[3 * (kTilePix + kTilePix / 32)];   \
+  __shared__ float2 sxy[kTilePix];                       \
+  __shared__ double dred[kWarps];                        \
+  __shared__ unsigned int next_seg;                      \
+  sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
+
+template <int kFmt, int U, int kMinBlocks>
+__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, const float* __restrict__ ydot,
+                                                                  const float* __restrict__ Fadd,
+                                                                  float* __restrict__ u,
+                                                                  double* __restrict__ sq_partials) {
+  if (cv.skip != nullptr && *cv.skip) return;
+  APPLY_J_SHARED
+  for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
+  if (threadIdx.x == 0) next_seg = 0;
+  __syncthreads();
+  apply_J_tile<kFmt, U>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg);
+}
+
+// Subset of a global tile index of a batch.
+__device__ __forceinline__ int batch_subset(const TileBatch& tb, long long gt) {
+  int b = 0;
+  while (b + 1 < tb.n && gt >= tb.tile_end[b]) ++b;
+  return b;
+}
+
+// Persistent J p over every subset of a batch: each CTA takes tiles from the
+// batch's queue until all are done (tiles of finished solves are skipped).
+template <int kFmt, int U, int kMinBlocks>
+__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J_batch(const __grid_constant__ TileBatch tb) {
+  APPLY_J_SHARED
+  __shared__ long long s_tile;
+  for (;;) {
+    for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
+    if (threadIdx.x == 0) {
+      next_seg = 0;
+      s_tile = (long long)atomicAdd(tb.queue, 1u);
+    }
+    __syncthreads();
+    const long long gt = s_tile;
+    if (gt >= tb.total_tiles) break;
+    const int b = batch_subset(tb, gt);
+    const CacheView& cv = tb.v[b];
+    if (cv.skip == nullptr || *cv.skip == 0)
+      apply_J_tile<kFmt, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
+                            nullptr, su, sxy, dred, &next_seg);
+    __syncthreads();
+  }
+}
+
 // One step of a recursive-halving reduction: lanes whose `upper` bit is set keep
 // the upper half of their N values, the others the lower half; each kept value
 // gains the partner lane's matching value.
@@ -275,14 +318,12 @@ __device__ __forceinline__ void warp_sum16(float (&v)[16], int lane) {
   v[0] += __shfl_xor_sync(kFull, v[0], 1);
 }
 
-template <int kFmt, int U, int kMinBlocks>
-__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv, const float* __restrict__ u,
-                                                                   float* __restrict__ seg_ybar) {
-  __shared__ float4 su4[kTilePix];
-  __shared__ float2 sxy[kTilePix];
-  __shared__ unsigned int next_seg;
-  if (cv.skip != nullptr && *cv.skip) return;
-  const int tile = blockIdx.x;
+// J^T u over one tile into per-segment partials. *next_seg must be zero on
+// entry; the caller synchronises before. sxy is filled here.
+template <int kFmt, int U>
+__device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, const float* __restrict__ u,
+                                              float* __restrict__ seg_ybar, float4* su4, float2* sxy,
+                                              unsigned int* next_seg) {
   const uint32_t g0 = cv.tile_seg_off[tile];
   const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
   if (n == 0) return;
@@ -300,14 +341,13 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv,
     su4[threadIdx.x] = uv;
     sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
   }
-  if (threadIdx.x == 0) next_seg = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  uint32_t k = grab(&next_seg);
+  uint32_t k = grab(next_seg);
   SegRec cur;
   if (k < n) cur = load_rec(cv.seg_rec + g0 + k);
   while (k < n) {
-    const uint32_t kn = grab(&next_seg);
+    const uint32_t kn = grab(next_seg);
     SegRec nxt;
     if (kn < n) nxt = load_rec(cv.seg_rec + g0 + kn);
     // moments of s = h . u over the segment's pixels (tile-local offsets from
@@ -370,6 +410,41 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv,
     }
     k = kn;
     cur = nxt;
+  }
+}
+
+template <int kFmt, int U, int kMinBlocks>
+__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv, const float* __restrict__ u,
+                                                                   float* __restrict__ seg_ybar) {
+  __shared__ float4 su4[kTilePix];
+  __shared__ float2 sxy[kTilePix];
+  __shared__ unsigned int next_seg;
+  if (cv.skip != nullptr && *cv.skip) return;
+  if (threadIdx.x == 0) next_seg = 0;
+  apply_JT_tile<kFmt, U>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg);
+}
+
+// Persistent J^T u over every subset of a batch (see k_apply_J_batch).
+template <int kFmt, int U, int kMinBlocks>
+__global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const __grid_constant__ TileBatch tb) {
+  __shared__ float4 su4[kTilePix];
+  __shared__ float2 sxy[kTilePix];
+  __shared__ unsigned int next_seg;
+  __shared__ long long s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      next_seg = 0;
+      s_tile = (long long)atomicAdd(tb.queue, 1u);
+    }
+    __syncthreads();
+    const long long gt = s_tile;
+    if (gt >= tb.total_tiles) break;
+    const int b = batch_subset(tb, gt);
+    const CacheView& cv = tb.v[b];
+    if (cv.skip == nullptr || *cv.skip == 0)
+      apply_JT_tile<kFmt, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.u[b], tb.seg_ybar[b], su4, sxy,
+                             &next_seg);
+    __syncthreads();
   }
 }
 
@@ -446,6 +521,40 @@ cudaError_t run_JT(const CacheView& cv, const float* u, float* seg_ybar, cudaStr
   return cudaGetLastError();
 }
 
+template <int kFmt, int U, int B>
+cudaError_t run_J_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
+  k_apply_J_batch<kFmt, U, B><<<ctas, kTilePix, 0, st>>>(tb);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int kFmt, int U, int B>
+cudaError_t run_JT_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
+  k_apply_JT_batch<kFmt, U, B><<<ctas, kTilePix, 0, st>>>(tb);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int kFmt>
+cudaError_t apply_J_batch_variant(int variant, const TileBatch& tb, int ctas, cudaStream_t st) {
+  switch (variant) {
+    case 0: return run_J_batch<kFmt, 1, 6>(tb, ctas, st);
+    case 1: return run_J_batch<kFmt, 2, 5>(tb, ctas, st);
+    case 2: return run_J_batch<kFmt, 4, 4>(tb, ctas, st);
+    default: return run_J_batch<kFmt, 8, 3>(tb, ctas, st);
+  }
+}
+
+template <int kFmt>
+cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, cudaStream_t st) {
+  switch (variant) {
+    case 0: return run_JT_batch<kFmt, 1, 6>(tb, ctas, st);
+    case 1: return run_JT_batch<kFmt, 2, 5>(tb, ctas, st);
+    case 2: return run_JT_batch<kFmt, 4, 4>(tb, ctas, st);
+    default: return run_JT_batch<kFmt, 8, 3>(tb, ctas, st);
+  }
+}
+
 template <int kFmt>
 cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot, const float* F_add, float* u,
                             double* sq, cudaStream_t st) {
@@ -486,6 +595,42 @@ cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar
   if (cv.fmt == GSLM_CACHE_FP32) return apply_JT_variant<GSLM_CACHE_FP32>(variant, cv, u, seg_ybar, st);
   if (cv.fmt == GSLM_CACHE_BF16) return apply_JT_variant<GSLM_CACHE_BF16>(variant, cv, u, seg_ybar, st);
   return apply_JT_variant<GSLM_CACHE_FP16S>(variant, cv, u, seg_ybar, st);
+}
+
+int device_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Resident CTAs of a persistent grid: never more than the kernel variant's
+// register budget lets share an SM (6, 5, 4, 3 for variants 0..3), never more
+// CTAs than tiles.
+static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
+  const int cap = variant == 0 ? 6 : variant == 1 ? 5 : variant == 2 ? 4 : 3;
+  const int per = ctas_per_sm < 1 ? 1 : (ctas_per_sm > cap ? cap : ctas_per_sm);
+  const long long c = (long long)device_sm_count() * per;
+  return (int)(c < tb.total_tiles ? c : tb.total_tiles);
+}
+
+cudaError_t launch_apply_J_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st) {
+  if (tb.n <= 0 || tb.total_tiles <= 0) return cudaSuccess;
+  const int ctas = batch_ctas(tb, variant, ctas_per_sm);
+  if (tb.fmt == GSLM_CACHE_FP32) return apply_J_batch_variant<GSLM_CACHE_FP32>(variant, tb, ctas, st);
+  if (tb.fmt == GSLM_CACHE_BF16) return apply_J_batch_variant<GSLM_CACHE_BF16>(variant, tb, ctas, st);
+  return apply_J_batch_variant<GSLM_CACHE_FP16S>(variant, tb, ctas, st);
+}
+
+cudaError_t launch_apply_JT_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st) {
+  if (tb.n <= 0 || tb.total_tiles <= 0) return cudaSuccess;
+  const int ctas = batch_ctas(tb, variant, ctas_per_sm);
+  if (tb.fmt == GSLM_CACHE_FP32) return apply_JT_batch_variant<GSLM_CACHE_FP32>(variant, tb, ctas, st);
+  if (tb.fmt == GSLM_CACHE_BF16) return apply_JT_batch_variant<GSLM_CACHE_BF16>(variant, tb, ctas, st);
+  return apply_JT_batch_variant<GSLM_CACHE_FP16S>(variant, tb, ctas, st);
 }
 
 cudaError_t launch_diag_entries(const CacheView& cv, float* seg_q, cudaStream_t st) {

@@ -146,6 +146,44 @@ struct CacheView {
 void note_launch();
 
 // Views of a cache and of a context for entry points defined outside api.cu.
+// ----------------------------------------------------------------------------
+// Batched solves: the PCG solves of up to kMaxBatch image subsets advance in
+// lock step, each phase one launch over every subset. Parameter-space vectors
+// of the subsets are stacked with a fixed stride (vs floats); float64 partials
+// with a fixed stride per subset; one PcgScalars per subset.
+constexpr int kMaxBatch = 16;
+
+// Per-subset geometry and per-subset buffers of the per-Gaussian kernels.
+struct SubsetRefs {
+  const DevCam* cams;
+  int V;
+  const uint8_t* slot_active;           // [N * V]
+  const unsigned long long* vmask;      // [N] or null
+  const uint32_t* s_start;              // segments of a slot (vjp)
+  const uint32_t* s_end;
+  const uint32_t* s_list;
+  float* ydot;                          // [N * V][12] splat tangents
+  float* seg_ybar;                      // [n_seg][12] per-segment adjoints
+};
+struct GaussBatch {
+  int n;
+  SubsetRefs s[kMaxBatch];
+};
+
+// The tile kernels' view of a batch: subset b owns the global tiles
+// [tile_end[b - 1], tile_end[b]).
+struct TileBatch {
+  int n;
+  int fmt;
+  long long total_tiles;
+  long long tile_end[kMaxBatch];
+  CacheView v[kMaxBatch];
+  const float* ydot[kMaxBatch];
+  float* u[kMaxBatch];
+  float* seg_ybar[kMaxBatch];
+  unsigned int* queue;      // persistent mode: global tile counter (zero at launch)
+};
+
 struct CacheParts {
   CacheView view;
   const float* params;
@@ -195,6 +233,14 @@ cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* 
                         const uint32_t* slot_seg_list, const unsigned long long* vmask,
                         const float* seg_q, float* diag, cudaStream_t st);
 int vjp_blocks(int N);
+// Batched forms: blockIdx.y = subset; p, z, pout, g, M stacked with stride vs;
+// scalars sc[b]; vjp partials at partials + b * vjp_blocks(N).
+cudaError_t launch_tangent_batch(const float* params, int N, long long ld, int smooth, const GaussBatch& gb,
+                                 const float* p, long long vs, const float* z_beta, float* p_out,
+                                 const PcgScalars* sc, cudaStream_t st);
+cudaError_t launch_vjp_batch(const float* params, int N, long long ld, int smooth, const GaussBatch& gb,
+                             float* g, long long vs, const float* p, const float* M, float lambda,
+                             double* partials, const PcgScalars* sc, cudaStream_t st);
 
 // sort.cu
 size_t scan_temp_bytes(long long n);
@@ -245,6 +291,11 @@ cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar
                             cudaStream_t st);
 cudaError_t launch_diag_entries(const CacheView& cv, float* seg_q, cudaStream_t st);
 int apply_J_partials(const CacheView& cv);
+// Batched persistent forms: `ctas_per_sm` resident CTAs per SM take the tiles
+// of every subset from tb.queue (which must be zero at launch).
+cudaError_t launch_apply_J_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st);
+cudaError_t launch_apply_JT_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st);
+int device_sm_count();
 
 // pcg.cu
 cudaError_t launch_reduce_partials(const double* partials, int n, double* out, cudaStream_t st);
@@ -260,6 +311,21 @@ cudaError_t launch_pcg_update(int N, long long ld, const PcgScalars* sc, const f
                               const float* g, const float* Minv, float* x, float* r, float* z,
                               double* partials, cudaStream_t st);
 int pcg_blocks(int N);
+// Batched forms: n subsets, grid (pcg_blocks(N), n); vectors at stride vs,
+// partials at stride pcg_blocks(N) (update: 2 * pcg_blocks(N)), scalars sc[b].
+// init: subset b uses D + b * vs when bit b of d_mask is set, else 1 / clamp(M).
+cudaError_t launch_pcg_init_batch(int n, int N, long long ld, long long vs, const float* b, const float* M,
+                                  const float* D, unsigned d_mask, float* x, float* Minv, double* partials,
+                                  cudaStream_t st);
+cudaError_t launch_pcg_residual0_batch(int n, int N, long long ld, long long vs, const float* b, const float* g,
+                                       const float* M, const float* x, float lambda, const float* Minv, float* r,
+                                       float* z, float* p, double* partials, cudaStream_t st);
+cudaError_t launch_pcg_update_batch(int n, int N, long long ld, long long vs, const PcgScalars* sc, const float* p,
+                                    const float* g, const float* Minv, float* x, float* r, float* z,
+                                    double* partials, cudaStream_t st);
+// scalars of n subsets; subset b reduces partials + b * pstride (n_partials of them).
+cudaError_t launch_pcg_scalars_batch(int n, PcgScalars* sc, const double* partials, int n_partials, int pstride,
+                                     int stage, float break_rel2, cudaStream_t st);
 cudaError_t launch_combine_acc(int N, long long ld, const float* delta, const float* diag,
                                float* num, float* den, cudaStream_t st);
 cudaError_t launch_combine_finish(int N, long long ld, const float* num, const float* den,

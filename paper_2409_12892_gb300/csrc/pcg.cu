@@ -29,10 +29,22 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // one float64 partial and the scalar kernel reduces at most kVecBlocks of them.
 constexpr int kVecBlocks = 2432;   // 16 blocks of 256 threads per SM on 152 SMs
 
-__global__ void k_pcg_init(int N, long long ld, const float* __restrict__ b, const float* __restrict__ M,
-                           const float* __restrict__ D, float* __restrict__ x, float* __restrict__ Minv,
-                           double* __restrict__ partials) {
+// Batched launches: blockIdx.y is the subset; its vectors sit at offset
+// blockIdx.y * vs and its partials at blockIdx.y * gridDim.x (times 2 for the
+// update kernel).
+__global__ void k_pcg_init(int N, long long ld, long long vs, const float* __restrict__ b,
+                           const float* __restrict__ M, const float* __restrict__ D, unsigned d_mask,
+                           float* __restrict__ x, float* __restrict__ Minv, double* __restrict__ partials) {
   __shared__ double red[kBS / 32];
+  {
+    const long long off = (long long)blockIdx.y * vs;
+    b += off;
+    M += off;
+    D = (D != nullptr && ((d_mask >> blockIdx.y) & 1u)) ? D + off : nullptr;
+    x += off;
+    Minv += off;
+    partials += (size_t)blockIdx.y * gridDim.x;
+  }
   double bb = 0.0;
   for (int i = blockIdx.x * kBS + threadIdx.x; i < N; i += gridDim.x * kBS) {
 #pragma unroll 4
@@ -49,11 +61,23 @@ __global__ void k_pcg_init(int N, long long ld, const float* __restrict__ b, con
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void k_pcg_residual0(int N, long long ld, const float* __restrict__ b, const float* __restrict__ g,
-                                const float* __restrict__ M, const float* __restrict__ x, float lambda,
-                                const float* __restrict__ Minv, float* __restrict__ r, float* __restrict__ z,
-                                float* __restrict__ p, double* __restrict__ partials) {
+__global__ void k_pcg_residual0(int N, long long ld, long long vs, const float* __restrict__ b,
+                                const float* __restrict__ g, const float* __restrict__ M, const float* __restrict__ x,
+                                float lambda, const float* __restrict__ Minv, float* __restrict__ r,
+                                float* __restrict__ z, float* __restrict__ p, double* __restrict__ partials) {
   __shared__ double red[kBS / 32];
+  {
+    const long long off = (long long)blockIdx.y * vs;
+    b += off;
+    g += off;
+    M += off;
+    x += off;
+    Minv += off;
+    r += off;
+    z += off;
+    p += off;
+    partials += (size_t)blockIdx.y * gridDim.x;
+  }
   double rz = 0.0;
   for (int i = blockIdx.x * kBS + threadIdx.x; i < N; i += gridDim.x * kBS) {
 #pragma unroll 4
@@ -71,10 +95,22 @@ __global__ void k_pcg_residual0(int N, long long ld, const float* __restrict__ b
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void k_pcg_update(int N, long long ld, const PcgScalars* __restrict__ sc, const float* __restrict__ p,
-                             const float* __restrict__ g, const float* __restrict__ Minv, float* __restrict__ x,
-                             float* __restrict__ r, float* __restrict__ z, double* __restrict__ partials) {
+__global__ void k_pcg_update(int N, long long ld, long long vs, const PcgScalars* __restrict__ sc,
+                             const float* __restrict__ p, const float* __restrict__ g, const float* __restrict__ Minv,
+                             float* __restrict__ x, float* __restrict__ r, float* __restrict__ z,
+                             double* __restrict__ partials) {
   __shared__ double red[kBS / 32];
+  {
+    const long long off = (long long)blockIdx.y * vs;
+    sc += blockIdx.y;
+    p += off;
+    g += off;
+    Minv += off;
+    x += off;
+    r += off;
+    z += off;
+    partials += (size_t)blockIdx.y * 2 * gridDim.x;
+  }
   if (sc->done) return;
   const float alpha = (float)sc->alpha;
   double rz = 0.0, rr = 0.0;
@@ -102,9 +138,11 @@ __global__ void k_pcg_update(int N, long long ld, const PcgScalars* __restrict__
 
 // stage 0: ||b||^2 (resets the solve state); 1: r^T z; 2: p^T g -> alpha;
 // 3: (r^T z, ||r||^2) -> beta and the break test.
-__global__ void k_pcg_scalars(PcgScalars* __restrict__ sc, const double* __restrict__ partials, int n, int stage,
-                              float break_rel2) {
+__global__ void k_pcg_scalars(PcgScalars* __restrict__ sc, const double* __restrict__ partials, int n, int pstride,
+                              int stage, float break_rel2) {
   __shared__ double red[kBS / 32];
+  sc += blockIdx.y;
+  partials += (size_t)blockIdx.y * pstride;
   double s0 = 0.0, s1 = 0.0;
   for (int i = threadIdx.x; i < n; i += kBS) {
     if (stage == 3) {
@@ -222,7 +260,7 @@ cudaError_t launch_pcg_init(long long n59, long long ld, int N, const float* b, 
                             float* x, float* Minv, double* partials, cudaStream_t st) {
   (void)n59;
   if (N <= 0) return cudaSuccess;
-  { k_pcg_init<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, b, M, D, x, Minv, partials); note_launch(); }
+  { k_pcg_init<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, 0, b, M, D, 1u, x, Minv, partials); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -230,20 +268,51 @@ cudaError_t launch_pcg_residual0(int N, long long ld, const float* b, const floa
                                  float lambda, const float* Minv, float* r, float* z, float* p, double* partials,
                                  cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  { k_pcg_residual0<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, b, g, M, x, lambda, Minv, r, z, p, partials); note_launch(); }
+  { k_pcg_residual0<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, 0, b, g, M, x, lambda, Minv, r, z, p, partials); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_scalars(PcgScalars* sc, const double* partials, int n_partials, int stage, float break_rel2,
                                cudaStream_t st) {
-  { k_pcg_scalars<<<1, kBS, 0, st>>>(sc, partials, n_partials, stage, break_rel2); note_launch(); }
+  { k_pcg_scalars<<<1, kBS, 0, st>>>(sc, partials, n_partials, 0, stage, break_rel2); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update(int N, long long ld, const PcgScalars* sc, const float* p, const float* g,
                               const float* Minv, float* x, float* r, float* z, double* partials, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  { k_pcg_update<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, sc, p, g, Minv, x, r, z, partials); note_launch(); }
+  { k_pcg_update<<<pcg_blocks(N), kBS, 0, st>>>(N, ld, 0, sc, p, g, Minv, x, r, z, partials); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_init_batch(int n, int N, long long ld, long long vs, const float* b, const float* M,
+                                  const float* D, unsigned d_mask, float* x, float* Minv, double* partials,
+                                  cudaStream_t st) {
+  if (N <= 0 || n <= 0) return cudaSuccess;
+  { k_pcg_init<<<dim3(pcg_blocks(N), n), kBS, 0, st>>>(N, ld, vs, b, M, D, d_mask, x, Minv, partials); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_residual0_batch(int n, int N, long long ld, long long vs, const float* b, const float* g,
+                                       const float* M, const float* x, float lambda, const float* Minv, float* r,
+                                       float* z, float* p, double* partials, cudaStream_t st) {
+  if (N <= 0 || n <= 0) return cudaSuccess;
+  { k_pcg_residual0<<<dim3(pcg_blocks(N), n), kBS, 0, st>>>(N, ld, vs, b, g, M, x, lambda, Minv, r, z, p, partials); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update_batch(int n, int N, long long ld, long long vs, const PcgScalars* sc, const float* p,
+                                    const float* g, const float* Minv, float* x, float* r, float* z,
+                                    double* partials, cudaStream_t st) {
+  if (N <= 0 || n <= 0) return cudaSuccess;
+  { k_pcg_update<<<dim3(pcg_blocks(N), n), kBS, 0, st>>>(N, ld, vs, sc, p, g, Minv, x, r, z, partials); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_scalars_batch(int n, PcgScalars* sc, const double* partials, int n_partials, int pstride,
+                                     int stage, float break_rel2, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { k_pcg_scalars<<<dim3(1, n), kBS, 0, st>>>(sc, partials, n_partials, pstride, stage, break_rel2); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -340,12 +340,11 @@ __global__ void k_project(const float* __restrict__ P, int N, long long ld, cons
 // ydot[slot] = (dy/dx) p for every active slot of every Gaussian. With z_beta
 // given, first p = z + beta p (Algorithm 1's last vector update, fused), and the
 // new p is written back to p_out.
-__global__ void __launch_bounds__(128) k_tangent(
-    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+__device__ __forceinline__ void tangent_body(
+    int g, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
     const float* __restrict__ pin, float* __restrict__ ydot, const float* __restrict__ zb,
     float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   if (sc != nullptr && sc->done) return;
   float pd[kNP];
@@ -415,14 +414,13 @@ __global__ void __launch_bounds__(128) k_tangent(
 // g = scale * (dy/dx)^T ybar summed over the views; ybar of a slot is the sum
 // of its segments' partial sums. Epilogue (M != null): g += lambda M p and a
 // per-block float64 partial of p^T g.
-__global__ void __launch_bounds__(128) k_vjp(
-    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+__device__ __forceinline__ void vjp_body(
+    int g, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
     const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ vmask,
     const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
     const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
     const PcgScalars* __restrict__ sc) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const bool skip = (sc != nullptr && sc->done);
   double local = 0.0;
   if (g < N && !skip) {
@@ -585,6 +583,57 @@ __global__ void __launch_bounds__(128) k_vjp(
   }
 }
 
+__global__ void __launch_bounds__(128) k_tangent(
+    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+    const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
+    const float* __restrict__ pin, float* __restrict__ ydot, const float* __restrict__ zb,
+    float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
+  tangent_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, cams, V, smooth, slot_active, vmask, pin, ydot, zb,
+               pout, sc);
+}
+
+// Batched: blockIdx.y is the subset; its p, z and pout sit at offset
+// blockIdx.y * vs, its scalars at sc[blockIdx.y].
+__global__ void __launch_bounds__(128) k_tangent_batch(const float* __restrict__ P, int N, long long ld, int smooth,
+                                                       const __grid_constant__ GaussBatch gb,
+                                                       const float* __restrict__ pin, long long vs,
+                                                       const float* __restrict__ zb, float* __restrict__ pout,
+                                                       const PcgScalars* __restrict__ sc) {
+  const int b = blockIdx.y;
+  const SubsetRefs& s = gb.s[b];
+  const long long off = (long long)b * vs;
+  tangent_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, s.cams, s.V, smooth, s.slot_active, s.vmask,
+               pin + off, s.ydot, zb != nullptr ? zb + off : nullptr, pout != nullptr ? pout + off : nullptr,
+               sc != nullptr ? sc + b : nullptr);
+}
+
+__global__ void __launch_bounds__(128) k_vjp(
+    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+    const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
+    const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ vmask,
+    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
+    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
+    const PcgScalars* __restrict__ sc) {
+  vjp_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, cams, V, smooth, s_start, s_end, s_list, vmask, seg_ybar,
+           scale, gout, p, Mdiag, lambda, partials, sc);
+}
+
+// Batched: blockIdx.y is the subset; g, p and M at offset blockIdx.y * vs, the
+// float64 partials at blockIdx.y * gridDim.x.
+__global__ void __launch_bounds__(128) k_vjp_batch(const float* __restrict__ P, int N, long long ld, int smooth,
+                                                   const __grid_constant__ GaussBatch gb, float* __restrict__ gout,
+                                                   long long vs, const float* __restrict__ p,
+                                                   const float* __restrict__ Mdiag, float lambda,
+                                                   double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
+  const int b = blockIdx.y;
+  const SubsetRefs& s = gb.s[b];
+  const long long off = (long long)b * vs;
+  vjp_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, s.cams, s.V, smooth, s.s_start, s.s_end, s.s_list,
+           s.vmask, s.seg_ybar, 1.f, gout + off, p != nullptr ? p + off : nullptr,
+           Mdiag != nullptr ? Mdiag + off : nullptr, lambda,
+           partials != nullptr ? partials + (size_t)b * gridDim.x : nullptr, sc != nullptr ? sc + b : nullptr);
+}
+
 // diag(J^T J) for every Gaussian: sum over views of v_k^T Q v_k, where v_k is
 // column k of dy/dx and Q (per slot) is the sum over its cache entries and
 // channels of (dc/dy)^T (dc/dy), stored as 21 geo-geo + 18 geo-rgb + 1 rgb values.
@@ -722,6 +771,24 @@ cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCa
 }
 
 int vjp_blocks(int N) { return (N + 127) / 128; }
+
+cudaError_t launch_tangent_batch(const float* params, int N, long long ld, int smooth, const GaussBatch& gb,
+                                 const float* p, long long vs, const float* z_beta, float* p_out,
+                                 const PcgScalars* sc, cudaStream_t st) {
+  if (N == 0 || gb.n <= 0) return cudaSuccess;
+  { k_tangent_batch<<<dim3((N + 127) / 128, gb.n), 128, 0, st>>>(params, N, ld, smooth, gb, p, vs, z_beta, p_out,
+                                                                 sc); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vjp_batch(const float* params, int N, long long ld, int smooth, const GaussBatch& gb,
+                             float* g, long long vs, const float* p, const float* M, float lambda,
+                             double* partials, const PcgScalars* sc, cudaStream_t st) {
+  if (N == 0 || gb.n <= 0) return cudaSuccess;
+  { k_vjp_batch<<<dim3(vjp_blocks(N), gb.n), 128, 0, st>>>(params, N, ld, smooth, gb, g, vs, p, M, lambda, partials,
+                                                           sc); note_launch(); }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
                        const uint32_t* s_start, const uint32_t* s_end, const uint32_t* s_list,

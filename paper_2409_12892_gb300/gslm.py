@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
     _fields_ = [("cache_fmt", c_int32), ("n_iters", c_int32), ("break_rel2", c_float),
                 ("lambda_min", c_float), ("lambda_max", c_float), ("smooth", c_int32),
                 ("mem_budget", c_size_t), ("group", c_int32), ("profile", c_int32), ("autotune", c_int32),
-                ("reserved", c_int32 * 5)]
+                ("batch", c_int32), ("graph", c_int32), ("batch_ctas", c_int32), ("reserved", c_int32 * 2)]
 
 
 class CacheInfo(ctypes.Structure):
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gslm_apply_JT": (c_int32, [P, P, P, P]),
         "gslm_jacobi_diag": (c_int32, [P, P, P]),
         "gslm_pcg_solve": (c_int32, [P, P, P, P, P, c_float, P, P]),
+        "gslm_pcg_solve_batch": (c_int32, [P, P, c_int32, P, P, P, c_float, P, P]),
         "gslm_combine_accumulate": (c_int32, [P, c_int64, c_int64, P, P, P, P]),
         "gslm_combine_finish": (c_int32, [P, c_int64, c_int64, P, P, P]),
         "gslm_lm_step": (c_int32, [P, P, c_int64, c_int64, P, c_int32, P, P, P, c_int32, P, P, P]),
@@ -136,7 +137,7 @@ def kernel_launches() -> int:
 def exported_symbols() -> list:
     return ["gslm_default_options", "gslm_create", "gslm_destroy", "gslm_last_error", "gslm_set_options",
             "gslm_render", "gslm_build_cache", "gslm_cache_stats", "gslm_cache_free", "gslm_apply_J",
-            "gslm_apply_JT", "gslm_jacobi_diag", "gslm_pcg_solve", "gslm_combine_accumulate",
+            "gslm_apply_JT", "gslm_jacobi_diag", "gslm_pcg_solve", "gslm_pcg_solve_batch", "gslm_combine_accumulate",
             "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches", "gslm_autotune_info",
             "gslm_apply_JT_noalloc", "gslm_precond_weight_count", "gslm_precond_create", "gslm_precond_free",
             "gslm_precond_get", "gslm_precond_set", "gslm_precond_features", "gslm_precond_fit_standardizer",
@@ -220,7 +221,8 @@ class Context:
     """A libgslm context on the current CUDA device and torch's current stream."""
 
     def __init__(self, cache_fmt="fp32", n_iters=8, break_rel2=0.01, lambda_min=1e-4, lambda_max=1e4,
-                 smooth=False, mem_budget=0, group=32, profile=False, autotune=True, stream=None):
+                 smooth=False, mem_budget=0, group=32, profile=False, autotune=True, batch=True, graph=True,
+                 batch_ctas=0, stream=None):
         self.lib = load_library()
         opt = Options()
         self.lib.gslm_default_options(ctypes.byref(opt))
@@ -230,6 +232,7 @@ class Context:
         opt.smooth, opt.mem_budget, opt.group = int(bool(smooth)), int(mem_budget), int(group)
         opt.profile = int(bool(profile))
         opt.autotune = int(bool(autotune))
+        opt.batch, opt.graph, opt.batch_ctas = int(bool(batch)), int(bool(graph)), int(batch_ctas)
         self.opt = opt
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
@@ -321,6 +324,19 @@ class Context:
                                                 _ptr(precond), float(lam), _ptr(x),
                                                 ctypes.byref(st) if stats else None))
         return x, st, s
+
+    def pcg_solve_batch(self, caches, bs, diags, lam: float, precond=None, xs=None):
+        """Algorithm 1 for several subsets in lock step. Returns (xs, [PcgStats], status)."""
+        n = len(caches)
+        if xs is None:
+            xs = [torch.zeros((N_PARAMS, c.ld), dtype=torch.float32, device=b.device) for c, b in zip(caches, bs)]
+        arr = lambda vals: (c_void_p * n)(*vals)
+        st = (PcgStats * n)()
+        pre = arr([_ptr(t) for t in precond]) if precond is not None else None
+        s = self._check(self.lib.gslm_pcg_solve_batch(self.h, arr([c.handle for c in caches]), n,
+                                                      arr([_ptr(b) for b in bs]), arr([_ptr(d) for d in diags]), pre,
+                                                      float(lam), arr([_ptr(x) for x in xs]), st))
+        return xs, list(st), s
 
     def combine_accumulate(self, n: int, delta, diag, num, den):
         self._check(self.lib.gslm_combine_accumulate(self.h, n, delta.shape[1], _ptr(delta), _ptr(diag),
