@@ -4,9 +4,15 @@
 Metric: LM-step ms and J p + J^T u HBM GB/s at 1.5M Gaussians, chosen form vs
 plain FP32. One step = one LM iteration of the paper-scale synthetic workload
 (1.5M Gaussians in 20 clusters, 200 cameras at 1264x832, four subsets of 25
-views): per subset the gradient cache, the Jacobi diagonal and the PCG solve
+views): per subset the gradient cache, the diagonal and the PCG solve
 (Algorithm 1, 8 iterations, break test 0.01), then the weighted mean of the
 subset directions, rho with the trial render and the damping update.
+
+Forms: "chosen" = BF16 cache, learned diagonal preconditioner (trained on the
+GPU on step 0's subset systems before timing), the subsets' solves batched and
+replayed from one CUDA graph; "plain" = FP32 cache, Jacobi, one subset after
+another. Besides the paper's fixed 8 iterations, one LM step of each form is
+also timed with PCG run to a relative residual of 1e-3 (equal_residual).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,6 +56,14 @@ def parse_args(argv=None):
     ap.add_argument("--subsets", type=int, default=0,
                     help="override: number of image subsets per LM step (profiling-sized cases)")
     ap.add_argument("--views", type=int, default=0, help="override: views per subset (profiling-sized cases)")
+    ap.add_argument("--precond", choices=["learned", "jacobi"], default="learned",
+                    help="preconditioner of the chosen form")
+    ap.add_argument("--train-steps", type=int, default=24, help="Adam steps of the learned preconditioner")
+    ap.add_argument("--train-K", type=int, default=8, help="unrolled PCG iterations of the training loss")
+    ap.add_argument("--train-lr", type=float, default=3e-3)
+    ap.add_argument("--train-systems", type=int, default=2, help="subset systems of step 0 trained on")
+    ap.add_argument("--skip-equal", action="store_true", help="skip the equal-residual comparison")
+    ap.add_argument("--equal-cap", type=int, default=1000, help="PCG iteration cap of the equal-residual step")
     return ap.parse_args(argv)
 
 
@@ -414,6 +428,87 @@ def pair_roofline(stats, peak: dict) -> dict:
             else "fallback 6.8 TB/s"}
 
 
+def subset_targets(targets, cams, views):
+    """The rows of `targets` that belong to `views`, concatenated (device copy)."""
+    import numpy as np
+    import torch
+    offs = np.cumsum([0] + [c.width * c.height for c in cams])
+    return torch.cat([targets[int(offs[v]):int(offs[v + 1])] for v in views])
+
+
+def train_precond(g, ctx, params, N, cams, targets, wl, args):
+    """The learned preconditioner, trained on the GPU on the subset systems of LM
+    step 0 (Adam on the unrolled-PCG residual). Returns (network, report)."""
+    import torch
+    import synth
+    t0 = time.perf_counter()
+    subsets = synth.subset_views(wl, 0)[:max(1, args.train_systems)]
+    systems = []
+    for vs in subsets:
+        cc = [cams[v] for v in vs]
+        cache = ctx.build_cache(params, N, cc, subset_targets(targets, cams, vs), want_F=False)
+        diag = ctx.jacobi_diag(cache)
+        systems.append((cache, diag, ctx.precond_features(cache, diag)))
+    pc = g.Precond(ctx, seed=0)
+    pc.fit_standardizer(torch.cat([phi for _, _, phi in systems]))
+    losses = []
+    for _ in range(args.train_steps):
+        L = 0.0
+        for cache, diag, phi in systems:
+            L += pc.accumulate(cache, phi, cache.b, diag, wl.lambda0, args.train_K, 1.0 / len(systems))
+        losses.append(L / len(systems))
+        pc.adam(args.train_lr)
+    for cache, _, _ in systems:
+        cache.free()
+    del systems
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    rep = {"systems": len(subsets), "adam_steps": args.train_steps, "K": args.train_K, "lr": args.train_lr,
+           "loss_first": losses[0] if losses else None, "loss_last": losses[-1] if losses else None,
+           "seconds": time.perf_counter() - t0,
+           "loss": "1/2 log(||r_K||^2/||b||^2) after K iterations of Algorithm 1 with D"}
+    return pc, rep
+
+
+def psnr_from_cost(cost: float, n_pix: int) -> float:
+    mse = cost / (3.0 * n_pix)
+    return 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")
+
+
+def equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap: int) -> dict:
+    """One LM step from the initial parameters with every subset's PCG run to
+    ||r|| <= 1e-3 ||b|| (at most `cap` iterations); device time by CUDA events."""
+    import torch
+    import synth
+    ctx.set_options(n_iters=cap, break_rel2=1e-6)
+    params = g.to_soa(P, device=dev, ld=ld)
+    subsets = synth.subset_views(wl, 0)
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(st)
+    state, lm = ctx.lm_step(params, N, cams, targets, subsets, wl.lambda0, 0)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    n_pix = sum(cams[v].width * cams[v].height for s in subsets for v in s)
+    ctx.set_options(n_iters=wl.pcg_iters, break_rel2=0.01)
+    del params
+    after = lm.cost_new if lm.accepted else lm.cost
+    return {"ms": ev0.elapsed_time(ev1), "pcg_iters_total": lm.pcg_iters,
+            "pcg_iters_per_subset": lm.pcg_iters / len(subsets), "accepted": int(lm.accepted), "rho": lm.rho,
+            "cost": lm.cost, "cost_new": lm.cost_new, "predicted": lm.predicted,
+            "psnr_before_db": psnr_from_cost(lm.cost, n_pix), "psnr_after_db": psnr_from_cost(after, n_pix)}
+
+
+def profiled_step(g, ctx, params, N, cams, targets, wl, step: int):
+    """One extra LM step with per-phase CUDA events (the timed steps run without them)."""
+    import synth
+    ctx.set_options(profile=1)
+    state, lm = ctx.lm_step(params, N, cams, targets, synth.subset_views(wl, step), wl.lambda0, step)
+    ctx.set_options(profile=0)
+    return lm
+
+
 def run_ours(args):
     import torch
     import paper_2409_12892_gb300 as g
@@ -435,39 +530,55 @@ def run_ours(args):
     if not args.skip_plain:
         forms.append(("plain", "fp32"))
     for form, fmt in forms:
+        chosen = form == "chosen"
         ctx = g.Context(cache_fmt=fmt, n_iters=wl.pcg_iters, break_rel2=0.01, lambda_min=wl.lambda_min,
-                        lambda_max=wl.lambda_max, profile=True, group=args.group)
+                        lambda_max=wl.lambda_max, profile=not chosen, group=args.group, batch=chosen, graph=chosen)
         params = g.to_soa(P, device=dev, ld=ld)
-        clocks = ClockSampler(local) if form == "chosen" else None
+        pc, train = None, None
+        if chosen and args.precond == "learned":
+            pc, train = train_precond(g, ctx, params, N, cams, targets, wl, args)
+            ctx.set_precond(pc)
+        clocks = ClockSampler(local) if chosen else None
         ms, stats, launches, clk = run_steps(g, ctx, params, N, cams, targets, wl, args.steps, args.warmup, dist,
                                              clocks)
         ms = max_over_ranks(ms, dist, dev)
-        result[form] = {"ms": ms, "stats": stats, "launches": launches, "clocks": clk, "fmt": fmt,
-                        "autotune": ctx.autotune_info()}
-        if form == "chosen" and not args.skip_e2e:
+        prof = [profiled_step(g, ctx, params, N, cams, targets, wl, args.warmup + args.steps)] if chosen else stats
+        result[form] = {"ms": ms, "stats": stats, "prof": prof, "launches": launches, "clocks": clk, "fmt": fmt,
+                        "autotune": ctx.autotune_info(), "train": train}
+        if chosen and not args.skip_e2e:
             e2e_ms, h2d, d2h = run_e2e(g, ctx, P, N, ld, cams, targets, wl, args.steps, args.warmup, dist)
             result["e2e"] = {"value": max_over_ranks(e2e_ms, dist, dev), "unit": "ms", "h2d_bytes_per_step": h2d,
                              "d2h_bytes_per_step": d2h}
-        ctx.close()
         del params
+        torch.cuda.empty_cache()
+        if not args.skip_equal:
+            result[form]["equal"] = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, args.equal_cap)
+        ctx.set_precond(None)
+        if pc is not None:
+            pc.free()
+        ctx.close()
         torch.cuda.empty_cache()
     if rank != 0:
         return 0
     ch = result["chosen"]
     stats = ch["stats"]
     E_step = statistics.mean(s.cache_entries for s in stats)
+    pre = "learned preconditioner" if args.precond == "learned" else "Jacobi"
     line = {
         "metric": METRIC, "value": ch["ms"], "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ch["ms"], "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(args, f"chosen: {ch['fmt']} cache, Jacobi PCG"), cache_fmt=ch["fmt"]),
-        "roofline": pair_roofline(stats, peak),
+        "config": dict(workload_config(args, f"chosen: {ch['fmt']} cache, {pre}, batched subsets in one CUDA graph"),
+                       cache_fmt=ch["fmt"]),
+        "roofline": pair_roofline(ch["prof"], peak),
         "e2e": result.get("e2e"),
         "clocks": ch["clocks"],
         "gpu_launches": ch["launches"] // max(args.steps, 1),
         "gpu_launches_total": ch["launches"],
-        "phase_ms": summarize_phases(stats),
+        "phase_ms": summarize_phases(ch["prof"]),
+        "phase_ms_note": "one extra LM step with per-phase CUDA events after the timed steps",
         "autotune": ch["autotune"],
+        "precond_training": ch["train"],
         "lm": {"accepted": [int(s.accepted) for s in stats], "rho": [s.rho for s in stats],
                "cost": [s.cost for s in stats], "cost_new": [s.cost_new for s in stats],
                "predicted": [s.predicted for s in stats], "pcg_iters": [s.pcg_iters for s in stats],
@@ -482,6 +593,16 @@ def run_ours(args):
                               "phase_ms": summarize_phases(pl["stats"]),
                               "cache_gb": statistics.mean(s.cache_bytes for s in pl["stats"]) / 1e9}
         line["speedup_vs_plain"] = pl["ms"] / ch["ms"]
+    if "equal" in ch:
+        eq = {"chosen": ch["equal"], "rel_residual": 1e-3, "pcg_iteration_cap": args.equal_cap,
+              "note": "one LM step from the initial parameters, every subset solved to ||r|| <= 1e-3 ||b||"}
+        if "plain" in result and "equal" in result["plain"]:
+            pe = result["plain"]["equal"]
+            eq["plain_fp32_jacobi"] = pe
+            eq["speedup"] = pe["ms"] / ch["equal"]["ms"]
+            eq["pcg_iteration_ratio"] = ch["equal"]["pcg_iters_total"] / max(pe["pcg_iters_total"], 1)
+            eq["psnr_after_diff_db"] = ch["equal"]["psnr_after_db"] - pe["psnr_after_db"]
+        line["equal_residual"] = eq
     if not args.skip_cpu:
         res = oracle_subprocess(1)
         t = res["times"][0]

@@ -24,7 +24,9 @@
  *   - All work is enqueued on the context's CUDA stream. Outputs are valid
  *     once that stream has been synchronised. gslm_build_cache synchronises
  *     once (to size the cache); gslm_lm_step synchronises to fill its stats;
- *     gslm_pcg_solve synchronises only when stats is non-NULL.
+ *     gslm_pcg_solve synchronises when stats is non-NULL and, for more than 16
+ *     iterations, every 16 iterations: it reads the break-test flag back and
+ *     launches no further iterations once the solve has ended.
  *   - Errors are returned as gslm_status codes; nothing throws across the
  *     ABI; gslm_last_error() gives a message for the last failure on a
  *     context. The library never traps on the device.
@@ -90,7 +92,8 @@ typedef struct {
   int32_t graph;       /* 1 (default): a batched solve is captured into one CUDA graph and launched
                           once (after the first batched solve of a context, which also autotunes) */
   int32_t batch_ctas;  /* resident CTAs per SM of the persistent batched tile kernels; 0 = autotune */
-  int32_t reserved[2];
+  int32_t apply_variant; /* 0: autotuned (or default) apply kernel variant; 1..4: always variant 0..3 */
+  int32_t reserved[1];
 } gslm_options;
 
 typedef struct gslm_ctx gslm_ctx;

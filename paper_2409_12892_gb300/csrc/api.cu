@@ -94,10 +94,11 @@ struct gslm_ctx {
   int bvar_JT[3] = {-1, -1, -1};
   int bctas_J[3] = {0, 0, 0};
   int bctas_JT[3] = {0, 0, 0};
-  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};   // start + first chunk, full chunk, last chunk
   cudaStream_t cap_st = nullptr;    // private stream the batched solve is captured on
   ~gslm_ctx() {
-    if (graph_exec != nullptr) cudaGraphExecDestroy(graph_exec);
+    for (auto ge : graph_exec)
+      if (ge != nullptr) cudaGraphExecDestroy(ge);
     if (cap_st != nullptr) cudaStreamDestroy(cap_st);
   }
 };
@@ -328,6 +329,9 @@ gslm_status reduce_to_host(gslm_ctx* ctx, const double* partials, int n, double*
 }
 
 constexpr int kDefaultVariant = 2;
+// Solves of more than kCheckEvery iterations read the done flags back every
+// kCheckEvery iterations and stop launching once every solve has ended.
+constexpr int kCheckEvery = 16;
 
 // Autotuner: times every kernel variant once on the caller's real inputs (all
 // variants compute the same result, so the last one run leaves valid outputs)
@@ -382,7 +386,9 @@ gslm_status do_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float
   ctx->timer.end(t);
   t = ctx->timer.begin(PH_APPLY_J);
   int& var = ctx->var_J[c->fmt];
-  if (var < 0 && ctx->opt.autotune) {
+  if (ctx->opt.apply_variant > 0) {
+    CK(launch_apply_J(cv, ctx->ydot.as<float>(), Fadd, u, sq_partials, ctx->opt.apply_variant - 1, st));
+  } else if (var < 0 && ctx->opt.autotune) {
     const float* yd = ctx->ydot.as<float>();
     CKS(tune_variant(ctx, [&](int v) { return launch_apply_J(cv, yd, Fadd, u, sq_partials, v, st); }, &var,
                      &ctx->ms_J[c->fmt]));
@@ -402,7 +408,9 @@ gslm_status do_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, floa
   bool t = ctx->timer.begin(PH_APPLY_JT);
   int& var = ctx->var_JT[c->fmt];
   float* sy = ctx->seg_ybar.as<float>();
-  if (var < 0 && ctx->opt.autotune) {
+  if (ctx->opt.apply_variant > 0) {
+    CK(launch_apply_JT(cv, u, sy, ctx->opt.apply_variant - 1, st));
+  } else if (var < 0 && ctx->opt.autotune) {
     CKS(tune_variant(ctx, [&](int v) { return launch_apply_JT(cv, u, sy, v, st); }, &var, &ctx->ms_JT[c->fmt]));
   } else {
     CK(launch_apply_JT(cv, u, sy, var < 0 ? kDefaultVariant : var, st));
@@ -450,6 +458,13 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
   CK(launch_pcg_scalars(sc, part, nvec, 1, ctx->opt.break_rel2, st));
   ctx->timer.end(t);
   for (int it = 0; it < ctx->opt.n_iters; ++it) {
+    if (it > 0 && it % kCheckEvery == 0) {
+      // long solves: stop launching once the break test (or a breakdown) has ended the solve
+      int done = 0;
+      CK(cudaMemcpyAsync(&done, &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (done) break;
+    }
     // p_i = z_i + beta p_{i-1} (fused), u_i = J p_i
     CKS(do_apply_J(ctx, c, p, u, it > 0 ? z : nullptr, it > 0 ? p : nullptr, sc, nullptr, nullptr));
     // g_i = J^T u_i + lambda M p_i, p^T g
@@ -550,7 +565,7 @@ gslm_status batch_alloc(gslm_ctx* ctx, const BatchLayout& L) {
 // d_mask is set); x ends in ctx->bt_x, the scalars in ctx->bt_sc[i]. Nothing
 // here synchronises unless `tune` (first use: the tile kernels are autotuned).
 gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const BatchLayout& L, unsigned d_mask,
-                              float lambda, bool tune) {
+                              float lambda, bool tune, bool init, int it0, int it1) {
   cudaStream_t st = ctx->st;
   const gslm_cache* c0 = cs[0];
   const int n = L.n, N = c0->N, fmt = c0->fmt;
@@ -603,8 +618,17 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     CK(launch_apply_JT_batch(tb, var, ctas, st));
     return GSLM_OK;
   };
+  const int forced = ctx->opt.apply_variant - 1;
   auto apply_pair = [&]() -> gslm_status {
     bool t = ctx->timer.begin(PH_APPLY_J);
+    if (forced >= 0) {
+      CKS(runJ(forced, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : 6 - forced));
+      ctx->timer.end(t);
+      t = ctx->timer.begin(PH_APPLY_JT);
+      CKS(runJT(forced, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : 6 - forced));
+      ctx->timer.end(t);
+      return GSLM_OK;
+    }
     if (vJ < 0 && tune) {
       CKS(tune_batch(ctx, runJ, &vJ, &cJ));
     } else {
@@ -621,26 +645,29 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     ctx->timer.end(t);
     return GSLM_OK;
   };
-  // x0 = M^-1 b
-  bool t = ctx->timer.begin(PH_VEC);
-  CK(launch_pcg_init_batch(n, N, ld, vs, b, M, D, d_mask, x, Minv, part, st));
-  CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 0, ctx->opt.break_rel2, st));
-  ctx->timer.end(t);
-  // u0 = J x0; g0 = J^T u0; r0 = b - (g0 + lambda M x0); z0 = M^-1 r0; p0 = z0
-  for (int i = 0; i < n; ++i) tb.v[i].skip = nullptr;
-  t = ctx->timer.begin(PH_TANGENT);
-  CK(launch_tangent_batch(params, N, ld, smooth, gb, x, vs, nullptr, nullptr, nullptr, st));
-  ctx->timer.end(t);
-  CKS(apply_pair());
-  t = ctx->timer.begin(PH_VJP);
-  CK(launch_vjp_batch(params, N, ld, smooth, gb, g, vs, nullptr, nullptr, 0.f, nullptr, nullptr, st));
-  ctx->timer.end(t);
-  t = ctx->timer.begin(PH_VEC);
-  CK(launch_pcg_residual0_batch(n, N, ld, vs, b, g, M, x, lambda, Minv, r, z, p, part, st));
-  CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 1, ctx->opt.break_rel2, st));
-  ctx->timer.end(t);
+  bool t = false;
+  if (init) {
+    // x0 = M^-1 b
+    t = ctx->timer.begin(PH_VEC);
+    CK(launch_pcg_init_batch(n, N, ld, vs, b, M, D, d_mask, x, Minv, part, st));
+    CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 0, ctx->opt.break_rel2, st));
+    ctx->timer.end(t);
+    // u0 = J x0; g0 = J^T u0; r0 = b - (g0 + lambda M x0); z0 = M^-1 r0; p0 = z0
+    for (int i = 0; i < n; ++i) tb.v[i].skip = nullptr;
+    t = ctx->timer.begin(PH_TANGENT);
+    CK(launch_tangent_batch(params, N, ld, smooth, gb, x, vs, nullptr, nullptr, nullptr, st));
+    ctx->timer.end(t);
+    CKS(apply_pair());
+    t = ctx->timer.begin(PH_VJP);
+    CK(launch_vjp_batch(params, N, ld, smooth, gb, g, vs, nullptr, nullptr, 0.f, nullptr, nullptr, st));
+    ctx->timer.end(t);
+    t = ctx->timer.begin(PH_VEC);
+    CK(launch_pcg_residual0_batch(n, N, ld, vs, b, g, M, x, lambda, Minv, r, z, p, part, st));
+    CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 1, ctx->opt.break_rel2, st));
+    ctx->timer.end(t);
+  }
   for (int i = 0; i < n; ++i) tb.v[i].skip = &sc[i].done;
-  for (int it = 0; it < ctx->opt.n_iters; ++it) {
+  for (int it = it0; it < it1; ++it) {
     t = ctx->timer.begin(PH_TANGENT);
     CK(launch_tangent_batch(params, N, ld, smooth, gb, p, vs, it > 0 ? z : nullptr, it > 0 ? p : nullptr, sc, st));
     ctx->timer.end(t);
@@ -658,42 +685,79 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
 }
 
 // Runs a batch whose inputs are already stacked: directly the first time (it
-// autotunes), from one captured CUDA graph afterwards when options.graph is
-// set and no per-phase profile is wanted.
+// autotunes), else from captured CUDA graphs when options.graph is set and no
+// per-phase profile is wanted: one graph for the start and the first chunk of
+// kCheckEvery iterations, one for each later chunk (replayed), one for a
+// shorter last chunk. Between chunks the done flags are read back and no more
+// work is launched once every solve has ended.
 gslm_status pcg_batch_run(gslm_ctx* ctx, const gslm_cache* const* cs, const BatchLayout& L, unsigned d_mask,
                           float lambda) {
   cudaStream_t st = ctx->st;
   const int fmt = cs[0]->fmt;
   const int N = cs[0]->N;
+  const int n_iters = ctx->opt.n_iters;
   CK(ctx->bt_part.ensure(sizeof(double) * L.n * std::max(2 * pcg_blocks(N), vjp_blocks(N)), st));
   CK(ctx->bt_sc.ensure(sizeof(PcgScalars) * L.n, st));
   CK(ctx->bt_queue.ensure(sizeof(unsigned int), st));
   const bool tuned = !ctx->opt.autotune || (ctx->bvar_J[fmt] >= 0 && ctx->bvar_JT[fmt] >= 0);
   const bool use_graph = ctx->opt.graph && tuned && !ctx->timer.on;
-  if (!use_graph) return pcg_batch_enqueue(ctx, cs, L, d_mask, lambda, !tuned);
-  if (ctx->graph_exec != nullptr) {
-    CK(cudaGraphExecDestroy(ctx->graph_exec));
-    ctx->graph_exec = nullptr;
+  auto all_done = [&](bool* out) -> gslm_status {
+    std::vector<PcgScalars> h(L.n);
+    CK(cudaMemcpyAsync(h.data(), ctx->bt_sc.p, sizeof(PcgScalars) * L.n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool d = true;
+    for (const auto& x : h) d = d && x.done != 0;
+    *out = d;
+    return GSLM_OK;
+  };
+  if (!use_graph) {
+    const int first = std::min(n_iters, kCheckEvery);
+    CKS(pcg_batch_enqueue(ctx, cs, L, d_mask, lambda, !tuned, true, 0, first));
+    for (int it = first; it < n_iters; it += kCheckEvery) {
+      bool done = false;
+      CKS(all_done(&done));
+      if (done) break;
+      CKS(pcg_batch_enqueue(ctx, cs, L, d_mask, lambda, false, false, it, std::min(n_iters, it + kCheckEvery)));
+    }
+    return GSLM_OK;
   }
   // Capture on a private stream (the caller's may be the legacy default
-  // stream, which cannot be captured); the graph is launched on the caller's.
+  // stream, which cannot be captured); the graphs are launched on the caller's.
   if (ctx->cap_st == nullptr) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
   (void)device_sm_count();
-  cudaGraph_t graph = nullptr;
-  CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
-  ctx->st = ctx->cap_st;
-  const gslm_status s = pcg_batch_enqueue(ctx, cs, L, d_mask, lambda, false);
-  ctx->st = st;
-  const cudaError_t e = cudaStreamEndCapture(ctx->cap_st, &graph);
-  if (s != GSLM_OK) {
-    if (graph != nullptr) cudaGraphDestroy(graph);
-    return s;
+  for (auto& ge : ctx->graph_exec) {
+    if (ge != nullptr) CK(cudaGraphExecDestroy(ge));
+    ge = nullptr;
   }
-  CK(e);
-  const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
-  cudaGraphDestroy(graph);
-  CK(ei);
-  CK(cudaGraphLaunch(ctx->graph_exec, st));
+  auto capture = [&](bool init, int it0, int it1, cudaGraphExec_t* out) -> gslm_status {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+    ctx->st = ctx->cap_st;
+    const gslm_status s = pcg_batch_enqueue(ctx, cs, L, d_mask, lambda, false, init, it0, it1);
+    ctx->st = st;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_st, &graph);
+    if (s != GSLM_OK) {
+      if (graph != nullptr) cudaGraphDestroy(graph);
+      return s;
+    }
+    CK(e);
+    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    return GSLM_OK;
+  };
+  const int first = std::min(n_iters, kCheckEvery);
+  CKS(capture(true, 0, first, &ctx->graph_exec[0]));
+  CK(cudaGraphLaunch(ctx->graph_exec[0], st));
+  for (int it = first; it < n_iters; it += kCheckEvery) {
+    bool done = false;
+    CKS(all_done(&done));
+    if (done) break;
+    const int len = std::min(kCheckEvery, n_iters - it);
+    cudaGraphExec_t& ge = ctx->graph_exec[len == kCheckEvery ? 1 : 2];
+    if (ge == nullptr) CKS(capture(false, it, it + len, &ge));
+    CK(cudaGraphLaunch(ge, st));
+  }
   return GSLM_OK;
 }
 
@@ -778,6 +842,8 @@ static gslm_status validate_opts(const gslm_options* o) {
   if (o->n_iters < 0 || o->n_iters > 100000) return GSLM_E_INVALID;
   if (!(o->lambda_min > 0.f) || !(o->lambda_max >= o->lambda_min)) return GSLM_E_INVALID;
   if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
+  if (o->batch_ctas < 0 || o->batch_ctas > 6) return GSLM_E_INVALID;
+  if (o->apply_variant < 0 || o->apply_variant > 4) return GSLM_E_INVALID;
   return GSLM_OK;
 }
 

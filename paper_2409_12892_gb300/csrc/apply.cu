@@ -73,28 +73,7 @@ constexpr int kWarps = kTilePix / 32;
 // 32 pixels (two tile rows) to spread a segment's pixels over more banks.
 __device__ __forceinline__ int upad(int ch, int p) { return ch * (kTilePix + kTilePix / 32) + p + (p >> 5); }
 
-__device__ __forceinline__ SegRec load_rec(const SegRec* __restrict__ r) {
-  const uint4* q = reinterpret_cast<const uint4*>(r);
-  const uint4 a = q[0], b = q[1], c = q[2];
-  SegRec s;
-  s.e0 = ((unsigned long long)a.y << 32) | a.x;
-  s.e1 = ((unsigned long long)a.w << 32) | a.z;
-  s.slot = b.x;
-  s.mx = __uint_as_float(b.y);
-  s.my = __uint_as_float(b.z);
-  s.A = __uint_as_float(b.w);
-  s.B = __uint_as_float(c.x);
-  s.C = __uint_as_float(c.y);
-  s.io = __uint_as_float(c.z);
-  s.scale = __uint_as_float(c.w);
-  return s;
-}
 
-__device__ __forceinline__ uint32_t grab(unsigned int* counter) {
-  uint32_t k = 0;
-  if ((threadIdx.x & 31) == 0) k = atomicAdd(counter, 1u);
-  return __shfl_sync(kFull, k, 0);
-}
 
 // Raw payload as loaded (float4 for FP32, two 32-bit words for the 16-bit
 // formats), decoded only when used so that U loads stay cheap in registers.
@@ -127,78 +106,140 @@ __device__ __forceinline__ float4 decode(const typename Raw<kFmt>::T& r, float s
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tile kernels. A CTA (256 threads) works on one 16 x 16 tile at a time. The
+// tile's segment records (and for J p the splat tangents the records point
+// to) are first staged in shared memory, kStage segments at a time, by one
+// coalesced cooperative load, so no warp waits on a chain of dependent
+// global loads. Warps then take the staged segments in order; a warp works
+// on 32 / G segments at once, one per group of G lanes, in lock step, with
+// each lane keeping U entries in flight.
+constexpr int kStage = 256;
+
 struct Tangent {
   float dmx, dmy, dA, dB, dC, od, dr, dg, db;
 };
 
-__device__ __forceinline__ Tangent load_tangent(const float* __restrict__ ydot, uint32_t slot, float io) {
-  const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)slot * 12);
-  const float4 y0 = yd[0], y1 = yd[1], y2 = yd[2];
-  Tangent t;
-  t.dmx = y0.x;
-  t.dmy = y0.y;
-  t.dA = y0.z;
-  t.dB = y0.w;
-  t.dC = y1.x;
-  t.od = y1.y * io;
-  t.dr = y1.z;
-  t.dg = y1.w;
-  t.db = y2.x;
-  return t;
+__device__ __forceinline__ SegRec rec_from(const uint4& a, const uint4& b, const uint4& c) {
+  SegRec s;
+  s.e0 = ((unsigned long long)a.y << 32) | a.x;
+  s.e1 = ((unsigned long long)a.w << 32) | a.z;
+  s.slot = b.x;
+  s.mx = __uint_as_float(b.y);
+  s.my = __uint_as_float(b.z);
+  s.A = __uint_as_float(b.w);
+  s.B = __uint_as_float(c.x);
+  s.C = __uint_as_float(c.y);
+  s.io = __uint_as_float(c.z);
+  s.scale = __uint_as_float(c.w);
+  return s;
 }
 
-// J p over one tile. su (u of the tile, padded planes) must be zero and
-// *next_seg zero on entry, sxy filled; the caller synchronises before.
-template <int kFmt, int U>
+// Shared staging area of one chunk of segments (records as three 16-byte
+// words each; splat tangents for J p).
+struct Stage {
+  uint4 r0[kStage], r1[kStage], r2[kStage];
+};
+struct StageT {
+  float4 t0[kStage], t1[kStage], t2[kStage];
+};
+
+// Stages segments [first, first + cnt) of the cache (and their tangents).
+template <bool kTangent>
+__device__ __forceinline__ void stage_chunk(const CacheView& cv, uint32_t first, int cnt, Stage& S, StageT* T,
+                                            const float* __restrict__ ydot) {
+  for (int t = threadIdx.x; t < cnt; t += kTilePix) {
+    const uint4* q = reinterpret_cast<const uint4*>(cv.seg_rec + first + t);
+    const uint4 a = q[0], b = q[1], c = q[2];
+    S.r0[t] = a;
+    S.r1[t] = b;
+    S.r2[t] = c;
+    if constexpr (kTangent) {
+      const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)b.x * 12);
+      T->t0[t] = yd[0];
+      T->t1[t] = yd[1];
+      T->t2[t] = yd[2];
+    }
+  }
+}
+
+// Largest value of v over the groups of G lanes of the warp (all lanes converged).
+template <int G>
+__device__ __forceinline__ uint32_t warp_max_groups(uint32_t v) {
+#pragma unroll
+  for (int o = G; o < 32; o <<= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// J p over one tile. su (u of the tile, padded planes) must be zero on entry;
+// sxy filled; the caller synchronises before.
+template <int kFmt, int G, int U>
 __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, const float* __restrict__ ydot,
                                              const float* __restrict__ Fadd, float* __restrict__ u,
                                              double* __restrict__ sq_partials, float* su, const float2* sxy,
-                                             double* dred, unsigned int* next_seg) {
+                                             double* dred, unsigned int* next_seg, Stage& S, StageT& T) {
+  static_assert(G == 16 || G == 32, "group size");
+  constexpr int kGPW = 32 / G;
   const int v = find_view(cv.cams, cv.V, tile);
   const DevCam& cam = cv.cams[v];
   const int lt = tile - cam.tile_off;
   const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane & (G - 1), grp = lane / G;
   const uint32_t g0 = cv.tile_seg_off[tile];
   const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
-  uint32_t k = grab(next_seg);
-  SegRec cur, nxt;
-  Tangent t;
-  if (k < n) {
-    cur = load_rec(cv.seg_rec + g0 + k);
-    t = load_tangent(ydot, cur.slot, cur.io);
-  }
-  uint32_t kn = grab(next_seg);
-  if (kn < n) nxt = load_rec(cv.seg_rec + g0 + kn);
-  while (k < n) {
-    // prefetch: the record after next, and the next segment's tangent
-    const uint32_t kn2 = grab(next_seg);
-    SegRec nxt2;
-    if (kn2 < n) nxt2 = load_rec(cv.seg_rec + g0 + kn2);
-    Tangent tn;
-    if (kn < n) tn = load_tangent(ydot, nxt.slot, nxt.io);
-    {
-      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + cur.e0;
-      const uint8_t* po = cv.pixoff + cur.e0;
-      const uint32_t len = (uint32_t)(cur.e1 - cur.e0);
-      for (uint32_t i = lane; i < len; i += 32 * U) {
+  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
+    const int cnt = (int)min((uint32_t)kStage, n - c0);
+    stage_chunk<true>(cv, g0 + c0, cnt, S, &T, ydot);
+    if (threadIdx.x == 0) *next_seg = 0;
+    __syncthreads();
+    for (;;) {
+      uint32_t kb = 0;
+      if (lane == 0) kb = atomicAdd(next_seg, (unsigned)kGPW);
+      kb = __shfl_sync(kFull, kb, 0);
+      if (kb >= (uint32_t)cnt) break;
+      const uint32_t k = kb + grp;
+      const bool has = k < (uint32_t)cnt;
+      SegRec r;
+      Tangent t;
+      uint32_t len = 0;
+      if (has) {
+        r = rec_from(S.r0[k], S.r1[k], S.r2[k]);
+        const float4 y0 = T.t0[k], y1 = T.t1[k], y2 = T.t2[k];
+        t.dmx = y0.x;
+        t.dmy = y0.y;
+        t.dA = y0.z;
+        t.dB = y0.w;
+        t.dC = y1.x;
+        t.od = y1.y * r.io;
+        t.dr = y1.z;
+        t.dg = y1.w;
+        t.db = y2.x;
+        len = (uint32_t)(r.e1 - r.e0);
+      }
+      const uint32_t mlen = warp_max_groups<G>(len);
+      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + (has ? r.e0 : 0);
+      const uint8_t* po = cv.pixoff + (has ? r.e0 : 0);
+      for (uint32_t base = 0; base < mlen; base += G * U) {
         typename Raw<kFmt>::T raw[U];
         int pp[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-          if (i + 32 * j < len) {
-            raw[j] = __ldcs(pl + i + 32 * j);
-            pp[j] = po[i + 32 * j];
+          const uint32_t i = base + gl + G * j;
+          if (i < len) {
+            raw[j] = __ldcs(pl + i);
+            pp[j] = po[i];
           }
         }
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-          if (i + 32 * j < len) {
+          const uint32_t i = base + gl + G * j;
+          if (i < len) {
             const int p = pp[j];
-            const float4 pe = decode<kFmt>(raw[j], cur.scale);
+            const float4 pe = decode<kFmt>(raw[j], r.scale);
             const float2 c = sxy[p];
-            const float dx = c.x - cur.mx, dy = c.y - cur.my;
-            const float q = (cur.A * dx + cur.B * dy) * t.dmx + (cur.B * dx + cur.C * dy) * t.dmy -
+            const float dx = c.x - r.mx, dy = c.y - r.my;
+            const float q = (r.A * dx + r.B * dy) * t.dmx + (r.B * dx + r.C * dy) * t.dmy -
                             0.5f * dx * dx * t.dA - dx * dy * t.dB - 0.5f * dy * dy * t.dC + t.od;
             atomicAdd(&su[upad(0, p)], pe.x * t.dr + pe.y * q);
             atomicAdd(&su[upad(1, p)], pe.x * t.dg + pe.z * q);
@@ -207,13 +248,8 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
         }
       }
     }
-    k = kn;
-    cur = nxt;
-    t = tn;
-    kn = kn2;
-    nxt = nxt2;
+    __syncthreads();
   }
-  __syncthreads();
   const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
   double local = 0.0;
   if (x < cam.W && y < cam.H) {
@@ -248,9 +284,11 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
   __shared__ float2 sxy[kTilePix];                       \
   __shared__ double dred[kWarps];                        \
   __shared__ unsigned int next_seg;                      \
+  __shared__ Stage S;                                    \
+  __shared__ StageT T;                                   \
   sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
 
-template <int kFmt, int U, int kMinBlocks>
+template <int kFmt, int G, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, const float* __restrict__ ydot,
                                                                   const float* __restrict__ Fadd,
                                                                   float* __restrict__ u,
@@ -258,9 +296,8 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, 
   if (cv.skip != nullptr && *cv.skip) return;
   APPLY_J_SHARED
   for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
-  if (threadIdx.x == 0) next_seg = 0;
   __syncthreads();
-  apply_J_tile<kFmt, U>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg);
+  apply_J_tile<kFmt, G, U>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg, S, T);
 }
 
 // Subset of a global tile index of a batch.
@@ -272,24 +309,21 @@ __device__ __forceinline__ int batch_subset(const TileBatch& tb, long long gt) {
 
 // Persistent J p over every subset of a batch: each CTA takes tiles from the
 // batch's queue until all are done (tiles of finished solves are skipped).
-template <int kFmt, int U, int kMinBlocks>
+template <int kFmt, int G, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J_batch(const __grid_constant__ TileBatch tb) {
   APPLY_J_SHARED
   __shared__ long long s_tile;
   for (;;) {
     for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
-    if (threadIdx.x == 0) {
-      next_seg = 0;
-      s_tile = (long long)atomicAdd(tb.queue, 1u);
-    }
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(tb.queue, 1u);
     __syncthreads();
     const long long gt = s_tile;
     if (gt >= tb.total_tiles) break;
     const int b = batch_subset(tb, gt);
     const CacheView& cv = tb.v[b];
     if (cv.skip == nullptr || *cv.skip == 0)
-      apply_J_tile<kFmt, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
-                            nullptr, su, sxy, dred, &next_seg);
+      apply_J_tile<kFmt, G, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
+                               nullptr, su, sxy, dred, &next_seg, S, T);
     __syncthreads();
   }
 }
@@ -307,23 +341,33 @@ __device__ __forceinline__ void halve(float (&v)[16], bool upper, int o) {
   }
 }
 
-// Sums 16 values over the 32 lanes of the warp (16 shuffles instead of the 80
-// of a butterfly per value). Lanes 0, 2, ..., 30 then hold the sum of value
-// index lane / 2 in v[0] (odd lanes hold the same sums).
-__device__ __forceinline__ void warp_sum16(float (&v)[16], int lane) {
-  halve<16>(v, lane & 16, 16);
-  halve<8>(v, lane & 8, 8);
-  halve<4>(v, lane & 4, 4);
-  halve<2>(v, lane & 2, 2);
-  v[0] += __shfl_xor_sync(kFull, v[0], 1);
+// Sums 16 values over each group of G lanes (all 32 lanes converged). G = 32:
+// lanes 0, 2, ..., 30 then hold the sum of value index lane / 2 in v[0]; G = 16:
+// lane l of a group holds the sum of value index l in v[0].
+template <int G>
+__device__ __forceinline__ void group_sum16(float (&v)[16], int lane) {
+  if constexpr (G == 32) {
+    halve<16>(v, lane & 16, 16);
+    halve<8>(v, lane & 8, 8);
+    halve<4>(v, lane & 4, 4);
+    halve<2>(v, lane & 2, 2);
+    v[0] += __shfl_xor_sync(kFull, v[0], 1);
+  } else {
+    halve<16>(v, lane & 8, 8);
+    halve<8>(v, lane & 4, 4);
+    halve<4>(v, lane & 2, 2);
+    halve<2>(v, lane & 1, 1);
+  }
 }
 
-// J^T u over one tile into per-segment partials. *next_seg must be zero on
-// entry; the caller synchronises before. sxy is filled here.
-template <int kFmt, int U>
+// J^T u over one tile into per-segment partials. The caller synchronises
+// before. su4 / sxy are filled here.
+template <int kFmt, int G, int U>
 __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, const float* __restrict__ u,
                                               float* __restrict__ seg_ybar, float4* su4, float2* sxy,
-                                              unsigned int* next_seg) {
+                                              unsigned int* next_seg, Stage& S) {
+  static_assert(G == 16 || G == 32, "group size");
+  constexpr int kGPW = 32 / G;
   const uint32_t g0 = cv.tile_seg_off[tile];
   const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
   if (n == 0) return;
@@ -341,42 +385,54 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
     su4[threadIdx.x] = uv;
     sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
   }
-  __syncthreads();
   const int lane = threadIdx.x & 31;
-  uint32_t k = grab(next_seg);
-  SegRec cur;
-  if (k < n) cur = load_rec(cv.seg_rec + g0 + k);
-  while (k < n) {
-    const uint32_t kn = grab(next_seg);
-    SegRec nxt;
-    if (kn < n) nxt = load_rec(cv.seg_rec + g0 + kn);
-    // moments of s = h . u over the segment's pixels (tile-local offsets from
-    // the splat mean), and sums of w u; the conic is applied once per segment
-    float a[16];
+  const int gl = lane & (G - 1), grp = lane / G;
+  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
+    const int cnt = (int)min((uint32_t)kStage, n - c0);
+    stage_chunk<false>(cv, g0 + c0, cnt, S, nullptr, nullptr);
+    if (threadIdx.x == 0) *next_seg = 0;
+    __syncthreads();
+    for (;;) {
+      uint32_t kb = 0;
+      if (lane == 0) kb = atomicAdd(next_seg, (unsigned)kGPW);
+      kb = __shfl_sync(kFull, kb, 0);
+      if (kb >= (uint32_t)cnt) break;
+      const uint32_t k = kb + grp;
+      const bool has = k < (uint32_t)cnt;
+      SegRec r;
+      uint32_t len = 0;
+      if (has) {
+        r = rec_from(S.r0[k], S.r1[k], S.r2[k]);
+        len = (uint32_t)(r.e1 - r.e0);
+      }
+      const uint32_t mlen = warp_max_groups<G>(len);
+      // moments of s = h . u over the segment's pixels (tile-local offsets from
+      // the splat mean), and sums of w u; the conic is applied once per segment
+      float a[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) a[i] = 0.f;
-    {
-      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + cur.e0;
-      const uint8_t* po = cv.pixoff + cur.e0;
-      const uint32_t len = (uint32_t)(cur.e1 - cur.e0);
-      for (uint32_t i = lane; i < len; i += 32 * U) {
+      for (int i = 0; i < 16; ++i) a[i] = 0.f;
+      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + (has ? r.e0 : 0);
+      const uint8_t* po = cv.pixoff + (has ? r.e0 : 0);
+      for (uint32_t base = 0; base < mlen; base += G * U) {
         typename Raw<kFmt>::T raw[U];
         int pp[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-          if (i + 32 * j < len) {
-            raw[j] = __ldcs(pl + i + 32 * j);
-            pp[j] = po[i + 32 * j];
+          const uint32_t i = base + gl + G * j;
+          if (i < len) {
+            raw[j] = __ldcs(pl + i);
+            pp[j] = po[i];
           }
         }
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-          if (i + 32 * j < len) {
+          const uint32_t i = base + gl + G * j;
+          if (i < len) {
             const int p = pp[j];
-            const float4 pej = decode<kFmt>(raw[j], cur.scale);
+            const float4 pej = decode<kFmt>(raw[j], r.scale);
             const float4 uv = su4[p];
             const float2 c = sxy[p];
-            const float dx = c.x - cur.mx, dy = c.y - cur.my;
+            const float dx = c.x - r.mx, dy = c.y - r.my;
             const float sv = pej.y * uv.x + pej.z * uv.y + pej.w * uv.z;
             const float t1 = sv * dx, t2 = sv * dy;
             a[0] += sv;
@@ -391,59 +447,56 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
           }
         }
       }
-    }
-    warp_sum16(a, lane);
-    // lane 2i holds moment i: m0 = sum s, m1 = sum s dx, m2 = sum s dy,
-    // m3 = sum s dx^2, m4 = sum s dx dy, m5 = sum s dy^2, m6..m8 = sum w u
-    float m[9];
+      group_sum16<G>(a, lane);
+      // moment i: m0 = sum s, m1 = sum s dx, m2 = sum s dy, m3 = sum s dx^2,
+      // m4 = sum s dx dy, m5 = sum s dy^2, m6..m8 = sum w u
+      float m[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) m[i] = __shfl_sync(kFull, a[0], 2 * i);
-    if (lane < 9) {
-      float val = m[lane < 9 ? lane : 0];
-      if (lane == 0) val = cur.A * m[1] + cur.B * m[2];
-      else if (lane == 1) val = cur.B * m[1] + cur.C * m[2];
-      else if (lane == 2) val = -0.5f * m[3];
-      else if (lane == 3) val = -m[4];
-      else if (lane == 4) val = -0.5f * m[5];
-      else if (lane == 5) val = m[0] * cur.io;
-      seg_ybar[(size_t)(g0 + k) * 12 + lane] = val;
+      for (int i = 0; i < 9; ++i) m[i] = __shfl_sync(kFull, a[0], G == 32 ? 2 * i : i, G);
+      if (has && gl < 9) {
+        float val = m[gl < 9 ? gl : 0];
+        if (gl == 0) val = r.A * m[1] + r.B * m[2];
+        else if (gl == 1) val = r.B * m[1] + r.C * m[2];
+        else if (gl == 2) val = -0.5f * m[3];
+        else if (gl == 3) val = -m[4];
+        else if (gl == 4) val = -0.5f * m[5];
+        else if (gl == 5) val = m[0] * r.io;
+        seg_ybar[(size_t)(g0 + c0 + k) * 12 + gl] = val;
+      }
     }
-    k = kn;
-    cur = nxt;
+    __syncthreads();
   }
 }
 
-template <int kFmt, int U, int kMinBlocks>
+#define APPLY_JT_SHARED                   \
+  __shared__ float4 su4[kTilePix];        \
+  __shared__ float2 sxy[kTilePix];        \
+  __shared__ unsigned int next_seg;       \
+  __shared__ Stage S;
+
+template <int kFmt, int G, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv, const float* __restrict__ u,
                                                                    float* __restrict__ seg_ybar) {
-  __shared__ float4 su4[kTilePix];
-  __shared__ float2 sxy[kTilePix];
-  __shared__ unsigned int next_seg;
+  APPLY_JT_SHARED
   if (cv.skip != nullptr && *cv.skip) return;
-  if (threadIdx.x == 0) next_seg = 0;
-  apply_JT_tile<kFmt, U>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg);
+  apply_JT_tile<kFmt, G, U>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg, S);
 }
 
 // Persistent J^T u over every subset of a batch (see k_apply_J_batch).
-template <int kFmt, int U, int kMinBlocks>
+template <int kFmt, int G, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const __grid_constant__ TileBatch tb) {
-  __shared__ float4 su4[kTilePix];
-  __shared__ float2 sxy[kTilePix];
-  __shared__ unsigned int next_seg;
+  APPLY_JT_SHARED
   __shared__ long long s_tile;
   for (;;) {
-    if (threadIdx.x == 0) {
-      next_seg = 0;
-      s_tile = (long long)atomicAdd(tb.queue, 1u);
-    }
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(tb.queue, 1u);
     __syncthreads();
     const long long gt = s_tile;
     if (gt >= tb.total_tiles) break;
     const int b = batch_subset(tb, gt);
     const CacheView& cv = tb.v[b];
     if (cv.skip == nullptr || *cv.skip == 0)
-      apply_JT_tile<kFmt, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.u[b], tb.seg_ybar[b], su4, sxy,
-                             &next_seg);
+      apply_JT_tile<kFmt, G, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.u[b], tb.seg_ybar[b], su4, sxy,
+                                &next_seg, S);
     __syncthreads();
   }
 }
@@ -505,32 +558,33 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
   }
 }
 
-// Variants: entries each lane keeps in flight (U) and the minimum number of
-// resident 256-thread blocks per SM the registers must allow.
-template <int kFmt, int U, int B>
+// Variants: lanes per segment (G), entries each lane keeps in flight (U) and
+// the minimum number of resident 256-thread blocks per SM the registers must
+// allow: 0 = (16, 2, 6), 1 = (16, 4, 5), 2 = (32, 2, 6), 3 = (32, 4, 4).
+template <int kFmt, int G, int U, int B>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
-  k_apply_J<kFmt, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
+  k_apply_J<kFmt, G, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int kFmt, int U, int B>
+template <int kFmt, int G, int U, int B>
 cudaError_t run_JT(const CacheView& cv, const float* u, float* seg_ybar, cudaStream_t st) {
-  k_apply_JT<kFmt, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar);
+  k_apply_JT<kFmt, G, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int kFmt, int U, int B>
+template <int kFmt, int G, int U, int B>
 cudaError_t run_J_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
-  k_apply_J_batch<kFmt, U, B><<<ctas, kTilePix, 0, st>>>(tb);
+  k_apply_J_batch<kFmt, G, U, B><<<ctas, kTilePix, 0, st>>>(tb);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int kFmt, int U, int B>
+template <int kFmt, int G, int U, int B>
 cudaError_t run_JT_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
-  k_apply_JT_batch<kFmt, U, B><<<ctas, kTilePix, 0, st>>>(tb);
+  k_apply_JT_batch<kFmt, G, U, B><<<ctas, kTilePix, 0, st>>>(tb);
   note_launch();
   return cudaGetLastError();
 }
@@ -538,20 +592,20 @@ cudaError_t run_JT_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
 template <int kFmt>
 cudaError_t apply_J_batch_variant(int variant, const TileBatch& tb, int ctas, cudaStream_t st) {
   switch (variant) {
-    case 0: return run_J_batch<kFmt, 1, 6>(tb, ctas, st);
-    case 1: return run_J_batch<kFmt, 2, 5>(tb, ctas, st);
-    case 2: return run_J_batch<kFmt, 4, 4>(tb, ctas, st);
-    default: return run_J_batch<kFmt, 8, 3>(tb, ctas, st);
+    case 0: return run_J_batch<kFmt, 16, 2, 6>(tb, ctas, st);
+    case 1: return run_J_batch<kFmt, 16, 4, 5>(tb, ctas, st);
+    case 2: return run_J_batch<kFmt, 32, 2, 6>(tb, ctas, st);
+    default: return run_J_batch<kFmt, 32, 4, 4>(tb, ctas, st);
   }
 }
 
 template <int kFmt>
 cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, cudaStream_t st) {
   switch (variant) {
-    case 0: return run_JT_batch<kFmt, 1, 6>(tb, ctas, st);
-    case 1: return run_JT_batch<kFmt, 2, 5>(tb, ctas, st);
-    case 2: return run_JT_batch<kFmt, 4, 4>(tb, ctas, st);
-    default: return run_JT_batch<kFmt, 8, 3>(tb, ctas, st);
+    case 0: return run_JT_batch<kFmt, 16, 2, 6>(tb, ctas, st);
+    case 1: return run_JT_batch<kFmt, 16, 4, 5>(tb, ctas, st);
+    case 2: return run_JT_batch<kFmt, 32, 2, 6>(tb, ctas, st);
+    default: return run_JT_batch<kFmt, 32, 4, 4>(tb, ctas, st);
   }
 }
 
@@ -559,20 +613,20 @@ template <int kFmt>
 cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot, const float* F_add, float* u,
                             double* sq, cudaStream_t st) {
   switch (variant) {
-    case 0: return run_J<kFmt, 1, 6>(cv, ydot, F_add, u, sq, st);
-    case 1: return run_J<kFmt, 2, 5>(cv, ydot, F_add, u, sq, st);
-    case 2: return run_J<kFmt, 4, 4>(cv, ydot, F_add, u, sq, st);
-    default: return run_J<kFmt, 8, 3>(cv, ydot, F_add, u, sq, st);
+    case 0: return run_J<kFmt, 16, 2, 6>(cv, ydot, F_add, u, sq, st);
+    case 1: return run_J<kFmt, 16, 4, 5>(cv, ydot, F_add, u, sq, st);
+    case 2: return run_J<kFmt, 32, 2, 6>(cv, ydot, F_add, u, sq, st);
+    default: return run_J<kFmt, 32, 4, 4>(cv, ydot, F_add, u, sq, st);
   }
 }
 
 template <int kFmt>
 cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, float* seg_ybar, cudaStream_t st) {
   switch (variant) {
-    case 0: return run_JT<kFmt, 1, 6>(cv, u, seg_ybar, st);
-    case 1: return run_JT<kFmt, 2, 5>(cv, u, seg_ybar, st);
-    case 2: return run_JT<kFmt, 4, 4>(cv, u, seg_ybar, st);
-    default: return run_JT<kFmt, 8, 3>(cv, u, seg_ybar, st);
+    case 0: return run_JT<kFmt, 16, 2, 6>(cv, u, seg_ybar, st);
+    case 1: return run_JT<kFmt, 16, 4, 5>(cv, u, seg_ybar, st);
+    case 2: return run_JT<kFmt, 32, 2, 6>(cv, u, seg_ybar, st);
+    default: return run_JT<kFmt, 32, 4, 4>(cv, u, seg_ybar, st);
   }
 }
 
@@ -608,10 +662,10 @@ int device_sm_count() {
 }
 
 // Resident CTAs of a persistent grid: never more than the kernel variant's
-// register budget lets share an SM (6, 5, 4, 3 for variants 0..3), never more
+// register budget lets share an SM (6, 5, 6, 4 for variants 0..3), never more
 // CTAs than tiles.
 static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
-  const int cap = variant == 0 ? 6 : variant == 1 ? 5 : variant == 2 ? 4 : 3;
+  const int cap = variant == 0 ? 6 : variant == 1 ? 5 : variant == 2 ? 6 : 4;
   const int per = ctas_per_sm < 1 ? 1 : (ctas_per_sm > cap ? cap : ctas_per_sm);
   const long long c = (long long)device_sm_count() * per;
   return (int)(c < tb.total_tiles ? c : tb.total_tiles);

@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
     _fields_ = [("cache_fmt", c_int32), ("n_iters", c_int32), ("break_rel2", c_float),
                 ("lambda_min", c_float), ("lambda_max", c_float), ("smooth", c_int32),
                 ("mem_budget", c_size_t), ("group", c_int32), ("profile", c_int32), ("autotune", c_int32),
-                ("batch", c_int32), ("graph", c_int32), ("batch_ctas", c_int32), ("reserved", c_int32 * 2)]
+                ("batch", c_int32), ("graph", c_int32), ("batch_ctas", c_int32), ("apply_variant", c_int32),
+                ("reserved", c_int32 * 1)]
 
 
 class CacheInfo(ctypes.Structure):
