@@ -92,7 +92,7 @@ typedef struct {
   int32_t graph;       /* 1 (default): a batched solve is captured into one CUDA graph and launched
                           once (after the first batched solve of a context, which also autotunes) */
   int32_t batch_ctas;  /* resident CTAs per SM of the persistent batched tile kernels; 0 = autotune */
-  int32_t apply_variant; /* 0: autotuned (or default) apply kernel variant; 1..4: always variant 0..3 */
+  int32_t apply_variant; /* 0: autotuned (or default) apply kernel variant; 1..5: always variant 0..4 */
   int32_t reserved[1];
 } gslm_options;
 

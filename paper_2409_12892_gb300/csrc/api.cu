@@ -117,7 +117,7 @@ struct gslm_cache {
   double cost = 0.0;
   std::vector<DevCam> hcams;
   Buf cams, rec, slot_active, tile_seg_off, seg_entry_off, seg_slot, seg_rec, payload, seg_scale, pixoff;
-  Buf slot_seg_start, slot_seg_end, slot_seg_list, F, own_params, vmask;
+  Buf slot_seg_start, slot_seg_end, slot_seg_list, seg_pos, F, own_params, vmask;
 
   CacheView view() const {
     CacheView cv;
@@ -138,6 +138,7 @@ struct gslm_cache {
     cv.slot_seg_start = slot_seg_start.as<uint32_t>();
     cv.slot_seg_end = slot_seg_end.as<uint32_t>();
     cv.slot_seg_list = slot_seg_list.as<uint32_t>();
+    cv.seg_pos = seg_pos.as<uint32_t>();
     cv.slot_active = slot_active.as<uint8_t>();
     cv.vmask = vmask.as<unsigned long long>();
     cv.n_seg = n_seg;
@@ -150,7 +151,7 @@ struct gslm_cache {
     return cams.bytes + rec.bytes + slot_active.bytes + tile_seg_off.bytes + seg_entry_off.bytes + seg_slot.bytes +
            seg_rec.bytes +
            payload.bytes + seg_scale.bytes + pixoff.bytes + slot_seg_start.bytes + slot_seg_end.bytes +
-           slot_seg_list.bytes + F.bytes + own_params.bytes + vmask.bytes;
+           slot_seg_list.bytes + seg_pos.bytes + F.bytes + own_params.bytes + vmask.bytes;
   }
 };
 
@@ -479,11 +480,13 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
 }
 
 
-// Candidates of the persistent tile kernels' autotuner: (variant, CTAs per SM).
-constexpr int kBatchCand = 8;
+// Candidates of the persistent tile kernels' autotuner: (variant, CTAs per SM),
+// each variant at the residency its registers allow and one CTA fewer.
+constexpr int kBatchCand = 10;
 inline int cand_variant(int c) { return c / 2; }
 inline int cand_ctas(int c) {
-  const int cap = 6 - c / 2;   // resident CTAs the variant's registers allow: 6, 5, 4, 3
+  const int v = c / 2;
+  const int cap = v == 1 ? 5 : v == 3 ? 4 : 6;
   return (c & 1) ? cap - 1 : cap;
 }
 
@@ -622,10 +625,10 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
   auto apply_pair = [&]() -> gslm_status {
     bool t = ctx->timer.begin(PH_APPLY_J);
     if (forced >= 0) {
-      CKS(runJ(forced, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : 6 - forced));
+      CKS(runJ(forced, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : 6));
       ctx->timer.end(t);
       t = ctx->timer.begin(PH_APPLY_JT);
-      CKS(runJT(forced, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : 6 - forced));
+      CKS(runJT(forced, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : 6));
       ctx->timer.end(t);
       return GSLM_OK;
     }
@@ -843,7 +846,7 @@ static gslm_status validate_opts(const gslm_options* o) {
   if (!(o->lambda_min > 0.f) || !(o->lambda_max >= o->lambda_min)) return GSLM_E_INVALID;
   if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
   if (o->batch_ctas < 0 || o->batch_ctas > 6) return GSLM_E_INVALID;
-  if (o->apply_variant < 0 || o->apply_variant > 4) return GSLM_E_INVALID;
+  if (o->apply_variant < 0 || o->apply_variant > 5) return GSLM_E_INVALID;
   return GSLM_OK;
 }
 
@@ -1014,6 +1017,8 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
     CK(launch_ranges(sk, nseg, c->slot_seg_start.as<uint32_t>(), c->slot_seg_end.as<uint32_t>(), st));
     CK(c->slot_seg_list.alloc(sizeof(uint32_t) * ns, st));
     CK(cudaMemcpyAsync(c->slot_seg_list.p, sv, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
+    CK(c->seg_pos.alloc(sizeof(uint32_t) * ns, st));
+    CK(launch_scatter_index_u32(sv, nseg, c->seg_pos.as<uint32_t>(), st));
   }
   if (V <= 64) {
     CK(c->vmask.alloc(sizeof(unsigned long long) * (size_t)N, st));

@@ -139,6 +139,7 @@ __device__ __forceinline__ SegRec rec_from(const uint4& a, const uint4& b, const
 // words each; splat tangents for J p).
 struct Stage {
   uint4 r0[kStage], r1[kStage], r2[kStage];
+  uint32_t pos[kStage];     // slot-order position of the segment (J^T u output)
 };
 struct StageT {
   float4 t0[kStage], t1[kStage], t2[kStage];
@@ -154,6 +155,7 @@ __device__ __forceinline__ void stage_chunk(const CacheView& cv, uint32_t first,
     S.r0[t] = a;
     S.r1[t] = b;
     S.r2[t] = c;
+    if constexpr (!kTangent) S.pos[t] = cv.seg_pos[first + t];
     if constexpr (kTangent) {
       const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)b.x * 12);
       T->t0[t] = yd[0];
@@ -178,7 +180,7 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
                                              const float* __restrict__ Fadd, float* __restrict__ u,
                                              double* __restrict__ sq_partials, float* su, const float2* sxy,
                                              double* dred, unsigned int* next_seg, Stage& S, StageT& T) {
-  static_assert(G == 16 || G == 32, "group size");
+  static_assert(G == 8 || G == 16 || G == 32, "group size");
   constexpr int kGPW = 32 / G;
   const int v = find_view(cv.cams, cv.V, tile);
   const DevCam& cam = cv.cams[v];
@@ -343,7 +345,8 @@ __device__ __forceinline__ void halve(float (&v)[16], bool upper, int o) {
 
 // Sums 16 values over each group of G lanes (all 32 lanes converged). G = 32:
 // lanes 0, 2, ..., 30 then hold the sum of value index lane / 2 in v[0]; G = 16:
-// lane l of a group holds the sum of value index l in v[0].
+// lane l of a group holds the sum of value index l in v[0]; G = 8: lane l of
+// a group holds the sums of value indices 2l and 2l + 1 in v[0] and v[1].
 template <int G>
 __device__ __forceinline__ void group_sum16(float (&v)[16], int lane) {
   if constexpr (G == 32) {
@@ -352,21 +355,34 @@ __device__ __forceinline__ void group_sum16(float (&v)[16], int lane) {
     halve<4>(v, lane & 4, 4);
     halve<2>(v, lane & 2, 2);
     v[0] += __shfl_xor_sync(kFull, v[0], 1);
-  } else {
+  } else if constexpr (G == 16) {
     halve<16>(v, lane & 8, 8);
     halve<8>(v, lane & 4, 4);
     halve<4>(v, lane & 2, 2);
     halve<2>(v, lane & 1, 1);
+  } else {
+    halve<16>(v, lane & 4, 4);
+    halve<8>(v, lane & 2, 2);
+    halve<4>(v, lane & 1, 1);
   }
 }
 
-// J^T u over one tile into per-segment partials. The caller synchronises
-// before. su4 / sxy are filled here.
+// Moment i of the group after group_sum16<G>, on every lane of the group.
+template <int G>
+__device__ __forceinline__ float group_moment(const float (&v)[16], int i) {
+  if constexpr (G == 32) return __shfl_sync(kFull, v[0], 2 * i, 32);
+  else if constexpr (G == 16) return __shfl_sync(kFull, v[0], i, 16);
+  else return __shfl_sync(kFull, (i & 1) ? v[1] : v[0], i >> 1, 8);
+}
+
+// J^T u over one tile into per-segment partials, stored at each segment's
+// slot-order position (so the adjoint kernel reads a splat's partials as one
+// contiguous range). The caller synchronises before. su4 / sxy are filled here.
 template <int kFmt, int G, int U>
 __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, const float* __restrict__ u,
                                               float* __restrict__ seg_ybar, float4* su4, float2* sxy,
                                               unsigned int* next_seg, Stage& S) {
-  static_assert(G == 16 || G == 32, "group size");
+  static_assert(G == 8 || G == 16 || G == 32, "group size");
   constexpr int kGPW = 32 / G;
   const uint32_t g0 = cv.tile_seg_off[tile];
   const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
@@ -452,16 +468,19 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
       // m4 = sum s dx dy, m5 = sum s dy^2, m6..m8 = sum w u
       float m[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) m[i] = __shfl_sync(kFull, a[0], G == 32 ? 2 * i : i, G);
-      if (has && gl < 9) {
-        float val = m[gl < 9 ? gl : 0];
-        if (gl == 0) val = r.A * m[1] + r.B * m[2];
-        else if (gl == 1) val = r.B * m[1] + r.C * m[2];
-        else if (gl == 2) val = -0.5f * m[3];
-        else if (gl == 3) val = -m[4];
-        else if (gl == 4) val = -0.5f * m[5];
-        else if (gl == 5) val = m[0] * r.io;
-        seg_ybar[(size_t)(g0 + c0 + k) * 12 + gl] = val;
+      for (int i = 0; i < 9; ++i) m[i] = group_moment<G>(a, i);
+      if (has) {
+        // output o of the segment's 9 (G = 8: lane 0 also writes output 8)
+        for (int o = gl; o < 9; o += G) {
+          float val = m[o];
+          if (o == 0) val = r.A * m[1] + r.B * m[2];
+          else if (o == 1) val = r.B * m[1] + r.C * m[2];
+          else if (o == 2) val = -0.5f * m[3];
+          else if (o == 3) val = -m[4];
+          else if (o == 4) val = -0.5f * m[5];
+          else if (o == 5) val = m[0] * r.io;
+          seg_ybar[(size_t)S.pos[k] * 12 + o] = val;
+        }
       }
     }
     __syncthreads();
@@ -553,14 +572,15 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
 #pragma unroll
       for (int i = 0; i < 10; ++i)
         if (lane == i) val = make_float4(q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]);
-      reinterpret_cast<float4*>(seg_q + (size_t)seg * 40)[lane] = val;
+      reinterpret_cast<float4*>(seg_q + (size_t)cv.seg_pos[seg] * 40)[lane] = val;
     }
   }
 }
 
 // Variants: lanes per segment (G), entries each lane keeps in flight (U) and
 // the minimum number of resident 256-thread blocks per SM the registers must
-// allow: 0 = (16, 2, 6), 1 = (16, 4, 5), 2 = (32, 2, 6), 3 = (32, 4, 4).
+// allow: 0 = (16, 2, 6), 1 = (16, 4, 5), 2 = (32, 2, 6), 3 = (32, 4, 4),
+// 4 = (8, 2, 6).
 template <int kFmt, int G, int U, int B>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
   k_apply_J<kFmt, G, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
@@ -595,7 +615,8 @@ cudaError_t apply_J_batch_variant(int variant, const TileBatch& tb, int ctas, cu
     case 0: return run_J_batch<kFmt, 16, 2, 6>(tb, ctas, st);
     case 1: return run_J_batch<kFmt, 16, 4, 5>(tb, ctas, st);
     case 2: return run_J_batch<kFmt, 32, 2, 6>(tb, ctas, st);
-    default: return run_J_batch<kFmt, 32, 4, 4>(tb, ctas, st);
+    case 3: return run_J_batch<kFmt, 32, 4, 4>(tb, ctas, st);
+    default: return run_J_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
 
@@ -605,7 +626,8 @@ cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, c
     case 0: return run_JT_batch<kFmt, 16, 2, 6>(tb, ctas, st);
     case 1: return run_JT_batch<kFmt, 16, 4, 5>(tb, ctas, st);
     case 2: return run_JT_batch<kFmt, 32, 2, 6>(tb, ctas, st);
-    default: return run_JT_batch<kFmt, 32, 4, 4>(tb, ctas, st);
+    case 3: return run_JT_batch<kFmt, 32, 4, 4>(tb, ctas, st);
+    default: return run_JT_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
 
@@ -616,7 +638,8 @@ cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot,
     case 0: return run_J<kFmt, 16, 2, 6>(cv, ydot, F_add, u, sq, st);
     case 1: return run_J<kFmt, 16, 4, 5>(cv, ydot, F_add, u, sq, st);
     case 2: return run_J<kFmt, 32, 2, 6>(cv, ydot, F_add, u, sq, st);
-    default: return run_J<kFmt, 32, 4, 4>(cv, ydot, F_add, u, sq, st);
+    case 3: return run_J<kFmt, 32, 4, 4>(cv, ydot, F_add, u, sq, st);
+    default: return run_J<kFmt, 8, 2, 6>(cv, ydot, F_add, u, sq, st);
   }
 }
 
@@ -626,7 +649,8 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
     case 0: return run_JT<kFmt, 16, 2, 6>(cv, u, seg_ybar, st);
     case 1: return run_JT<kFmt, 16, 4, 5>(cv, u, seg_ybar, st);
     case 2: return run_JT<kFmt, 32, 2, 6>(cv, u, seg_ybar, st);
-    default: return run_JT<kFmt, 32, 4, 4>(cv, u, seg_ybar, st);
+    case 3: return run_JT<kFmt, 32, 4, 4>(cv, u, seg_ybar, st);
+    default: return run_JT<kFmt, 8, 2, 6>(cv, u, seg_ybar, st);
   }
 }
 
@@ -634,7 +658,7 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
 
 int apply_J_partials(const CacheView& cv) { return cv.n_tiles; }
 
-int apply_variants() { return 4; }
+int apply_variants() { return 5; }
 
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add, float* u,
                            double* sq_partials, int variant, cudaStream_t st) {
@@ -662,10 +686,10 @@ int device_sm_count() {
 }
 
 // Resident CTAs of a persistent grid: never more than the kernel variant's
-// register budget lets share an SM (6, 5, 6, 4 for variants 0..3), never more
-// CTAs than tiles.
+// register budget lets share an SM (6, 5, 6, 4, 6 for variants 0..4), never
+// more CTAs than tiles.
 static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
-  const int cap = variant == 0 ? 6 : variant == 1 ? 5 : variant == 2 ? 6 : 4;
+  const int cap = variant == 1 ? 5 : variant == 3 ? 4 : 6;
   const int per = ctas_per_sm < 1 ? 1 : (ctas_per_sm > cap ? cap : ctas_per_sm);
   const long long c = (long long)device_sm_count() * per;
   return (int)(c < tb.total_tiles ? c : tb.total_tiles);

@@ -134,6 +134,8 @@ struct CacheView {
   const uint32_t* slot_seg_start;  // [n_slots] segments of a slot, as a range of slot_seg_list
   const uint32_t* slot_seg_end;
   const uint32_t* slot_seg_list;   // [n_seg] segment ids ordered by slot
+  const uint32_t* seg_pos;         // [n_seg] position of a segment in slot_seg_list: per-segment
+                                   // adjoints and diagonal blocks are stored in this (slot) order
   const uint8_t* slot_active;      // [n_slots]
   const unsigned long long* vmask; // [N] active views per Gaussian (null when V > 64)
   long long n_seg;
@@ -163,7 +165,7 @@ struct SubsetRefs {
   const uint32_t* s_end;
   const uint32_t* s_list;
   float* ydot;                          // [N * V][12] splat tangents
-  float* seg_ybar;                      // [n_seg][12] per-segment adjoints
+  float* seg_ybar;                      // [n_seg][12] per-segment adjoints, in slot order
 };
 struct GaussBatch {
   int n;
@@ -260,6 +262,8 @@ cudaError_t launch_compact_flags(const uint32_t* counts, const uint32_t* pos, lo
 cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, long long n,
                               uint32_t* dst, cudaStream_t st);
 cudaError_t launch_iota_u32(uint32_t* dst, long long n, cudaStream_t st);
+// dst[idx[i]] = i for i < n (inverse of a permutation)
+cudaError_t launch_scatter_index_u32(const uint32_t* idx, long long n, uint32_t* dst, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t* sorted_keys, long long n, uint32_t* start,
                           uint32_t* end, cudaStream_t st);
 

@@ -337,104 +337,130 @@ __global__ void k_project(const float* __restrict__ P, int N, long long ld, cons
   depth_key[s] = __float_as_uint(VG.tc[2]);
 }
 
-// ydot[slot] = (dy/dx) p for every active slot of every Gaussian. With z_beta
-// given, first p = z + beta p (Algorithm 1's last vector update, fused), and the
-// new p is written back to p_out.
+// The per-Gaussian kernels split each Gaussian's work over the four warps of a
+// 128-thread block (32 Gaussians per block, lane = Gaussian): warp 0 takes the
+// geometry (mean, scale, rotation, opacity), warp 1 + c the SH coefficients of
+// colour channel c and that channel's view-direction term of the mean. Warps
+// never diverge on the role, and no thread holds all 59 parameters at once.
+constexpr int kGPB = 32;   // Gaussians per block
+
+// Parameter rows owned by a role: 0 -> rows 0..10; 1 + c -> rows 11 + 3k + c.
+__device__ __forceinline__ int role_rows(int role) { return role == 0 ? 11 : 16; }
+__device__ __forceinline__ int role_row(int role, int i) { return role == 0 ? i : 11 + 3 * i + (role - 1); }
+
+// ydot[slot] = (dy/dx) p for every active slot of Gaussian g. With z_beta
+// given, first p = z + beta p (Algorithm 1's last vector update, fused), and
+// the new p is written back to p_out. Roles: see above; the geometry warp
+// writes floats 0..5 of the slot's 12, warp 1 + c float 6 + c.
 __device__ __forceinline__ void tangent_body(
-    int g, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
-    const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
+    int g, int role, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V,
+    int smooth, const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
     const float* __restrict__ pin, float* __restrict__ ydot, const float* __restrict__ zb,
     float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
   if (g >= N) return;
   if (sc != nullptr && sc->done) return;
-  float pd[kNP];
-  if (zb != nullptr) {
-    const float beta = (float)sc->beta;
+  const float beta = zb != nullptr ? (float)sc->beta : 0.f;
+  auto pval = [&](int row) -> float {
+    const long long o = (long long)row * ld + g;
+    return zb != nullptr ? zb[o] + beta * pin[o] : pin[o];
+  };
+  // own rows (updated and written back when fused), and the mean rows
+  float pm[3];
 #pragma unroll
-    for (int k = 0; k < kNP; ++k) {
-      const float v = zb[k * ld + g] + beta * pin[k * ld + g];
-      pd[k] = v;
-      pout[k * ld + g] = v;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < kNP; ++k) pd[k] = pin[k * ld + g];
-  }
+  for (int i = 0; i < 3; ++i) pm[i] = pval(i);
   const bool use_mask = vmask != nullptr;
   unsigned long long mm = use_mask ? vmask[g] : 0ull;
-  if (use_mask) {
-    if (mm == 0) return;
+  if (role == 0) {
+    float pg[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) {
+      pg[i] = i < 3 ? pm[i] : pval(i);
+      if (pout != nullptr) pout[(long long)i * ld + g] = pg[i];
+    }
+    if (use_mask && mm == 0) return;
+    GaussGeo G;
+    gauss_geo(P, ld, g, G);
+    float Sd[6];
+    sigma_tangent(G, pg + 3, pg + 6, Sd);
+    const float od = G.o * (1.f - G.o) * pg[10];
+    for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
+      const long long slot = (long long)v * N + g;
+      if (!slot_active[slot]) continue;
+      const DevCam& cam = cams[v];
+      ViewGeo VG;
+      view_geo(G, cam, VG);
+      float yd[5];
+      geo_tangent(VG, cam, pm, Sd, yd);
+      float* out = ydot + slot * 12;
+      reinterpret_cast<float4*>(out)[0] = make_float4(yd[0], yd[1], yd[2], yd[3]);
+      reinterpret_cast<float2*>(out)[2] = make_float2(yd[4], od);
+    }
   } else {
-    bool any = false;
-    for (int v = 0; v < V; ++v) any |= slot_active[(long long)v * N + g] != 0;
-    if (!any) return;
-  }
-  GaussGeo G;
-  gauss_geo(P, ld, g, G);
-  float Sd[6];
-  sigma_tangent(G, pd + 3, pd + 6, Sd);
-  const float od = G.o * (1.f - G.o) * pd[10];
-  for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
-    const long long slot = (long long)v * N + g;
-    if (!slot_active[slot]) continue;
-    const DevCam& cam = cams[v];
-    ViewGeo VG;
-    view_geo(G, cam, VG);
-    float yd[5];
-    geo_tangent(VG, cam, pd, Sd, yd);
-    float Y[16];
-    sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
-    const float mdot = VG.dir[0] * pd[0] + VG.dir[1] * pd[1] + VG.dir[2] * pd[2];
-    float dd[3];
+    const int ch = role - 1;
+    float ps[16], w[16];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dd[i] = (pd[i] - VG.dir[i] * mdot) * VG.inv_dlen;
-    float rgbd[3];
+    for (int k = 0; k < 16; ++k) {
+      const int row = 11 + 3 * k + ch;
+      ps[k] = pval(row);
+      if (pout != nullptr) pout[(long long)row * ld + g] = ps[k];
+    }
+    if (use_mask && mm == 0) return;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float w[16];
+    for (int k = 0; k < 16; ++k) w[k] = P[(11 + 3 * k + ch) * ld + g];
+    const float mu0 = P[g], mu1 = P[ld + g], mu2 = P[2 * ld + g];
+    for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
+      const long long slot = (long long)v * N + g;
+      if (!slot_active[slot]) continue;
+      const DevCam& cam = cams[v];
+      const float d0 = mu0 - cam.campos[0], d1 = mu1 - cam.campos[1], d2 = mu2 - cam.campos[2];
+      const float inv_dlen = 1.f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      const float dir[3] = {d0 * inv_dlen, d1 * inv_dlen, d2 * inv_dlen};
+      float Y[16];
+      sh_basis(dir[0], dir[1], dir[2], Y);
+      const float mdot = dir[0] * pm[0] + dir[1] * pm[1] + dir[2] * pm[2];
       float raw = kShOffset, acc = 0.f;
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        w[k] = P[(11 + 3 * k + ch) * ld + g];
         raw += Y[k] * w[k];
-        acc += Y[k] * pd[11 + 3 * k + ch];
+        acc += Y[k] * ps[k];
       }
       float gr[3];
-      sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], w, gr);
-      acc += gr[0] * dd[0] + gr[1] * dd[1] + gr[2] * dd[2];
-      rgbd[ch] = (!smooth && raw < 0.f) ? 0.f : acc;
+      sh_grad(dir[0], dir[1], dir[2], w, gr);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc += gr[i] * (pm[i] - dir[i] * mdot) * inv_dlen;
+      ydot[slot * 12 + 6 + ch] = (!smooth && raw < 0.f) ? 0.f : acc;
     }
-    float4* out = reinterpret_cast<float4*>(ydot + slot * 12);
-    out[0] = make_float4(yd[0], yd[1], yd[2], yd[3]);
-    out[1] = make_float4(yd[4], od, rgbd[0], rgbd[1]);
-    out[2] = make_float4(rgbd[2], 0.f, 0.f, 0.f);
   }
 }
 
 // g = scale * (dy/dx)^T ybar summed over the views; ybar of a slot is the sum
-// of its segments' partial sums. Epilogue (M != null): g += lambda M p and a
-// per-block float64 partial of p^T g.
+// of its segments' partial sums, which the tile kernel stores in slot order:
+// the slot's range [s_start, s_end) of positions (s_list is not read here).
+// Epilogue (M != null): g += lambda M p and a per-block float64 partial of
+// p^T g. Roles as for the tangent; the colour warps hand their view-direction
+// terms of the mean gradient to the geometry warp through shared memory.
+// All 128 threads of the block call this with the same g0.
 __device__ __forceinline__ void vjp_body(
-    int g, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+    int g0, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ vmask,
-    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
-    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
-    const PcgScalars* __restrict__ sc) {
-  const bool skip = (sc != nullptr && sc->done);
-  double local = 0.0;
-  if (g < N && !skip) {
-    float mub[3] = {0.f, 0.f, 0.f};
+    const unsigned long long* __restrict__ vmask, const float* __restrict__ seg_ybar, float scale,
+    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
+    float (*s_mub)[kGPB][3], double& local) {
+  const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
+  const int g = g0 + lane;
+  const bool valid = g < N;
+  const bool use_mask = vmask != nullptr;
+  unsigned long long mm = (use_mask && valid) ? vmask[g] : 0ull;
+  float mub[3] = {0.f, 0.f, 0.f};
+  float out[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) out[k] = 0.f;
+  if (role == 0) {
     float GS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float ob = 0.f;
-    float shb[48];
-#pragma unroll
-    for (int k = 0; k < 48; ++k) shb[k] = 0.f;
     bool any = false;
     GaussGeo G;
-    const bool use_mask = vmask != nullptr;
-    unsigned long long mm = use_mask ? vmask[g] : 0ull;
-    for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
+    for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
       const long long slot = (long long)v * N + g;
       const uint32_t a = s_start[slot], b = s_end[slot];
       if (a == b) continue;
@@ -442,45 +468,16 @@ __device__ __forceinline__ void vjp_body(
         gauss_geo(P, ld, g, G);
         any = true;
       }
-      float yb[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) yb[i] = 0.f;
+      float yb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (uint32_t j = a; j < b; ++j) {
-        const float4* s4 = reinterpret_cast<const float4*>(seg_ybar + (size_t)s_list[j] * 12);
-        const float4 u0 = s4[0], u1 = s4[1], u2 = s4[2];
-        yb[0] += u0.x; yb[1] += u0.y; yb[2] += u0.z; yb[3] += u0.w;
-        yb[4] += u1.x; yb[5] += u1.y; yb[6] += u1.z; yb[7] += u1.w; yb[8] += u2.x;
+        const float* sy = seg_ybar + (size_t)j * 12;
+        const float4 u0 = *reinterpret_cast<const float4*>(sy);
+        const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
+        yb[0] += u0.x; yb[1] += u0.y; yb[2] += u0.z; yb[3] += u0.w; yb[4] += u1.x; yb[5] += u1.y;
       }
       const DevCam& cam = cams[v];
       ViewGeo VG;
       view_geo(G, cam, VG);
-      // colour -> SH coefficients and view direction
-      float Y[16];
-      sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
-      float wsum[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float raw = kShOffset;
-        float shv[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          shv[k] = P[(11 + 3 * k + ch) * ld + g];
-          raw += Y[k] * shv[k];
-        }
-        const float rb = (!smooth && raw < 0.f) ? 0.f : yb[6 + ch];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          shb[3 * k + ch] += Y[k] * rb;
-          wsum[k] += rb * shv[k];
-        }
-      }
-      float db[3];
-      sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], wsum, db);
-      const float dd = VG.dir[0] * db[0] + VG.dir[1] * db[1] + VG.dir[2] * db[2];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) mub[i] += (db[i] - VG.dir[i] * dd) * VG.inv_dlen;
       ob += yb[5];
       // conic -> 2D covariance
       const float A = VG.A, B = VG.B, C = VG.C;
@@ -519,11 +516,7 @@ __device__ __forceinline__ void vjp_body(
 #pragma unroll
       for (int i = 0; i < 3; ++i) mub[i] += W[0 * 3 + i] * tb[0] + W[1 * 3 + i] * tb[1] + W[2 * 3 + i] * tb[2];
     }
-    float out[kNP];
-#pragma unroll
-    for (int k = 0; k < kNP; ++k) out[k] = 0.f;
     if (any) {
-      out[0] = mub[0]; out[1] = mub[1]; out[2] = mub[2];
       // 3D covariance -> M = R diag(S): Mb = 2 GS M
       float Mb[9];
 #pragma unroll
@@ -553,34 +546,83 @@ __device__ __forceinline__ void vjp_body(
 #pragma unroll
       for (int i = 0; i < 4; ++i) out[6 + i] = (qb[i] - G.qn[i] * qd) * G.qinv;
       out[10] = ob * G.o * (1.f - G.o);
-#pragma unroll
-      for (int k = 0; k < 48; ++k) out[11 + k] = shb[k];
     }
-    if (Mdiag != nullptr) {
+  } else {
+    // colour channel ch: SH coefficient gradients and the view-direction term of the mean
+    const int ch = role - 1;
+    float w[16];
+    float mu0 = 0.f, mu1 = 0.f, mu2 = 0.f;
+    if (valid && (!use_mask || mm != 0)) {
 #pragma unroll
-      for (int k = 0; k < kNP; ++k) {
-        const float pk = p[k * ld + g];
-        const float gk = scale * out[k] + lambda * clamp_diag(Mdiag[k * ld + g]) * pk;
-        gout[k * ld + g] = gk;
-        local += (double)pk * (double)gk;
+      for (int k = 0; k < 16; ++k) w[k] = P[(11 + 3 * k + ch) * ld + g];
+      mu0 = P[g];
+      mu1 = P[ld + g];
+      mu2 = P[2 * ld + g];
+    }
+    for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
+      const long long slot = (long long)v * N + g;
+      const uint32_t a = s_start[slot], b = s_end[slot];
+      if (a == b) continue;
+      float yc = 0.f;
+      for (uint32_t j = a; j < b; ++j) yc += seg_ybar[(size_t)j * 12 + 6 + ch];
+      const DevCam& cam = cams[v];
+      const float d0 = mu0 - cam.campos[0], d1 = mu1 - cam.campos[1], d2 = mu2 - cam.campos[2];
+      const float inv_dlen = 1.f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      const float dir[3] = {d0 * inv_dlen, d1 * inv_dlen, d2 * inv_dlen};
+      float Y[16];
+      sh_basis(dir[0], dir[1], dir[2], Y);
+      float raw = kShOffset;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) raw += Y[k] * w[k];
+      const float rb = (!smooth && raw < 0.f) ? 0.f : yc;
+      float wsum[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        out[k] += Y[k] * rb;
+        wsum[k] = rb * w[k];
       }
-    } else {
+      float db[3];
+      sh_grad(dir[0], dir[1], dir[2], wsum, db);
+      const float dd = dir[0] * db[0] + dir[1] * db[1] + dir[2] * db[2];
 #pragma unroll
-      for (int k = 0; k < kNP; ++k) gout[k * ld + g] = scale * out[k];
+      for (int i = 0; i < 3; ++i) mub[i] += (db[i] - dir[i] * dd) * inv_dlen;
     }
   }
-  if (partials != nullptr) {
-    // block reduction of the float64 partial dot
-    __shared__ double red[4];
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-      partials[blockIdx.x] = s;
+  s_mub[role][lane][0] = mub[0];
+  s_mub[role][lane][1] = mub[1];
+  s_mub[role][lane][2] = mub[2];
+  __syncthreads();
+  if (role == 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] = s_mub[0][lane][i] + s_mub[1][lane][i] + s_mub[2][lane][i] + s_mub[3][lane][i];
+  }
+  if (valid) {
+    const int nr = role_rows(role);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (i < nr) {
+        const long long o = (long long)role_row(role, i) * ld + g;
+        if (Mdiag != nullptr) {
+          const float pk = p[o];
+          const float gk = scale * out[i] + lambda * clamp_diag(Mdiag[o]) * pk;
+          gout[o] = gk;
+          local += (double)pk * (double)gk;
+        } else {
+          gout[o] = scale * out[i];
+        }
+      }
     }
   }
+  __syncthreads();   // s_mub is reused by the next group of Gaussians
+}
+
+// Block reduction of the float64 partial dot into partials[blockIdx.x].
+__device__ __forceinline__ void write_dot_partial(double local, double* __restrict__ partials) {
+  __shared__ double red[4];
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
 }
 
 __global__ void __launch_bounds__(128) k_tangent(
@@ -588,8 +630,8 @@ __global__ void __launch_bounds__(128) k_tangent(
     const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
     const float* __restrict__ pin, float* __restrict__ ydot, const float* __restrict__ zb,
     float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
-  tangent_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, cams, V, smooth, slot_active, vmask, pin, ydot, zb,
-               pout, sc);
+  tangent_body(blockIdx.x * kGPB + (threadIdx.x & 31), threadIdx.x >> 5, P, N, ld, cams, V, smooth, slot_active,
+               vmask, pin, ydot, zb, pout, sc);
 }
 
 // Batched: blockIdx.y is the subset; its p, z and pout sit at offset
@@ -602,25 +644,44 @@ __global__ void __launch_bounds__(128) k_tangent_batch(const float* __restrict__
   const int b = blockIdx.y;
   const SubsetRefs& s = gb.s[b];
   const long long off = (long long)b * vs;
-  tangent_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, s.cams, s.V, smooth, s.slot_active, s.vmask,
-               pin + off, s.ydot, zb != nullptr ? zb + off : nullptr, pout != nullptr ? pout + off : nullptr,
-               sc != nullptr ? sc + b : nullptr);
+  tangent_body(blockIdx.x * kGPB + (threadIdx.x & 31), threadIdx.x >> 5, P, N, ld, s.cams, s.V, smooth,
+               s.slot_active, s.vmask, pin + off, s.ydot, zb != nullptr ? zb + off : nullptr,
+               pout != nullptr ? pout + off : nullptr, sc != nullptr ? sc + b : nullptr);
 }
 
-__global__ void __launch_bounds__(128) k_vjp(
+// Each block loops over groups of 32 Gaussians (bounded grid: at most
+// kVjpBlocks float64 partials per call).
+constexpr int kVjpBlocks = 2432;
+
+__device__ __forceinline__ void vjp_blocks_loop(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ vmask,
-    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
-    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
-    const PcgScalars* __restrict__ sc) {
-  vjp_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, cams, V, smooth, s_start, s_end, s_list, vmask, seg_ybar,
-           scale, gout, p, Mdiag, lambda, partials, sc);
+    const unsigned long long* __restrict__ vmask, const float* __restrict__ seg_ybar, float scale,
+    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
+    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
+  __shared__ float s_mub[4][kGPB][3];
+  double local = 0.0;
+  if (sc == nullptr || !sc->done) {
+    for (int g0 = blockIdx.x * kGPB; g0 < N; g0 += gridDim.x * kGPB)
+      vjp_body(g0, P, N, ld, cams, V, smooth, s_start, s_end, vmask, seg_ybar, scale, gout, p, Mdiag, lambda, s_mub,
+               local);
+  }
+  if (partials != nullptr) write_dot_partial(local, partials);
+}
+
+__global__ void __launch_bounds__(128, 4) k_vjp(
+    const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
+    const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
+    const unsigned long long* __restrict__ vmask, const float* __restrict__ seg_ybar, float scale,
+    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
+    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
+  vjp_blocks_loop(P, N, ld, cams, V, smooth, s_start, s_end, vmask, seg_ybar, scale, gout, p, Mdiag, lambda, partials,
+                  sc);
 }
 
 // Batched: blockIdx.y is the subset; g, p and M at offset blockIdx.y * vs, the
 // float64 partials at blockIdx.y * gridDim.x.
-__global__ void __launch_bounds__(128) k_vjp_batch(const float* __restrict__ P, int N, long long ld, int smooth,
+__global__ void __launch_bounds__(128, 4) k_vjp_batch(const float* __restrict__ P, int N, long long ld, int smooth,
                                                    const __grid_constant__ GaussBatch gb, float* __restrict__ gout,
                                                    long long vs, const float* __restrict__ p,
                                                    const float* __restrict__ Mdiag, float lambda,
@@ -628,10 +689,9 @@ __global__ void __launch_bounds__(128) k_vjp_batch(const float* __restrict__ P, 
   const int b = blockIdx.y;
   const SubsetRefs& s = gb.s[b];
   const long long off = (long long)b * vs;
-  vjp_body(blockIdx.x * blockDim.x + threadIdx.x, P, N, ld, s.cams, s.V, smooth, s.s_start, s.s_end, s.s_list,
-           s.vmask, s.seg_ybar, 1.f, gout + off, p != nullptr ? p + off : nullptr,
-           Mdiag != nullptr ? Mdiag + off : nullptr, lambda,
-           partials != nullptr ? partials + (size_t)b * gridDim.x : nullptr, sc != nullptr ? sc + b : nullptr);
+  vjp_blocks_loop(P, N, ld, s.cams, s.V, smooth, s.s_start, s.s_end, s.vmask, s.seg_ybar, 1.f, gout + off,
+                  p != nullptr ? p + off : nullptr, Mdiag != nullptr ? Mdiag + off : nullptr, lambda,
+                  partials != nullptr ? partials + (size_t)b * gridDim.x : nullptr, sc != nullptr ? sc + b : nullptr);
 }
 
 // diag(J^T J) for every Gaussian: sum over views of v_k^T Q v_k, where v_k is
@@ -663,7 +723,7 @@ __global__ void __launch_bounds__(128) k_diag(
 #pragma unroll
     for (int i = 0; i < 40; ++i) Q[i] = 0.f;
     for (uint32_t j = a; j < b; ++j) {
-      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)s_list[j] * 40);
+      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * 40);   // slot order
 #pragma unroll
       for (int i = 0; i < 10; ++i) {
         const float4 t = q4[i];
@@ -765,19 +825,19 @@ cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCa
                            const uint8_t* slot_active, const unsigned long long* vmask, const float* p,
                            float* ydot, const float* z_beta, float* p_out, const PcgScalars* sc, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_tangent<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, slot_active, vmask, p, ydot,
-                                             z_beta, p_out, sc); note_launch(); }
+  { k_tangent<<<(N + kGPB - 1) / kGPB, 128, 0, st>>>(params, N, ld, cams, V, smooth, slot_active, vmask, p, ydot,
+                                                     z_beta, p_out, sc); note_launch(); }
   return cudaGetLastError();
 }
 
-int vjp_blocks(int N) { return (N + 127) / 128; }
+int vjp_blocks(int N) { return std::max(1, std::min((N + kGPB - 1) / kGPB, kVjpBlocks)); }
 
 cudaError_t launch_tangent_batch(const float* params, int N, long long ld, int smooth, const GaussBatch& gb,
                                  const float* p, long long vs, const float* z_beta, float* p_out,
                                  const PcgScalars* sc, cudaStream_t st) {
   if (N == 0 || gb.n <= 0) return cudaSuccess;
-  { k_tangent_batch<<<dim3((N + 127) / 128, gb.n), 128, 0, st>>>(params, N, ld, smooth, gb, p, vs, z_beta, p_out,
-                                                                 sc); note_launch(); }
+  { k_tangent_batch<<<dim3((N + kGPB - 1) / kGPB, gb.n), 128, 0, st>>>(params, N, ld, smooth, gb, p, vs, z_beta,
+                                                                       p_out, sc); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -796,8 +856,9 @@ cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* c
                        const float* p, const float* M, float lambda, double* partials, const PcgScalars* sc,
                        cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, vmask, seg_ybar,
-                                       scale, g, p, M, lambda, partials, sc); note_launch(); }
+  (void)s_list;   // segment adjoints are stored in slot order
+  { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, vmask, seg_ybar, scale, g,
+                                       p, M, lambda, partials, sc); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -252,6 +252,11 @@ __global__ void k_gather(const uint32_t* __restrict__ src, const uint32_t* __res
   if (i < n) dst[i] = src[idx[i]];
 }
 
+__global__ void k_scatter_index(const uint32_t* __restrict__ idx, long long n, uint32_t* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[idx[i]] = (uint32_t)i;
+}
+
 __global__ void k_iota(uint32_t* __restrict__ dst, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = (uint32_t)i;
@@ -332,6 +337,12 @@ cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, long lon
                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   { k_gather<<<grid_for(n, 256), 256, 0, st>>>(src, idx, n, dst); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_index_u32(const uint32_t* idx, long long n, uint32_t* dst, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { k_scatter_index<<<grid_for(n, 256), 256, 0, st>>>(idx, n, dst); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -223,7 +223,7 @@ class Context:
 
     def __init__(self, cache_fmt="fp32", n_iters=8, break_rel2=0.01, lambda_min=1e-4, lambda_max=1e4,
                  smooth=False, mem_budget=0, group=32, profile=False, autotune=True, batch=True, graph=True,
-                 batch_ctas=0, stream=None):
+                 batch_ctas=0, apply_variant=0, stream=None):
         self.lib = load_library()
         opt = Options()
         self.lib.gslm_default_options(ctypes.byref(opt))
@@ -234,6 +234,7 @@ class Context:
         opt.profile = int(bool(profile))
         opt.autotune = int(bool(autotune))
         opt.batch, opt.graph, opt.batch_ctas = int(bool(batch)), int(bool(graph)), int(batch_ctas)
+        opt.apply_variant = int(apply_variant)
         self.opt = opt
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
