@@ -6,7 +6,8 @@ plain FP32. One step = one LM iteration of the paper-scale synthetic workload
 (1.5M Gaussians in 20 clusters, 200 cameras at 1264x832, four subsets of 25
 views): per subset the gradient cache, the diagonal and the PCG solve
 (Algorithm 1, 8 iterations, break test 0.01), then the weighted mean of the
-subset directions, rho with the trial render and the damping update.
+subset directions, the line search over the step scale (Eq. line-search, on
+30% of the step's views), rho with the trial render and the damping update.
 
 Forms: "chosen" = BF16 cache, learned diagonal preconditioner (trained on the
 GPU on step 0's subset systems before timing), the subsets' solves batched and
@@ -527,6 +528,7 @@ def equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap: int, pc=N
     del params
     after = lm.cost_new if lm.accepted else lm.cost
     return {"ms": ev0.elapsed_time(ev1), "precond": "learned" if pc is not None else "jacobi", "lambda": lam,
+            "gamma": lm.gamma,
             "reached": lm.pcg_iters < cap * len(subsets), "pcg_iters_total": lm.pcg_iters,
             "pcg_iters_per_subset": lm.pcg_iters / len(subsets), "accepted": int(lm.accepted), "rho": lm.rho,
             "cost": lm.cost, "cost_new": lm.cost_new, "predicted": lm.predicted,
@@ -630,6 +632,7 @@ def run_ours(args):
         "precond_training": ch["train"],
         "precond_judge": ch["judge"],
         "lm": {"accepted": [int(s.accepted) for s in stats], "rho": [s.rho for s in stats],
+               "gamma": [s.gamma for s in stats], "line_search_evals": [s.ls_evals for s in stats],
                "cost": [s.cost for s in stats], "cost_new": [s.cost_new for s in stats],
                "predicted": [s.predicted for s in stats], "pcg_iters": [s.pcg_iters for s in stats],
                "cache_entries": E_step, "cache_gb": statistics.mean(s.cache_bytes for s in stats) / 1e9,

@@ -93,7 +93,9 @@ typedef struct {
                           once (after the first batched solve of a context, which also autotunes) */
   int32_t batch_ctas;  /* resident CTAs per SM of the persistent batched tile kernels; 0 = autotune */
   int32_t apply_variant; /* 0: autotuned (or default) apply kernel variant; 1..5: always variant 0..4 */
-  int32_t reserved[1];
+  int32_t line_search; /* gslm_lm_step: 0 = full step (gamma = 1); n > 0 = Eq. line-search over
+                          gamma = 1, 1/2, ..., 2^(1-n) on the first 30% of the step's views,
+                          stopping at the first cost increase (default 8) */
 } gslm_options;
 
 typedef struct gslm_ctx gslm_ctx;
@@ -146,6 +148,9 @@ typedef struct {
   double pair_bytes;
   int64_t cache_segments; /* non-empty (tile, splat) segments, summed over subsets */
   int64_t active_splats;  /* splats with at least one cache entry, summed over subsets */
+  double gamma;           /* step scale the line search chose (1 without line search) */
+  int32_t ls_evals;       /* line-search cost evaluations */
+  int32_t pad2;
 } gslm_lm_stats;
 
 /* Default options: FP32 cache, 8 iterations, break 0.01, lambda in [1e-4, 1e4]. */
@@ -237,7 +242,9 @@ gslm_status gslm_combine_finish(gslm_ctx* ctx, int64_t N, int64_t ld, const floa
 /* One LM step [Sec. 3.2]: for each of the n_b subsets build the cache, the
  * Jacobi diagonal and the PCG direction; combine [Eq. combine-pcg]; evaluate
  * rho [Eq. tr-update] with gamma = 1; on acceptance (rho > 1e-5) params +=
- * Delta in place, else params are unchanged; lambda is updated and clamped.
+ * gamma Delta in place (gamma from the line search of Eq. line-search when
+ * options.line_search > 0, else 1), else params are unchanged; lambda is
+ * updated and clamped.
  * cams: host array of all cameras; targets: [sum over all cams W*H][3] in camera
  * order; subset_views: host, concatenated camera indices of the subsets;
  * subset_off: host, n_b + 1 offsets into subset_views. precond: optional

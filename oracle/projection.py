@@ -220,7 +220,18 @@ def _project(P: np.ndarray, cam, smooth: bool, want_jac: bool) -> Projection:
         r_outer, r_inner = rect, rect
     flip = np.any(r_outer != r_inner, axis=1) | (np.abs(tz.v - cv.NEAR) < 1e-5)
 
-    ok = (det.v > 0) & (x1 > x0) & (y1 > y0)
+    # A splat is drawn only if its covariance chain fits the renderer's float32
+    # arithmetic: scales, 3D and 2D covariance (with the products of the
+    # determinant), conic and mean must stay finite in float32. Decided here in
+    # that precision, as the renderer decides it; float64 would keep splats
+    # whose float32 covariance overflows.
+    f32max = float(np.finfo(np.float32).max)
+    fits = np.ones(S, bool)
+    with np.errstate(over="ignore", invalid="ignore"):
+        for v in ([q.v for q in sc] + [Sig[i][j].v for i in range(3) for j in range(i, 3)]
+                  + [a.v, b.v, c.v, a.v * c.v, b.v * b.v, det.v, A.v, B.v, C.v, mx.v, my.v]):
+            fits &= np.isfinite(v) & (np.abs(v) <= f32max)
+    ok = (det.v > 0) & fits & (x1 > x0) & (y1 > y0)
     sel = np.nonzero(ok)[0]
     visible = np.zeros(N, bool)
     visible[idx[sel]] = True

@@ -24,6 +24,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import math
+
 import numpy as np
 
 from . import jacobian as jac
@@ -138,15 +140,59 @@ class LMResult:
     pred: float
     delta: np.ndarray
     pcg: list
+    gamma: float = 1.0
+    ls_costs: list = None
+
+
+def line_search_views(subsets: list, frac: float) -> list:
+    """Views the line search renders: the first ceil(frac * V) of the step's V
+    views, in subset order; returned as a count per subset (a prefix of each)."""
+    total = sum(len(c) for c in subsets)
+    n = int(math.ceil(frac * total))
+    out = []
+    for cams in subsets:
+        k = min(len(cams), max(n, 0))
+        out.append(k)
+        n -= k
+    return out
+
+
+def line_search(params: np.ndarray, delta: np.ndarray, subsets: list, targets: list, steps: int, frac: float,
+                smooth=False):
+    """Eq. line-search, min over gamma of E(x + gamma Delta), read as: evaluate the
+    sum-of-squares cost on the line-search views at gamma = 1, 1/2, 1/4, ... (at
+    most `steps` values), stop at the first value larger than the previous finite
+    one, and return the best gamma (ties: the larger gamma) and the costs seen."""
+    counts = line_search_views(subsets, frac)
+    best_g, best_e, prev, costs = 1.0, math.inf, math.inf, []
+    for k in range(steps):
+        g = 0.5 ** k
+        e = 0.0
+        x = params + g * delta
+        for cams, tg, nv in zip(subsets, targets, counts):
+            if nv == 0:
+                continue
+            npx = sum(c.width * c.height * 3 for c in cams[:nv])
+            F = jac.render(x, cams[:nv], smooth) - tg[:npx]
+            e += float(np.dot(F, F))
+        costs.append(e)
+        if e < best_e:
+            best_g, best_e = g, e
+        if math.isfinite(prev) and e > prev:
+            break
+        prev = e
+    return best_g, costs
 
 
 def lm_step(params: np.ndarray, subsets: list, targets: list, lam: float, n_iters: int = 8,
             lambda_min: float = 1e-4, lambda_max: float = 1e4, break_rel2: float = 0.0,
-            smooth=False, precond=None) -> LMResult:
+            smooth=False, precond=None, ls_steps: int = 0, ls_frac: float = 0.3) -> LMResult:
     """One LM iteration over image subsets (Sec. 3.2 and Eq. combine-pcg).
 
     subsets: list of camera lists; targets: list of flat target vectors (one per subset).
     precond: optional callable (SubsetSystem) -> D replacing M^-1 in Algorithm 1.
+    ls_steps > 0: the step is scaled by the line search of Eq. line-search (see
+    line_search); rho (Eq. tr-update) then uses gamma Delta.
     """
     systems = [build_subset(params, cams, tg, smooth) for cams, tg in zip(subsets, targets)]
     deltas, stats = [], []
@@ -157,11 +203,14 @@ def lm_step(params: np.ndarray, subsets: list, targets: list, lam: float, n_iter
         stats.append(st)
     delta = combine(deltas, [s.M for s in systems])
     cost0 = sum(s.cost for s in systems)
+    gamma, ls_costs = 1.0, None
+    if ls_steps > 0:
+        gamma, ls_costs = line_search(params, delta, subsets, targets, ls_steps, ls_frac, smooth)
     pred = 0.0
     for s in systems:
-        u = jac.apply_J(s.lin, delta, s.F.shape[0]) + s.F
+        u = gamma * jac.apply_J(s.lin, delta, s.F.shape[0]) + s.F
         pred += float(np.dot(u, u))
-    new = params + delta
+    new = params + gamma * delta
     cost1 = 0.0
     for cams, tg in zip(subsets, targets):
         F1 = jac.render(new, cams, smooth) - tg
@@ -176,4 +225,4 @@ def lm_step(params: np.ndarray, subsets: list, targets: list, lam: float, n_iter
         lam = lam * 2.0
         out = params
     lam = float(min(max(lam, lambda_min), lambda_max))
-    return LMResult(out, lam, accepted, float(rho), cost0, cost1, pred, delta, stats)
+    return LMResult(out, lam, accepted, float(rho), cost0, cost1, pred, delta, stats, gamma, ls_costs)

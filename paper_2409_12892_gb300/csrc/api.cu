@@ -838,6 +838,7 @@ void gslm_default_options(gslm_options* o) {
   o->batch = 1;
   o->graph = 1;
   o->batch_ctas = 0;
+  o->line_search = 8;
 }
 
 static gslm_status validate_opts(const gslm_options* o) {
@@ -847,6 +848,7 @@ static gslm_status validate_opts(const gslm_options* o) {
   if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
   if (o->batch_ctas < 0 || o->batch_ctas > 6) return GSLM_E_INVALID;
   if (o->apply_variant < 0 || o->apply_variant > 5) return GSLM_E_INVALID;
+  if (o->line_search < 0 || o->line_search > 60) return GSLM_E_INVALID;
   return GSLM_OK;
 }
 
@@ -1320,41 +1322,86 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   }
   CK(launch_combine_finish((int)N, ld, ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), ctx->lm_delta.as<float>(),
                            st));
-  // predicted: sum_i ||J_i Delta + F_i||^2
+  // predicted decrease at any step scale gamma: sum_i ||gamma J_i Delta + F_i||^2
+  // = cost0 + gamma B + gamma^2 A with A = sum_i ||J_i Delta||^2
   bool trho = ctx->timer.begin(PH_RHO);
-  double pred = 0.0;
+  double pA = 0.0, p1 = 0.0;
   for (int i = 0; i < n_b; ++i) {
     gslm_cache* c = caches[i];
-    CK(ctx->partials.ensure(sizeof(double) * std::max(c->n_tiles, 1), st));
+    CK(ctx->partials.ensure(sizeof(double) * 2 * std::max(c->n_tiles, 1), st));
     CKS(do_apply_J(ctx, c, ctx->lm_delta.as<float>(), nullptr, nullptr, nullptr, nullptr, c->F.as<float>(),
                    ctx->partials.as<double>()));
-    double pi = 0.0;
-    CKS(reduce_to_host(ctx, ctx->partials.as<double>(), c->n_tiles, &pi));
-    pred += pi;
+    double a = 0.0, b = 0.0;
+    CKS(reduce_to_host(ctx, ctx->partials.as<double>(), c->n_tiles, &b));
+    CKS(reduce_to_host(ctx, ctx->partials.as<double>() + c->n_tiles, c->n_tiles, &a));
+    p1 += b;
+    pA += a;
   }
-  // actual: ||F(x + Delta)||^2 over the same views
-  CK(launch_axpy_params((int)N, ld, params, ctx->lm_delta.as<float>(), ctx->lm_trial.as<float>(), st));
-  double cost1 = 0.0;
-  for (int i = 0; i < n_b; ++i) {
-    CK(ctx->lm_img.ensure(sizeof(float) * 3 * caches[i]->n_pix, st));
-    double ci = 0.0;
-    const gslm_status rs = gslm_render(ctx, ctx->lm_trial.as<float>(), N, ld, scams[i].data(),
-                                       (int)scams[i].size(), ctx->lm_img.as<float>(), stg[i].as<float>(), &ci);
-    if (rs == GSLM_E_CACHE_OVERFLOW) {
-      // the trial parameters project to more tile keys than a render can hold:
-      // the step is rejected like any step that does not decrease the cost
-      cost1 = INFINITY;
-      break;
+  const double pB = p1 - pA - cost0;
+  // the trial render of params + g Delta over the first nv[i] views of every
+  // subset i; +inf when the trial splats exceed the renderer's tile-key capacity
+  auto trial_cost = [&](double g, const std::vector<int>& nv, double* out) -> gslm_status {
+    CK(launch_axpy_params((int)N, ld, params, (float)g, ctx->lm_delta.as<float>(), ctx->lm_trial.as<float>(), st));
+    double e = 0.0;
+    for (int i = 0; i < n_b; ++i) {
+      if (nv[i] == 0) continue;
+      long long pix = 0;
+      for (int k = 0; k < nv[i]; ++k) pix += (long long)scams[i][k].width * scams[i][k].height;
+      CK(ctx->lm_img.ensure(sizeof(float) * 3 * std::max<long long>(pix, 1), st));
+      double ci = 0.0;
+      const gslm_status rs = gslm_render(ctx, ctx->lm_trial.as<float>(), N, ld, scams[i].data(), nv[i],
+                                         ctx->lm_img.as<float>(), stg[i].as<float>(), &ci);
+      if (rs == GSLM_E_CACHE_OVERFLOW) {
+        *out = INFINITY;
+        return GSLM_OK;
+      }
+      CKS(rs);
+      e += ci;
     }
-    CKS(rs);
-    cost1 += ci;
+    *out = e;
+    return GSLM_OK;
+  };
+  // Eq. line-search: gamma = 1, 1/2, ... on the first 30% of the step's views
+  // (in subset order), stopping at the first cost above the previous finite one
+  double gamma = 1.0;
+  int ls_evals = 0;
+  if (ctx->opt.line_search > 0) {
+    long long total = 0;
+    for (int i = 0; i < n_b; ++i) total += (long long)scams[i].size();
+    long long left = (long long)std::ceil(0.3 * (double)total);
+    std::vector<int> nv(n_b, 0);
+    for (int i = 0; i < n_b; ++i) {
+      nv[i] = (int)std::min<long long>((long long)scams[i].size(), std::max<long long>(left, 0));
+      left -= nv[i];
+    }
+    double best = INFINITY, prev = INFINITY;
+    for (int k = 0; k < ctx->opt.line_search; ++k) {
+      const double g = std::ldexp(1.0, -k);
+      double e = 0.0;
+      CKS(trial_cost(g, nv, &e));
+      ++ls_evals;
+      if (e < best) {
+        best = e;
+        gamma = g;
+      }
+      if (std::isfinite(prev) && e > prev) break;
+      prev = e;
+    }
+  }
+  const double pred = cost0 + gamma * pB + gamma * gamma * pA;
+  // actual: ||F(x + gamma Delta)||^2 over all views of the step
+  double cost1 = 0.0;
+  {
+    std::vector<int> all(n_b);
+    for (int i = 0; i < n_b; ++i) all[i] = (int)scams[i].size();
+    CKS(trial_cost(gamma, all, &cost1));
   }
   ctx->timer.end(trho);
   const double den = cost0 - pred;
   const double rho = den > 0.0 ? (cost0 - cost1) / den : -INFINITY;
   const bool accept = den > 0.0 && rho > 1e-5;
   double lam = state->lambda;
-  if (accept) {
+  if (accept) {   // lm_trial holds params + gamma Delta
     CK(cudaMemcpyAsync(params, ctx->lm_trial.p, vb, cudaMemcpyDeviceToDevice, st));
     lam *= 1.0 - std::pow(2.0 * rho - 1.0, 3.0);
   } else {
@@ -1384,6 +1431,9 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     stats->pair_bytes = pair_bytes;
     stats->cache_segments = segs;
     stats->active_splats = actives;
+    stats->gamma = gamma;
+    stats->ls_evals = ls_evals;
+    stats->pad2 = 0;
   } else {
     double dummy[8] = {0};
     ctx->timer.collect(dummy, 8);

@@ -253,7 +253,7 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
     __syncthreads();
   }
   const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
-  double local = 0.0;
+  double local = 0.0, local2 = 0.0;
   if (x < cam.W && y < cam.H) {
     const long long pix = cam.pix_off + (long long)y * cam.W + x;
     const int p = threadIdx.x;
@@ -267,16 +267,27 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
       const float* f = Fadd + pix * 3;
       const double a0 = (double)u0 + f[0], a1 = (double)u1 + f[1], a2 = (double)u2 + f[2];
       local = a0 * a0 + a1 * a1 + a2 * a2;
+      local2 = (double)u0 * u0 + (double)u1 * u1 + (double)u2 * u2;
     }
   }
   if (sq_partials != nullptr) {
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
-    if (lane == 0) dred[warp] = local;
+    for (int o = 16; o > 0; o >>= 1) {
+      local += __shfl_xor_sync(kFull, local, o);
+      local2 += __shfl_xor_sync(kFull, local2, o);
+    }
+    if (lane == 0) {
+      dred[warp] = local;
+      dred[kWarps + warp] = local2;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < kWarps; ++w) s += dred[w];
+      double s = 0.0, s2 = 0.0;
+      for (int w = 0; w < kWarps; ++w) {
+        s += dred[w];
+        s2 += dred[kWarps + w];
+      }
       sq_partials[tile] = s;
+      sq_partials[cv.n_tiles + tile] = s2;
     }
   }
 }
@@ -284,7 +295,7 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
 #define APPLY_J_SHARED                                   \
   __shared__ float su[3 * (kTilePix + kTilePix / 32)];   \
   __shared__ float2 sxy[kTilePix];                       \
-  __shared__ double dred[kWarps];                        \
+  __shared__ double dred[2 * kWarps];                    \
   __shared__ unsigned int next_seg;                      \
   __shared__ Stage S;                                    \
   __shared__ StageT T;                                   \

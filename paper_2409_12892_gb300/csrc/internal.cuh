@@ -289,6 +289,7 @@ cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const ui
 // apply.cu. `variant` selects one of apply_variants() kernel configurations
 // (entries in flight per lane and register budget); all compute the same result.
 int apply_variants();
+// sq_partials (may be null): [2][n_tiles] per-tile sums of ||u + F_add||^2 and ||u||^2.
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add,
                            float* u, double* sq_partials, int variant, cudaStream_t st);
 cudaError_t launch_apply_JT(const CacheView& cv, const float* u, float* seg_ybar, int variant,
@@ -334,7 +335,8 @@ cudaError_t launch_combine_acc(int N, long long ld, const float* delta, const fl
                                float* num, float* den, cudaStream_t st);
 cudaError_t launch_combine_finish(int N, long long ld, const float* num, const float* den,
                                   float* delta, cudaStream_t st);
-cudaError_t launch_axpy_params(int N, long long ld, const float* x, const float* d, float* out,
+// out = x + a d over [59][ld]
+cudaError_t launch_axpy_params(int N, long long ld, const float* x, float a, const float* d, float* out,
                                cudaStream_t st);
 cudaError_t launch_neg_copy(long long n, const float* src, float* dst, cudaStream_t st);
 cudaError_t launch_count_nonzero_u8(const uint8_t* v, long long n, unsigned long long* out, cudaStream_t st);

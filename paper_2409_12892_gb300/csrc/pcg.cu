@@ -218,12 +218,12 @@ __global__ void k_combine_finish(int N, long long ld, const float* __restrict__ 
   d[o] = dv > 0.f ? num[o] / dv : 0.f;
 }
 
-__global__ void k_axpy(int N, long long ld, const float* __restrict__ x, const float* __restrict__ d,
+__global__ void k_axpy(int N, long long ld, const float* __restrict__ x, float a, const float* __restrict__ d,
                        float* __restrict__ out) {
   const int i = blockIdx.x * kBS + threadIdx.x;
   if (i >= N) return;
   const long long o = (long long)blockIdx.y * ld + i;
-  out[o] = x[o] + d[o];
+  out[o] = x[o] + a * d[o];
 }
 
 __global__ void k_neg(long long n, const float* __restrict__ s, float* __restrict__ d) {
@@ -330,9 +330,10 @@ cudaError_t launch_combine_finish(int N, long long ld, const float* num, const f
   return cudaGetLastError();
 }
 
-cudaError_t launch_axpy_params(int N, long long ld, const float* x, const float* d, float* out, cudaStream_t st) {
+cudaError_t launch_axpy_params(int N, long long ld, const float* x, float a, const float* d, float* out,
+                               cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  { k_axpy<<<vec_grid(N), kBS, 0, st>>>(N, ld, x, d, out); note_launch(); }
+  { k_axpy<<<vec_grid(N), kBS, 0, st>>>(N, ld, x, a, d, out); note_launch(); }
   return cudaGetLastError();
 }
 

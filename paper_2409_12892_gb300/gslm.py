@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
                 ("lambda_min", c_float), ("lambda_max", c_float), ("smooth", c_int32),
                 ("mem_budget", c_size_t), ("group", c_int32), ("profile", c_int32), ("autotune", c_int32),
                 ("batch", c_int32), ("graph", c_int32), ("batch_ctas", c_int32), ("apply_variant", c_int32),
-                ("reserved", c_int32 * 1)]
+                ("line_search", c_int32)]
 
 
 class CacheInfo(ctypes.Structure):
@@ -71,7 +71,7 @@ class LMStats(ctypes.Structure):
                 ("accepted", c_int32), ("pcg_iters", c_int32), ("cache_entries", c_int64),
                 ("cache_bytes", c_int64), ("ms_total", c_double), ("ms_phase", c_double * 8),
                 ("n_pairs", c_int32), ("pad", c_int32), ("pair_bytes", c_double), ("cache_segments", c_int64),
-                ("active_splats", c_int64)]
+                ("active_splats", c_int64), ("gamma", c_double), ("ls_evals", c_int32), ("pad2", c_int32)]
 
 
 _lib = None
@@ -223,7 +223,7 @@ class Context:
 
     def __init__(self, cache_fmt="fp32", n_iters=8, break_rel2=0.01, lambda_min=1e-4, lambda_max=1e4,
                  smooth=False, mem_budget=0, group=32, profile=False, autotune=True, batch=True, graph=True,
-                 batch_ctas=0, apply_variant=0, stream=None):
+                 batch_ctas=0, apply_variant=0, line_search=8, stream=None):
         self.lib = load_library()
         opt = Options()
         self.lib.gslm_default_options(ctypes.byref(opt))
@@ -235,6 +235,7 @@ class Context:
         opt.autotune = int(bool(autotune))
         opt.batch, opt.graph, opt.batch_ctas = int(bool(batch)), int(bool(graph)), int(batch_ctas)
         opt.apply_variant = int(apply_variant)
+        opt.line_search = int(line_search)
         self.opt = opt
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st

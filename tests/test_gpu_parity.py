@@ -182,21 +182,35 @@ def test_pcg_break_test_stops_early(lib):
     cache.free()
 
 
-def test_lm_step_matches_oracle(lib):
+@pytest.mark.parametrize("name,ls", [("tiny", 0), ("tiny", 8), ("ragged", 8)])
+def test_lm_step_matches_oracle(lib, name, ls):
+    import warnings
     from oracle import solver
-    wl, P, cams, tgt = tiny_case()
-    res = solver.lm_step(P.astype(np.float64), [cams], [tgt.astype(np.float64)], 1e-3, n_iters=8)
-    ctx = lib.Context(n_iters=8, break_rel2=0.0)
+    warnings.filterwarnings("ignore")
+    wl, P, cams, tgt = CASES[name]()
+    res = solver.lm_step(P.astype(np.float64), [cams], [tgt.astype(np.float64)], 1e-3, n_iters=8, ls_steps=ls)
+    ctx = lib.Context(n_iters=8, break_rel2=0.0, line_search=ls)
     params = lib.to_soa(P)
     state, stats = ctx.lm_step(params, P.shape[0], cams, torch.from_numpy(tgt).cuda().view(-1, 3),
                                [list(range(len(cams)))], 1e-3)
+    assert stats.gamma == res.gamma
+    if ls:
+        assert stats.ls_evals == len(res.ls_costs)
     assert abs(stats.cost - res.cost) <= 1e-5 * res.cost
+    if name == "ragged":
+        # the ragged trial points hold splats at the float32 covariance limit: the
+        # cost there jumps (6575 -> 2134 -> 1597 -> 2007 along gamma) and changes
+        # by hundreds for Delta differences inside the 1e-3 PCG tolerance, so only
+        # the decisions and the quantities smooth in Delta are compared
+        assert abs(stats.predicted - res.pred) <= 1e-3 * res.cost
+        assert bool(stats.accepted) == res.accepted
+        return
     assert abs(stats.predicted - res.pred) <= 1e-3 * res.cost
     assert abs(stats.cost_new - res.cost_new) <= 1e-3 * res.cost
     assert bool(stats.accepted) == res.accepted
     assert abs(state.lambda_ - res.lam) <= 1e-3 * res.lam + 1e-9
     if res.accepted:
-        assert rel_l2(lib.from_soa(params, P.shape[0]) - P, res.delta) < 1e-3
+        assert rel_l2(lib.from_soa(params, P.shape[0]) - P, res.gamma * res.delta) < 1e-3
 
 
 def test_apply_JT_is_deterministic(lib):
@@ -229,3 +243,38 @@ def test_reduced_precision_cache_error_bound(lib, fmt, tol):
     assert rel_l2(Jp[mask], J.apply_J(lin, p.astype(np.float64), n_res)[mask]) < tol
     assert rel_l2(JTu, J.apply_JT(lin, u.astype(np.float64), P.shape[0])) < tol
     cache.free()
+
+
+def _multi_subset_case():
+    """600 Gaussians, 16 views of 64x64 in 4 random subsets of 4; targets from a perturbed copy + noise."""
+    from oracle import jacobian as J
+    wl = synth.small_workload("multi", 606, 600, 16, 64, 64, cam_radius=4.0, subset_sizes=[4, 4, 4, 4])
+    P = synth.make_gaussians(wl)
+    cams = synth.make_cameras(wl)
+    tgt = J.render(synth.perturbed_copy(wl, P).astype(np.float64), cams)
+    tgt = (tgt + synth.pixel_noise(wl, tgt.size)).astype(np.float32)
+    return wl, P, cams, tgt, synth.subset_views(wl, 0)
+
+
+@pytest.mark.parametrize("batch", [False, True])
+def test_lm_step_over_several_subsets_matches_oracle(lib, batch):
+    # Eq. combine-pcg over 4 subsets, then the line search and rho
+    import warnings
+    from oracle import solver
+    warnings.filterwarnings("ignore")
+    wl, P, cams, tgt, subsets = _multi_subset_case()
+    offs = np.concatenate([[0], np.cumsum([c.width * c.height * 3 for c in cams])])
+    sc = [[cams[v] for v in s] for s in subsets]
+    st = [np.concatenate([tgt[offs[v]:offs[v + 1]] for v in s]).astype(np.float64) for s in subsets]
+    res = solver.lm_step(P.astype(np.float64), sc, st, 1e-3, n_iters=8, break_rel2=0.01, ls_steps=8)
+    ctx = lib.Context(n_iters=8, break_rel2=0.01, line_search=8, batch=batch)
+    params = lib.to_soa(P)
+    state, stats = ctx.lm_step(params, P.shape[0], cams, torch.from_numpy(tgt).cuda().view(-1, 3), subsets, 1e-3)
+    assert stats.gamma == res.gamma
+    assert abs(stats.cost - res.cost) <= 1e-5 * res.cost
+    assert abs(stats.predicted - res.pred) <= 1e-3 * res.cost
+    assert abs(stats.cost_new - res.cost_new) <= 1e-3 * res.cost
+    assert bool(stats.accepted) == res.accepted
+    assert stats.pcg_iters == sum(s.iters for s in res.pcg)
+    if res.accepted:
+        assert rel_l2(lib.from_soa(params, P.shape[0]) - P, res.gamma * res.delta) < 1e-3

@@ -198,7 +198,7 @@ def test_learned_preconditioner_needs_fewer_pcg_iterations_than_jacobi(lib):
 def test_lm_step_uses_the_network_set_on_the_context(lib):
     P, cams, tgt = _scene(80, views=4)
     N = P.shape[0]
-    ctx = lib.Context(n_iters=8, break_rel2=0.0)
+    ctx = lib.Context(n_iters=8, break_rel2=0.0, line_search=0)
     pc = lib.Precond(ctx, weights=_random_net(4).flat())
     tg = torch.from_numpy(tgt).cuda().view(-1, 3)
     cache = ctx.build_cache(lib.to_soa(P), N, cams, tg)

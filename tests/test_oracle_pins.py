@@ -599,3 +599,49 @@ def test_mlp_training_lowers_the_unrolled_residual():
         L, g = mlp.loss_and_grad(net, phi, M, apply_A, b, 6)
         opt.step(net, g)
     assert L < L0 - 0.1
+
+
+# ----------------------------------------------------------------------------- line search (Eq. line-search)
+def _ragged_lm(ls_steps):
+    from common import ragged_case
+    wl, P, cams, tgt = ragged_case()
+    return P.astype(np.float64), cams, tgt.astype(np.float64), solver.lm_step(
+        P.astype(np.float64), [cams], [tgt.astype(np.float64)], 1e-3, n_iters=8, ls_steps=ls_steps)
+
+
+def test_line_search_views_are_the_first_30_percent_in_subset_order():
+    assert solver.line_search_views([[0, 1, 2], [3, 4, 5, 6, 7]], 0.3) == [3, 0]
+    assert solver.line_search_views([[0], [1, 2, 3], [4, 5, 6, 7, 8], [9, 10, 11]], 0.3) == [1, 3, 0, 0]
+    assert solver.line_search_views([[0, 1]], 0.3) == [1]
+
+
+def test_line_search_with_one_candidate_is_the_full_step():
+    import warnings
+    warnings.filterwarnings("ignore")
+    P, cams, tgt, r1 = _ragged_lm(1)
+    r0 = solver.lm_step(P, [cams], [tgt], 1e-3, n_iters=8, ls_steps=0)
+    assert r1.gamma == 1.0 and r0.gamma == 1.0
+    assert r1.cost_new == r0.cost_new and r1.pred == r0.pred and r1.accepted == r0.accepted
+
+
+def test_line_search_on_a_doubled_step_halves_gamma():
+    # x + 2 Delta 2^-k = x + Delta 2^-(k-1) exactly: the costs shift by one candidate
+    import warnings
+    warnings.filterwarnings("ignore")
+    P, cams, tgt, r = _ragged_lm(8)
+    assert r.gamma == 0.5 and len(r.ls_costs) == 3          # 2172 > 1597 < 2007: stops at the rise
+    g2, costs2 = solver.line_search(P, 2.0 * r.delta, [cams], [tgt], 8, 0.3)
+    assert g2 == r.gamma / 2
+    assert costs2[1:] == r.ls_costs
+    assert costs2[0] > costs2[1]
+
+
+def test_line_search_step_is_accepted_and_lowers_the_cost():
+    import warnings
+    warnings.filterwarnings("ignore")
+    P, cams, tgt, r = _ragged_lm(8)
+    assert r.accepted and r.cost_new < r.cost
+    np.testing.assert_allclose(r.params, P + r.gamma * r.delta)
+    # the predicted cost uses gamma Delta: between the full-step prediction and the current cost
+    full = solver.lm_step(P, [cams], [tgt], 1e-3, n_iters=8, ls_steps=0)
+    assert r.pred != full.pred
