@@ -6,8 +6,8 @@ plain FP32. One step = one LM iteration of the paper-scale synthetic workload
 (1.5M Gaussians in 20 clusters, 200 cameras at 1264x832, four subsets of 25
 views): per subset the gradient cache, the diagonal and the PCG solve
 (Algorithm 1, 8 iterations, break test 0.01), then the weighted mean of the
-subset directions, the line search over the step scale (Eq. line-search, on
-30% of the step's views), rho with the trial render and the damping update.
+subset directions, rho with the trial render at gamma = 1 and the damping
+update (--line-search n adds Eq. line-search over n step scales).
 
 Forms: "chosen" = BF16 cache, learned diagonal preconditioner (trained on the
 GPU on step 0's subset systems before timing), the subsets' solves batched and
@@ -67,6 +67,16 @@ def parse_args(argv=None):
     ap.add_argument("--equal-cap", type=int, default=1000, help="PCG iteration cap of the equal-residual step")
     ap.add_argument("--equal-lambda", type=float, default=1.0,
                     help="LM damping of the equal-residual step (both forms)")
+    ap.add_argument("--line-search", type=int, default=0,
+                    help="line-search candidates of the timed LM steps (0: gamma = 1, the workload's setting)")
+    ap.add_argument("--equal-line-search", type=int, default=8,
+                    help="line-search candidates of the equal-residual step")
+    ap.add_argument("--apply-pass", action="store_true",
+                    help="kernel mode: one cache of the first --apply-views cameras, then one J^T u and one J p "
+                         "(for ncu captures); with --sweep, every kernel variant timed")
+    ap.add_argument("--apply-views", type=int, default=8)
+    ap.add_argument("--apply-variant", type=int, default=3, help="1..5: forced apply kernel variant 0..4")
+    ap.add_argument("--sweep", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -405,6 +415,7 @@ def workload_config(args, form: str) -> dict:
                      f"{wl.resolutions[0][0]}x{wl.resolutions[0][1]}, {len(wl.subset_sizes)} subsets x "
                      f"{wl.subset_sizes[0]} views per LM step"),
         "form": form, "pcg_iters": wl.pcg_iters, "break_rel2": 0.01, "lambda0": wl.lambda0,
+        "line_search": args.line_search,
         "l2_flush": "inputs larger than L2: the gradient caches of a step are tens of GB",
         "parallelism": f"{args.gpus} independent replicas" if args.gpus > 1 else "single GPU",
     }
@@ -505,14 +516,15 @@ def psnr_from_cost(cost: float, n_pix: int) -> float:
     return 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")
 
 
-def equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap: int, pc=None, lam: float = 1e-3) -> dict:
+def equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap: int, pc=None, lam: float = 1e-3,
+                        ls: int = 8, ls_timed: int = 0) -> dict:
     """One LM step from the initial parameters with every subset's PCG run to
     ||r|| <= 1e-3 ||b|| (at most `cap` iterations), with the network `pc` as
     preconditioner or Jacobi; device time by CUDA events."""
     import torch
     import synth
     ctx.set_precond(pc)
-    ctx.set_options(n_iters=cap, break_rel2=1e-6)
+    ctx.set_options(n_iters=cap, break_rel2=1e-6, line_search=ls)
     params = g.to_soa(P, device=dev, ld=ld)
     subsets = synth.subset_views(wl, 0)
     st = torch.cuda.current_stream()
@@ -523,7 +535,7 @@ def equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap: int, pc=N
     ev1.record(st)
     torch.cuda.synchronize()
     n_pix = sum(cams[v].width * cams[v].height for s in subsets for v in s)
-    ctx.set_options(n_iters=wl.pcg_iters, break_rel2=0.01)
+    ctx.set_options(n_iters=wl.pcg_iters, break_rel2=0.01, line_search=ls_timed)
     ctx.set_precond(None)
     del params
     after = lm.cost_new if lm.accepted else lm.cost
@@ -567,7 +579,8 @@ def run_ours(args):
     for form, fmt in forms:
         chosen = form == "chosen"
         ctx = g.Context(cache_fmt=fmt, n_iters=wl.pcg_iters, break_rel2=0.01, lambda_min=wl.lambda_min,
-                        lambda_max=wl.lambda_max, profile=not chosen, group=args.group, batch=chosen, graph=chosen)
+                        lambda_max=wl.lambda_max, profile=not chosen, group=args.group, batch=chosen, graph=chosen,
+                        line_search=args.line_search)
         params = g.to_soa(P, device=dev, ld=ld)
         pc, train, judge = None, None, None
         if chosen and args.precond == "learned":
@@ -593,17 +606,20 @@ def run_ours(args):
             if chosen:
                 # the plain form runs later; the learned run is capped at the cap, Jacobi first
                 eq_j = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, args.equal_cap,
-                                           lam=args.equal_lambda)
+                                           lam=args.equal_lambda, ls=args.equal_line_search,
+                                           ls_timed=args.line_search)
                 eq = {"jacobi": eq_j}
                 if pc is not None:
                     cap_l = max(1, int(math.ceil(eq_j["pcg_iters_per_subset"])))
                     eq["learned"] = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap_l, pc,
-                                                        lam=args.equal_lambda)
+                                                        lam=args.equal_lambda, ls=args.equal_line_search,
+                                                        ls_timed=args.line_search)
                     eq["learned"]["cap"] = cap_l
                 result[form]["equal"] = eq
             else:
                 result[form]["equal"] = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, args.equal_cap,
-                                                            lam=args.equal_lambda)
+                                                            lam=args.equal_lambda, ls=args.equal_line_search,
+                                                            ls_timed=args.line_search)
         ctx.set_precond(None)
         if pc is not None:
             pc.free()
@@ -673,8 +689,60 @@ def run_ours(args):
     return 0
 
 
+def run_apply_pass(args):
+    """One subset cache (FP32, or --cache-fmt) of the first --apply-views cameras of the
+    workload, then one J^T u and one J p with a forced kernel variant; with --sweep the
+    median of 5 timed calls of each variant (CUDA events), as one JSON line."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2409_12892_gb300 as g
+    from paper_2409_12892_gb300 import build as b
+    b.build()
+    wl = workload(args)
+    P = synth.make_gaussians(wl)
+    cams = synth.make_cameras(wl)[:args.apply_views]
+    N = P.shape[0]
+    params = g.to_soa(P)
+    ctx = g.Context(cache_fmt=args.cache_fmt, autotune=False, apply_variant=args.apply_variant)
+    tg = torch.empty((g.n_pixels(cams), 3), device="cuda")
+    ctx.render(g.to_soa(synth.perturbed_copy(wl, P)), N, cams, img=tg)
+    cache = ctx.build_cache(params, N, cams, tg)
+    info = cache.info()
+    u = torch.from_numpy(synth.random_vector(5, (g.n_pixels(cams), 3)).astype(np.float32)).cuda()
+    p = torch.from_numpy(synth.random_vector(3, (59, cache.ld)).astype(np.float32)).cuda()
+    gout = ctx.apply_JT(cache, u)
+    uo = ctx.apply_J(cache, p)
+    torch.cuda.synchronize()
+    out = {"mode": "apply-pass", "workload": wl.name, "views": len(cams), "cache_fmt": args.cache_fmt,
+           "entries": info.entries, "segments": info.segments, "pixels": info.pixels}
+    if args.sweep:
+        pay = 16 if args.cache_fmt == "fp32" else 8
+        for v in range(1, 6):
+            ctx.set_options(apply_variant=v)
+            for name, call in (("J", lambda: ctx.apply_J(cache, p, uo)), ("JT", lambda: ctx.apply_JT(cache, u, gout))):
+                ts = []
+                for r in range(6):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    call()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if r:
+                        ts.append(e0.elapsed_time(e1))
+                ms = float(np.median(ts))
+                out[f"{name}_variant{v - 1}_ms"] = ms
+                out[f"{name}_variant{v - 1}_entry_GBps"] = info.entries * (pay + 1) / ms / 1e6
+    print(json.dumps(out), flush=True)
+    cache.free()
+    ctx.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.apply_pass:
+        return run_apply_pass(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

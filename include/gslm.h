@@ -20,7 +20,10 @@
  *   - Every array pointer is a DEVICE pointer unless its comment says "host".
  *     Arrays passed in are owned by the caller; the library never frees them.
  *   - The library owns gslm_ctx and gslm_cache objects and the device memory
- *     behind them (allocated with cudaMallocAsync on the context's stream).
+ *     behind them (allocated with cudaMallocAsync on the context's stream, from
+ *     the device's default memory pool). gslm_create sets that pool to keep
+ *     freed memory (release threshold: maximum), so caches rebuilt every LM
+ *     step reuse it; gslm_destroy trims the pool back to the driver.
  *   - All work is enqueued on the context's CUDA stream. Outputs are valid
  *     once that stream has been synchronised. gslm_build_cache synchronises
  *     once (to size the cache); gslm_lm_step synchronises to fill its stats;

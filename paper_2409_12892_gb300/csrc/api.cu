@@ -869,6 +869,15 @@ gslm_status gslm_create(const gslm_options* opt, void* stream, gslm_ctx** out) {
   c->opt = o;
   c->st = static_cast<cudaStream_t>(stream);
   c->device = dev;
+  // The library allocates stream-ordered from the device's default memory pool.
+  // Caches of tens of GB are freed and rebuilt every LM step: keep freed memory
+  // in the pool instead of returning it to the driver at every synchronisation.
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
   *out = c;
   return GSLM_OK;
 }
@@ -876,7 +885,15 @@ gslm_status gslm_create(const gslm_options* opt, void* stream, gslm_ctx** out) {
 void gslm_destroy(gslm_ctx* ctx) {
   if (ctx == nullptr) return;
   cudaStreamSynchronize(ctx->st);
+  const int dev = ctx->device;
   delete ctx;
+  // hand the pool's cached memory back to the driver
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    cudaStreamSynchronize(nullptr);
+    cudaMemPoolTrimTo(pool, 0);
+  }
+  cudaGetLastError();
 }
 
 const char* gslm_last_error(const gslm_ctx* ctx) { return ctx == nullptr ? "null context" : ctx->err.c_str(); }

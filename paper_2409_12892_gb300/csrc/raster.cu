@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
   __shared__ int segidx[32];
   __shared__ uint32_t segmax[32];
   __shared__ uint32_t add_e, add_s;
+  __shared__ float sAraw[32][kTilePix];   // o G of the sub-batch's splats at each pixel (phase A -> D)
   const int tile = blockIdx.x;
   const int v = find_view(cams, V, tile);
   const DevCam& cam = cams[v];
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
           } else {
             mask |= 1u << j;
             Tl = test;
+            sAraw[j][threadIdx.x] = bl.araw;
           }
         }
       }
@@ -363,8 +365,8 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
         float Tq = T, q0 = p0, q1 = p1, q2 = p2;
         for (int j = 0; j < m; ++j) {
           if (!((mask >> j) & 1u)) continue;
-          const Blend bl = blend_weight(ts.px, ts.py, sA[sub + j], sB[sub + j], smooth);
-          const float alpha = bl.alpha, araw = bl.araw;
+          const float araw = sAraw[j][threadIdx.x];
+          const float alpha = smooth ? araw : fminf(kAlphaMax, araw);
           const float4 c = sC[sub + j];
           const float w = __fmul_rn(alpha, Tq);
           q0 = __fmaf_rn(c.x, w, q0);
@@ -387,8 +389,8 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
       }
       for (int j = 0; j < m; ++j) {
         if (!((mask >> j) & 1u)) continue;
-        const Blend bl = blend_weight(ts.px, ts.py, sA[sub + j], sB[sub + j], smooth);
-        const float alpha = bl.alpha, araw = bl.araw;
+        const float araw = sAraw[j][threadIdx.x];   // as blend_weight computed it in phase A
+        const float alpha = smooth ? araw : fminf(kAlphaMax, araw);
         const float4 c = sC[sub + j];
         const float w = __fmul_rn(alpha, T);
         p0 = __fmaf_rn(c.x, w, p0);
