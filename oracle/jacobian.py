@@ -65,6 +65,29 @@ def linearise_view(params: np.ndarray, cam, pix_off: int = 0, smooth: bool = Fal
     return ViewLin(proj, ras, dc_dy(proj, ras), proj.idx[ras.rec_splat], pix_off)
 
 
+def linearise_view_tiles(params: np.ndarray, cam, tiles, pix_off: int = 0, smooth: bool = False) -> ViewLin:
+    """linearise_view restricted to the listed (tx, ty) tiles, for scenes too large
+    to linearise whole: every Gaussian is projected without derivatives, those
+    whose splat rect (outer rect, to keep the near-flip flags) meets a listed tile
+    are projected again with derivatives, and only the listed tiles are blended.
+    Records, pixel indices and Gaussian indices are those of linearise_view."""
+    P = np.asarray(params, np.float64)
+    pv = project(P, cam, smooth=smooth, want_jac=False)
+    r = pv.rect_outer if pv.rect_outer is not None else pv.rect
+    hit = np.zeros(pv.idx.shape[0], bool)
+    for tx, ty in tiles:
+        hit |= (r[:, 0] <= tx) & (tx < r[:, 2]) & (r[:, 1] <= ty) & (ty < r[:, 3])
+    keep = np.unique(pv.idx[hit])
+    proj = project(P[keep], cam, smooth=smooth)
+    proj.idx = keep[proj.idx]              # back to the scene's Gaussian indices (depth tie-break)
+    proj.n = P.shape[0]
+    vis = np.zeros(P.shape[0], bool)
+    vis[proj.idx] = True
+    proj.visible = vis
+    ras = rasterize(proj, cam, smooth=smooth, tiles=tiles)
+    return ViewLin(proj, ras, dc_dy(proj, ras), proj.idx[ras.rec_splat], pix_off)
+
+
 def linearise(params: np.ndarray, cams: list, smooth: bool = False) -> list:
     out, off = [], 0
     for cam in cams:

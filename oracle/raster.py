@@ -45,7 +45,9 @@ def blend_order(proj: Projection) -> np.ndarray:
     return np.lexsort((proj.idx, proj.depth.astype(np.float32)))
 
 
-def rasterize(proj: Projection, cam, smooth: bool = False) -> ViewRaster:
+def rasterize(proj: Projection, cam, smooth: bool = False, tiles=None) -> ViewRaster:
+    """Blend every 16x16 tile of the view, or only the (tx, ty) tiles listed in
+    `tiles` (the other pixels stay black and carry no records)."""
     W, H = int(cam.width), int(cam.height)
     T_ = cv.TILE
     tiles_x, tiles_y = (W + T_ - 1) // T_, (H + T_ - 1) // T_
@@ -60,8 +62,11 @@ def rasterize(proj: Projection, cam, smooth: bool = False) -> ViewRaster:
     depth32 = proj.depth.astype(np.float32).astype(np.float64)
     rect_flip = proj.rect_flip if proj.rect_flip is not None else np.zeros(proj.idx.shape[0], bool)
 
+    only = None if tiles is None else {(int(a), int(b)) for a, b in tiles}
     for ty in range(tiles_y):
         for tx in range(tiles_x):
+            if only is not None and (tx, ty) not in only:
+                continue
             xs = np.arange(tx * T_, min(W, tx * T_ + T_))
             ys = np.arange(ty * T_, min(H, ty * T_ + T_))
             gy, gx = np.meshgrid(ys, xs, indexing="ij")

@@ -645,3 +645,37 @@ def test_line_search_step_is_accepted_and_lowers_the_cost():
     # the predicted cost uses gamma Delta: between the full-step prediction and the current cost
     full = solver.lm_step(P, [cams], [tgt], 1e-3, n_iters=8, ls_steps=0)
     assert r.pred != full.pred
+
+
+# ----------------------------------------------------------------------------- sampled tiles of large scenes
+def _records(vl, pixels=None):
+    order = np.lexsort((vl.gauss, vl.ras.rec_pix))
+    pix, gs, a = vl.ras.rec_pix[order], vl.gauss[order], vl.a[order]
+    if pixels is not None:
+        keep = np.isin(pix, pixels)
+        pix, gs, a = pix[keep], gs[keep], a[keep]
+    return pix, gs, a
+
+
+def test_linearising_selected_tiles_matches_the_whole_view():
+    from common import ragged_case
+    wl, P, cams, tgt = ragged_case()
+    cam = cams[1]
+    full = J.linearise_view(P.astype(np.float64), cam)
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    every = [(x, y) for y in range(ty) for x in range(tx)]
+    part = J.linearise_view_tiles(P, cam, every)
+    for u, v in zip(_records(full), _records(part)):
+        np.testing.assert_array_equal(u, v) if u.dtype != np.float64 else np.testing.assert_allclose(u, v, rtol=1e-12)
+    np.testing.assert_array_equal(full.ras.image, part.ras.image)
+    # a few tiles: exactly the whole view's records on their pixels, black elsewhere
+    some = [(0, 0), (tx - 1, ty - 1), (1, 2)]
+    sub = J.linearise_view_tiles(P, cam, some)
+    pixels = np.concatenate([((np.arange(y * 16, min(cam.height, y * 16 + 16))[:, None] * cam.width)
+                              + np.arange(x * 16, min(cam.width, x * 16 + 16))[None, :]).ravel() for x, y in some])
+    for u, v in zip(_records(full, pixels), _records(sub)):
+        np.testing.assert_array_equal(u, v) if u.dtype != np.float64 else np.testing.assert_allclose(u, v, rtol=1e-12)
+    img = full.ras.image.reshape(-1, 3)
+    np.testing.assert_array_equal(sub.ras.image.reshape(-1, 3)[pixels], img[pixels])
+    others = np.setdiff1d(np.arange(cam.width * cam.height), pixels)
+    assert not sub.ras.image.reshape(-1, 3)[others].any()
