@@ -714,8 +714,11 @@ def run_apply_pass(args):
     gout = ctx.apply_JT(cache, u)
     uo = ctx.apply_J(cache, p)
     torch.cuda.synchronize()
+    free_b, total_b = torch.cuda.mem_get_info()
     out = {"mode": "apply-pass", "workload": wl.name, "views": len(cams), "cache_fmt": args.cache_fmt,
-           "entries": info.entries, "segments": info.segments, "pixels": info.pixels}
+           "entries": info.entries, "segments": info.segments, "pixels": info.pixels, "splats": info.splats,
+           "active_splats": info.active_splats, "cache_bytes": info.bytes,
+           "device_free_gb": free_b / 1e9, "device_total_gb": total_b / 1e9}
     if args.sweep:
         pay = 16 if args.cache_fmt == "fp32" else 8
         for v in range(1, 6):

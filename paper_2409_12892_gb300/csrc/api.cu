@@ -117,7 +117,7 @@ struct gslm_cache {
   double cost = 0.0;
   std::vector<DevCam> hcams;
   Buf cams, rec, slot_active, tile_seg_off, seg_entry_off, seg_slot, seg_rec, payload, seg_scale, pixoff;
-  Buf slot_seg_start, slot_seg_end, slot_seg_list, seg_pos, F, own_params, vmask;
+  Buf slot_seg_start, slot_seg_end, slot_seg_list, seg_pos, F, own_params, vmask, act_off;
 
   CacheView view() const {
     CacheView cv;
@@ -141,17 +141,21 @@ struct gslm_cache {
     cv.seg_pos = seg_pos.as<uint32_t>();
     cv.slot_active = slot_active.as<uint8_t>();
     cv.vmask = vmask.as<unsigned long long>();
+    cv.act_off = act_off.as<uint32_t>();
     cv.n_seg = n_seg;
     cv.n_entries = n_entries;
     cv.fmt = fmt;
     cv.skip = nullptr;
     return cv;
   }
+  // splat tangents the tangent kernel writes: one per active splat (compact
+  // index) when the view masks exist, else one per (view, Gaussian) slot
+  long long tangent_rows() const { return act_off.p != nullptr ? std::max<long long>(n_active, 1) : std::max<long long>((long long)N * V, 1); }
   size_t device_bytes() const {
     return cams.bytes + rec.bytes + slot_active.bytes + tile_seg_off.bytes + seg_entry_off.bytes + seg_slot.bytes +
            seg_rec.bytes +
            payload.bytes + seg_scale.bytes + pixoff.bytes + slot_seg_start.bytes + slot_seg_end.bytes +
-           slot_seg_list.bytes + seg_pos.bytes + F.bytes + own_params.bytes + vmask.bytes;
+           slot_seg_list.bytes + seg_pos.bytes + F.bytes + own_params.bytes + vmask.bytes + act_off.bytes;
   }
 };
 
@@ -377,10 +381,11 @@ gslm_status do_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float
                        float* p_out, const PcgScalars* sc, const float* Fadd, double* sq_partials) {
   cudaStream_t st = ctx->st;
   const long long S = (long long)c->N * c->V;
-  CK(ctx->ydot.ensure(sizeof(float) * 12 * std::max<long long>(S, 1), st));
+  (void)S;
+  CK(ctx->ydot.ensure(sizeof(float) * 12 * c->tangent_rows(), st));
   bool t = ctx->timer.begin(PH_TANGENT);
   CK(launch_tangent(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_active.as<uint8_t>(),
-                    c->vmask.as<unsigned long long>(), p,
+                    c->vmask.as<unsigned long long>(), c->act_off.as<uint32_t>(), p,
                     ctx->ydot.as<float>(), z_beta, p_out, sc, st));
   CacheView cv = c->view();
   cv.skip = sc != nullptr ? &sc->done : nullptr;
@@ -545,7 +550,7 @@ gslm_status batch_layout(gslm_ctx* ctx, const gslm_cache* const* cs, int n, Batc
       return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: caches differ in N, ld, format or mode");
     auto up = [](long long v) { return (v + 3) & ~3ll; };   // 16-byte aligned sub-buffers
     L->u_off[i + 1] = L->u_off[i] + up(3 * std::max<long long>(c->n_pix, 1));
-    L->y_off[i + 1] = L->y_off[i] + up(12 * std::max<long long>((long long)c->N * c->V, 1));
+    L->y_off[i + 1] = L->y_off[i] + up(12 * c->tangent_rows());
     L->s_off[i + 1] = L->s_off[i] + up(12 * std::max<long long>(c->n_seg, 1));
   }
   return GSLM_OK;
@@ -592,6 +597,7 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     R.V = c->V;
     R.slot_active = c->slot_active.as<uint8_t>();
     R.vmask = c->vmask.as<unsigned long long>();
+    R.act_off = c->act_off.as<uint32_t>();
     R.s_start = c->slot_seg_start.as<uint32_t>();
     R.s_end = c->slot_seg_end.as<uint32_t>();
     R.s_list = c->slot_seg_list.as<uint32_t>();
@@ -1052,11 +1058,16 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
     CK(cudaStreamSynchronize(st));
     c->n_active = (long long)na;
   }
-  // keep the splats and cameras; drop the binning buffers
-  c->rec.p = B.rec.p;
-  c->rec.bytes = B.rec.bytes;
-  c->rec.st = st;
-  B.rec.p = nullptr;
+  // compact splat indices: act_off from the view masks, SegRec.slot rewritten
+  if (c->vmask.p != nullptr) {
+    CK(c->act_off.alloc(sizeof(uint32_t) * ((size_t)N + 1), st));
+    Buf tmp;
+    CK(tmp.alloc(sizeof(uint32_t) * ((size_t)N + 1) + 64 + scan_temp_bytes((long long)N + 1), st));
+    CK(launch_compact_splats(c->vmask.as<unsigned long long>(), (int)N, c->act_off.as<uint32_t>(), tmp.p,
+                             c->seg_slot.as<uint32_t>(), c->n_seg, c->seg_rec.as<SegRec>(), st));
+  }
+  // keep the cameras; drop the per-slot splat records (the segment records
+  // hold what the kernels need) and the binning buffers
   c->cams.p = B.cams.p;
   c->cams.bytes = B.cams.bytes;
   c->cams.st = st;

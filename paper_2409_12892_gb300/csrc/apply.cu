@@ -539,20 +539,14 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
   const int tile = blockIdx.x;
   const uint32_t g0 = cv.tile_seg_off[tile], g1 = cv.tile_seg_off[tile + 1];
   if (g0 == g1) return;
-  const int v = find_view(cv.cams, cv.V, tile);
-  const DevCam& cam = cv.cams[v];
-  const int lt = tile - cam.tile_off;
-  const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
-  const float ox = tx * kTile + 0.5f, oy = ty * kTile + 0.5f;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t seg = g0 + warp; seg < g1; seg += kTilePix / 32) {
-    const uint32_t slot = cv.seg_slot[seg];
-    const unsigned long long e0 = cv.seg_entry_off[seg], e1 = cv.seg_entry_off[seg + 1];
-    const float4 ra = cv.rec[slot].a;
-    const float2 rb = *reinterpret_cast<const float2*>(&cv.rec[slot].b);
-    const float mx = ra.x - ox, my = ra.y - oy, A = ra.z, B = ra.w, C = rb.x;
-    const float io = 1.f / rb.y;
-    const float scale = kFmt == GSLM_CACHE_FP16S ? cv.seg_scale[seg] : 1.f;
+    const uint4* rq = reinterpret_cast<const uint4*>(cv.seg_rec + seg);
+    const SegRec r = rec_from(rq[0], rq[1], rq[2]);   // tile-local mean, conic, 1/o, FP16 scale
+    const unsigned long long e0 = r.e0, e1 = r.e1;
+    const float mx = r.mx, my = r.my, A = r.A, B = r.B, C = r.C;
+    const float io = r.io;
+    const float scale = kFmt == GSLM_CACHE_FP16S ? r.scale : 1.f;
     float q[40];
 #pragma unroll
     for (int i = 0; i < 40; ++i) q[i] = 0.f;

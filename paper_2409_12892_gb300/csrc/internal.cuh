@@ -138,6 +138,9 @@ struct CacheView {
                                    // adjoints and diagonal blocks are stored in this (slot) order
   const uint8_t* slot_active;      // [n_slots]
   const unsigned long long* vmask; // [N] active views per Gaussian (null when V > 64)
+  const uint32_t* act_off;         // [N + 1] with vmask: first compact splat index of each Gaussian; the
+                                   // splat tangents are stored by compact index (act_off[g] + rank of the
+                                   // view among g's active views) and SegRec.slot holds that index
   long long n_seg;
   long long n_entries;
   int fmt;
@@ -161,6 +164,7 @@ struct SubsetRefs {
   int V;
   const uint8_t* slot_active;           // [N * V]
   const unsigned long long* vmask;      // [N] or null
+  const uint32_t* act_off;              // [N + 1] compact splat offsets (with vmask) or null
   const uint32_t* s_start;              // segments of a slot (vjp)
   const uint32_t* s_end;
   const uint32_t* s_list;
@@ -221,10 +225,14 @@ cudaError_t launch_view_mask(const uint8_t* slot_active, int N, int V, unsigned 
                              cudaStream_t st);
 // vmask (per Gaussian, bit v = view v has cache entries) may be null, and must
 // be null when V > 64; the kernels then visit every view.
+// act_off (with vmask; may be null): ydot stored by compact splat index (CacheView.act_off).
 cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCam* cams, int V,
                            int smooth, const uint8_t* slot_active, const unsigned long long* vmask,
-                           const float* p, float* ydot, const float* z_beta, float* p_out,
-                           const PcgScalars* sc, cudaStream_t st);
+                           const uint32_t* act_off, const float* p, float* ydot, const float* z_beta,
+                           float* p_out, const PcgScalars* sc, cudaStream_t st);
+// act_off[0..N] from the view masks, and SegRec.slot rewritten to the compact splat index.
+cudaError_t launch_compact_splats(const unsigned long long* vmask, int N, uint32_t* act_off, void* scan_temp,
+                                  const uint32_t* seg_slot, long long n_seg, SegRec* seg_rec, cudaStream_t st);
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V,
                        int smooth, const uint32_t* slot_seg_start, const uint32_t* slot_seg_end,
                        const uint32_t* slot_seg_list, const unsigned long long* vmask,

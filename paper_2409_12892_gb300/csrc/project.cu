@@ -355,8 +355,8 @@ __device__ __forceinline__ int role_row(int role, int i) { return role == 0 ? i 
 __device__ __forceinline__ void tangent_body(
     int g, int role, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V,
     int smooth, const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
-    const float* __restrict__ pin, float* __restrict__ ydot, const float* __restrict__ zb,
-    float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
+    const uint32_t* __restrict__ act_off, const float* __restrict__ pin, float* __restrict__ ydot,
+    const float* __restrict__ zb, float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
   if (g >= N) return;
   if (sc != nullptr && sc->done) return;
   const float beta = zb != nullptr ? (float)sc->beta : 0.f;
@@ -383,6 +383,7 @@ __device__ __forceinline__ void tangent_body(
     float Sd[6];
     sigma_tangent(G, pg + 3, pg + 6, Sd);
     const float od = G.o * (1.f - G.o) * pg[10];
+    long long ti = act_off != nullptr ? (long long)act_off[g] : 0;   // compact splat index
     for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
       const long long slot = (long long)v * N + g;
       if (!slot_active[slot]) continue;
@@ -391,7 +392,7 @@ __device__ __forceinline__ void tangent_body(
       view_geo(G, cam, VG);
       float yd[5];
       geo_tangent(VG, cam, pm, Sd, yd);
-      float* out = ydot + slot * 12;
+      float* out = ydot + (act_off != nullptr ? ti++ : slot) * 12;
       reinterpret_cast<float4*>(out)[0] = make_float4(yd[0], yd[1], yd[2], yd[3]);
       reinterpret_cast<float2*>(out)[2] = make_float2(yd[4], od);
     }
@@ -408,9 +409,11 @@ __device__ __forceinline__ void tangent_body(
 #pragma unroll
     for (int k = 0; k < 16; ++k) w[k] = P[(11 + 3 * k + ch) * ld + g];
     const float mu0 = P[g], mu1 = P[ld + g], mu2 = P[2 * ld + g];
+    long long ti = act_off != nullptr ? (long long)act_off[g] : 0;   // compact splat index
     for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
       const long long slot = (long long)v * N + g;
       if (!slot_active[slot]) continue;
+      const long long yi = act_off != nullptr ? ti++ : slot;
       const DevCam& cam = cams[v];
       const float d0 = mu0 - cam.campos[0], d1 = mu1 - cam.campos[1], d2 = mu2 - cam.campos[2];
       const float inv_dlen = 1.f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -428,7 +431,7 @@ __device__ __forceinline__ void tangent_body(
       sh_grad(dir[0], dir[1], dir[2], w, gr);
 #pragma unroll
       for (int i = 0; i < 3; ++i) acc += gr[i] * (pm[i] - dir[i] * mdot) * inv_dlen;
-      ydot[slot * 12 + 6 + ch] = (!smooth && raw < 0.f) ? 0.f : acc;
+      ydot[yi * 12 + 6 + ch] = (!smooth && raw < 0.f) ? 0.f : acc;
     }
   }
 }
@@ -628,10 +631,10 @@ __device__ __forceinline__ void write_dot_partial(double local, double* __restri
 __global__ void __launch_bounds__(128) k_tangent(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
-    const float* __restrict__ pin, float* __restrict__ ydot, const float* __restrict__ zb,
-    float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
+    const uint32_t* __restrict__ act_off, const float* __restrict__ pin, float* __restrict__ ydot,
+    const float* __restrict__ zb, float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
   tangent_body(blockIdx.x * kGPB + (threadIdx.x & 31), threadIdx.x >> 5, P, N, ld, cams, V, smooth, slot_active,
-               vmask, pin, ydot, zb, pout, sc);
+               vmask, act_off, pin, ydot, zb, pout, sc);
 }
 
 // Batched: blockIdx.y is the subset; its p, z and pout sit at offset
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(128) k_tangent_batch(const float* __restrict__
   const SubsetRefs& s = gb.s[b];
   const long long off = (long long)b * vs;
   tangent_body(blockIdx.x * kGPB + (threadIdx.x & 31), threadIdx.x >> 5, P, N, ld, s.cams, s.V, smooth,
-               s.slot_active, s.vmask, pin + off, s.ydot, zb != nullptr ? zb + off : nullptr,
+               s.slot_active, s.vmask, s.act_off, pin + off, s.ydot, zb != nullptr ? zb + off : nullptr,
                pout != nullptr ? pout + off : nullptr, sc != nullptr ? sc + b : nullptr);
 }
 
@@ -822,11 +825,45 @@ cudaError_t launch_view_mask(const uint8_t* slot_active, int N, int V, unsigned 
 }
 
 cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
-                           const uint8_t* slot_active, const unsigned long long* vmask, const float* p,
-                           float* ydot, const float* z_beta, float* p_out, const PcgScalars* sc, cudaStream_t st) {
+                           const uint8_t* slot_active, const unsigned long long* vmask, const uint32_t* act_off,
+                           const float* p, float* ydot, const float* z_beta, float* p_out, const PcgScalars* sc,
+                           cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_tangent<<<(N + kGPB - 1) / kGPB, 128, 0, st>>>(params, N, ld, cams, V, smooth, slot_active, vmask, p, ydot,
-                                                     z_beta, p_out, sc); note_launch(); }
+  { k_tangent<<<(N + kGPB - 1) / kGPB, 128, 0, st>>>(params, N, ld, cams, V, smooth, slot_active, vmask, act_off, p,
+                                                     ydot, z_beta, p_out, sc); note_launch(); }
+  return cudaGetLastError();
+}
+
+__global__ void k_active_count(const unsigned long long* __restrict__ vmask, int N, uint32_t* __restrict__ cnt) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < N) cnt[g] = (uint32_t)__popcll(vmask[g]);
+}
+
+__global__ void k_seg_compact_slot(const unsigned long long* __restrict__ vmask, int N,
+                                   const uint32_t* __restrict__ act_off, const uint32_t* __restrict__ seg_slot,
+                                   long long n_seg, SegRec* __restrict__ seg_rec) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_seg) return;
+  const uint32_t slot = seg_slot[s];
+  const int v = (int)(slot / (uint32_t)N);
+  const int g = (int)(slot - (uint32_t)v * (uint32_t)N);
+  const unsigned long long below = v > 0 ? (vmask[g] & ((1ull << v) - 1ull)) : 0ull;
+  seg_rec[s].slot = act_off[g] + (uint32_t)__popcll(below);
+}
+
+cudaError_t launch_compact_splats(const unsigned long long* vmask, int N, uint32_t* act_off, void* scan_temp,
+                                  const uint32_t* seg_slot, long long n_seg, SegRec* seg_rec, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  // counts in act_off[0..N), then an in-place-safe scan into act_off via a second buffer
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(scan_temp);
+  { k_active_count<<<(N + 255) / 256, 256, 0, st>>>(vmask, N, cnt); note_launch(); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  void* tmp = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(cnt + N + 1) + 63) & ~uintptr_t(63));
+  e = exclusive_scan_u32(cnt, act_off, N, tmp, st);
+  if (e != cudaSuccess || n_seg <= 0) return e;
+  { k_seg_compact_slot<<<(unsigned)((n_seg + 255) / 256), 256, 0, st>>>(vmask, N, act_off, seg_slot, n_seg, seg_rec);
+    note_launch(); }
   return cudaGetLastError();
 }
 
