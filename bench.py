@@ -212,6 +212,7 @@ def build_workload(wl, device):
     del noise
     torch.cuda.synchronize()
     ctx.close()
+    torch.cuda.empty_cache()      # hand torch's cached blocks back: the LM step's caches need the room
     return wl, P, cams, targets
 
 
@@ -231,7 +232,9 @@ def run_steps(g, ctx, params, N, cams, targets, wl, steps: int, warmup: int, dis
             launches0 = g.kernel_launches()
             ev0.record(st)
         subsets = synth.subset_views(wl, s)
+        ctx.memory_usage(reset_peak=True)         # host-side read of the pool's counters
         state, lm = ctx.lm_step(params, N, cams, targets, subsets, lam, s)
+        lm.mem_peak = ctx.memory_usage()["peak"]
         lam = state.lambda_
         if s >= warmup:
             stats.append(lm)
@@ -412,8 +415,10 @@ def workload_config(args, form: str) -> dict:
     wl = workload(args)
     return {
         "workload": (f"{wl.name}: {wl.n_gaussians} Gaussians ({wl.n_clusters} clusters), {wl.n_cameras} cameras "
-                     f"{wl.resolutions[0][0]}x{wl.resolutions[0][1]}, {len(wl.subset_sizes)} subsets x "
-                     f"{wl.subset_sizes[0]} views per LM step"),
+                     f"{'/'.join(f'{w}x{h}' for w, h in wl.resolutions)}, {len(wl.subset_sizes)} subsets of "
+                     + (f"{wl.subset_sizes[0]}" if len(set(wl.subset_sizes)) == 1
+                        else "+".join(str(v) for v in wl.subset_sizes))
+                     + " views per LM step"),
         "form": form, "pcg_iters": wl.pcg_iters, "break_rel2": 0.01, "lambda0": wl.lambda0,
         "line_search": args.line_search,
         "l2_flush": "inputs larger than L2: the gradient caches of a step are tens of GB",
@@ -653,7 +658,9 @@ def run_ours(args):
                "predicted": [s.predicted for s in stats], "pcg_iters": [s.pcg_iters for s in stats],
                "cache_entries": E_step, "cache_gb": statistics.mean(s.cache_bytes for s in stats) / 1e9,
                "cache_segments": statistics.mean(s.cache_segments for s in stats),
-               "active_splats": statistics.mean(s.active_splats for s in stats)},
+               "active_splats": statistics.mean(s.active_splats for s in stats),
+               "sequential_groups": [s.seq_groups for s in stats],
+               "device_peak_gb": max(s.mem_peak for s in stats) / 1e9},
     }
     if "plain" in result:
         pl = result["plain"]

@@ -38,7 +38,8 @@
  *   - Gaussian parameters and every parameter-space vector (b, p, g, x, M,
  *     preconditioner, Delta): structure of arrays, float32 [59][ld], element
  *     (k, i) at offset k*ld + i for parameter k of Gaussian i; ld >= N and a
- *     multiple of 4. Parameter order per Gaussian: position (3), log-scale (3),
+ *     multiple of 4; gslm_pcg_solve's vectors start on a 16-byte boundary
+ *     (every cudaMalloc'd or torch-allocated buffer does). Parameter order per Gaussian: position (3), log-scale (3),
  *     quaternion w,x,y,z (4, not normalised), opacity logit (1), SH (48, index
  *     3*coeff + channel, coeff l-major, degree <= 3). This is the paper's
  *     per-attribute layout q (Sec. A, "Design of applyJ and diagJTJ").
@@ -99,6 +100,10 @@ typedef struct {
   int32_t line_search; /* gslm_lm_step: 0 = full step (gamma = 1); n > 0 = Eq. line-search over
                           gamma = 1, 1/2, ..., 2^(1-n) on the first 30% of the step's views,
                           stopping at the first cost increase (default 8) */
+  int32_t pad;
+  size_t batch_mem;    /* gslm_lm_step with batch: bytes the stacked PCG vectors of a group of
+                          subsets may take (0 = as much as the device gives); a group above it,
+                          or whose vectors cannot be allocated, is solved subset by subset */
 } gslm_options;
 
 typedef struct gslm_ctx gslm_ctx;
@@ -153,7 +158,8 @@ typedef struct {
   int64_t active_splats;  /* splats with at least one cache entry, summed over subsets */
   double gamma;           /* step scale the line search chose (1 without line search) */
   int32_t ls_evals;       /* line-search cost evaluations */
-  int32_t pad2;
+  int32_t seq_groups;     /* groups of subsets solved one after another because their stacked
+                             PCG vectors did not fit in device memory beside the caches (batch mode) */
 } gslm_lm_stats;
 
 /* Default options: FP32 cache, 8 iterations, break 0.01, lambda in [1e-4, 1e4]. */
@@ -251,7 +257,13 @@ gslm_status gslm_combine_finish(gslm_ctx* ctx, int64_t N, int64_t ld, const floa
  * cams: host array of all cameras; targets: [sum over all cams W*H][3] in camera
  * order; subset_views: host, concatenated camera indices of the subsets;
  * subset_off: host, n_b + 1 offsets into subset_views. precond: optional
- * per-subset preconditioners (host array of n_b device pointers, or NULL). */
+ * per-subset preconditioners (host array of n_b device pointers, or NULL).
+ * Memory: every subset's cache stays resident until the step ends (they read
+ * params in place, so params must not change during the call). With
+ * options.batch the subsets' solves run in groups of up to 16 that keep six
+ * stacked [59][ld] vectors per subset (seven with a preconditioner); a group
+ * whose vectors do not fit beside its caches is solved one subset after
+ * another instead (reported in stats->seq_groups), with the same arithmetic. */
 gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld,
                          const gslm_camera* cams, int32_t n_cams, const float* targets,
                          const int32_t* subset_views, const int32_t* subset_off, int32_t n_b,
@@ -326,6 +338,12 @@ gslm_status gslm_set_precond(gslm_ctx* ctx, gslm_precond* pc);
 const char* gslm_version(void);
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t gslm_kernel_launches(void);
+/* Device memory of the pool the library allocates from (the context device's
+ * default pool, see Conventions), host out[3]: out[0] bytes in use, out[1]
+ * bytes the pool holds (in use + kept for reuse), out[2] the most bytes in use
+ * since the last reset. reset_peak != 0 then resets out[2]'s mark to the
+ * bytes in use. Reads only; nothing is enqueued. */
+gslm_status gslm_memory_usage(const gslm_ctx* ctx, int32_t reset_peak, int64_t out[3]);
 /* Kernel variants the autotuner chose on this context: out[0..2] apply_J and
  * out[3..5] apply_JT for the FP32, BF16 and FP16S caches (-1 = not tuned yet);
  * ms[0..5] (may be NULL) the time of the chosen variant when it was tuned. */

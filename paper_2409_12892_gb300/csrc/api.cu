@@ -85,11 +85,11 @@ struct gslm_ctx {
   float ms_JT[3] = {0.f, 0.f, 0.f};
   // scratch reused across calls
   Buf ydot, seg_ybar, seg_q, u, partials, scalars, reduce_out;
-  Buf r, z, p, g, minv;
+  Buf r, z, p, g;
   Buf lm_num, lm_den, lm_delta, lm_trial, lm_x, lm_b, lm_M, lm_tgt, lm_img, lm_D;
   gslm_precond* pc = nullptr;       // learned preconditioner used by lm_step, if set
   // batched solves: stacked per-subset vectors and per-subset scratch
-  Buf bt_b, bt_M, bt_D, bt_x, bt_r, bt_z, bt_p, bt_g, bt_minv, bt_u, bt_ydot, bt_segy, bt_part, bt_sc, bt_queue;
+  Buf bt_b, bt_M, bt_D, bt_x, bt_z, bt_p, bt_g, bt_u, bt_ydot, bt_segy, bt_part, bt_sc, bt_queue;
   int bvar_J[3] = {-1, -1, -1};     // autotuned (variant, CTAs per SM) of the persistent tile kernels
   int bvar_JT[3] = {-1, -1, -1};
   int bctas_J[3] = {0, 0, 0};
@@ -296,16 +296,16 @@ gslm_status bin_splats(gslm_ctx* ctx, const float* params, int N, long long ld, 
   Buf sorted_slots;
   CK(sorted_slots.alloc(sizeof(uint32_t) * nv, st));
   CK(cudaMemcpyAsync(sorted_slots.p, dv, sizeof(uint32_t) * B.n_vis, cudaMemcpyDeviceToDevice, st));
-  B.keys_a.release();
-  B.keys_b.release();
-  B.vals_b.release();
-  B.vis.release();
+  // Per-slot buffers are dropped as soon as they are dead, so that the peak
+  // of a build is the splat records plus the key buffers.
+  for (Buf* b : {&B.keys_a, &B.keys_b, &B.vals_b, &B.vis, &B.ntiles, &B.depth, &B.flags, &B.pos}) b->release();
   CK(B.keys_a.alloc(sizeof(uint32_t) * nk, st));
   CK(B.vals_a.alloc(sizeof(uint32_t) * nk, st));
-  CK(B.keys_b.alloc(sizeof(uint32_t) * nk, st));
-  CK(B.vals_b.alloc(sizeof(uint32_t) * nk, st));
   CK(launch_emit_keys(sorted_slots.as<uint32_t>(), B.n_vis, B.rect.as<uint2>(), B.cams.as<DevCam>(), V, N,
                       B.key_off.as<unsigned long long>(), B.keys_a.as<uint32_t>(), B.vals_a.as<uint32_t>(), st));
+  for (Buf* b : {&sorted_slots, &B.rect, &B.key_off}) b->release();
+  CK(B.keys_b.alloc(sizeof(uint32_t) * nk, st));
+  CK(B.vals_b.alloc(sizeof(uint32_t) * nk, st));
   CK(B.sort_tmp.ensure(radix_temp_bytes(nk), st));
   CK(radix_sort_pairs(B.keys_a.as<uint32_t>(), B.vals_a.as<uint32_t>(), B.keys_b.as<uint32_t>(),
                       B.vals_b.as<uint32_t>(), B.n_keys, bits_for((unsigned long long)n_tiles), B.sort_tmp.p,
@@ -315,12 +315,10 @@ gslm_status bin_splats(gslm_ctx* ctx, const float* params, int N, long long ld, 
   CK(cudaMemsetAsync(B.tile_start.p, 0, sizeof(uint32_t) * (n_tiles + 1), st));
   CK(cudaMemsetAsync(B.tile_end.p, 0, sizeof(uint32_t) * (n_tiles + 1), st));
   CK(launch_ranges(B.tile_keys, B.n_keys, B.tile_start.as<uint32_t>(), B.tile_end.as<uint32_t>(), st));
-  B.ntiles.release();
-  B.depth.release();
-  B.flags.release();
-  B.pos.release();
-  B.key_off.release();
-  B.sort_tmp.release();
+  // only the sorted splat list of the keys is read from here on
+  const bool vals_in_a = B.tile_vals == B.vals_a.as<uint32_t>();
+  for (Buf* b : {&B.keys_a, &B.keys_b, vals_in_a ? &B.vals_b : &B.vals_a, &B.sort_tmp}) b->release();
+  B.tile_keys = nullptr;
   return GSLM_OK;
 }
 
@@ -441,7 +439,6 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
   CK(ctx->z.ensure(vb, st));
   CK(ctx->p.ensure(vb, st));
   CK(ctx->g.ensure(vb, st));
-  CK(ctx->minv.ensure(vb, st));
   CK(ctx->u.ensure(sizeof(float) * 3 * std::max<long long>(c->n_pix, 1), st));
   const int nvec = pcg_blocks(N), nvjp = vjp_blocks(N);
   CK(ctx->partials.ensure(sizeof(double) * 2 * std::max(nvec, nvjp), st));
@@ -449,18 +446,17 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
   PcgScalars* sc = ctx->scalars.as<PcgScalars>();
   double* part = ctx->partials.as<double>();
   float *r = ctx->r.as<float>(), *z = ctx->z.as<float>(), *p = ctx->p.as<float>(), *g = ctx->g.as<float>();
-  float* Minv = ctx->minv.as<float>();
   float* u = ctx->u.as<float>();
   // x0 = M^-1 b
   bool t = ctx->timer.begin(PH_VEC);
-  CK(launch_pcg_init(0, ld, N, b, diag, D, x, Minv, part, st));
+  CK(launch_pcg_init(N, ld, b, diag, D, x, part, st));
   CK(launch_pcg_scalars(sc, part, nvec, 0, ctx->opt.break_rel2, st));
   ctx->timer.end(t);
   // u0 = J x0; g0 = J^T u0; r0 = b - (g0 + lambda M x0); z0 = M^-1 r0; p0 = z0
   CKS(do_apply_J(ctx, c, x, u, nullptr, nullptr, nullptr, nullptr, nullptr));
   CKS(do_apply_JT(ctx, c, u, g, 1.f, nullptr, nullptr, 0.f, nullptr, nullptr));
   t = ctx->timer.begin(PH_VEC);
-  CK(launch_pcg_residual0(N, ld, b, g, diag, x, lambda, Minv, r, z, p, part, st));
+  CK(launch_pcg_residual0(N, ld, b, g, diag, D, x, lambda, r, z, p, part, st));
   CK(launch_pcg_scalars(sc, part, nvec, 1, ctx->opt.break_rel2, st));
   ctx->timer.end(t);
   for (int it = 0; it < ctx->opt.n_iters; ++it) {
@@ -477,7 +473,7 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
     CKS(do_apply_JT(ctx, c, u, g, 1.f, p, diag, lambda, part, sc));
     t = ctx->timer.begin(PH_VEC);
     CK(launch_pcg_scalars(sc, part, nvjp, 2, ctx->opt.break_rel2, st));
-    CK(launch_pcg_update(N, ld, sc, p, g, Minv, x, r, z, part, st));
+    CK(launch_pcg_update(N, ld, sc, p, g, diag, D, x, r, z, part, st));
     CK(launch_pcg_scalars(sc, part, nvec, 3, ctx->opt.break_rel2, st));
     ctx->timer.end(t);
   }
@@ -556,12 +552,14 @@ gslm_status batch_layout(gslm_ctx* ctx, const gslm_cache* const* cs, int n, Batc
   return GSLM_OK;
 }
 
-gslm_status batch_alloc(gslm_ctx* ctx, const BatchLayout& L) {
+gslm_status batch_alloc(gslm_ctx* ctx, const BatchLayout& L, unsigned d_mask, size_t limit) {
   cudaStream_t st = ctx->st;
   const size_t vb = sizeof(float) * (size_t)L.vs * L.n;
-  for (Buf* b : {&ctx->bt_b, &ctx->bt_M, &ctx->bt_D, &ctx->bt_x, &ctx->bt_r, &ctx->bt_z, &ctx->bt_p, &ctx->bt_g,
-                 &ctx->bt_minv})
-    CK(b->ensure(vb, st));
+  const size_t need = (d_mask != 0 ? 7 : 6) * vb + sizeof(float) * (L.u_off[L.n] + L.y_off[L.n] + L.s_off[L.n]);
+  if (limit != 0 && need > limit) return fail(ctx, GSLM_E_OOM, "batch: stacked vectors above options.batch_mem");
+  // r lives in b's place (b is read only by the first residual); M^-1 is not stored
+  for (Buf* b : {&ctx->bt_b, &ctx->bt_M, &ctx->bt_x, &ctx->bt_z, &ctx->bt_p, &ctx->bt_g}) CK(b->ensure(vb, st));
+  if (d_mask != 0) CK(ctx->bt_D.ensure(vb, st));
   CK(ctx->bt_u.ensure(sizeof(float) * L.u_off[L.n], st));
   CK(ctx->bt_ydot.ensure(sizeof(float) * L.y_off[L.n], st));
   CK(ctx->bt_segy.ensure(sizeof(float) * L.s_off[L.n], st));
@@ -582,8 +580,8 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
   PcgScalars* sc = ctx->bt_sc.as<PcgScalars>();
   double* part = ctx->bt_part.as<double>();
   float *b = ctx->bt_b.as<float>(), *M = ctx->bt_M.as<float>(), *D = ctx->bt_D.as<float>();
-  float *x = ctx->bt_x.as<float>(), *r = ctx->bt_r.as<float>(), *z = ctx->bt_z.as<float>();
-  float *p = ctx->bt_p.as<float>(), *g = ctx->bt_g.as<float>(), *Minv = ctx->bt_minv.as<float>();
+  float *x = ctx->bt_x.as<float>(), *r = b, *z = ctx->bt_z.as<float>();   // r overwrites b
+  float *p = ctx->bt_p.as<float>(), *g = ctx->bt_g.as<float>();
   GaussBatch gb;
   TileBatch tb;
   gb.n = tb.n = n;
@@ -658,7 +656,7 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
   if (init) {
     // x0 = M^-1 b
     t = ctx->timer.begin(PH_VEC);
-    CK(launch_pcg_init_batch(n, N, ld, vs, b, M, D, d_mask, x, Minv, part, st));
+    CK(launch_pcg_init_batch(n, N, ld, vs, b, M, D, d_mask, x, part, st));
     CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 0, ctx->opt.break_rel2, st));
     ctx->timer.end(t);
     // u0 = J x0; g0 = J^T u0; r0 = b - (g0 + lambda M x0); z0 = M^-1 r0; p0 = z0
@@ -671,7 +669,7 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     CK(launch_vjp_batch(params, N, ld, smooth, gb, g, vs, nullptr, nullptr, 0.f, nullptr, nullptr, st));
     ctx->timer.end(t);
     t = ctx->timer.begin(PH_VEC);
-    CK(launch_pcg_residual0_batch(n, N, ld, vs, b, g, M, x, lambda, Minv, r, z, p, part, st));
+    CK(launch_pcg_residual0_batch(n, N, ld, vs, b, g, M, D, d_mask, x, lambda, r, z, p, part, st));
     CK(launch_pcg_scalars_batch(n, sc, part, nvec, nvec, 1, ctx->opt.break_rel2, st));
     ctx->timer.end(t);
   }
@@ -686,7 +684,7 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     ctx->timer.end(t);
     t = ctx->timer.begin(PH_VEC);
     CK(launch_pcg_scalars_batch(n, sc, part, nvjp, nvjp, 2, ctx->opt.break_rel2, st));
-    CK(launch_pcg_update_batch(n, N, ld, vs, sc, p, g, Minv, x, r, z, part, st));
+    CK(launch_pcg_update_batch(n, N, ld, vs, sc, p, g, M, D, d_mask, x, r, z, part, st));
     CK(launch_pcg_scalars_batch(n, sc, part, nvec, 2 * nvec, 3, ctx->opt.break_rel2, st));
     ctx->timer.end(t);
   }
@@ -815,6 +813,30 @@ const char* gslm_version(void) { return "gslm 0.1 (sm_103a)"; }
 
 int64_t gslm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+gslm_status gslm_memory_usage(const gslm_ctx* ctx, int32_t reset_peak, int64_t out[3]) {
+  if (ctx == nullptr || out == nullptr) return GSLM_E_INVALID;
+  cudaMemPool_t pool = nullptr;
+  uint64_t used = 0, reserved = 0, high = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high) != cudaSuccess) {
+    cudaGetLastError();
+    return GSLM_E_CUDA;
+  }
+  out[0] = (int64_t)used;
+  out[1] = (int64_t)reserved;
+  out[2] = (int64_t)high;
+  if (reset_peak != 0) {
+    uint64_t zero = 0;   // the only value the mark can be set to: it restarts from the bytes in use
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess) {
+      cudaGetLastError();
+      return GSLM_E_CUDA;
+    }
+  }
+  return GSLM_OK;
+}
+
 gslm_status gslm_autotune_info(const gslm_ctx* ctx, int32_t out[6], float ms[6]) {
   if (ctx == nullptr || out == nullptr) return GSLM_E_INVALID;
   for (int f = 0; f < 3; ++f) {
@@ -933,8 +955,13 @@ gslm_status gslm_render(gslm_ctx* ctx, const float* params, int64_t N, int64_t l
   return GSLM_OK;
 }
 
-gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld, const gslm_camera* cams,
-                             int32_t V, const float* targets, gslm_cache** out, float* F, float* b, double* cost) {
+// Builds a cache; with copy_params the cache keeps its own copy of the
+// parameters, else it reads the caller's, which must then stay unchanged for
+// the cache's lifetime (the LM step's caches: it writes the parameters only
+// after its last use of them).
+static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld,
+                                    const gslm_camera* cams, int32_t V, const float* targets, gslm_cache** out,
+                                    float* F, float* b, double* cost, bool copy_params) {
   CKS(check_vec_args(ctx, N, ld));
   if (out == nullptr) return fail(ctx, GSLM_E_INVALID, "build_cache: null cache pointer");
   *out = nullptr;
@@ -953,10 +980,13 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
   c->smooth = ctx->opt.smooth;
   c->fmt = ctx->opt.cache_fmt;
   CKS(make_cams(ctx, cams, V, c->hcams, c->n_tiles, c->n_pix));
-  // The cache keeps its own copy of the parameters it linearises around.
-  CK(c->own_params.alloc(sizeof(float) * kNP * (size_t)ld, st));
-  CK(cudaMemcpyAsync(c->own_params.p, params, sizeof(float) * kNP * (size_t)ld, cudaMemcpyDeviceToDevice, st));
-  c->params = c->own_params.as<float>();
+  if (copy_params) {
+    CK(c->own_params.alloc(sizeof(float) * kNP * (size_t)ld, st));
+    CK(cudaMemcpyAsync(c->own_params.p, params, sizeof(float) * kNP * (size_t)ld, cudaMemcpyDeviceToDevice, st));
+    c->params = c->own_params.as<float>();
+  } else {
+    c->params = params;
+  }
   params = c->params;
   const int n_tiles = c->n_tiles;
   const long long S = (long long)N * V;
@@ -1058,6 +1088,7 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
     CK(cudaStreamSynchronize(st));
     c->n_active = (long long)na;
   }
+  if (c->vmask.p != nullptr) c->slot_active.release();   // the view masks replace the per-slot flags
   // compact splat indices: act_off from the view masks, SegRec.slot rewritten
   if (c->vmask.p != nullptr) {
     CK(c->act_off.alloc(sizeof(uint32_t) * ((size_t)N + 1), st));
@@ -1080,6 +1111,12 @@ gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int6
   *out = c;
   c = nullptr;   // release from the guard
   return GSLM_OK;
+}
+
+gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld, const gslm_camera* cams,
+                             int32_t V, const float* targets, gslm_cache** out, float* F, float* b, double* cost) {
+  // the public cache keeps its own copy of the parameters it linearises around
+  return build_cache_impl(ctx, params, N, ld, cams, V, targets, out, F, b, cost, true);
 }
 
 gslm_status gslm_cache_stats(const gslm_cache* c, gslm_cache_info* info) {
@@ -1123,6 +1160,9 @@ gslm_status gslm_pcg_solve(gslm_ctx* ctx, const gslm_cache* c, const float* b, c
                            float lambda, float* x, gslm_pcg_stats* stats) {
   if (ctx == nullptr || c == nullptr || b == nullptr || diag == nullptr || x == nullptr)
     return fail(ctx, GSLM_E_INVALID, "pcg_solve: null");
+  // the vector kernels move float4s
+  for (const void* v : {(const void*)b, (const void*)diag, (const void*)D, (const void*)x})
+    if ((reinterpret_cast<uintptr_t>(v) & 15u) != 0) return fail(ctx, GSLM_E_INVALID, "pcg_solve: vector not 16-byte aligned");
   CKS(pcg_enqueue(ctx, c, b, diag, D, lambda, x));
   if (stats != nullptr) {
     PcgScalars h;
@@ -1154,17 +1194,17 @@ gslm_status gslm_pcg_solve_batch(gslm_ctx* ctx, const gslm_cache* const* caches,
     CKS(batch_layout(ctx, caches + g0, gn, &L));
     if (caches[g0]->N != caches[0]->N || caches[g0]->ld != caches[0]->ld)
       return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: caches differ in N or ld");
-    CKS(batch_alloc(ctx, L));
-    const size_t vb = sizeof(float) * (size_t)L.vs;
     unsigned mask = 0;
+    for (int k = 0; k < gn; ++k)
+      if (D != nullptr && D[g0 + k] != nullptr) mask |= 1u << k;
+    CKS(batch_alloc(ctx, L, mask, 0));
+    const size_t vb = sizeof(float) * (size_t)L.vs;
     for (int k = 0; k < gn; ++k) {
       const int i = g0 + k;
       CK(cudaMemcpyAsync(ctx->bt_b.as<float>() + k * L.vs, b[i], vb, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(ctx->bt_M.as<float>() + k * L.vs, diag[i], vb, cudaMemcpyDeviceToDevice, st));
-      if (D != nullptr && D[i] != nullptr) {
+      if ((mask >> k) & 1u)
         CK(cudaMemcpyAsync(ctx->bt_D.as<float>() + k * L.vs, D[i], vb, cudaMemcpyDeviceToDevice, st));
-        mask |= 1u << k;
-      }
     }
     CKS(pcg_batch_run(ctx, caches + g0, L, mask, lambda));
     for (int k = 0; k < gn; ++k)
@@ -1215,6 +1255,10 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   if (params == nullptr || cams == nullptr || targets == nullptr || subset_views == nullptr ||
       subset_off == nullptr || n_b <= 0 || state == nullptr)
     return fail(ctx, GSLM_E_INVALID, "lm_step: null argument");
+  if (precond != nullptr)
+    for (int i = 0; i < n_b; ++i)
+      if ((reinterpret_cast<uintptr_t>(precond[i]) & 15u) != 0)
+        return fail(ctx, GSLM_E_INVALID, "lm_step: preconditioner not 16-byte aligned");
   cudaStream_t st = ctx->st;
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0));
@@ -1235,9 +1279,12 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   CK(ctx->lm_den.ensure(vb, st));
   CK(ctx->lm_delta.ensure(vb, st));
   CK(ctx->lm_trial.ensure(vb, st));
-  CK(ctx->lm_x.ensure(vb, st));
-  CK(ctx->lm_b.ensure(vb, st));
-  CK(ctx->lm_M.ensure(vb, st));
+  const bool batched = ctx->opt.batch != 0;
+  if (!batched) {
+    CK(ctx->lm_x.ensure(vb, st));
+    CK(ctx->lm_b.ensure(vb, st));
+    CK(ctx->lm_M.ensure(vb, st));
+  }
   CK(cudaMemsetAsync(ctx->lm_num.p, 0, vb, st));
   CK(cudaMemsetAsync(ctx->lm_den.p, 0, vb, st));
   std::vector<gslm_cache*> caches(n_b, nullptr);
@@ -1248,9 +1295,24 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     }
   } cg{caches};
   std::vector<std::vector<gslm_camera>> scams(n_b);
-  std::vector<Buf> stg(n_b);
+  std::vector<std::vector<int>> sviews(n_b);
+  // the targets of the first nv views of subset i, made contiguous in lm_tgt
+  auto stage_targets = [&](int i, int nv) -> gslm_status {
+    long long pix = 0;
+    for (int q = 0; q < nv; ++q) pix += cam_pix[sviews[i][q] + 1] - cam_pix[sviews[i][q]];
+    CK(ctx->lm_tgt.ensure(sizeof(float) * 3 * std::max<long long>(pix, 1), st));
+    long long o = 0;
+    for (int q = 0; q < nv; ++q) {
+      const int v = sviews[i][q];
+      const long long np = cam_pix[v + 1] - cam_pix[v];
+      CK(cudaMemcpyAsync(ctx->lm_tgt.as<float>() + 3 * o, targets + 3 * cam_pix[v], sizeof(float) * 3 * np,
+                         cudaMemcpyDeviceToDevice, st));
+      o += np;
+    }
+    return GSLM_OK;
+  };
   double cost0 = 0.0, pair_bytes = 0.0;
-  int pcg_iters = 0, n_pairs = 0;
+  int pcg_iters = 0, n_pairs = 0, seq_groups = 0;
   long long segs = 0, actives = 0;
   ctx->timer.on = ctx->opt.profile != 0;
   ctx->timer.st = st;
@@ -1260,42 +1322,43 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   } toff{ctx->timer};
   long long entries = 0, bytes = 0;
   const float lambda = state->lambda;
-  const bool batched = ctx->opt.batch != 0;
   const long long vsn = (long long)kNP * ld;
+  std::vector<long long> spix(n_b, 0);
+  for (int i = 0; i < n_b; ++i) {
+    const int a = subset_off[i], e = subset_off[i + 1];
+    if (e <= a) return fail(ctx, GSLM_E_INVALID, "lm_step: empty subset");
+    for (int q = a; q < e; ++q) {
+      const int v = subset_views[q];
+      if (v < 0 || v >= n_cams) return fail(ctx, GSLM_E_INVALID, "lm_step: bad camera index");
+      scams[i].push_back(cams[v]);
+      sviews[i].push_back(v);
+      spix[i] += cam_pix[v + 1] - cam_pix[v];
+    }
+  }
   for (int g0 = 0; g0 < n_b; g0 += batched ? kMaxBatch : 1) {
     const int gn = batched ? std::min(kMaxBatch, n_b - g0) : 1;
     if (batched) {
       CK(ctx->bt_b.ensure(vb * gn, st));
       CK(ctx->bt_M.ensure(vb * gn, st));
-      CK(ctx->bt_D.ensure(vb * gn, st));
+      if (precond != nullptr || ctx->pc != nullptr) CK(ctx->bt_D.ensure(vb * gn, st));
     }
+    // A group's caches are built largest first: each build's transient buffers
+    // then come when the fewest caches are resident, and the memory pool reuses
+    // the large blocks they leave for the smaller caches that follow.
+    std::vector<int> order(gn);
+    for (int k = 0; k < gn; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return spix[g0 + x] > spix[g0 + y]; });
     unsigned dmask = 0;
-    for (int k = 0; k < gn; ++k) {
+    for (int kk = 0; kk < gn; ++kk) {
+      const int k = order[kk];
       const int i = g0 + k;
-      const int a = subset_off[i], e = subset_off[i + 1];
-      if (e <= a) return fail(ctx, GSLM_E_INVALID, "lm_step: empty subset");
-      long long pix = 0;
-      for (int q = a; q < e; ++q) {
-        const int v = subset_views[q];
-        if (v < 0 || v >= n_cams) return fail(ctx, GSLM_E_INVALID, "lm_step: bad camera index");
-        scams[i].push_back(cams[v]);
-        pix += (long long)cams[v].width * cams[v].height;
-      }
-      CK(stg[i].alloc(sizeof(float) * 3 * pix, st));
-      long long o = 0;
-      for (int q = a; q < e; ++q) {
-        const int v = subset_views[q];
-        const long long np = cam_pix[v + 1] - cam_pix[v];
-        CK(cudaMemcpyAsync(stg[i].as<float>() + 3 * o, targets + 3 * cam_pix[v], sizeof(float) * 3 * np,
-                           cudaMemcpyDeviceToDevice, st));
-        o += np;
-      }
+      CKS(stage_targets(i, (int)sviews[i].size()));
       float* bi = batched ? ctx->bt_b.as<float>() + k * vsn : ctx->lm_b.as<float>();
       float* Mi = batched ? ctx->bt_M.as<float>() + k * vsn : ctx->lm_M.as<float>();
       double ci = 0.0;
       bool t = ctx->timer.begin(PH_BUILD);
-      CKS(gslm_build_cache(ctx, params, N, ld, scams[i].data(), (int)scams[i].size(), stg[i].as<float>(),
-                           &caches[i], nullptr, bi, &ci));
+      CKS(build_cache_impl(ctx, params, N, ld, scams[i].data(), (int)scams[i].size(), ctx->lm_tgt.as<float>(),
+                           &caches[i], nullptr, bi, &ci, false));
       ctx->timer.end(t);
       cost0 += ci;
       entries += caches[i]->n_entries;
@@ -1332,13 +1395,33 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     if (!batched) continue;
     BatchLayout L;
     CKS(batch_layout(ctx, caches.data() + g0, gn, &L));
-    CKS(batch_alloc(ctx, L));
-    CKS(pcg_batch_run(ctx, caches.data() + g0, L, dmask, lambda));
+    const gslm_status sa = batch_alloc(ctx, L, dmask, ctx->opt.batch_mem);
     std::vector<PcgScalars> h(gn);
-    CK(cudaMemcpyAsync(h.data(), ctx->bt_sc.p, sizeof(PcgScalars) * gn, cudaMemcpyDeviceToHost, st));
-    for (int k = 0; k < gn; ++k)
-      CK(launch_combine_acc((int)N, ld, ctx->bt_x.as<float>() + k * vsn, ctx->bt_M.as<float>() + k * vsn,
-                            ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), st));
+    if (sa == GSLM_E_OOM) {
+      // The stacked vectors of the group do not fit beside its caches: solve
+      // the subsets one after another with one set of scratch vectors.
+      for (Buf* bf : {&ctx->bt_x, &ctx->bt_z, &ctx->bt_p, &ctx->bt_g, &ctx->bt_u, &ctx->bt_ydot, &ctx->bt_segy})
+        bf->release();
+      ctx->err.clear();
+      ++seq_groups;
+      CK(ctx->lm_x.ensure(vb, st));
+      for (int k = 0; k < gn; ++k) {
+        float* Mk = ctx->bt_M.as<float>() + k * vsn;
+        const float* Dk = ((dmask >> k) & 1u) ? ctx->bt_D.as<float>() + k * vsn : nullptr;
+        CKS(pcg_enqueue(ctx, caches[g0 + k], ctx->bt_b.as<float>() + k * vsn, Mk, Dk, lambda,
+                        ctx->lm_x.as<float>()));
+        CK(cudaMemcpyAsync(&h[k], ctx->scalars.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+        CK(launch_combine_acc((int)N, ld, ctx->lm_x.as<float>(), Mk, ctx->lm_num.as<float>(),
+                              ctx->lm_den.as<float>(), st));
+      }
+    } else {
+      CKS(sa);
+      CKS(pcg_batch_run(ctx, caches.data() + g0, L, dmask, lambda));
+      CK(cudaMemcpyAsync(h.data(), ctx->bt_sc.p, sizeof(PcgScalars) * gn, cudaMemcpyDeviceToHost, st));
+      for (int k = 0; k < gn; ++k)
+        CK(launch_combine_acc((int)N, ld, ctx->bt_x.as<float>() + k * vsn, ctx->bt_M.as<float>() + k * vsn,
+                              ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), st));
+    }
     CK(cudaStreamSynchronize(st));
     for (int k = 0; k < gn; ++k) {
       const gslm_cache* c = caches[g0 + k];
@@ -1347,6 +1430,11 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
       pair_bytes += (1.0 + h[k].iters) * (2.0 * (double)c->n_entries * (double)(payload_bytes(c->fmt) + 1) +
                                           24.0 * (double)c->n_pix + 472.0 * (double)N + 192.0 * (double)c->n_active);
     }
+    // back to the pool (which keeps them for the next step): the trial renders
+    // below need room beside the caches
+    for (Buf* bf : {&ctx->bt_b, &ctx->bt_M, &ctx->bt_D, &ctx->bt_x, &ctx->bt_z, &ctx->bt_p, &ctx->bt_g, &ctx->bt_u,
+                    &ctx->bt_ydot, &ctx->bt_segy})
+      bf->release();
   }
   CK(launch_combine_finish((int)N, ld, ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), ctx->lm_delta.as<float>(),
                            st));
@@ -1376,9 +1464,10 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
       long long pix = 0;
       for (int k = 0; k < nv[i]; ++k) pix += (long long)scams[i][k].width * scams[i][k].height;
       CK(ctx->lm_img.ensure(sizeof(float) * 3 * std::max<long long>(pix, 1), st));
+      CKS(stage_targets(i, nv[i]));
       double ci = 0.0;
       const gslm_status rs = gslm_render(ctx, ctx->lm_trial.as<float>(), N, ld, scams[i].data(), nv[i],
-                                         ctx->lm_img.as<float>(), stg[i].as<float>(), &ci);
+                                         ctx->lm_img.as<float>(), ctx->lm_tgt.as<float>(), &ci);
       if (rs == GSLM_E_CACHE_OVERFLOW) {
         *out = INFINITY;
         return GSLM_OK;
@@ -1461,7 +1550,7 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     stats->active_splats = actives;
     stats->gamma = gamma;
     stats->ls_evals = ls_evals;
-    stats->pad2 = 0;
+    stats->seq_groups = seq_groups;
   } else {
     double dummy[8] = {0};
     ctx->timer.collect(dummy, 8);

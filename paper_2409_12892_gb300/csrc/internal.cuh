@@ -48,7 +48,21 @@ struct Buf {
     release();
     st = s;
     if (n == 0) n = 16;
-    const cudaError_t e = cudaMallocAsync(&p, n, s);
+    cudaError_t e = cudaMallocAsync(&p, n, s);
+    if (e == cudaErrorMemoryAllocation) {
+      // The pool keeps freed blocks reserved; hand them back to the device
+      // and try once more (not while a graph is being captured).
+      cudaGetLastError();
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+        cudaMemPool_t pool;
+        int dev = 0;
+        if (cudaStreamSynchronize(s) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
+          e = cudaMallocAsync(&p, n, s);
+        if (e != cudaSuccess) cudaGetLastError();
+      }
+    }
     if (e != cudaSuccess) {
       p = nullptr;
       return e;
@@ -136,7 +150,7 @@ struct CacheView {
   const uint32_t* slot_seg_list;   // [n_seg] segment ids ordered by slot
   const uint32_t* seg_pos;         // [n_seg] position of a segment in slot_seg_list: per-segment
                                    // adjoints and diagonal blocks are stored in this (slot) order
-  const uint8_t* slot_active;      // [n_slots]
+  const uint8_t* slot_active;      // [n_slots] (null when vmask is set)
   const unsigned long long* vmask; // [N] active views per Gaussian (null when V > 64)
   const uint32_t* act_off;         // [N + 1] with vmask: first compact splat index of each Gaussian; the
                                    // splat tangents are stored by compact index (act_off[g] + rank of the
@@ -162,7 +176,7 @@ constexpr int kMaxBatch = 16;
 struct SubsetRefs {
   const DevCam* cams;
   int V;
-  const uint8_t* slot_active;           // [N * V]
+  const uint8_t* slot_active;           // [N * V] (null when vmask is set)
   const unsigned long long* vmask;      // [N] or null
   const uint32_t* act_off;              // [N + 1] compact splat offsets (with vmask) or null
   const uint32_t* s_start;              // segments of a slot (vjp)
@@ -312,30 +326,30 @@ int device_sm_count();
 
 // pcg.cu
 cudaError_t launch_reduce_partials(const double* partials, int n, double* out, cudaStream_t st);
-cudaError_t launch_pcg_init(long long n59, long long ld, int N, const float* b, const float* M,
-                            const float* D, float* x, float* Minv_out, double* partials,
-                            cudaStream_t st);
-cudaError_t launch_pcg_residual0(int N, long long ld, const float* b, const float* g,
-                                 const float* M, const float* x, float lambda, const float* Minv,
-                                 float* r, float* z, float* p, double* partials, cudaStream_t st);
+// M^-1 of Algorithm 1 is D where given, else 1 / clamp(M) (not stored).
+// residual0: r may be b itself.
+cudaError_t launch_pcg_init(int N, long long ld, const float* b, const float* M, const float* D, float* x,
+                            double* partials, cudaStream_t st);
+cudaError_t launch_pcg_residual0(int N, long long ld, const float* b, const float* g, const float* M, const float* D,
+                                 const float* x, float lambda, float* r, float* z, float* p, double* partials,
+                                 cudaStream_t st);
 cudaError_t launch_pcg_scalars(PcgScalars* sc, const double* partials, int n_partials, int stage,
                                float break_rel2, cudaStream_t st);
-cudaError_t launch_pcg_update(int N, long long ld, const PcgScalars* sc, const float* p,
-                              const float* g, const float* Minv, float* x, float* r, float* z,
-                              double* partials, cudaStream_t st);
+cudaError_t launch_pcg_update(int N, long long ld, const PcgScalars* sc, const float* p, const float* g,
+                              const float* M, const float* D, float* x, float* r, float* z, double* partials,
+                              cudaStream_t st);
 int pcg_blocks(int N);
 // Batched forms: n subsets, grid (pcg_blocks(N), n); vectors at stride vs,
 // partials at stride pcg_blocks(N) (update: 2 * pcg_blocks(N)), scalars sc[b].
-// init: subset b uses D + b * vs when bit b of d_mask is set, else 1 / clamp(M).
+// Subset b uses D + b * vs when bit b of d_mask is set, else 1 / clamp(M).
 cudaError_t launch_pcg_init_batch(int n, int N, long long ld, long long vs, const float* b, const float* M,
-                                  const float* D, unsigned d_mask, float* x, float* Minv, double* partials,
-                                  cudaStream_t st);
+                                  const float* D, unsigned d_mask, float* x, double* partials, cudaStream_t st);
 cudaError_t launch_pcg_residual0_batch(int n, int N, long long ld, long long vs, const float* b, const float* g,
-                                       const float* M, const float* x, float lambda, const float* Minv, float* r,
-                                       float* z, float* p, double* partials, cudaStream_t st);
+                                       const float* M, const float* D, unsigned d_mask, const float* x, float lambda,
+                                       float* r, float* z, float* p, double* partials, cudaStream_t st);
 cudaError_t launch_pcg_update_batch(int n, int N, long long ld, long long vs, const PcgScalars* sc, const float* p,
-                                    const float* g, const float* Minv, float* x, float* r, float* z,
-                                    double* partials, cudaStream_t st);
+                                    const float* g, const float* M, const float* D, unsigned d_mask, float* x,
+                                    float* r, float* z, double* partials, cudaStream_t st);
 // scalars of n subsets; subset b reduces partials + b * pstride (n_partials of them).
 cudaError_t launch_pcg_scalars_batch(int n, PcgScalars* sc, const double* partials, int n_partials, int pstride,
                                      int stage, float break_rel2, cudaStream_t st);

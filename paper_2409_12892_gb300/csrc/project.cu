@@ -386,7 +386,7 @@ __device__ __forceinline__ void tangent_body(
     long long ti = act_off != nullptr ? (long long)act_off[g] : 0;   // compact splat index
     for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
       const long long slot = (long long)v * N + g;
-      if (!slot_active[slot]) continue;
+      if (!use_mask && !slot_active[slot]) continue;   // the mask holds exactly the active views
       const DevCam& cam = cams[v];
       ViewGeo VG;
       view_geo(G, cam, VG);
@@ -412,7 +412,7 @@ __device__ __forceinline__ void tangent_body(
     long long ti = act_off != nullptr ? (long long)act_off[g] : 0;   // compact splat index
     for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
       const long long slot = (long long)v * N + g;
-      if (!slot_active[slot]) continue;
+      if (!use_mask && !slot_active[slot]) continue;   // the mask holds exactly the active views
       const long long yi = act_off != nullptr ? ti++ : slot;
       const DevCam& cam = cams[v];
       const float d0 = mu0 - cam.campos[0], d1 = mu1 - cam.campos[1], d2 = mu2 - cam.campos[2];
@@ -601,6 +601,7 @@ __device__ __forceinline__ void vjp_body(
   }
   if (valid) {
     const int nr = role_rows(role);
+    float lf = 0.f;   // this role's rows of p^T g in float32; the sum over Gaussians in float64
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       if (i < nr) {
@@ -609,12 +610,13 @@ __device__ __forceinline__ void vjp_body(
           const float pk = p[o];
           const float gk = scale * out[i] + lambda * clamp_diag(Mdiag[o]) * pk;
           gout[o] = gk;
-          local += (double)pk * (double)gk;
+          lf = fmaf(pk, gk, lf);
         } else {
           gout[o] = scale * out[i];
         }
       }
     }
+    local += (double)lf;
   }
   __syncthreads();   // s_mub is reused by the next group of Gaussians
 }

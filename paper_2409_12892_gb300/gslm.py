@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
                 ("lambda_min", c_float), ("lambda_max", c_float), ("smooth", c_int32),
                 ("mem_budget", c_size_t), ("group", c_int32), ("profile", c_int32), ("autotune", c_int32),
                 ("batch", c_int32), ("graph", c_int32), ("batch_ctas", c_int32), ("apply_variant", c_int32),
-                ("line_search", c_int32)]
+                ("line_search", c_int32), ("pad", c_int32), ("batch_mem", c_size_t)]
 
 
 class CacheInfo(ctypes.Structure):
@@ -71,7 +71,7 @@ class LMStats(ctypes.Structure):
                 ("accepted", c_int32), ("pcg_iters", c_int32), ("cache_entries", c_int64),
                 ("cache_bytes", c_int64), ("ms_total", c_double), ("ms_phase", c_double * 8),
                 ("n_pairs", c_int32), ("pad", c_int32), ("pair_bytes", c_double), ("cache_segments", c_int64),
-                ("active_splats", c_int64), ("gamma", c_double), ("ls_evals", c_int32), ("pad2", c_int32)]
+                ("active_splats", c_int64), ("gamma", c_double), ("ls_evals", c_int32), ("seq_groups", c_int32)]
 
 
 _lib = None
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gslm_lm_step": (c_int32, [P, P, c_int64, c_int64, P, c_int32, P, P, P, c_int32, P, P, P]),
         "gslm_version": (ctypes.c_char_p, []),
         "gslm_kernel_launches": (c_int64, []),
+        "gslm_memory_usage": (c_int32, [P, c_int32, P]),
         "gslm_autotune_info": (c_int32, [P, P, P]),
         "gslm_apply_JT_noalloc": (c_int32, [P, P, P, P]),
         "gslm_precond_weight_count": (c_int32, []),
@@ -139,7 +140,8 @@ def exported_symbols() -> list:
     return ["gslm_default_options", "gslm_create", "gslm_destroy", "gslm_last_error", "gslm_set_options",
             "gslm_render", "gslm_build_cache", "gslm_cache_stats", "gslm_cache_free", "gslm_apply_J",
             "gslm_apply_JT", "gslm_jacobi_diag", "gslm_pcg_solve", "gslm_pcg_solve_batch", "gslm_combine_accumulate",
-            "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches", "gslm_autotune_info",
+            "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches", "gslm_memory_usage",
+            "gslm_autotune_info",
             "gslm_apply_JT_noalloc", "gslm_precond_weight_count", "gslm_precond_create", "gslm_precond_free",
             "gslm_precond_get", "gslm_precond_set", "gslm_precond_features", "gslm_precond_fit_standardizer",
             "gslm_precond_apply", "gslm_precond_backward", "gslm_precond_unrolled_grad",
@@ -223,7 +225,7 @@ class Context:
 
     def __init__(self, cache_fmt="fp32", n_iters=8, break_rel2=0.01, lambda_min=1e-4, lambda_max=1e4,
                  smooth=False, mem_budget=0, group=32, profile=False, autotune=True, batch=True, graph=True,
-                 batch_ctas=0, apply_variant=0, line_search=8, stream=None):
+                 batch_ctas=0, apply_variant=0, line_search=8, batch_mem=0, stream=None):
         self.lib = load_library()
         opt = Options()
         self.lib.gslm_default_options(ctypes.byref(opt))
@@ -236,6 +238,7 @@ class Context:
         opt.batch, opt.graph, opt.batch_ctas = int(bool(batch)), int(bool(graph)), int(batch_ctas)
         opt.apply_variant = int(apply_variant)
         opt.line_search = int(line_search)
+        opt.batch_mem = int(batch_mem)
         self.opt = opt
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
@@ -268,6 +271,12 @@ class Context:
         ms = (c_float * 6)()
         self._check(self.lib.gslm_autotune_info(self.h, out, ms))
         return {"apply_J": list(out[0:3]), "apply_JT": list(out[3:6]), "ms_J": list(ms[0:3]), "ms_JT": list(ms[3:6])}
+
+    def memory_usage(self, reset_peak=False) -> dict:
+        """Bytes of the library's memory pool: in use, held (in use + kept for reuse), peak in use."""
+        out = (c_int64 * 3)()
+        self._check(self.lib.gslm_memory_usage(self.h, int(bool(reset_peak)), out))
+        return {"used": out[0], "reserved": out[1], "peak": out[2]}
 
     def set_options(self, **kw):
         for k, v in kw.items():

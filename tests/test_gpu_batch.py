@@ -174,3 +174,22 @@ def test_lm_step_with_more_subsets_than_one_batch(lib):
     assert abs(res[True].pcg_iters - res[False].pcg_iters) <= 18
     assert res[True].pcg_iters > 18
     assert abs(res[True].predicted - res[False].predicted) <= 1e-3 * res[False].cost
+
+
+def test_group_above_the_memory_limit_is_solved_subset_by_subset(lib):
+    P, cams, tgt, subsets = _uneven_case()
+    N = P.shape[0]
+    tg = torch.from_numpy(tgt).cuda().view(-1, 3)
+    out = {}
+    for name, kw in (("sequential", dict(batch=False)), ("limited", dict(batch=True, batch_mem=1)),
+                     ("batched", dict(batch=True))):
+        ctx = lib.Context(n_iters=8, break_rel2=1e-6, line_search=0, **kw)
+        _, stats = ctx.lm_step(lib.to_soa(P), N, cams, tg, subsets, 1e-3)
+        out[name] = stats
+        ctx.close()
+    assert out["limited"].seq_groups == 1
+    assert out["batched"].seq_groups == 0 and out["sequential"].seq_groups == 0
+    s0, s1 = out["sequential"], out["limited"]
+    assert abs(s0.pcg_iters - s1.pcg_iters) <= len(subsets)
+    assert abs(s0.cost - s1.cost) <= 1e-6 * s0.cost
+    assert abs(s0.predicted - s1.predicted) <= 1e-3 * s0.cost

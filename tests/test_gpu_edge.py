@@ -127,4 +127,15 @@ def test_invalid_arguments_are_rejected(lib):
     # a valid call after the rejected ones still works
     cache = ctx.build_cache(params, P.shape[0], cams, tg)
     assert cache.info().views == 1
+    # vectors of the PCG solve must start on a 16-byte boundary (the kernels move float4s)
+    ld = params.shape[1]
+    shifted = torch.zeros(N_PARAMS * ld + 1, device="cuda")[1:]
+    diag = ctx.jacobi_diag(cache)
+    x = torch.zeros_like(diag)
+    P_ = lambda t: ctypes.c_void_p(t.data_ptr())
+    assert L.gslm_pcg_solve(ctx.h, ctypes.c_void_p(cache.handle), P_(shifted), P_(diag), None, ctypes.c_float(1e-3),
+                            P_(x), None) == -1
+    assert b"16-byte" in L.gslm_last_error(ctx.h)
+    assert L.gslm_pcg_solve(ctx.h, ctypes.c_void_p(cache.handle), P_(cache.b), P_(diag), None, ctypes.c_float(1e-3),
+                            P_(x), None) == 0
     cache.free()
