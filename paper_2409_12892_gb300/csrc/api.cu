@@ -422,7 +422,7 @@ gslm_status do_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, floa
   ctx->timer.end(t);
   t = ctx->timer.begin(PH_VJP);
   CK(launch_vjp(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
-                c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), c->vmask.as<unsigned long long>(),
+                c->slot_seg_end.as<uint32_t>(), c->vmask.as<unsigned long long>(), c->act_off.as<uint32_t>(),
                 ctx->seg_ybar.as<float>(), scale, g,
                 p, M, lambda, partials, sc, st));
   ctx->timer.end(t);
@@ -1052,29 +1052,6 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
     return fail(ctx, GSLM_E_NUMERIC, msg);
   }
   CK(cudaMemcpyAsync(c->seg_entry_off.as<unsigned long long>() + nseg, &E, sizeof(E), cudaMemcpyHostToDevice, st));
-  // segments ordered by splat (the paper's sortCacheByGaussians, on segments)
-  {
-    Buf ka, va, kb, vb, tmp;
-    CK(ka.alloc(sizeof(uint32_t) * ns, st));
-    CK(va.alloc(sizeof(uint32_t) * ns, st));
-    CK(kb.alloc(sizeof(uint32_t) * ns, st));
-    CK(vb.alloc(sizeof(uint32_t) * ns, st));
-    CK(tmp.alloc(radix_temp_bytes(ns), st));
-    CK(cudaMemcpyAsync(ka.p, c->seg_slot.p, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
-    CK(launch_iota_u32(va.as<uint32_t>(), nseg, st));
-    uint32_t *sk = nullptr, *sv = nullptr;
-    CK(radix_sort_pairs(ka.as<uint32_t>(), va.as<uint32_t>(), kb.as<uint32_t>(), vb.as<uint32_t>(), nseg,
-                        bits_for((unsigned long long)S), tmp.p, &sk, &sv, st));
-    CK(c->slot_seg_start.alloc(sizeof(uint32_t) * std::max<long long>(S, 1), st));
-    CK(c->slot_seg_end.alloc(sizeof(uint32_t) * std::max<long long>(S, 1), st));
-    CK(cudaMemsetAsync(c->slot_seg_start.p, 0, sizeof(uint32_t) * std::max<long long>(S, 1), st));
-    CK(cudaMemsetAsync(c->slot_seg_end.p, 0, sizeof(uint32_t) * std::max<long long>(S, 1), st));
-    CK(launch_ranges(sk, nseg, c->slot_seg_start.as<uint32_t>(), c->slot_seg_end.as<uint32_t>(), st));
-    CK(c->slot_seg_list.alloc(sizeof(uint32_t) * ns, st));
-    CK(cudaMemcpyAsync(c->slot_seg_list.p, sv, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
-    CK(c->seg_pos.alloc(sizeof(uint32_t) * ns, st));
-    CK(launch_scatter_index_u32(sv, nseg, c->seg_pos.as<uint32_t>(), st));
-  }
   if (V <= 64) {
     CK(c->vmask.alloc(sizeof(unsigned long long) * (size_t)N, st));
     CK(launch_view_mask(c->slot_active.as<uint8_t>(), (int)N, V, c->vmask.as<unsigned long long>(), st));
@@ -1089,13 +1066,43 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
     c->n_active = (long long)na;
   }
   if (c->vmask.p != nullptr) c->slot_active.release();   // the view masks replace the per-slot flags
-  // compact splat indices: act_off from the view masks, SegRec.slot rewritten
-  if (c->vmask.p != nullptr) {
-    CK(c->act_off.alloc(sizeof(uint32_t) * ((size_t)N + 1), st));
-    Buf tmp;
-    CK(tmp.alloc(sizeof(uint32_t) * ((size_t)N + 1) + 64 + scan_temp_bytes((long long)N + 1), st));
-    CK(launch_compact_splats(c->vmask.as<unsigned long long>(), (int)N, c->act_off.as<uint32_t>(), tmp.p,
-                             c->seg_slot.as<uint32_t>(), c->n_seg, c->seg_rec.as<SegRec>(), st));
+  // Segments ordered by splat (the paper's sortCacheByGaussians, on segments).
+  // With the view masks the splat key is the compact splat index (act_off from
+  // the masks; SegRec.slot rewritten to it): Gaussian-major, so a Gaussian's
+  // segments of all its views are one contiguous run. Else the slot v * N + g.
+  {
+    Buf ka, va, kb, vb, tmp;
+    CK(ka.alloc(sizeof(uint32_t) * ns, st));
+    CK(va.alloc(sizeof(uint32_t) * ns, st));
+    CK(kb.alloc(sizeof(uint32_t) * ns, st));
+    CK(vb.alloc(sizeof(uint32_t) * ns, st));
+    long long n_keys = S;
+    if (c->vmask.p != nullptr) {
+      CK(c->act_off.alloc(sizeof(uint32_t) * ((size_t)N + 1), st));
+      CK(tmp.alloc(sizeof(uint32_t) * ((size_t)N + 1) + 64 + scan_temp_bytes((long long)N + 1), st));
+      CK(launch_compact_splats(c->vmask.as<unsigned long long>(), (int)N, c->act_off.as<uint32_t>(), tmp.p,
+                               c->seg_slot.as<uint32_t>(), c->n_seg, c->seg_rec.as<SegRec>(), ka.as<uint32_t>(),
+                               st));
+      n_keys = c->n_active;
+    } else {
+      CK(cudaMemcpyAsync(ka.p, c->seg_slot.p, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
+    }
+    c->seg_slot.release();   // the segment records hold the splat key
+    CK(tmp.ensure(radix_temp_bytes(ns), st));
+    CK(launch_iota_u32(va.as<uint32_t>(), nseg, st));
+    uint32_t *sk = nullptr, *sv = nullptr;
+    CK(radix_sort_pairs(ka.as<uint32_t>(), va.as<uint32_t>(), kb.as<uint32_t>(), vb.as<uint32_t>(), nseg,
+                        bits_for((unsigned long long)n_keys), tmp.p, &sk, &sv, st));
+    const long long nr = std::max<long long>(n_keys, 1);
+    CK(c->slot_seg_start.alloc(sizeof(uint32_t) * nr, st));
+    CK(c->slot_seg_end.alloc(sizeof(uint32_t) * nr, st));
+    CK(cudaMemsetAsync(c->slot_seg_start.p, 0, sizeof(uint32_t) * nr, st));
+    CK(cudaMemsetAsync(c->slot_seg_end.p, 0, sizeof(uint32_t) * nr, st));
+    CK(launch_ranges(sk, nseg, c->slot_seg_start.as<uint32_t>(), c->slot_seg_end.as<uint32_t>(), st));
+    CK(c->slot_seg_list.alloc(sizeof(uint32_t) * ns, st));
+    CK(cudaMemcpyAsync(c->slot_seg_list.p, sv, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToDevice, st));
+    CK(c->seg_pos.alloc(sizeof(uint32_t) * ns, st));
+    CK(launch_scatter_index_u32(sv, nseg, c->seg_pos.as<uint32_t>(), st));
   }
   // keep the cameras; drop the per-slot splat records (the segment records
   // hold what the kernels need) and the binning buffers
@@ -1151,7 +1158,7 @@ gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* c, float* diag) {
   CK(ctx->seg_q.ensure(sizeof(float) * 40 * std::max<long long>(c->n_seg, 1), st));
   CK(launch_diag_entries(c->view(), ctx->seg_q.as<float>(), st));
   CK(launch_diag(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
-                 c->slot_seg_end.as<uint32_t>(), c->slot_seg_list.as<uint32_t>(), c->vmask.as<unsigned long long>(),
+                 c->slot_seg_end.as<uint32_t>(), c->vmask.as<unsigned long long>(), c->act_off.as<uint32_t>(),
                  ctx->seg_q.as<float>(), diag, st));
   return GSLM_OK;
 }

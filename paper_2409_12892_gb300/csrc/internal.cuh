@@ -145,11 +145,11 @@ struct CacheView {
   const void* payload;             // [E] float4 (FP32) or 4 x 16-bit
   const float* seg_scale;          // [n_seg] (FP16S only)
   const uint8_t* pixoff;           // [E] pixel index inside the tile (row-major 16 x 16)
-  const uint32_t* slot_seg_start;  // [n_slots] segments of a slot, as a range of slot_seg_list
-  const uint32_t* slot_seg_end;
-  const uint32_t* slot_seg_list;   // [n_seg] segment ids ordered by slot
+  const uint32_t* slot_seg_start;  // segments of a splat, as a range of slot_seg_list; indexed by the
+  const uint32_t* slot_seg_end;    // compact splat index [n_active] with vmask, else by slot [n_slots]
+  const uint32_t* slot_seg_list;   // [n_seg] segment ids in splat order (compact index or slot; stable)
   const uint32_t* seg_pos;         // [n_seg] position of a segment in slot_seg_list: per-segment
-                                   // adjoints and diagonal blocks are stored in this (slot) order
+                                   // adjoints and diagonal blocks are stored in this (splat) order
   const uint8_t* slot_active;      // [n_slots] (null when vmask is set)
   const unsigned long long* vmask; // [N] active views per Gaussian (null when V > 64)
   const uint32_t* act_off;         // [N + 1] with vmask: first compact splat index of each Gaussian; the
@@ -179,7 +179,7 @@ struct SubsetRefs {
   const uint8_t* slot_active;           // [N * V] (null when vmask is set)
   const unsigned long long* vmask;      // [N] or null
   const uint32_t* act_off;              // [N + 1] compact splat offsets (with vmask) or null
-  const uint32_t* s_start;              // segments of a slot (vjp)
+  const uint32_t* s_start;              // segments of a splat (vjp), keyed as CacheView.slot_seg_start
   const uint32_t* s_end;
   const uint32_t* s_list;
   float* ydot;                          // [N * V][12] splat tangents
@@ -244,17 +244,22 @@ cudaError_t launch_tangent(const float* params, int N, long long ld, const DevCa
                            int smooth, const uint8_t* slot_active, const unsigned long long* vmask,
                            const uint32_t* act_off, const float* p, float* ydot, const float* z_beta,
                            float* p_out, const PcgScalars* sc, cudaStream_t st);
-// act_off[0..N] from the view masks, and SegRec.slot rewritten to the compact splat index.
+// act_off[0..N] from the view masks, SegRec.slot rewritten to the compact
+// splat index, and that index per segment in key[n_seg] (the sort key of the
+// splat order).
 cudaError_t launch_compact_splats(const unsigned long long* vmask, int N, uint32_t* act_off, void* scan_temp,
-                                  const uint32_t* seg_slot, long long n_seg, SegRec* seg_rec, cudaStream_t st);
+                                  const uint32_t* seg_slot, long long n_seg, SegRec* seg_rec, uint32_t* key,
+                                  cudaStream_t st);
+// s_start/s_end: segment positions of a splat, keyed by compact splat index
+// when vmask (and act_off) are given, else by slot v * N + g.
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V,
-                       int smooth, const uint32_t* slot_seg_start, const uint32_t* slot_seg_end,
-                       const uint32_t* slot_seg_list, const unsigned long long* vmask,
+                       int smooth, const uint32_t* s_start, const uint32_t* s_end,
+                       const unsigned long long* vmask, const uint32_t* act_off,
                        const float* seg_ybar, float scale, float* g, const float* p, const float* M,
                        float lambda, double* dot_partials, const PcgScalars* sc, cudaStream_t st);
 cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V,
-                        int smooth, const uint32_t* slot_seg_start, const uint32_t* slot_seg_end,
-                        const uint32_t* slot_seg_list, const unsigned long long* vmask,
+                        int smooth, const uint32_t* s_start, const uint32_t* s_end,
+                        const unsigned long long* vmask, const uint32_t* act_off,
                         const float* seg_q, float* diag, cudaStream_t st);
 int vjp_blocks(int N);
 // Batched forms: blockIdx.y = subset; p, z, pout, g, M stacked with stride vs;

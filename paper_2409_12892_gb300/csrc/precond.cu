@@ -47,7 +47,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __global__ void k_features(const float* __restrict__ P, int N, long long ld, const float* __restrict__ M, int V,
                            const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
                            const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ seg_off,
-                           float* __restrict__ phi) {
+                           const uint32_t* __restrict__ act_off, float* __restrict__ phi) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   float* f = phi + (size_t)g * kIn;
@@ -57,11 +57,21 @@ __global__ void k_features(const float* __restrict__ P, int N, long long ld, con
   f[61] = P[5 * ld + g];
   f[62] = sigmoid(P[10 * ld + g]);
   unsigned long long entries = 0;
-  for (int v = 0; v < V; ++v) {
-    const long long slot = (long long)v * N + g;
-    for (uint32_t j = s_start[slot]; j < s_end[slot]; ++j) {
-      const uint32_t s = s_list[j];
-      entries += seg_off[s + 1] - seg_off[s];
+  if (act_off != nullptr) {
+    // splats keyed by compact index: the Gaussian's segments are one run
+    const uint32_t c0 = act_off[g], c1 = act_off[g + 1];
+    if (c1 > c0)
+      for (uint32_t j = s_start[c0]; j < s_end[c1 - 1]; ++j) {
+        const uint32_t s = s_list[j];
+        entries += seg_off[s + 1] - seg_off[s];
+      }
+  } else {
+    for (int v = 0; v < V; ++v) {
+      const long long slot = (long long)v * N + g;
+      for (uint32_t j = s_start[slot]; j < s_end[slot]; ++j) {
+        const uint32_t s = s_list[j];
+        entries += seg_off[s + 1] - seg_off[s];
+      }
     }
   }
   f[63] = log1pf((float)entries);
@@ -475,7 +485,9 @@ gslm_status features(gslm_ctx* ctx, const gslm_cache* cache, const float* diag, 
   if (cp.N <= 0) return GSLM_OK;
   LAUNCH((k_features<<<(cp.N + 255) / 256, 256, 0, st>>>(cp.params, cp.N, cp.ld, diag, cp.V, cp.view.slot_seg_start,
                                                           cp.view.slot_seg_end, cp.view.slot_seg_list,
-                                                          cp.view.seg_entry_off, phi)));
+                                                          cp.view.seg_entry_off,
+                                                          cp.view.vmask != nullptr ? cp.view.act_off : nullptr,
+                                                          phi)));
   PCK(cudaGetLastError());
   return GSLM_OK;
 }

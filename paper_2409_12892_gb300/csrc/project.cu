@@ -437,8 +437,11 @@ __device__ __forceinline__ void tangent_body(
 }
 
 // g = scale * (dy/dx)^T ybar summed over the views; ybar of a slot is the sum
-// of its segments' partial sums, which the tile kernel stores in slot order:
-// the slot's range [s_start, s_end) of positions (s_list is not read here).
+// of its segments' partial sums, which the tile kernel stores in splat order:
+// the splat's range [s_start, s_end) of positions. A splat is keyed by its
+// compact index act_off[g] + (rank of the view among g's active views) when
+// the view masks exist, so that a Gaussian's segments of all its views form
+// one contiguous run; else by its slot v * N + g.
 // Epilogue (M != null): g += lambda M p and a per-block float64 partial of
 // p^T g. Roles as for the tangent; the colour warps hand their view-direction
 // terms of the mean gradient to the geometry warp through shared memory.
@@ -446,14 +449,15 @@ __device__ __forceinline__ void tangent_body(
 __device__ __forceinline__ void vjp_body(
     int g0, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const unsigned long long* __restrict__ vmask, const float* __restrict__ seg_ybar, float scale,
-    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
-    float (*s_mub)[kGPB][3], double& local) {
+    const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
+    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
+    const float* __restrict__ Mdiag, float lambda, float (*s_mub)[kGPB][3], double& local) {
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
   const int g = g0 + lane;
   const bool valid = g < N;
   const bool use_mask = vmask != nullptr;
   unsigned long long mm = (use_mask && valid) ? vmask[g] : 0ull;
+  long long key = (use_mask && valid) ? (long long)act_off[g] : 0;   // compact splat index
   float mub[3] = {0.f, 0.f, 0.f};
   float out[16];
 #pragma unroll
@@ -464,8 +468,8 @@ __device__ __forceinline__ void vjp_body(
     bool any = false;
     GaussGeo G;
     for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
-      const long long slot = (long long)v * N + g;
-      const uint32_t a = s_start[slot], b = s_end[slot];
+      const long long sk = use_mask ? key++ : (long long)v * N + g;
+      const uint32_t a = s_start[sk], b = s_end[sk];
       if (a == b) continue;
       if (!any) {
         gauss_geo(P, ld, g, G);
@@ -563,8 +567,8 @@ __device__ __forceinline__ void vjp_body(
       mu2 = P[2 * ld + g];
     }
     for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
-      const long long slot = (long long)v * N + g;
-      const uint32_t a = s_start[slot], b = s_end[slot];
+      const long long sk = use_mask ? key++ : (long long)v * N + g;
+      const uint32_t a = s_start[sk], b = s_end[sk];
       if (a == b) continue;
       float yc = 0.f;
       for (uint32_t j = a; j < b; ++j) yc += seg_ybar[(size_t)j * 12 + 6 + ch];
@@ -661,15 +665,16 @@ constexpr int kVjpBlocks = 2432;
 __device__ __forceinline__ void vjp_blocks_loop(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const unsigned long long* __restrict__ vmask, const float* __restrict__ seg_ybar, float scale,
-    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
-    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
+    const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
+    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
+    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
+    const PcgScalars* __restrict__ sc) {
   __shared__ float s_mub[4][kGPB][3];
   double local = 0.0;
   if (sc == nullptr || !sc->done) {
     for (int g0 = blockIdx.x * kGPB; g0 < N; g0 += gridDim.x * kGPB)
-      vjp_body(g0, P, N, ld, cams, V, smooth, s_start, s_end, vmask, seg_ybar, scale, gout, p, Mdiag, lambda, s_mub,
-               local);
+      vjp_body(g0, P, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar, scale, gout, p, Mdiag,
+               lambda, s_mub, local);
   }
   if (partials != nullptr) write_dot_partial(local, partials);
 }
@@ -677,11 +682,12 @@ __device__ __forceinline__ void vjp_blocks_loop(
 __global__ void __launch_bounds__(128, 4) k_vjp(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const unsigned long long* __restrict__ vmask, const float* __restrict__ seg_ybar, float scale,
-    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
-    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
-  vjp_blocks_loop(P, N, ld, cams, V, smooth, s_start, s_end, vmask, seg_ybar, scale, gout, p, Mdiag, lambda, partials,
-                  sc);
+    const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
+    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
+    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
+    const PcgScalars* __restrict__ sc) {
+  vjp_blocks_loop(P, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar, scale, gout, p, Mdiag, lambda,
+                  partials, sc);
 }
 
 // Batched: blockIdx.y is the subset; g, p and M at offset blockIdx.y * vs, the
@@ -694,7 +700,7 @@ __global__ void __launch_bounds__(128, 4) k_vjp_batch(const float* __restrict__ 
   const int b = blockIdx.y;
   const SubsetRefs& s = gb.s[b];
   const long long off = (long long)b * vs;
-  vjp_blocks_loop(P, N, ld, s.cams, s.V, smooth, s.s_start, s.s_end, s.vmask, s.seg_ybar, 1.f, gout + off,
+  vjp_blocks_loop(P, N, ld, s.cams, s.V, smooth, s.s_start, s.s_end, s.vmask, s.act_off, s.seg_ybar, 1.f, gout + off,
                   p != nullptr ? p + off : nullptr, Mdiag != nullptr ? Mdiag + off : nullptr, lambda,
                   partials != nullptr ? partials + (size_t)b * gridDim.x : nullptr, sc != nullptr ? sc + b : nullptr);
 }
@@ -705,7 +711,7 @@ __global__ void __launch_bounds__(128, 4) k_vjp_batch(const float* __restrict__ 
 __global__ void __launch_bounds__(128) k_diag(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
-    const uint32_t* __restrict__ s_list, const unsigned long long* __restrict__ vmask,
+    const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
     const float* __restrict__ seg_q, float* __restrict__ dout) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
@@ -716,9 +722,10 @@ __global__ void __launch_bounds__(128) k_diag(
   GaussGeo G;
   const bool use_mask = vmask != nullptr;
   unsigned long long mm = use_mask ? vmask[g] : 0ull;
+  long long key = use_mask ? (long long)act_off[g] : 0;   // splat key as in vjp_body
   for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
-    const long long slot = (long long)v * N + g;
-    const uint32_t a = s_start[slot], b = s_end[slot];
+    const long long sk = use_mask ? key++ : (long long)v * N + g;
+    const uint32_t a = s_start[sk], b = s_end[sk];
     if (a == b) continue;
     if (!any) {
       gauss_geo(P, ld, g, G);
@@ -728,7 +735,7 @@ __global__ void __launch_bounds__(128) k_diag(
 #pragma unroll
     for (int i = 0; i < 40; ++i) Q[i] = 0.f;
     for (uint32_t j = a; j < b; ++j) {
-      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * 40);   // slot order
+      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * 40);   // splat order
 #pragma unroll
       for (int i = 0; i < 10; ++i) {
         const float4 t = q4[i];
@@ -843,18 +850,21 @@ __global__ void k_active_count(const unsigned long long* __restrict__ vmask, int
 
 __global__ void k_seg_compact_slot(const unsigned long long* __restrict__ vmask, int N,
                                    const uint32_t* __restrict__ act_off, const uint32_t* __restrict__ seg_slot,
-                                   long long n_seg, SegRec* __restrict__ seg_rec) {
+                                   long long n_seg, SegRec* __restrict__ seg_rec, uint32_t* __restrict__ key) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_seg) return;
   const uint32_t slot = seg_slot[s];
   const int v = (int)(slot / (uint32_t)N);
   const int g = (int)(slot - (uint32_t)v * (uint32_t)N);
   const unsigned long long below = v > 0 ? (vmask[g] & ((1ull << v) - 1ull)) : 0ull;
-  seg_rec[s].slot = act_off[g] + (uint32_t)__popcll(below);
+  const uint32_t c = act_off[g] + (uint32_t)__popcll(below);
+  seg_rec[s].slot = c;
+  key[s] = c;
 }
 
 cudaError_t launch_compact_splats(const unsigned long long* vmask, int N, uint32_t* act_off, void* scan_temp,
-                                  const uint32_t* seg_slot, long long n_seg, SegRec* seg_rec, cudaStream_t st) {
+                                  const uint32_t* seg_slot, long long n_seg, SegRec* seg_rec, uint32_t* key,
+                                  cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   // counts in act_off[0..N), then an in-place-safe scan into act_off via a second buffer
   uint32_t* cnt = reinterpret_cast<uint32_t*>(scan_temp);
@@ -862,9 +872,10 @@ cudaError_t launch_compact_splats(const unsigned long long* vmask, int N, uint32
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   void* tmp = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(cnt + N + 1) + 63) & ~uintptr_t(63));
-  e = exclusive_scan_u32(cnt, act_off, N, tmp, st);
+  e = exclusive_scan_u32(cnt, act_off, N, tmp, st);   // act_off[N] = the total
   if (e != cudaSuccess || n_seg <= 0) return e;
-  { k_seg_compact_slot<<<(unsigned)((n_seg + 255) / 256), 256, 0, st>>>(vmask, N, act_off, seg_slot, n_seg, seg_rec);
+  { k_seg_compact_slot<<<(unsigned)((n_seg + 255) / 256), 256, 0, st>>>(vmask, N, act_off, seg_slot, n_seg, seg_rec,
+                                                                       key);
     note_launch(); }
   return cudaGetLastError();
 }
@@ -890,22 +901,20 @@ cudaError_t launch_vjp_batch(const float* params, int N, long long ld, int smoot
 }
 
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
-                       const uint32_t* s_start, const uint32_t* s_end, const uint32_t* s_list,
-                       const unsigned long long* vmask, const float* seg_ybar, float scale, float* g,
-                       const float* p, const float* M, float lambda, double* partials, const PcgScalars* sc,
-                       cudaStream_t st) {
+                       const uint32_t* s_start, const uint32_t* s_end, const unsigned long long* vmask,
+                       const uint32_t* act_off, const float* seg_ybar, float scale, float* g, const float* p,
+                       const float* M, float lambda, double* partials, const PcgScalars* sc, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  (void)s_list;   // segment adjoints are stored in slot order
-  { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, vmask, seg_ybar, scale, g,
-                                       p, M, lambda, partials, sc); note_launch(); }
+  { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar,
+                                       scale, g, p, M, lambda, partials, sc); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
-                        const uint32_t* s_start, const uint32_t* s_end, const uint32_t* s_list,
-                        const unsigned long long* vmask, const float* seg_q, float* diag, cudaStream_t st) {
+                        const uint32_t* s_start, const uint32_t* s_end, const unsigned long long* vmask,
+                        const uint32_t* act_off, const float* seg_q, float* diag, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_diag<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, s_list, vmask, seg_q,
+  { k_diag<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_q,
                                             diag); note_launch(); }
   return cudaGetLastError();
 }
