@@ -140,15 +140,21 @@ def _record_rows(vl: ViewLin, lo: int, hi: int) -> np.ndarray:
     return np.einsum("rcj,rjk->rck", vl.a[lo:hi], vl.proj.jac[vl.ras.rec_splat[lo:hi]])
 
 
-def jacobi_diag(lin: list, n_gauss: int, chunk: int = 50000) -> np.ndarray:
-    """M = diag(J^T J) (Eq. diag-jtj): sum of squared full partials. Returns (N, 59)."""
+def jacobi_diag(lin: list, n_gauss: int, chunk: int = 50000, weights: np.ndarray | None = None) -> np.ndarray:
+    """M = diag(J^T J) (Eq. diag-jtj): sum of squared full partials. Returns (N, 59).
+    weights (flat, residual order): per pixel channel factors (dr/dc)^2 of a
+    non-L2 residual (Eq. res-sq-root-weights-sum); None means 1."""
     d = np.zeros((n_gauss, 59))
     for vl in lin:
         R = vl.a.shape[0]
         for lo in range(0, R, chunk):
             hi = min(R, lo + chunk)
             rows = _record_rows(vl, lo, hi)
-            np.add.at(d, vl.gauss[lo:hi], (rows * rows).sum(axis=1))
+            sq = rows * rows
+            if weights is not None:
+                res = vl.pix_off + vl.ras.rec_pix[lo:hi, None] * 3 + np.arange(3)[None, :]
+                sq = sq * weights[res][:, :, None]
+            np.add.at(d, vl.gauss[lo:hi], sq.sum(axis=1))
     return d
 
 

@@ -29,6 +29,7 @@ import math
 import numpy as np
 
 from . import jacobian as jac
+from . import residual as res
 
 
 @dataclass
@@ -105,28 +106,50 @@ def combine(deltas: list, diags: list) -> np.ndarray:
 class SubsetSystem:
     cams: list
     lin: list
-    F: np.ndarray
+    F: np.ndarray        # L2: c - C; L1 + SSIM: e = (dr/dc) r summed over both residuals
     cost: float
     b: np.ndarray
     M: np.ndarray
+    W: np.ndarray | None = None   # L1 + SSIM: (dr1/dc)^2 + (dr2/dc)^2 per pixel channel; None for L2
 
 
-def build_subset(params: np.ndarray, cams: list, targets_flat: np.ndarray, smooth=False) -> SubsetSystem:
-    """buildCache + diagJTJ of Algorithm 1: F, b = -J^T F and M = diag(J^T J) for one subset."""
+def objective_cost(img_flat: np.ndarray, tgt_flat: np.ndarray, cams: list, objective=None) -> float:
+    """E at a rendered image: ||c - C||^2 (L2) or Eq. gn-loss (objective given)."""
+    if objective is None:
+        F = jac.residual(img_flat, tgt_flat)
+        return jac.cost(F)
+    return res.cost(img_flat, tgt_flat, cams, objective)
+
+
+def build_subset(params: np.ndarray, cams: list, targets_flat: np.ndarray, smooth=False,
+                 objective=None) -> SubsetSystem:
+    """buildCache + diagJTJ of Algorithm 1: F, b = -J^T F and M = diag(J^T J) for one subset.
+    objective: None for the sum-of-squares residual c - C, or a residual.Objective
+    (L1 + SSIM, Eq. gn-loss), whose weights enter through (dr/dc) (Sec. C)."""
     lin = jac.linearise(params, cams, smooth)
     img = np.concatenate([vl.ras.image.ravel() for vl in lin])
-    F = jac.residual(img, targets_flat)
     N = params.shape[0]
-    b = -jac.apply_JT(lin, F, N)
-    M = jac.jacobi_diag(lin, N)
-    return SubsetSystem(cams, lin, F, jac.cost(F), b, M)
+    if objective is None:
+        F = jac.residual(img, targets_flat)
+        return SubsetSystem(cams, lin, F, jac.cost(F), -jac.apply_JT(lin, F, N), jac.jacobi_diag(lin, N))
+    wt = res.weights(img, targets_flat, cams, objective)
+    b = -jac.apply_JT(lin, wt.e, N)                      # J^T F = (dc/dx)^T e
+    M = jac.jacobi_diag(lin, N, weights=wt.w)
+    return SubsetSystem(cams, lin, wt.e, wt.cost, b, M, wt.w)
+
+
+def apply_JTJ(sys_: SubsetSystem, v: np.ndarray) -> np.ndarray:
+    """J^T J v: (dc/dx)^T ((dc/dx) v), weighted by W between the two products when
+    the residual is not L2 (Eq. apply-jtj-simplified-vec-vec)."""
+    N = sys_.b.shape[0]
+    u = jac.apply_J(sys_.lin, v, sys_.F.shape[0])
+    if sys_.W is not None:
+        u = sys_.W * u
+    return jac.apply_JT(sys_.lin, u, N)
 
 
 def solve_subset(sys_: SubsetSystem, lam: float, n_iters: int, break_rel2: float = 0.0, Minv=None):
-    N = sys_.b.shape[0]
-    n_res = sys_.F.shape[0]
-    A = lambda v: jac.apply_JT(sys_.lin, jac.apply_J(sys_.lin, v, n_res), N)
-    return pcg(A, sys_.b, sys_.M, lam, n_iters, break_rel2, Minv)
+    return pcg(lambda v: apply_JTJ(sys_, v), sys_.b, sys_.M, lam, n_iters, break_rel2, Minv)
 
 
 @dataclass
@@ -158,7 +181,7 @@ def line_search_views(subsets: list, frac: float) -> list:
 
 
 def line_search(params: np.ndarray, delta: np.ndarray, subsets: list, targets: list, steps: int, frac: float,
-                smooth=False):
+                smooth=False, objective=None):
     """Eq. line-search, min over gamma of E(x + gamma Delta), read as: evaluate the
     sum-of-squares cost on the line-search views at gamma = 1, 1/2, 1/4, ... (at
     most `steps` values), stop at the first value larger than the previous finite
@@ -173,8 +196,7 @@ def line_search(params: np.ndarray, delta: np.ndarray, subsets: list, targets: l
             if nv == 0:
                 continue
             npx = sum(c.width * c.height * 3 for c in cams[:nv])
-            F = jac.render(x, cams[:nv], smooth) - tg[:npx]
-            e += float(np.dot(F, F))
+            e += objective_cost(jac.render(x, cams[:nv], smooth), tg[:npx], cams[:nv], objective)
         costs.append(e)
         if e < best_e:
             best_g, best_e = g, e
@@ -186,15 +208,16 @@ def line_search(params: np.ndarray, delta: np.ndarray, subsets: list, targets: l
 
 def lm_step(params: np.ndarray, subsets: list, targets: list, lam: float, n_iters: int = 8,
             lambda_min: float = 1e-4, lambda_max: float = 1e4, break_rel2: float = 0.0,
-            smooth=False, precond=None, ls_steps: int = 0, ls_frac: float = 0.3) -> LMResult:
+            smooth=False, precond=None, ls_steps: int = 0, ls_frac: float = 0.3, objective=None) -> LMResult:
     """One LM iteration over image subsets (Sec. 3.2 and Eq. combine-pcg).
 
     subsets: list of camera lists; targets: list of flat target vectors (one per subset).
     precond: optional callable (SubsetSystem) -> D replacing M^-1 in Algorithm 1.
     ls_steps > 0: the step is scaled by the line search of Eq. line-search (see
     line_search); rho (Eq. tr-update) then uses gamma Delta.
+    objective: None (sum of squares) or a residual.Objective (L1 + SSIM).
     """
-    systems = [build_subset(params, cams, tg, smooth) for cams, tg in zip(subsets, targets)]
+    systems = [build_subset(params, cams, tg, smooth, objective) for cams, tg in zip(subsets, targets)]
     deltas, stats = [], []
     for s in systems:
         Minv = precond(s) if precond is not None else None
@@ -205,16 +228,19 @@ def lm_step(params: np.ndarray, subsets: list, targets: list, lam: float, n_iter
     cost0 = sum(s.cost for s in systems)
     gamma, ls_costs = 1.0, None
     if ls_steps > 0:
-        gamma, ls_costs = line_search(params, delta, subsets, targets, ls_steps, ls_frac, smooth)
+        gamma, ls_costs = line_search(params, delta, subsets, targets, ls_steps, ls_frac, smooth, objective)
     pred = 0.0
     for s in systems:
-        u = gamma * jac.apply_J(s.lin, delta, s.F.shape[0]) + s.F
-        pred += float(np.dot(u, u))
+        u = jac.apply_J(s.lin, delta, s.F.shape[0])
+        if s.W is None:
+            v = gamma * u + s.F
+            pred += float(np.dot(v, v))
+        else:   # the Gauss-Newton model E + 2 gamma e.u + gamma^2 W.u^2
+            pred += s.cost + 2.0 * gamma * float(np.dot(s.F, u)) + gamma * gamma * float(np.dot(s.W, u * u))
     new = params + gamma * delta
     cost1 = 0.0
     for cams, tg in zip(subsets, targets):
-        F1 = jac.render(new, cams, smooth) - tg
-        cost1 += float(np.dot(F1, F1))
+        cost1 += objective_cost(jac.render(new, cams, smooth), tg, cams, objective)
     den = cost0 - pred
     rho = (cost0 - cost1) / den if den > 0 else -np.inf
     accepted = bool(den > 0 and rho > 1e-5)
