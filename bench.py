@@ -67,6 +67,8 @@ def parse_args(argv=None):
     ap.add_argument("--equal-cap", type=int, default=1000, help="PCG iteration cap of the equal-residual step")
     ap.add_argument("--equal-lambda", type=float, default=1.0,
                     help="LM damping of the equal-residual step (both forms)")
+    ap.add_argument("--objective", choices=["l2", "l1ssim"], default="l2",
+                    help="energy of the LM step: sum of squares (the timed configuration) or Eq. gn-loss")
     ap.add_argument("--line-search", type=int, default=0,
                     help="line-search candidates of the timed LM steps (0: gamma = 1, the workload's setting)")
     ap.add_argument("--equal-line-search", type=int, default=8,
@@ -420,7 +422,7 @@ def workload_config(args, form: str) -> dict:
                         else "+".join(str(v) for v in wl.subset_sizes))
                      + " views per LM step"),
         "form": form, "pcg_iters": wl.pcg_iters, "break_rel2": 0.01, "lambda0": wl.lambda0,
-        "line_search": args.line_search,
+        "line_search": args.line_search, "objective": args.objective,
         "l2_flush": "inputs larger than L2: the gradient caches of a step are tens of GB",
         "parallelism": f"{args.gpus} independent replicas" if args.gpus > 1 else "single GPU",
     }
@@ -585,7 +587,7 @@ def run_ours(args):
         chosen = form == "chosen"
         ctx = g.Context(cache_fmt=fmt, n_iters=wl.pcg_iters, break_rel2=0.01, lambda_min=wl.lambda_min,
                         lambda_max=wl.lambda_max, profile=not chosen, group=args.group, batch=chosen, graph=chosen,
-                        line_search=args.line_search)
+                        line_search=args.line_search, objective=args.objective)
         params = g.to_soa(P, device=dev, ld=ld)
         pc, train, judge = None, None, None
         if chosen and args.precond == "learned":

@@ -69,6 +69,19 @@ typedef enum {
 
 typedef enum { GSLM_CACHE_FP32 = 0, GSLM_CACHE_BF16 = 1, GSLM_CACHE_FP16S = 2 } gslm_cache_fmt;
 
+/* The energy the LM step minimises.
+ * GSLM_OBJ_L2: residual c - C per pixel channel, E = ||c - C||^2.
+ * GSLM_OBJ_L1_SSIM: Eq. gn-loss, two residuals per pixel channel,
+ *   r1 = sqrt(l1 |c - C|), r2 = sqrt(l2 (1 - SSIM)), E = sum of l1 |c - C| + l2 (1 - SSIM);
+ *   SSIM per channel with an 11 x 11 Gaussian window (sd 1.5, zero outside the
+ *   view), C1 = 0.01^2, C2 = 0.03^2; dSSIM/dc keeps only the centre pixel's own
+ *   term (Sec. C). Their Jacobian enters through the per pixel channel weights
+ *   w = (dr1/dc)^2 + (dr2/dc)^2 and e = (dr1/dc) r1 + (dr2/dc) r2 (Sec. C,
+ *   "Precomputation Of Residual-To-Pixel Weights"): J^T J p = (dc/dx)^T (w (dc/dx) p),
+ *   J^T F = (dc/dx)^T e, diag(J^T J) = sum w (dc/dx)^2. Under the square roots of
+ *   the derivatives |c - C| and 1 - SSIM are floored at options.res_eps. */
+typedef enum { GSLM_OBJ_L2 = 0, GSLM_OBJ_L1_SSIM = 1 } gslm_objective;
+
 /* A posed pinhole camera. World point X maps to camera point R X + t (OpenCV
  * axes: x right, y down, z forward) and to pixel (fx x/z + cx, fy y/z + cy).
  * Pixel (px, py) has its centre at (px + 0.5, py + 0.5). */
@@ -104,6 +117,10 @@ typedef struct {
   size_t batch_mem;    /* gslm_lm_step with batch: bytes the stacked PCG vectors of a group of
                           subsets may take (0 = as much as the device gives); a group above it,
                           or whose vectors cannot be allocated, is solved subset by subset */
+  int32_t objective;   /* gslm_objective (default GSLM_OBJ_L2) */
+  float lambda_l1;     /* GSLM_OBJ_L1_SSIM weights (paper: 0.8 and 0.2) */
+  float lambda_ssim;
+  float res_eps;       /* floor under the square roots of the residual derivatives (1e-4) */
 } gslm_options;
 
 typedef struct gslm_ctx gslm_ctx;
@@ -175,24 +192,33 @@ gslm_status gslm_set_options(gslm_ctx* ctx, const gslm_options* opt);
 
 /* Render the V views [Sec. 3.1, Eq. alpha-blending].
  * params: [59][ld]; cams: host array of V cameras; img: [sum W*H][3].
- * If targets is non-NULL, also writes cost[0] = ||img - targets||^2 (cost: host
- * double*, may be NULL). */
+ * If targets is non-NULL, also writes cost[0] = E of options.objective:
+ * ||img - targets||^2 or Eq. gn-loss (cost: host double*, may be NULL). */
 gslm_status gslm_render(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld,
                         const gslm_camera* cams, int32_t V, float* img,
                         const float* targets, double* cost);
 
-/* Build the gradient cache of one image subset [Sec. 3.3, Algorithm 1 lines 1-2].
+/* Build the gradient cache of one image subset [Sec. 3.3; the inputs F and b of Algorithm 1].
  * Writes F = img - targets into F (may be NULL), b = -J^T F into b ([59][ld], may be
- * NULL) and cost ||F||^2 into *cost (host, may be NULL). The cache holds its
+ * NULL) and cost ||F||^2 into *cost (host, may be NULL); with GSLM_OBJ_L1_SSIM,
+ * F is e (see gslm_objective) and cost is Eq. gn-loss. The cache holds its
  * own device copy of params, so the caller may change or free params afterwards.
  * Returns GSLM_E_CACHE_OVERFLOW (and no cache) if options.mem_budget is exceeded. */
 gslm_status gslm_build_cache(gslm_ctx* ctx, const float* params, int64_t N, int64_t ld,
                              const gslm_camera* cams, int32_t V, const float* targets,
                              gslm_cache** cache, float* F, float* b, double* cost);
 gslm_status gslm_cache_stats(const gslm_cache* cache, gslm_cache_info* info);
+/* The cache's residual-to-pixel weights w = (dr/dc)^2 summed over the pixel
+ * channel's residuals, [pixels][3] into w (device): 1 everywhere for
+ * GSLM_OBJ_L2. With GSLM_OBJ_L1_SSIM the cache's F (gslm_build_cache's F
+ * output) is e = sum (dr/dc) r, and cost is Eq. gn-loss. */
+gslm_status gslm_cache_weights(const gslm_cache* cache, float* w);
 void gslm_cache_free(gslm_cache* cache);
 
-/* u = J p [Eq. apply-j]. p: [59][ld]; u: [pixels][3]. */
+/* u = J p [Eq. apply-j]. p: [59][ld]; u: [pixels][3]. With GSLM_OBJ_L1_SSIM
+ * the cache's weights are applied: u = w . ((dc/dx) p), the vector
+ * (u-hat . grad r) of Eq. apply-jtj-simplified-vec-vec that gslm_apply_JT
+ * takes, so that gslm_apply_JT(gslm_apply_J(p)) = J^T J p. */
 gslm_status gslm_apply_J(gslm_ctx* ctx, const gslm_cache* cache, const float* p, float* u);
 /* g = J^T u [Eq. apply-jt]. u: [pixels][3]; g: [59][ld]. */
 gslm_status gslm_apply_JT(gslm_ctx* ctx, const gslm_cache* cache, const float* u, float* g);

@@ -118,6 +118,7 @@ struct gslm_cache {
   std::vector<DevCam> hcams;
   Buf cams, rec, slot_active, tile_seg_off, seg_entry_off, seg_slot, seg_rec, payload, seg_scale, pixoff;
   Buf slot_seg_start, slot_seg_end, slot_seg_list, seg_pos, F, own_params, vmask, act_off;
+  Buf W;   // residual-to-pixel weights [n_pix][3] (L1 + SSIM objective only)
 
   CacheView view() const {
     CacheView cv;
@@ -146,6 +147,7 @@ struct gslm_cache {
     cv.n_entries = n_entries;
     cv.fmt = fmt;
     cv.skip = nullptr;
+    cv.wres = W.as<float>();
     return cv;
   }
   // splat tangents the tangent kernel writes: one per active splat (compact
@@ -155,7 +157,7 @@ struct gslm_cache {
     return cams.bytes + rec.bytes + slot_active.bytes + tile_seg_off.bytes + seg_entry_off.bytes + seg_slot.bytes +
            seg_rec.bytes +
            payload.bytes + seg_scale.bytes + pixoff.bytes + slot_seg_start.bytes + slot_seg_end.bytes +
-           slot_seg_list.bytes + seg_pos.bytes + F.bytes + own_params.bytes + vmask.bytes + act_off.bytes;
+           slot_seg_list.bytes + seg_pos.bytes + F.bytes + own_params.bytes + vmask.bytes + act_off.bytes + W.bytes;
   }
 };
 
@@ -867,6 +869,10 @@ void gslm_default_options(gslm_options* o) {
   o->graph = 1;
   o->batch_ctas = 0;
   o->line_search = 8;
+  o->objective = GSLM_OBJ_L2;
+  o->lambda_l1 = 0.8f;
+  o->lambda_ssim = 0.2f;
+  o->res_eps = 1e-4f;
 }
 
 static gslm_status validate_opts(const gslm_options* o) {
@@ -877,6 +883,10 @@ static gslm_status validate_opts(const gslm_options* o) {
   if (o->batch_ctas < 0 || o->batch_ctas > 6) return GSLM_E_INVALID;
   if (o->apply_variant < 0 || o->apply_variant > 5) return GSLM_E_INVALID;
   if (o->line_search < 0 || o->line_search > 60) return GSLM_E_INVALID;
+  if (o->objective != GSLM_OBJ_L2 && o->objective != GSLM_OBJ_L1_SSIM) return GSLM_E_INVALID;
+  if (!(o->lambda_l1 >= 0.f) || !(o->lambda_ssim >= 0.f) || !(o->res_eps > 0.f) || !std::isfinite(o->lambda_l1) ||
+      !std::isfinite(o->lambda_ssim) || !std::isfinite(o->res_eps))
+    return GSLM_E_INVALID;
   return GSLM_OK;
 }
 
@@ -951,6 +961,9 @@ gslm_status gslm_render(gslm_ctx* ctx, const float* params, int64_t N, int64_t l
   CK(launch_raster_count(B.cams.as<DevCam>(), V, n_tiles, B.tile_start.as<uint32_t>(), B.tile_end.as<uint32_t>(),
                          B.tile_vals, B.rec.as<SplatRec>(), ctx->opt.smooth, targets, img, nullptr,
                          targets != nullptr ? partials.as<double>() : nullptr, nullptr, nullptr, ctx->st));
+  if (targets != nullptr && cost != nullptr && ctx->opt.objective == GSLM_OBJ_L1_SSIM)
+    CK(launch_l1ssim(B.cams.as<DevCam>(), V, n_tiles, img, targets, ctx->opt.lambda_l1, ctx->opt.lambda_ssim,
+                     ctx->opt.res_eps, nullptr, nullptr, partials.as<double>(), ctx->st));
   if (targets != nullptr && cost != nullptr) CKS(reduce_to_host(ctx, partials.as<double>(), n_tiles, cost));
   return GSLM_OK;
 }
@@ -1015,6 +1028,14 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
   CK(cudaMemcpyAsync(&E, tile_entry_off.as<unsigned long long>() + n_tiles, sizeof(E), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&nseg, c->tile_seg_off.as<uint32_t>() + n_tiles, sizeof(nseg), cudaMemcpyDeviceToHost, st));
   CKS(reduce_to_host(ctx, cost_part.as<double>(), n_tiles, &c->cost));
+  if (ctx->opt.objective == GSLM_OBJ_L1_SSIM) {
+    // Eq. gn-loss: F becomes e = sum (dr/dc) r, the weights w = sum (dr/dc)^2 are kept
+    CK(c->W.alloc(sizeof(float) * 3 * std::max<long long>(c->n_pix, 1), st));
+    CK(launch_l1ssim(B.cams.as<DevCam>(), V, n_tiles, img.as<float>(), targets, ctx->opt.lambda_l1,
+                     ctx->opt.lambda_ssim, ctx->opt.res_eps, c->F.as<float>(), c->W.as<float>(),
+                     cost_part.as<double>(), st));
+    CKS(reduce_to_host(ctx, cost_part.as<double>(), n_tiles, &c->cost));
+  }
   c->n_entries = (long long)E;
   c->n_seg = nseg;
   const size_t need = E * (payload_bytes(c->fmt) + 1) + (size_t)nseg * (8 + 4 + 4 + 48 + 4 * (c->fmt == 2)) +
@@ -1140,6 +1161,15 @@ gslm_status gslm_cache_stats(const gslm_cache* c, gslm_cache_info* info) {
   return GSLM_OK;
 }
 
+gslm_status gslm_cache_weights(const gslm_cache* c, float* w) {
+  if (c == nullptr || w == nullptr) return GSLM_E_INVALID;
+  gslm_ctx* ctx = c->ctx;
+  const long long n = 3 * c->n_pix;
+  if (c->W.p != nullptr) CK(cudaMemcpyAsync(w, c->W.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  else CK(launch_fill_f32(n, 1.f, w, ctx->st));
+  return GSLM_OK;
+}
+
 void gslm_cache_free(gslm_cache* c) { delete c; }
 
 gslm_status gslm_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float* u) {
@@ -1155,7 +1185,7 @@ gslm_status gslm_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, fl
 gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* c, float* diag) {
   if (ctx == nullptr || c == nullptr || diag == nullptr) return fail(ctx, GSLM_E_INVALID, "jacobi_diag: null");
   cudaStream_t st = ctx->st;
-  CK(ctx->seg_q.ensure(sizeof(float) * 40 * std::max<long long>(c->n_seg, 1), st));
+  CK(ctx->seg_q.ensure(sizeof(float) * kDiagBlock * std::max<long long>(c->n_seg, 1), st));
   CK(launch_diag_entries(c->view(), ctx->seg_q.as<float>(), st));
   CK(launch_diag(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
                  c->slot_seg_end.as<uint32_t>(), c->vmask.as<unsigned long long>(), c->act_off.as<uint32_t>(),
@@ -1445,22 +1475,22 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   }
   CK(launch_combine_finish((int)N, ld, ctx->lm_num.as<float>(), ctx->lm_den.as<float>(), ctx->lm_delta.as<float>(),
                            st));
-  // predicted decrease at any step scale gamma: sum_i ||gamma J_i Delta + F_i||^2
-  // = cost0 + gamma B + gamma^2 A with A = sum_i ||J_i Delta||^2
+  // predicted cost at any step scale gamma, the Gauss-Newton model
+  // cost0 + gamma B + gamma^2 A with u_i = (dc/dx)_i Delta, B = 2 sum_i e_i.u_i and
+  // A = sum_i w_i.u_i^2 (for L2, e = F and w = 1: sum_i ||gamma u_i + F_i||^2)
   bool trho = ctx->timer.begin(PH_RHO);
-  double pA = 0.0, p1 = 0.0;
+  double pA = 0.0, pB = 0.0;
   for (int i = 0; i < n_b; ++i) {
     gslm_cache* c = caches[i];
     CK(ctx->partials.ensure(sizeof(double) * 2 * std::max(c->n_tiles, 1), st));
     CKS(do_apply_J(ctx, c, ctx->lm_delta.as<float>(), nullptr, nullptr, nullptr, nullptr, c->F.as<float>(),
                    ctx->partials.as<double>()));
-    double a = 0.0, b = 0.0;
-    CKS(reduce_to_host(ctx, ctx->partials.as<double>(), c->n_tiles, &b));
+    double a = 0.0, eu = 0.0;
+    CKS(reduce_to_host(ctx, ctx->partials.as<double>(), c->n_tiles, &eu));
     CKS(reduce_to_host(ctx, ctx->partials.as<double>() + c->n_tiles, c->n_tiles, &a));
-    p1 += b;
+    pB += 2.0 * eu;
     pA += a;
   }
-  const double pB = p1 - pA - cost0;
   // the trial render of params + g Delta over the first nv[i] views of every
   // subset i; +inf when the trial splats exceed the renderer's tile-key capacity
   auto trial_cost = [&](double g, const std::vector<int>& nv, double* out) -> gslm_status {

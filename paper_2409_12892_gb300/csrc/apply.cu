@@ -253,21 +253,29 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
     __syncthreads();
   }
   const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
+  // Epilogue: u = w (dc/dx) p with the residual-to-pixel weights (1 without
+  // them); for the predicted decrease, per-tile sums of e.u (Fadd holds e, or F
+  // for L2) and w.u^2, where u is the unweighted (dc/dx) p.
   double local = 0.0, local2 = 0.0;
   if (x < cam.W && y < cam.H) {
     const long long pix = cam.pix_off + (long long)y * cam.W + x;
     const int p = threadIdx.x;
     const float u0 = su[upad(0, p)], u1 = su[upad(1, p)], u2 = su[upad(2, p)];
+    float w0 = 1.f, w1 = 1.f, w2 = 1.f;
+    if (cv.wres != nullptr) {
+      w0 = cv.wres[pix * 3 + 0];
+      w1 = cv.wres[pix * 3 + 1];
+      w2 = cv.wres[pix * 3 + 2];
+    }
     if (u != nullptr) {
-      u[pix * 3 + 0] = u0;
-      u[pix * 3 + 1] = u1;
-      u[pix * 3 + 2] = u2;
+      u[pix * 3 + 0] = w0 * u0;
+      u[pix * 3 + 1] = w1 * u1;
+      u[pix * 3 + 2] = w2 * u2;
     }
     if (sq_partials != nullptr) {
       const float* f = Fadd + pix * 3;
-      const double a0 = (double)u0 + f[0], a1 = (double)u1 + f[1], a2 = (double)u2 + f[2];
-      local = a0 * a0 + a1 * a1 + a2 * a2;
-      local2 = (double)u0 * u0 + (double)u1 * u1 + (double)u2 * u2;
+      local = (double)(f[0] * u0 + f[1] * u1 + f[2] * u2);
+      local2 = (double)(w0 * u0 * u0 + w1 * u1 * u1 + w2 * u2 * u2);
     }
   }
   if (sq_partials != nullptr) {
@@ -531,15 +539,35 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const _
   }
 }
 
-// Per segment: Q = sum over entries and channels of a_ch a_ch^T with
-// a_ch = [h_ch gamma, w e_ch]; stored as Qgg (21, upper triangle of the 6x6
-// block, row-major), X (18, 6x3: sum w h_c gamma_i), D (sum w^2).
+// Per segment: Q = sum over entries and channels of rho_ch a_ch a_ch^T with
+// a_ch = [h_ch gamma, w e_ch] and rho_ch the residual-to-pixel weight of the
+// entry's pixel channel (1 for L2); stored as kDiagBlock floats: Qgg (21,
+// upper triangle of the 6x6 block, row-major), X (18, 6x3: sum rho_c w h_c
+// gamma_i), D_ch (3: sum rho_ch w^2) and two zeros of padding.
 template <int kFmt>
 __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* __restrict__ seg_q) {
+  __shared__ float sw[3][kTilePix];   // residual-to-pixel weights of the tile's pixels
   const int tile = blockIdx.x;
   const uint32_t g0 = cv.tile_seg_off[tile], g1 = cv.tile_seg_off[tile + 1];
   if (g0 == g1) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const DevCam& cam = cv.cams[find_view(cv.cams, cv.V, tile)];
+    const int lt = tile - cam.tile_off;
+    const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
+    const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
+    float w0 = 1.f, w1 = 1.f, w2 = 1.f;
+    if (cv.wres != nullptr && x < cam.W && y < cam.H) {
+      const long long pix = cam.pix_off + (long long)y * cam.W + x;
+      w0 = cv.wres[pix * 3 + 0];
+      w1 = cv.wres[pix * 3 + 1];
+      w2 = cv.wres[pix * 3 + 2];
+    }
+    sw[0][threadIdx.x] = w0;
+    sw[1][threadIdx.x] = w1;
+    sw[2][threadIdx.x] = w2;
+    __syncthreads();
+  }
   for (uint32_t seg = g0 + warp; seg < g1; seg += kTilePix / 32) {
     const uint4* rq = reinterpret_cast<const uint4*>(cv.seg_rec + seg);
     const SegRec r = rec_from(rq[0], rq[1], rq[2]);   // tile-local mean, conic, 1/o, FP16 scale
@@ -547,27 +575,32 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
     const float mx = r.mx, my = r.my, A = r.A, B = r.B, C = r.C;
     const float io = r.io;
     const float scale = kFmt == GSLM_CACHE_FP16S ? r.scale : 1.f;
-    float q[40];
+    float q[42];
 #pragma unroll
-    for (int i = 0; i < 40; ++i) q[i] = 0.f;
+    for (int i = 0; i < 42; ++i) q[i] = 0.f;
     for (unsigned long long e = e0 + lane; e < e1; e += 32) {
       const float4 pe = load_entry<kFmt>(cv.payload, e, scale);
       const int p = cv.pixoff[e];
+      const float wr = sw[0][p], wg = sw[1][p], wb = sw[2][p];
       const float dx = (float)(p & (kTile - 1)) - mx, dy = (float)(p / kTile) - my;
       float gam[6] = {A * dx + B * dy, B * dx + C * dy, -0.5f * dx * dx, -dx * dy, -0.5f * dy * dy, io};
-      const float H2 = pe.y * pe.y + pe.z * pe.z + pe.w * pe.w;
+      const float H2 = wr * pe.y * pe.y + wg * pe.z * pe.z + wb * pe.w * pe.w;
       int k = 0;
 #pragma unroll
       for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = i; j < 6; ++j) q[k++] += H2 * gam[i] * gam[j];
+      const float xr = wr * pe.x * pe.y, xg = wg * pe.x * pe.z, xb = wb * pe.x * pe.w;
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        q[21 + 3 * i + 0] += pe.x * pe.y * gam[i];
-        q[21 + 3 * i + 1] += pe.x * pe.z * gam[i];
-        q[21 + 3 * i + 2] += pe.x * pe.w * gam[i];
+        q[21 + 3 * i + 0] += xr * gam[i];
+        q[21 + 3 * i + 1] += xg * gam[i];
+        q[21 + 3 * i + 2] += xb * gam[i];
       }
-      q[39] += pe.x * pe.x;
+      const float aa = pe.x * pe.x;
+      q[39] += wr * aa;
+      q[40] += wg * aa;
+      q[41] += wb * aa;
     }
     // three recursive-halving reductions of 16 values (48 shuffles instead of
     // 200 for a butterfly per value): lane 2i then holds sum i of each block
@@ -576,17 +609,17 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
     for (int i = 0; i < 16; ++i) {
       b0[i] = q[i];
       b1[i] = q[16 + i];
-      b2[i] = i < 8 ? q[32 + i] : 0.f;
+      b2[i] = i < 10 ? q[32 + i] : 0.f;
     }
     group_sum16<32>(b0, lane);
     group_sum16<32>(b1, lane);
     group_sum16<32>(b2, lane);
     if ((lane & 1) == 0) {
-      float* out = seg_q + (size_t)cv.seg_pos[seg] * 40;
+      float* out = seg_q + (size_t)cv.seg_pos[seg] * kDiagBlock;
       const int i = lane >> 1;
       out[i] = b0[0];
       out[16 + i] = b1[0];
-      if (i < 8) out[32 + i] = b2[0];
+      if (i < kDiagBlock - 32) out[32 + i] = b2[0];   // the last two are zero padding
     }
   }
 }

@@ -23,6 +23,7 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr float kShOffset = 0.5f;
 constexpr int kNP = 59;                     // parameters per Gaussian
+constexpr int kDiagBlock = 44;              // floats per segment block of diag(J^T J) (42 used)
 // Bounds applied to diag(J^T J) where it serves as the Jacobi preconditioner and
 // as the LM damping term (the Levenberg-Marquardt diagonal bounds of Ceres, whose
 // LM implementation the paper follows, Sec. 3.2). Subset weights use the raw diagonal.
@@ -159,6 +160,7 @@ struct CacheView {
   long long n_entries;
   int fmt;
   const int* skip;                 // if non-null and *skip != 0 the kernels do nothing (PCG finished)
+  const float* wres;               // [n_pix][3] residual-to-pixel weights (dr/dc)^2, or null (L2: 1)
 };
 
 // Counts kernel launches of this library (reported by gslm_kernel_launches).
@@ -328,6 +330,12 @@ int apply_J_partials(const CacheView& cv);
 cudaError_t launch_apply_J_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st);
 cudaError_t launch_apply_JT_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st);
 int device_sm_count();
+
+// residual.cu: e (may be null), w (may be null) [n_pix][3] and per-tile float64
+// energies of the L1 + SSIM objective for rendered img against tgt.
+cudaError_t launch_l1ssim(const DevCam* cams, int V, int n_tiles, const float* img, const float* tgt, float lam1,
+                          float lam2, float eps, float* e, float* w, double* cost_partials, cudaStream_t st);
+cudaError_t launch_fill_f32(long long n, float v, float* out, cudaStream_t st);
 
 // pcg.cu
 cudaError_t launch_reduce_partials(const double* partials, int n, double* out, cudaStream_t st);

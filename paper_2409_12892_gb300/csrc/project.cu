@@ -706,8 +706,9 @@ __global__ void __launch_bounds__(128, 4) k_vjp_batch(const float* __restrict__ 
 }
 
 // diag(J^T J) for every Gaussian: sum over views of v_k^T Q v_k, where v_k is
-// column k of dy/dx and Q (per slot) is the sum over its cache entries and
-// channels of (dc/dy)^T (dc/dy), stored as 21 geo-geo + 18 geo-rgb + 1 rgb values.
+// column k of dy/dx and Q (per splat) is the sum over its cache entries and
+// channels of (dc/dy)^T (dc/dy), weighted by the residual-to-pixel weights,
+// stored as 21 geo-geo + 18 geo-rgb + 3 rgb values (and 2 of padding).
 __global__ void __launch_bounds__(128) k_diag(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
@@ -731,13 +732,13 @@ __global__ void __launch_bounds__(128) k_diag(
       gauss_geo(P, ld, g, G);
       any = true;
     }
-    float Q[40];
+    float Q[kDiagBlock];
 #pragma unroll
-    for (int i = 0; i < 40; ++i) Q[i] = 0.f;
+    for (int i = 0; i < kDiagBlock; ++i) Q[i] = 0.f;
     for (uint32_t j = a; j < b; ++j) {
-      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * 40);   // splat order
+      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * kDiagBlock);   // splat order
 #pragma unroll
-      for (int i = 0; i < 10; ++i) {
+      for (int i = 0; i < kDiagBlock / 4; ++i) {
         const float4 t = q4[i];
         Q[4 * i + 0] += t.x; Q[4 * i + 1] += t.y; Q[4 * i + 2] += t.z; Q[4 * i + 3] += t.w;
       }
@@ -761,12 +762,12 @@ __global__ void __launch_bounds__(128) k_diag(
       live[ch] = smooth || raw >= 0.f;
       sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], w, grad[ch]);
     }
-    const float D = Q[39];
+    const float D[3] = {Q[39], Q[40], Q[41]};   // per channel: the weights differ between channels
 #pragma unroll
     for (int k = 0; k < 16; ++k)
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch)
-        if (live[ch]) d[11 + 3 * k + ch] += D * Y[k] * Y[k];
+        if (live[ch]) d[11 + 3 * k + ch] += D[ch] * Y[k] * Y[k];
     // the 11 geometric parameters: unit tangents
 #pragma unroll 1
     for (int k = 0; k < 11; ++k) {
@@ -792,7 +793,7 @@ __global__ void __launch_bounds__(128) k_diag(
       } else {
         yv[6] = yv[7] = yv[8] = 0.f;
       }
-      // v^T Q v with Q = [[Qgg, X], [X^T, D I]]
+      // v^T Q v with Q = [[Qgg, X], [X^T, diag(D)]]
       float acc = 0.f;
       int idx = 0;
 #pragma unroll
@@ -806,7 +807,7 @@ __global__ void __launch_bounds__(128) k_diag(
       for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc += 2.f * Q[21 + i * 3 + c] * yv[i] * yv[6 + c];
-      acc += D * (yv[6] * yv[6] + yv[7] * yv[7] + yv[8] * yv[8]);
+      acc += D[0] * yv[6] * yv[6] + D[1] * yv[7] * yv[7] + D[2] * yv[8] * yv[8];
       d[k] += acc;
     }
   }

@@ -31,6 +31,7 @@ c_float, c_double, c_int32, c_int64, c_void_p, c_size_t = (
 STATUS = {0: "GSLM_OK", -1: "GSLM_E_INVALID", -2: "GSLM_E_OOM", -3: "GSLM_E_CUDA",
           -4: "GSLM_E_CACHE_OVERFLOW", -5: "GSLM_E_TIMEOUT", -6: "GSLM_E_NUMERIC", 1: "GSLM_W_PCG_BREAKDOWN"}
 CACHE_FMT = {"fp32": 0, "bf16": 1, "fp16s": 2}
+OBJECTIVE = {"l2": 0, "l1ssim": 1}
 
 
 class GslmError(RuntimeError):
@@ -49,7 +50,8 @@ class Options(ctypes.Structure):
                 ("lambda_min", c_float), ("lambda_max", c_float), ("smooth", c_int32),
                 ("mem_budget", c_size_t), ("group", c_int32), ("profile", c_int32), ("autotune", c_int32),
                 ("batch", c_int32), ("graph", c_int32), ("batch_ctas", c_int32), ("apply_variant", c_int32),
-                ("line_search", c_int32), ("pad", c_int32), ("batch_mem", c_size_t)]
+                ("line_search", c_int32), ("pad", c_int32), ("batch_mem", c_size_t), ("objective", c_int32),
+                ("lambda_l1", c_float), ("lambda_ssim", c_float), ("res_eps", c_float)]
 
 
 class CacheInfo(ctypes.Structure):
@@ -108,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gslm_version": (ctypes.c_char_p, []),
         "gslm_kernel_launches": (c_int64, []),
         "gslm_memory_usage": (c_int32, [P, c_int32, P]),
+        "gslm_cache_weights": (c_int32, [P, P]),
         "gslm_autotune_info": (c_int32, [P, P, P]),
         "gslm_apply_JT_noalloc": (c_int32, [P, P, P, P]),
         "gslm_precond_weight_count": (c_int32, []),
@@ -141,7 +144,7 @@ def exported_symbols() -> list:
             "gslm_render", "gslm_build_cache", "gslm_cache_stats", "gslm_cache_free", "gslm_apply_J",
             "gslm_apply_JT", "gslm_jacobi_diag", "gslm_pcg_solve", "gslm_pcg_solve_batch", "gslm_combine_accumulate",
             "gslm_combine_finish", "gslm_lm_step", "gslm_version", "gslm_kernel_launches", "gslm_memory_usage",
-            "gslm_autotune_info",
+            "gslm_cache_weights", "gslm_autotune_info",
             "gslm_apply_JT_noalloc", "gslm_precond_weight_count", "gslm_precond_create", "gslm_precond_free",
             "gslm_precond_get", "gslm_precond_set", "gslm_precond_features", "gslm_precond_fit_standardizer",
             "gslm_precond_apply", "gslm_precond_backward", "gslm_precond_unrolled_grad",
@@ -208,6 +211,13 @@ class Cache:
         self.ctx._check(self.ctx.lib.gslm_cache_stats(ctypes.c_void_p(self.handle), ctypes.byref(ci)))
         return ci
 
+    def weights(self):
+        """Residual-to-pixel weights (dr/dc)^2 per pixel channel, [pixels][3] (1 for L2)."""
+        w = torch.empty((n_pixels(self.cams), 3), dtype=torch.float32, device=self.b.device if self.b is not None
+                        else "cuda")
+        self.ctx._check(self.ctx.lib.gslm_cache_weights(ctypes.c_void_p(self.handle), _ptr(w)))
+        return w
+
     def free(self):
         if self.handle:
             self.ctx.lib.gslm_cache_free(ctypes.c_void_p(self.handle))
@@ -225,7 +235,8 @@ class Context:
 
     def __init__(self, cache_fmt="fp32", n_iters=8, break_rel2=0.01, lambda_min=1e-4, lambda_max=1e4,
                  smooth=False, mem_budget=0, group=32, profile=False, autotune=True, batch=True, graph=True,
-                 batch_ctas=0, apply_variant=0, line_search=8, batch_mem=0, stream=None):
+                 batch_ctas=0, apply_variant=0, line_search=8, batch_mem=0, objective="l2", lambda_l1=0.8,
+                 lambda_ssim=0.2, res_eps=1e-4, stream=None):
         self.lib = load_library()
         opt = Options()
         self.lib.gslm_default_options(ctypes.byref(opt))
@@ -239,6 +250,8 @@ class Context:
         opt.apply_variant = int(apply_variant)
         opt.line_search = int(line_search)
         opt.batch_mem = int(batch_mem)
+        opt.objective = OBJECTIVE[objective] if isinstance(objective, str) else int(objective)
+        opt.lambda_l1, opt.lambda_ssim, opt.res_eps = float(lambda_l1), float(lambda_ssim), float(res_eps)
         self.opt = opt
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
