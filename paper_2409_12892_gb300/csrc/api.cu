@@ -423,10 +423,18 @@ gslm_status do_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, floa
   }
   ctx->timer.end(t);
   t = ctx->timer.begin(PH_VJP);
+  // with compact splat keys, the per-splat sums go to the tangent buffer (free
+  // once J p has read it) and the adjoint reads one record per splat
+  float* splat_ybar = nullptr;
+  if (c->act_off.p != nullptr) {
+    CK(ctx->ydot.ensure(sizeof(float) * 12 * c->tangent_rows(), st));
+    splat_ybar = ctx->ydot.as<float>();
+    CK(launch_splat_sum(c->n_active, c->slot_seg_start.as<uint32_t>(), c->slot_seg_end.as<uint32_t>(), sy,
+                        splat_ybar, sc, st));
+  }
   CK(launch_vjp(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
-                c->slot_seg_end.as<uint32_t>(), c->vmask.as<unsigned long long>(), c->act_off.as<uint32_t>(),
-                ctx->seg_ybar.as<float>(), scale, g,
-                p, M, lambda, partials, sc, st));
+                c->slot_seg_end.as<uint32_t>(), c->vmask.as<unsigned long long>(), c->act_off.as<uint32_t>(), sy,
+                splat_ybar, scale, g, p, M, lambda, partials, sc, st));
   ctx->timer.end(t);
   return GSLM_OK;
 }
@@ -603,6 +611,7 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     R.s_list = c->slot_seg_list.as<uint32_t>();
     R.ydot = ctx->bt_ydot.as<float>() + L.y_off[i];
     R.seg_ybar = ctx->bt_segy.as<float>() + L.s_off[i];
+    R.n_splats = c->act_off.p != nullptr ? c->n_active : 0;
     tiles += c->n_tiles;
     tb.tile_end[i] = tiles;
     tb.v[i] = c->view();
@@ -668,6 +677,7 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     ctx->timer.end(t);
     CKS(apply_pair());
     t = ctx->timer.begin(PH_VJP);
+    CK(launch_splat_sum_batch(gb, nullptr, st));
     CK(launch_vjp_batch(params, N, ld, smooth, gb, g, vs, nullptr, nullptr, 0.f, nullptr, nullptr, st));
     ctx->timer.end(t);
     t = ctx->timer.begin(PH_VEC);
@@ -682,6 +692,7 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
     ctx->timer.end(t);
     CKS(apply_pair());
     t = ctx->timer.begin(PH_VJP);
+    CK(launch_splat_sum_batch(gb, sc, st));
     CK(launch_vjp_batch(params, N, ld, smooth, gb, g, vs, p, M, lambda, part, sc, st));
     ctx->timer.end(t);
     t = ctx->timer.begin(PH_VEC);
@@ -1187,9 +1198,18 @@ gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* c, float* diag) {
   cudaStream_t st = ctx->st;
   CK(ctx->seg_q.ensure(sizeof(float) * kDiagBlock * std::max<long long>(c->n_seg, 1), st));
   CK(launch_diag_entries(c->view(), ctx->seg_q.as<float>(), st));
+  // with compact splat keys, one block per splat first (segments summed in splat order)
+  float* splat_q = nullptr;
+  Buf sq;
+  if (c->act_off.p != nullptr) {
+    CK(sq.alloc(sizeof(float) * kDiagBlock * std::max<long long>(c->n_active, 1), st));
+    splat_q = sq.as<float>();
+    CK(launch_splat_sum_q(c->n_active, c->slot_seg_start.as<uint32_t>(), c->slot_seg_end.as<uint32_t>(),
+                          ctx->seg_q.as<float>(), splat_q, st));
+  }
   CK(launch_diag(c->params, c->N, c->ld, c->cams.as<DevCam>(), c->V, c->smooth, c->slot_seg_start.as<uint32_t>(),
                  c->slot_seg_end.as<uint32_t>(), c->vmask.as<unsigned long long>(), c->act_off.as<uint32_t>(),
-                 ctx->seg_q.as<float>(), diag, st));
+                 ctx->seg_q.as<float>(), splat_q, diag, st));
   return GSLM_OK;
 }
 

@@ -543,21 +543,28 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const _
 // a_ch = [h_ch gamma, w e_ch] and rho_ch the residual-to-pixel weight of the
 // entry's pixel channel (1 for L2); stored as kDiagBlock floats: Qgg (21,
 // upper triangle of the 6x6 block, row-major), X (18, 6x3: sum rho_c w h_c
-// gamma_i), D_ch (3: sum rho_ch w^2) and two zeros of padding.
-template <int kFmt>
+// gamma_i), D_ch (3: sum rho_ch w^2) and two zeros of padding. A group of
+// kDiagG lanes takes one segment (two segments per warp in lock step), so
+// short segments leave fewer lanes idle and the three 16-value reductions
+// serve two segments at once.
+constexpr int kDiagG = 16;
+
+template <int kFmt, bool kWeighted>
 __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* __restrict__ seg_q) {
-  __shared__ float sw[3][kTilePix];   // residual-to-pixel weights of the tile's pixels
+  constexpr int kGPW = 32 / kDiagG;
+  __shared__ float sw[3][kWeighted ? kTilePix : 1];   // residual-to-pixel weights of the tile's pixels
   const int tile = blockIdx.x;
   const uint32_t g0 = cv.tile_seg_off[tile], g1 = cv.tile_seg_off[tile + 1];
   if (g0 == g1) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  {
+  const int gl = lane & (kDiagG - 1), grp = lane / kDiagG;
+  if constexpr (kWeighted) {
     const DevCam& cam = cv.cams[find_view(cv.cams, cv.V, tile)];
     const int lt = tile - cam.tile_off;
     const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
     const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
     float w0 = 1.f, w1 = 1.f, w2 = 1.f;
-    if (cv.wres != nullptr && x < cam.W && y < cam.H) {
+    if (x < cam.W && y < cam.H) {
       const long long pix = cam.pix_off + (long long)y * cam.W + x;
       w0 = cv.wres[pix * 3 + 0];
       w1 = cv.wres[pix * 3 + 1];
@@ -568,42 +575,50 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
     sw[2][threadIdx.x] = w2;
     __syncthreads();
   }
-  for (uint32_t seg = g0 + warp; seg < g1; seg += kTilePix / 32) {
-    const uint4* rq = reinterpret_cast<const uint4*>(cv.seg_rec + seg);
-    const SegRec r = rec_from(rq[0], rq[1], rq[2]);   // tile-local mean, conic, 1/o, FP16 scale
-    const unsigned long long e0 = r.e0, e1 = r.e1;
-    const float mx = r.mx, my = r.my, A = r.A, B = r.B, C = r.C;
-    const float io = r.io;
-    const float scale = kFmt == GSLM_CACHE_FP16S ? r.scale : 1.f;
+  // every lane of a warp runs the same number of rounds (the reductions shuffle over the warp)
+  for (uint32_t base = g0 + warp * kGPW; base < g1; base += kWarps * kGPW) {
+    const uint32_t seg = base + grp;
+    const bool has = seg < g1;
     float q[42];
 #pragma unroll
     for (int i = 0; i < 42; ++i) q[i] = 0.f;
-    for (unsigned long long e = e0 + lane; e < e1; e += 32) {
-      const float4 pe = load_entry<kFmt>(cv.payload, e, scale);
-      const int p = cv.pixoff[e];
-      const float wr = sw[0][p], wg = sw[1][p], wb = sw[2][p];
-      const float dx = (float)(p & (kTile - 1)) - mx, dy = (float)(p / kTile) - my;
-      float gam[6] = {A * dx + B * dy, B * dx + C * dy, -0.5f * dx * dx, -dx * dy, -0.5f * dy * dy, io};
-      const float H2 = wr * pe.y * pe.y + wg * pe.z * pe.z + wb * pe.w * pe.w;
-      int k = 0;
+    if (has) {
+      const uint4* rq = reinterpret_cast<const uint4*>(cv.seg_rec + seg);
+      const SegRec r = rec_from(rq[0], rq[1], rq[2]);   // tile-local mean, conic, 1/o, FP16 scale
+      const float mx = r.mx, my = r.my, A = r.A, B = r.B, C = r.C, io = r.io;
+      const float scale = kFmt == GSLM_CACHE_FP16S ? r.scale : 1.f;
+      for (unsigned long long e = r.e0 + gl; e < r.e1; e += kDiagG) {
+        const float4 pe = load_entry<kFmt>(cv.payload, e, scale);
+        const int p = cv.pixoff[e];
+        float wr = 1.f, wg = 1.f, wb = 1.f;
+        if constexpr (kWeighted) {
+          wr = sw[0][p];
+          wg = sw[1][p];
+          wb = sw[2][p];
+        }
+        const float dx = (float)(p & (kTile - 1)) - mx, dy = (float)(p / kTile) - my;
+        float gam[6] = {A * dx + B * dy, B * dx + C * dy, -0.5f * dx * dx, -dx * dy, -0.5f * dy * dy, io};
+        const float H2 = wr * pe.y * pe.y + wg * pe.z * pe.z + wb * pe.w * pe.w;
+        int k = 0;
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int j = i; j < 6; ++j) q[k++] += H2 * gam[i] * gam[j];
-      const float xr = wr * pe.x * pe.y, xg = wg * pe.x * pe.z, xb = wb * pe.x * pe.w;
+          for (int j = i; j < 6; ++j) q[k++] += H2 * gam[i] * gam[j];
+        const float xr = wr * pe.x * pe.y, xg = wg * pe.x * pe.z, xb = wb * pe.x * pe.w;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        q[21 + 3 * i + 0] += xr * gam[i];
-        q[21 + 3 * i + 1] += xg * gam[i];
-        q[21 + 3 * i + 2] += xb * gam[i];
+        for (int i = 0; i < 6; ++i) {
+          q[21 + 3 * i + 0] += xr * gam[i];
+          q[21 + 3 * i + 1] += xg * gam[i];
+          q[21 + 3 * i + 2] += xb * gam[i];
+        }
+        const float aa = pe.x * pe.x;
+        q[39] += wr * aa;
+        q[40] += wg * aa;
+        q[41] += wb * aa;
       }
-      const float aa = pe.x * pe.x;
-      q[39] += wr * aa;
-      q[40] += wg * aa;
-      q[41] += wb * aa;
     }
-    // three recursive-halving reductions of 16 values (48 shuffles instead of
-    // 200 for a butterfly per value): lane 2i then holds sum i of each block
+    // three recursive-halving reductions of 16 values over the group: lane gl
+    // then holds sum gl of each block
     float b0[16], b1[16], b2[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -611,15 +626,14 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
       b1[i] = q[16 + i];
       b2[i] = i < 10 ? q[32 + i] : 0.f;
     }
-    group_sum16<32>(b0, lane);
-    group_sum16<32>(b1, lane);
-    group_sum16<32>(b2, lane);
-    if ((lane & 1) == 0) {
+    group_sum16<kDiagG>(b0, lane);
+    group_sum16<kDiagG>(b1, lane);
+    group_sum16<kDiagG>(b2, lane);
+    if (has) {
       float* out = seg_q + (size_t)cv.seg_pos[seg] * kDiagBlock;
-      const int i = lane >> 1;
-      out[i] = b0[0];
-      out[16 + i] = b1[0];
-      if (i < kDiagBlock - 32) out[32 + i] = b2[0];   // the last two are zero padding
+      out[gl] = b0[0];
+      out[16 + gl] = b1[0];
+      if (gl < kDiagBlock - 32) out[32 + gl] = b2[0];   // the last two are zero padding
     }
   }
 }
@@ -760,9 +774,12 @@ cudaError_t launch_apply_JT_batch(const TileBatch& tb, int variant, int ctas_per
 
 cudaError_t launch_diag_entries(const CacheView& cv, float* seg_q, cudaStream_t st) {
   if (cv.n_tiles <= 0) return cudaSuccess;
-  if (cv.fmt == GSLM_CACHE_FP32) { k_diag_entries<GSLM_CACHE_FP32><<<cv.n_tiles, kTilePix, 0, st>>>(cv, seg_q); note_launch(); }
-  else if (cv.fmt == GSLM_CACHE_BF16) { k_diag_entries<GSLM_CACHE_BF16><<<cv.n_tiles, kTilePix, 0, st>>>(cv, seg_q); note_launch(); }
-  else { k_diag_entries<GSLM_CACHE_FP16S><<<cv.n_tiles, kTilePix, 0, st>>>(cv, seg_q); note_launch(); }
+#define DIAG_LAUNCH(F, W) { k_diag_entries<F, W><<<cv.n_tiles, kTilePix, 0, st>>>(cv, seg_q); note_launch(); }
+  const bool w = cv.wres != nullptr;
+  if (cv.fmt == GSLM_CACHE_FP32) { if (w) DIAG_LAUNCH(GSLM_CACHE_FP32, true) else DIAG_LAUNCH(GSLM_CACHE_FP32, false) }
+  else if (cv.fmt == GSLM_CACHE_BF16) { if (w) DIAG_LAUNCH(GSLM_CACHE_BF16, true) else DIAG_LAUNCH(GSLM_CACHE_BF16, false) }
+  else { if (w) DIAG_LAUNCH(GSLM_CACHE_FP16S, true) else DIAG_LAUNCH(GSLM_CACHE_FP16S, false) }
+#undef DIAG_LAUNCH
   return cudaGetLastError();
 }
 

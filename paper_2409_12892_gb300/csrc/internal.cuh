@@ -184,8 +184,10 @@ struct SubsetRefs {
   const uint32_t* s_start;              // segments of a splat (vjp), keyed as CacheView.slot_seg_start
   const uint32_t* s_end;
   const uint32_t* s_list;
-  float* ydot;                          // [N * V][12] splat tangents
-  float* seg_ybar;                      // [n_seg][12] per-segment adjoints, in slot order
+  float* ydot;                          // [splats][12] splat tangents; after J p, the per-splat sums
+                                        // of the J^T u partials (compact splat keys only)
+  float* seg_ybar;                      // [n_seg][12] per-segment adjoints, in splat order
+  long long n_splats;                   // compact splats (n_active) with act_off, else 0
 };
 struct GaussBatch {
   int n;
@@ -254,21 +256,34 @@ cudaError_t launch_compact_splats(const unsigned long long* vmask, int N, uint32
                                   cudaStream_t st);
 // s_start/s_end: segment positions of a splat, keyed by compact splat index
 // when vmask (and act_off) are given, else by slot v * N + g.
+// splat_ybar (with vmask and act_off; may be null): the per-splat sums of
+// launch_splat_sum, read instead of the segment ranges.
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V,
                        int smooth, const uint32_t* s_start, const uint32_t* s_end,
                        const unsigned long long* vmask, const uint32_t* act_off,
-                       const float* seg_ybar, float scale, float* g, const float* p, const float* M,
-                       float lambda, double* dot_partials, const PcgScalars* sc, cudaStream_t st);
+                       const float* seg_ybar, const float* splat_ybar, float scale, float* g, const float* p,
+                       const float* M, float lambda, double* dot_partials, const PcgScalars* sc, cudaStream_t st);
+// splat_q (with compact keys; may be null): the per-splat sums of the
+// segment blocks (launch_splat_sum_q), read instead of the segment ranges.
 cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V,
                         int smooth, const uint32_t* s_start, const uint32_t* s_end,
                         const unsigned long long* vmask, const uint32_t* act_off,
-                        const float* seg_q, float* diag, cudaStream_t st);
+                        const float* seg_q, const float* splat_q, float* diag, cudaStream_t st);
+cudaError_t launch_splat_sum_q(long long n_splats, const uint32_t* s_start, const uint32_t* s_end, const float* seg_q,
+                               float* splat_q, cudaStream_t st);
 int vjp_blocks(int N);
 // Batched forms: blockIdx.y = subset; p, z, pout, g, M stacked with stride vs;
 // scalars sc[b]; vjp partials at partials + b * vjp_blocks(N).
 cudaError_t launch_tangent_batch(const float* params, int N, long long ld, int smooth, const GaussBatch& gb,
                                  const float* p, long long vs, const float* z_beta, float* p_out,
                                  const PcgScalars* sc, cudaStream_t st);
+// Per compact splat c < n_splats: splat_ybar[c] = sum of seg_ybar over the
+// splat's segment range [s_start[c], s_end[c]) (12 floats). Skipped when
+// sc->done. The batched form does every subset whose act_off is set, into its
+// ydot buffer.
+cudaError_t launch_splat_sum(long long n_splats, const uint32_t* s_start, const uint32_t* s_end,
+                             const float* seg_ybar, float* splat_ybar, const PcgScalars* sc, cudaStream_t st);
+cudaError_t launch_splat_sum_batch(const GaussBatch& gb, const PcgScalars* sc, cudaStream_t st);
 cudaError_t launch_vjp_batch(const float* params, int N, long long ld, int smooth, const GaussBatch& gb,
                              float* g, long long vs, const float* p, const float* M, float lambda,
                              double* partials, const PcgScalars* sc, cudaStream_t st);

@@ -66,7 +66,7 @@ extern "C" gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* ca
   cudaError_t e = gslm::launch_apply_JT(cp.view, u, seg_ybar, xp.variant_JT, xp.st);
   if (e == cudaSuccess)
     e = gslm::launch_vjp(cp.params, cp.N, cp.ld, cp.cams, cp.V, cp.smooth, cp.view.slot_seg_start,
-                         cp.view.slot_seg_end, cp.view.vmask, cp.view.act_off, seg_ybar, 1.f, g, nullptr,
+                         cp.view.slot_seg_end, cp.view.vmask, cp.view.act_off, seg_ybar, nullptr, 1.f, g, nullptr,
                          nullptr, 0.f, nullptr, nullptr, xp.st);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -11,6 +11,8 @@
 //
 // Splat attributes y (9): mean (mx, my), conic (A, B, C) = inverse of the 2D
 // covariance [[a, b], [b, c]], opacity o, colour (r, g, b).
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace gslm {
@@ -450,8 +452,9 @@ __device__ __forceinline__ void vjp_body(
     int g0, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
     const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
-    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
-    const float* __restrict__ Mdiag, float lambda, float (*s_mub)[kGPB][3], double& local) {
+    const float* __restrict__ seg_ybar, const float* __restrict__ splat_ybar, float scale,
+    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
+    float (*s_mub)[kGPB][3], double& local) {
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
   const int g = g0 + lane;
   const bool valid = g < N;
@@ -469,18 +472,25 @@ __device__ __forceinline__ void vjp_body(
     GaussGeo G;
     for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
       const long long sk = use_mask ? key++ : (long long)v * N + g;
-      const uint32_t a = s_start[sk], b = s_end[sk];
-      if (a == b) continue;
+      float yb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (splat_ybar != nullptr) {   // the splat's sum, one record per (Gaussian, view)
+        const float* sy = splat_ybar + (size_t)sk * 12;
+        const float4 u0 = *reinterpret_cast<const float4*>(sy);
+        const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
+        yb[0] = u0.x; yb[1] = u0.y; yb[2] = u0.z; yb[3] = u0.w; yb[4] = u1.x; yb[5] = u1.y;
+      } else {
+        const uint32_t a = s_start[sk], b = s_end[sk];
+        if (a == b) continue;
+        for (uint32_t j = a; j < b; ++j) {
+          const float* sy = seg_ybar + (size_t)j * 12;
+          const float4 u0 = *reinterpret_cast<const float4*>(sy);
+          const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
+          yb[0] += u0.x; yb[1] += u0.y; yb[2] += u0.z; yb[3] += u0.w; yb[4] += u1.x; yb[5] += u1.y;
+        }
+      }
       if (!any) {
         gauss_geo(P, ld, g, G);
         any = true;
-      }
-      float yb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (uint32_t j = a; j < b; ++j) {
-        const float* sy = seg_ybar + (size_t)j * 12;
-        const float4 u0 = *reinterpret_cast<const float4*>(sy);
-        const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
-        yb[0] += u0.x; yb[1] += u0.y; yb[2] += u0.z; yb[3] += u0.w; yb[4] += u1.x; yb[5] += u1.y;
       }
       const DevCam& cam = cams[v];
       ViewGeo VG;
@@ -568,10 +578,14 @@ __device__ __forceinline__ void vjp_body(
     }
     for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
       const long long sk = use_mask ? key++ : (long long)v * N + g;
-      const uint32_t a = s_start[sk], b = s_end[sk];
-      if (a == b) continue;
       float yc = 0.f;
-      for (uint32_t j = a; j < b; ++j) yc += seg_ybar[(size_t)j * 12 + 6 + ch];
+      if (splat_ybar != nullptr) {
+        yc = splat_ybar[(size_t)sk * 12 + 6 + ch];
+      } else {
+        const uint32_t a = s_start[sk], b = s_end[sk];
+        if (a == b) continue;
+        for (uint32_t j = a; j < b; ++j) yc += seg_ybar[(size_t)j * 12 + 6 + ch];
+      }
       const DevCam& cam = cams[v];
       const float d0 = mu0 - cam.campos[0], d1 = mu1 - cam.campos[1], d2 = mu2 - cam.campos[2];
       const float inv_dlen = 1.f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -666,15 +680,15 @@ __device__ __forceinline__ void vjp_blocks_loop(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
     const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
-    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
-    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
-    const PcgScalars* __restrict__ sc) {
+    const float* __restrict__ seg_ybar, const float* __restrict__ splat_ybar, float scale,
+    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
+    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
   __shared__ float s_mub[4][kGPB][3];
   double local = 0.0;
   if (sc == nullptr || !sc->done) {
     for (int g0 = blockIdx.x * kGPB; g0 < N; g0 += gridDim.x * kGPB)
-      vjp_body(g0, P, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar, scale, gout, p, Mdiag,
-               lambda, s_mub, local);
+      vjp_body(g0, P, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar, splat_ybar, scale, gout, p,
+               Mdiag, lambda, s_mub, local);
   }
   if (partials != nullptr) write_dot_partial(local, partials);
 }
@@ -683,11 +697,11 @@ __global__ void __launch_bounds__(128, 4) k_vjp(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
     const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
-    const float* __restrict__ seg_ybar, float scale, float* __restrict__ gout, const float* __restrict__ p,
-    const float* __restrict__ Mdiag, float lambda, double* __restrict__ partials,
-    const PcgScalars* __restrict__ sc) {
-  vjp_blocks_loop(P, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar, scale, gout, p, Mdiag, lambda,
-                  partials, sc);
+    const float* __restrict__ seg_ybar, const float* __restrict__ splat_ybar, float scale,
+    float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
+    double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
+  vjp_blocks_loop(P, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar, splat_ybar, scale, gout, p,
+                  Mdiag, lambda, partials, sc);
 }
 
 // Batched: blockIdx.y is the subset; g, p and M at offset blockIdx.y * vs, the
@@ -700,7 +714,8 @@ __global__ void __launch_bounds__(128, 4) k_vjp_batch(const float* __restrict__ 
   const int b = blockIdx.y;
   const SubsetRefs& s = gb.s[b];
   const long long off = (long long)b * vs;
-  vjp_blocks_loop(P, N, ld, s.cams, s.V, smooth, s.s_start, s.s_end, s.vmask, s.act_off, s.seg_ybar, 1.f, gout + off,
+  vjp_blocks_loop(P, N, ld, s.cams, s.V, smooth, s.s_start, s.s_end, s.vmask, s.act_off, s.seg_ybar,
+                  s.act_off != nullptr ? s.ydot : nullptr, 1.f, gout + off,
                   p != nullptr ? p + off : nullptr, Mdiag != nullptr ? Mdiag + off : nullptr, lambda,
                   partials != nullptr ? partials + (size_t)b * gridDim.x : nullptr, sc != nullptr ? sc + b : nullptr);
 }
@@ -713,7 +728,7 @@ __global__ void __launch_bounds__(128) k_diag(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
     const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
-    const float* __restrict__ seg_q, float* __restrict__ dout) {
+    const float* __restrict__ seg_q, const float* __restrict__ splat_q, float* __restrict__ dout) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   float d[kNP];
@@ -726,15 +741,25 @@ __global__ void __launch_bounds__(128) k_diag(
   long long key = use_mask ? (long long)act_off[g] : 0;   // splat key as in vjp_body
   for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
     const long long sk = use_mask ? key++ : (long long)v * N + g;
-    const uint32_t a = s_start[sk], b = s_end[sk];
-    if (a == b) continue;
+    float Q[kDiagBlock];
+#pragma unroll
+    for (int i = 0; i < kDiagBlock; ++i) Q[i] = 0.f;
+    // the splat's block: summed over its segments beforehand (splat_q), or here
+    const uint32_t a = splat_q != nullptr ? 0u : s_start[sk], b = splat_q != nullptr ? 0u : s_end[sk];
+    if (splat_q != nullptr) {
+      const float4* q4 = reinterpret_cast<const float4*>(splat_q + (size_t)sk * kDiagBlock);
+#pragma unroll
+      for (int i = 0; i < kDiagBlock / 4; ++i) {
+        const float4 t = q4[i];
+        Q[4 * i + 0] = t.x; Q[4 * i + 1] = t.y; Q[4 * i + 2] = t.z; Q[4 * i + 3] = t.w;
+      }
+    } else if (a == b) {
+      continue;
+    }
     if (!any) {
       gauss_geo(P, ld, g, G);
       any = true;
     }
-    float Q[kDiagBlock];
-#pragma unroll
-    for (int i = 0; i < kDiagBlock; ++i) Q[i] = 0.f;
     for (uint32_t j = a; j < b; ++j) {
       const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * kDiagBlock);   // splat order
 #pragma unroll
@@ -813,6 +838,46 @@ __global__ void __launch_bounds__(128) k_diag(
   }
 #pragma unroll
   for (int k = 0; k < kNP; ++k) dout[k * ld + g] = d[k];
+}
+
+// Per compact splat: the sum of its segments' J^T u partials. The segments of
+// a splat are one contiguous run in splat order, so consecutive threads read
+// consecutive records; the adjoint then reads one record per (Gaussian, view)
+// instead of walking a range per view behind a dependent load.
+template <int kW4>   // float4s per record
+__device__ __forceinline__ void splat_sum_body(long long c, const uint32_t* __restrict__ s_start,
+                                               const uint32_t* __restrict__ s_end,
+                                               const float* __restrict__ seg_rec, float* __restrict__ out) {
+  float4 acc[kW4];
+#pragma unroll
+  for (int i = 0; i < kW4; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (uint32_t j = s_start[c], e = s_end[c]; j < e; ++j) {
+    const float4* q = reinterpret_cast<const float4*>(seg_rec + (size_t)j * (4 * kW4));
+#pragma unroll
+    for (int i = 0; i < kW4; ++i) {
+      const float4 t = q[i];
+      acc[i].x += t.x; acc[i].y += t.y; acc[i].z += t.z; acc[i].w += t.w;
+    }
+  }
+  float4* o = reinterpret_cast<float4*>(out + (size_t)c * (4 * kW4));
+#pragma unroll
+  for (int i = 0; i < kW4; ++i) o[i] = acc[i];
+}
+
+template <int kW4>
+__global__ void k_splat_sum(long long n, const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
+                            const float* __restrict__ seg_rec, float* __restrict__ out,
+                            const PcgScalars* __restrict__ sc) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n || (sc != nullptr && sc->done)) return;
+  splat_sum_body<kW4>(c, s_start, s_end, seg_rec, out);
+}
+
+__global__ void k_splat_sum_batch(const __grid_constant__ GaussBatch gb, const PcgScalars* __restrict__ sc) {
+  const SubsetRefs& s = gb.s[blockIdx.y];
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s.act_off == nullptr || c >= s.n_splats || (sc != nullptr && sc[blockIdx.y].done)) return;
+  splat_sum_body<3>(c, s.s_start, s.s_end, s.seg_ybar, s.ydot);
 }
 
 }  // namespace
@@ -903,20 +968,46 @@ cudaError_t launch_vjp_batch(const float* params, int N, long long ld, int smoot
 
 cudaError_t launch_vjp(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
                        const uint32_t* s_start, const uint32_t* s_end, const unsigned long long* vmask,
-                       const uint32_t* act_off, const float* seg_ybar, float scale, float* g, const float* p,
-                       const float* M, float lambda, double* partials, const PcgScalars* sc, cudaStream_t st) {
+                       const uint32_t* act_off, const float* seg_ybar, const float* splat_ybar, float scale,
+                       float* g, const float* p, const float* M, float lambda, double* partials,
+                       const PcgScalars* sc, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
   { k_vjp<<<vjp_blocks(N), 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar,
-                                       scale, g, p, M, lambda, partials, sc); note_launch(); }
+                                       splat_ybar, scale, g, p, M, lambda, partials, sc); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
                         const uint32_t* s_start, const uint32_t* s_end, const unsigned long long* vmask,
-                        const uint32_t* act_off, const float* seg_q, float* diag, cudaStream_t st) {
+                        const uint32_t* act_off, const float* seg_q, const float* splat_q, float* diag,
+                        cudaStream_t st) {
   if (N == 0) return cudaSuccess;
   { k_diag<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_q,
-                                            diag); note_launch(); }
+                                            splat_q, diag); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splat_sum(long long n_splats, const uint32_t* s_start, const uint32_t* s_end,
+                             const float* seg_ybar, float* splat_ybar, const PcgScalars* sc, cudaStream_t st) {
+  if (n_splats <= 0) return cudaSuccess;
+  { k_splat_sum<3><<<(unsigned)((n_splats + 255) / 256), 256, 0, st>>>(n_splats, s_start, s_end, seg_ybar,
+                                                                      splat_ybar, sc); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splat_sum_q(long long n_splats, const uint32_t* s_start, const uint32_t* s_end, const float* seg_q,
+                               float* splat_q, cudaStream_t st) {
+  if (n_splats <= 0) return cudaSuccess;
+  { k_splat_sum<kDiagBlock / 4><<<(unsigned)((n_splats + 127) / 128), 128, 0, st>>>(n_splats, s_start, s_end, seg_q,
+                                                                                   splat_q, nullptr); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splat_sum_batch(const GaussBatch& gb, const PcgScalars* sc, cudaStream_t st) {
+  long long n = 0;
+  for (int i = 0; i < gb.n; ++i) n = std::max(n, gb.s[i].act_off != nullptr ? gb.s[i].n_splats : 0ll);
+  if (n <= 0 || gb.n <= 0) return cudaSuccess;
+  { k_splat_sum_batch<<<dim3((unsigned)((n + 255) / 256), gb.n), 256, 0, st>>>(gb, sc); note_launch(); }
   return cudaGetLastError();
 }
 
