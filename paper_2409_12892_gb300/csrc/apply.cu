@@ -222,6 +222,10 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
       const uint32_t mlen = warp_max_groups<G>(len);
       const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + (has ? r.e0 : 0);
       const uint8_t* po = cv.pixoff + (has ? r.e0 : 0);
+      // the tangent of the blending exponent is a quadratic in (dx, dy) per
+      // segment: q = k0 + dx (k1 + k3 dx + k4 dy) + dy (k2 + k5 dy)
+      const float k1 = r.A * t.dmx + r.B * t.dmy, k2 = r.B * t.dmx + r.C * t.dmy;
+      const float k3 = -0.5f * t.dA, k4 = -t.dB, k5 = -0.5f * t.dC, k0 = t.od;
       for (uint32_t base = 0; base < mlen; base += G * U) {
         typename Raw<kFmt>::T raw[U];
         int pp[U];
@@ -241,11 +245,11 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
             const float4 pe = decode<kFmt>(raw[j], r.scale);
             const float2 c = sxy[p];
             const float dx = c.x - r.mx, dy = c.y - r.my;
-            const float q = (r.A * dx + r.B * dy) * t.dmx + (r.B * dx + r.C * dy) * t.dmy -
-                            0.5f * dx * dx * t.dA - dx * dy * t.dB - 0.5f * dy * dy * t.dC + t.od;
-            atomicAdd(&su[upad(0, p)], pe.x * t.dr + pe.y * q);
-            atomicAdd(&su[upad(1, p)], pe.x * t.dg + pe.z * q);
-            atomicAdd(&su[upad(2, p)], pe.x * t.db + pe.w * q);
+            const float q = fmaf(dx, fmaf(k3, dx, fmaf(k4, dy, k1)), fmaf(dy, fmaf(k5, dy, k2), k0));
+            float* sp = su + p + (p >> 5);   // upad(ch, p) = sp + ch * (kTilePix + kTilePix / 32)
+            atomicAdd(sp, fmaf(pe.x, t.dr, pe.y * q));
+            atomicAdd(sp + (kTilePix + kTilePix / 32), fmaf(pe.x, t.dg, pe.z * q));
+            atomicAdd(sp + 2 * (kTilePix + kTilePix / 32), fmaf(pe.x, t.db, pe.w * q));
           }
         }
       }
