@@ -493,11 +493,10 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
 
 // Candidates of the persistent tile kernels' autotuner: (variant, CTAs per SM),
 // each variant at the residency its registers allow and one CTA fewer.
-constexpr int kBatchCand = 10;
+constexpr int kBatchCand = 12;
 inline int cand_variant(int c) { return c / 2; }
 inline int cand_ctas(int c) {
-  const int v = c / 2;
-  const int cap = v == 1 ? 5 : v == 3 ? 4 : 6;
+  const int cap = variant_cta_cap(c / 2);
   return (c & 1) ? cap - 1 : cap;
 }
 
@@ -892,7 +891,7 @@ static gslm_status validate_opts(const gslm_options* o) {
   if (!(o->lambda_min > 0.f) || !(o->lambda_max >= o->lambda_min)) return GSLM_E_INVALID;
   if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
   if (o->batch_ctas < 0 || o->batch_ctas > 6) return GSLM_E_INVALID;
-  if (o->apply_variant < 0 || o->apply_variant > 5) return GSLM_E_INVALID;
+  if (o->apply_variant < 0 || o->apply_variant > 6) return GSLM_E_INVALID;
   if (o->line_search < 0 || o->line_search > 60) return GSLM_E_INVALID;
   if (o->objective != GSLM_OBJ_L2 && o->objective != GSLM_OBJ_L1_SSIM) return GSLM_E_INVALID;
   if (!(o->lambda_l1 >= 0.f) || !(o->lambda_ssim >= 0.f) || !(o->res_eps > 0.f) || !std::isfinite(o->lambda_l1) ||

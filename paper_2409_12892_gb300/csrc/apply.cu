@@ -72,6 +72,7 @@ constexpr int kWarps = kTilePix / 32;
 // Shared-memory index of pixel p of colour plane ch, padded by one word every
 // 32 pixels (two tile rows) to spread a segment's pixels over more banks.
 __device__ __forceinline__ int upad(int ch, int p) { return ch * (kTilePix + kTilePix / 32) + p + (p >> 5); }
+constexpr int kPlane3 = 3 * (kTilePix + kTilePix / 32);   // floats of one padded 3-plane tile of u
 
 
 
@@ -137,30 +138,33 @@ __device__ __forceinline__ SegRec rec_from(const uint4& a, const uint4& b, const
 
 // Shared staging area of one chunk of segments (records as three 16-byte
 // words each; splat tangents for J p).
-struct Stage {
+struct StageRec {
   uint4 r0[kStage], r1[kStage], r2[kStage];
-  uint32_t pos[kStage];     // slot-order position of the segment (J^T u output)
 };
-struct StageT {
-  float4 t0[kStage], t1[kStage], t2[kStage];
+struct Stage : StageRec {
+  uint32_t pos[kStage];     // splat-order position of the segment (J^T u output)
+};
+struct StageT {             // the 9 floats of a splat tangent that J p reads
+  float4 t0[kStage], t1[kStage];
+  float t2[kStage];
 };
 
 // Stages segments [first, first + cnt) of the cache (and their tangents).
 template <bool kTangent>
-__device__ __forceinline__ void stage_chunk(const CacheView& cv, uint32_t first, int cnt, Stage& S, StageT* T,
-                                            const float* __restrict__ ydot) {
+__device__ __forceinline__ void stage_chunk(const CacheView& cv, uint32_t first, int cnt, StageRec& S, StageT* T,
+                                            const float* __restrict__ ydot, uint32_t* pos) {
   for (int t = threadIdx.x; t < cnt; t += kTilePix) {
     const uint4* q = reinterpret_cast<const uint4*>(cv.seg_rec + first + t);
     const uint4 a = q[0], b = q[1], c = q[2];
     S.r0[t] = a;
     S.r1[t] = b;
     S.r2[t] = c;
-    if constexpr (!kTangent) S.pos[t] = cv.seg_pos[first + t];
+    if constexpr (!kTangent) pos[t] = cv.seg_pos[first + t];
     if constexpr (kTangent) {
       const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)b.x * 12);
       T->t0[t] = yd[0];
       T->t1[t] = yd[1];
-      T->t2[t] = yd[2];
+      T->t2[t] = ydot[(size_t)b.x * 12 + 8];
     }
   }
 }
@@ -175,96 +179,35 @@ __device__ __forceinline__ uint32_t warp_max_groups(uint32_t v) {
 
 // J p over one tile. su (u of the tile, padded planes) must be zero on entry;
 // sxy filled; the caller synchronises before.
-template <int kFmt, int G, int U>
-__device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, const float* __restrict__ ydot,
-                                             const float* __restrict__ Fadd, float* __restrict__ u,
-                                             double* __restrict__ sq_partials, float* su, const float2* sxy,
-                                             double* dred, unsigned int* next_seg, Stage& S, StageT& T) {
-  static_assert(G == 8 || G == 16 || G == 32, "group size");
-  constexpr int kGPW = 32 / G;
-  const int v = find_view(cv.cams, cv.V, tile);
-  const DevCam& cam = cv.cams[v];
-  const int lt = tile - cam.tile_off;
-  const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
+// Epilogue of a J p tile: u = w (dc/dx) p with the residual-to-pixel weights
+// (1 without them); for the predicted decrease, per-tile sums of e.u (Fadd
+// holds e, or F for L2) and w.u^2, where u is the unweighted (dc/dx) p. The
+// caller has synchronised after the last accumulation.
+template <int kMode>
+__device__ __forceinline__ void apply_J_epilogue(const CacheView& cv, int tile, const DevCam& cam, int tx, int ty,
+                                                 const float* su, const float* __restrict__ Fadd,
+                                                 float* __restrict__ u, double* __restrict__ sq_partials,
+                                                 double* dred) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gl = lane & (G - 1), grp = lane / G;
-  const uint32_t g0 = cv.tile_seg_off[tile];
-  const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
-  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
-    const int cnt = (int)min((uint32_t)kStage, n - c0);
-    stage_chunk<true>(cv, g0 + c0, cnt, S, &T, ydot);
-    if (threadIdx.x == 0) *next_seg = 0;
-    __syncthreads();
-    for (;;) {
-      uint32_t kb = 0;
-      if (lane == 0) kb = atomicAdd(next_seg, (unsigned)kGPW);
-      kb = __shfl_sync(kFull, kb, 0);
-      if (kb >= (uint32_t)cnt) break;
-      const uint32_t k = kb + grp;
-      const bool has = k < (uint32_t)cnt;
-      SegRec r;
-      Tangent t;
-      uint32_t len = 0;
-      if (has) {
-        r = rec_from(S.r0[k], S.r1[k], S.r2[k]);
-        const float4 y0 = T.t0[k], y1 = T.t1[k], y2 = T.t2[k];
-        t.dmx = y0.x;
-        t.dmy = y0.y;
-        t.dA = y0.z;
-        t.dB = y0.w;
-        t.dC = y1.x;
-        t.od = y1.y * r.io;
-        t.dr = y1.z;
-        t.dg = y1.w;
-        t.db = y2.x;
-        len = (uint32_t)(r.e1 - r.e0);
-      }
-      const uint32_t mlen = warp_max_groups<G>(len);
-      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + (has ? r.e0 : 0);
-      const uint8_t* po = cv.pixoff + (has ? r.e0 : 0);
-      // the tangent of the blending exponent is a quadratic in (dx, dy) per
-      // segment: q = k0 + dx (k1 + k3 dx + k4 dy) + dy (k2 + k5 dy)
-      const float k1 = r.A * t.dmx + r.B * t.dmy, k2 = r.B * t.dmx + r.C * t.dmy;
-      const float k3 = -0.5f * t.dA, k4 = -t.dB, k5 = -0.5f * t.dC, k0 = t.od;
-      for (uint32_t base = 0; base < mlen; base += G * U) {
-        typename Raw<kFmt>::T raw[U];
-        int pp[U];
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-          const uint32_t i = base + gl + G * j;
-          if (i < len) {
-            raw[j] = __ldcs(pl + i);
-            pp[j] = po[i];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-          const uint32_t i = base + gl + G * j;
-          if (i < len) {
-            const int p = pp[j];
-            const float4 pe = decode<kFmt>(raw[j], r.scale);
-            const float2 c = sxy[p];
-            const float dx = c.x - r.mx, dy = c.y - r.my;
-            const float q = fmaf(dx, fmaf(k3, dx, fmaf(k4, dy, k1)), fmaf(dy, fmaf(k5, dy, k2), k0));
-            float* sp = su + p + (p >> 5);   // upad(ch, p) = sp + ch * (kTilePix + kTilePix / 32)
-            atomicAdd(sp, fmaf(pe.x, t.dr, pe.y * q));
-            atomicAdd(sp + (kTilePix + kTilePix / 32), fmaf(pe.x, t.dg, pe.z * q));
-            atomicAdd(sp + 2 * (kTilePix + kTilePix / 32), fmaf(pe.x, t.db, pe.w * q));
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
   const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
-  // Epilogue: u = w (dc/dx) p with the residual-to-pixel weights (1 without
-  // them); for the predicted decrease, per-tile sums of e.u (Fadd holds e, or F
-  // for L2) and w.u^2, where u is the unweighted (dc/dx) p.
   double local = 0.0, local2 = 0.0;
   if (x < cam.W && y < cam.H) {
     const long long pix = cam.pix_off + (long long)y * cam.W + x;
     const int p = threadIdx.x;
-    const float u0 = su[upad(0, p)], u1 = su[upad(1, p)], u2 = su[upad(2, p)];
+    float u0, u1, u2;
+    if constexpr (kMode == 1) {
+      u0 = u1 = u2 = 0.f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        u0 += su[w * (3 * kTilePix) + p];
+        u1 += su[w * (3 * kTilePix) + kTilePix + p];
+        u2 += su[w * (3 * kTilePix) + 2 * kTilePix + p];
+      }
+    } else {
+      u0 = su[upad(0, p)];
+      u1 = su[upad(1, p)];
+      u2 = su[upad(2, p)];
+    }
     float w0 = 1.f, w1 = 1.f, w2 = 1.f;
     if (cv.wres != nullptr) {
       w0 = cv.wres[pix * 3 + 0];
@@ -304,25 +247,124 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
   }
 }
 
+// kMode 0: one tile of u accumulated with shared-memory atomics. kMode 1 (G =
+// 32 only): a warp works on one segment at a time, whose entries are distinct
+// pixels, so each warp adds into its own copy of the tile with plain
+// read-modify-writes and the copies are summed in the epilogue.
+template <int kFmt, int G, int U, int kMode>
+__device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, const float* __restrict__ ydot,
+                                             const float* __restrict__ Fadd, float* __restrict__ u,
+                                             double* __restrict__ sq_partials, float* su, const float2* sxy,
+                                             double* dred, unsigned int* next_seg, StageRec& S, StageT& T) {
+  static_assert(G == 8 || G == 16 || G == 32, "group size");
+  static_assert(kMode == 0 || G == 32, "private tiles need one segment per warp");
+  constexpr int kGPW = 32 / G;
+  const int v = find_view(cv.cams, cv.V, tile);
+  const DevCam& cam = cv.cams[v];
+  const int lt = tile - cam.tile_off;
+  const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane & (G - 1), grp = lane / G;
+  const uint32_t g0 = cv.tile_seg_off[tile];
+  const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
+  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
+    const int cnt = (int)min((uint32_t)kStage, n - c0);
+    stage_chunk<true>(cv, g0 + c0, cnt, S, &T, ydot, nullptr);
+    if (threadIdx.x == 0) *next_seg = 0;
+    __syncthreads();
+    for (;;) {
+      uint32_t kb = 0;
+      if (lane == 0) kb = atomicAdd(next_seg, (unsigned)kGPW);
+      kb = __shfl_sync(kFull, kb, 0);
+      if (kb >= (uint32_t)cnt) break;
+      const uint32_t k = kb + grp;
+      const bool has = k < (uint32_t)cnt;
+      SegRec r;
+      Tangent t;
+      uint32_t len = 0;
+      if (has) {
+        r = rec_from(S.r0[k], S.r1[k], S.r2[k]);
+        const float4 y0 = T.t0[k], y1 = T.t1[k];
+        const float y2x = T.t2[k];
+        t.dmx = y0.x;
+        t.dmy = y0.y;
+        t.dA = y0.z;
+        t.dB = y0.w;
+        t.dC = y1.x;
+        t.od = y1.y * r.io;
+        t.dr = y1.z;
+        t.dg = y1.w;
+        t.db = y2x;
+        len = (uint32_t)(r.e1 - r.e0);
+      }
+      const uint32_t mlen = warp_max_groups<G>(len);
+      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + (has ? r.e0 : 0);
+      const uint8_t* po = cv.pixoff + (has ? r.e0 : 0);
+      // the tangent of the blending exponent is a quadratic in (dx, dy) per
+      // segment: q = k0 + dx (k1 + k3 dx + k4 dy) + dy (k2 + k5 dy)
+      const float k1 = r.A * t.dmx + r.B * t.dmy, k2 = r.B * t.dmx + r.C * t.dmy;
+      const float k3 = -0.5f * t.dA, k4 = -t.dB, k5 = -0.5f * t.dC, k0 = t.od;
+      for (uint32_t base = 0; base < mlen; base += G * U) {
+        typename Raw<kFmt>::T raw[U];
+        int pp[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          const uint32_t i = base + gl + G * j;
+          if (i < len) {
+            raw[j] = __ldcs(pl + i);
+            pp[j] = po[i];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          const uint32_t i = base + gl + G * j;
+          if (i < len) {
+            const int p = pp[j];
+            const float4 pe = decode<kFmt>(raw[j], r.scale);
+            const float2 c = sxy[p];
+            const float dx = c.x - r.mx, dy = c.y - r.my;
+            const float q = fmaf(dx, fmaf(k3, dx, fmaf(k4, dy, k1)), fmaf(dy, fmaf(k5, dy, k2), k0));
+            const float v0 = fmaf(pe.x, t.dr, pe.y * q), v1 = fmaf(pe.x, t.dg, pe.z * q);
+            const float v2 = fmaf(pe.x, t.db, pe.w * q);
+            if constexpr (kMode == 1) {   // the warp's own unpadded planes [ch][p]
+              float* sp = su + warp * (3 * kTilePix) + p;
+              sp[0] += v0;
+              sp[kTilePix] += v1;
+              sp[2 * kTilePix] += v2;
+            } else {   // upad(ch, p) = sp + ch * (kTilePix + kTilePix / 32)
+              float* sp = su + p + (p >> 5);
+              atomicAdd(sp, v0);
+              atomicAdd(sp + (kTilePix + kTilePix / 32), v1);
+              atomicAdd(sp + 2 * (kTilePix + kTilePix / 32), v2);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  apply_J_epilogue<kMode>(cv, tile, cam, tx, ty, su, Fadd, u, sq_partials, dred);
+}
+
 #define APPLY_J_SHARED                                   \
-  __shared__ float su[3 * (kTilePix + kTilePix / 32)];   \
+  __shared__ float su[kMode ? kWarps * 3 * kTilePix : kPlane3];   \
   __shared__ float2 sxy[kTilePix];                       \
   __shared__ double dred[2 * kWarps];                    \
   __shared__ unsigned int next_seg;                      \
-  __shared__ Stage S;                                    \
+  __shared__ StageRec S;                                 \
   __shared__ StageT T;                                   \
   sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
 
-template <int kFmt, int G, int U, int kMinBlocks>
+template <int kFmt, int G, int U, int kMinBlocks, int kMode>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, const float* __restrict__ ydot,
                                                                   const float* __restrict__ Fadd,
                                                                   float* __restrict__ u,
                                                                   double* __restrict__ sq_partials) {
   if (cv.skip != nullptr && *cv.skip) return;
   APPLY_J_SHARED
-  for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
+  for (int i = threadIdx.x; i < (kMode ? kWarps * 3 * kTilePix : kPlane3); i += kTilePix) su[i] = 0.f;
   __syncthreads();
-  apply_J_tile<kFmt, G, U>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg, S, T);
+  apply_J_tile<kFmt, G, U, kMode>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg, S, T);
 }
 
 // Subset of a global tile index of a batch.
@@ -334,12 +376,12 @@ __device__ __forceinline__ int batch_subset(const TileBatch& tb, long long gt) {
 
 // Persistent J p over every subset of a batch: each CTA takes tiles from the
 // batch's queue until all are done (tiles of finished solves are skipped).
-template <int kFmt, int G, int U, int kMinBlocks>
+template <int kFmt, int G, int U, int kMinBlocks, int kMode>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J_batch(const __grid_constant__ TileBatch tb) {
   APPLY_J_SHARED
   __shared__ long long s_tile;
   for (;;) {
-    for (int i = threadIdx.x; i < 3 * (kTilePix + kTilePix / 32); i += kTilePix) su[i] = 0.f;
+    for (int i = threadIdx.x; i < (kMode ? kWarps * 3 * kTilePix : kPlane3); i += kTilePix) su[i] = 0.f;
     if (threadIdx.x == 0) s_tile = (long long)atomicAdd(tb.queue, 1u);
     __syncthreads();
     const long long gt = s_tile;
@@ -347,7 +389,7 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J_batch(const __
     const int b = batch_subset(tb, gt);
     const CacheView& cv = tb.v[b];
     if (cv.skip == nullptr || *cv.skip == 0)
-      apply_J_tile<kFmt, G, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
+      apply_J_tile<kFmt, G, U, kMode>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
                                nullptr, su, sxy, dred, &next_seg, S, T);
     __syncthreads();
   }
@@ -428,7 +470,7 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
   const int gl = lane & (G - 1), grp = lane / G;
   for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
     const int cnt = (int)min((uint32_t)kStage, n - c0);
-    stage_chunk<false>(cv, g0 + c0, cnt, S, nullptr, nullptr);
+    stage_chunk<false>(cv, g0 + c0, cnt, S, nullptr, nullptr, S.pos);
     if (threadIdx.x == 0) *next_seg = 0;
     __syncthreads();
     for (;;) {
@@ -645,10 +687,11 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
 // Variants: lanes per segment (G), entries each lane keeps in flight (U) and
 // the minimum number of resident 256-thread blocks per SM the registers must
 // allow: 0 = (16, 2, 6), 1 = (16, 4, 5), 2 = (32, 2, 6), 3 = (32, 4, 4),
-// 4 = (8, 2, 6).
-template <int kFmt, int G, int U, int B>
+// 4 = (8, 2, 6); 5 = J p with per-warp private tiles (32, 2, 4) and J^T u
+// (16, 4, 4).
+template <int kFmt, int G, int U, int B, int kMode = 0>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
-  k_apply_J<kFmt, G, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
+  k_apply_J<kFmt, G, U, B, kMode><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
   note_launch();
   return cudaGetLastError();
 }
@@ -660,9 +703,9 @@ cudaError_t run_JT(const CacheView& cv, const float* u, float* seg_ybar, cudaStr
   return cudaGetLastError();
 }
 
-template <int kFmt, int G, int U, int B>
+template <int kFmt, int G, int U, int B, int kMode = 0>
 cudaError_t run_J_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
-  k_apply_J_batch<kFmt, G, U, B><<<ctas, kTilePix, 0, st>>>(tb);
+  k_apply_J_batch<kFmt, G, U, B, kMode><<<ctas, kTilePix, 0, st>>>(tb);
   note_launch();
   return cudaGetLastError();
 }
@@ -681,6 +724,7 @@ cudaError_t apply_J_batch_variant(int variant, const TileBatch& tb, int ctas, cu
     case 1: return run_J_batch<kFmt, 16, 4, 5>(tb, ctas, st);
     case 2: return run_J_batch<kFmt, 32, 2, 6>(tb, ctas, st);
     case 3: return run_J_batch<kFmt, 32, 4, 4>(tb, ctas, st);
+    case 5: return run_J_batch<kFmt, 32, 2, 4, 1>(tb, ctas, st);
     default: return run_J_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -692,6 +736,7 @@ cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, c
     case 1: return run_JT_batch<kFmt, 16, 4, 5>(tb, ctas, st);
     case 2: return run_JT_batch<kFmt, 32, 2, 6>(tb, ctas, st);
     case 3: return run_JT_batch<kFmt, 32, 4, 4>(tb, ctas, st);
+    case 5: return run_JT_batch<kFmt, 16, 4, 4>(tb, ctas, st);
     default: return run_JT_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -704,6 +749,7 @@ cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot,
     case 1: return run_J<kFmt, 16, 4, 5>(cv, ydot, F_add, u, sq, st);
     case 2: return run_J<kFmt, 32, 2, 6>(cv, ydot, F_add, u, sq, st);
     case 3: return run_J<kFmt, 32, 4, 4>(cv, ydot, F_add, u, sq, st);
+    case 5: return run_J<kFmt, 32, 2, 4, 1>(cv, ydot, F_add, u, sq, st);
     default: return run_J<kFmt, 8, 2, 6>(cv, ydot, F_add, u, sq, st);
   }
 }
@@ -715,6 +761,7 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
     case 1: return run_JT<kFmt, 16, 4, 5>(cv, u, seg_ybar, st);
     case 2: return run_JT<kFmt, 32, 2, 6>(cv, u, seg_ybar, st);
     case 3: return run_JT<kFmt, 32, 4, 4>(cv, u, seg_ybar, st);
+    case 5: return run_JT<kFmt, 16, 4, 4>(cv, u, seg_ybar, st);
     default: return run_JT<kFmt, 8, 2, 6>(cv, u, seg_ybar, st);
   }
 }
@@ -723,7 +770,7 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
 
 int apply_J_partials(const CacheView& cv) { return cv.n_tiles; }
 
-int apply_variants() { return 5; }
+int apply_variants() { return 6; }
 
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add, float* u,
                            double* sq_partials, int variant, cudaStream_t st) {
@@ -751,10 +798,10 @@ int device_sm_count() {
 }
 
 // Resident CTAs of a persistent grid: never more than the kernel variant's
-// register budget lets share an SM (6, 5, 6, 4, 6 for variants 0..4), never
-// more CTAs than tiles.
+// register and shared-memory budget lets share an SM (6, 5, 6, 4, 6, 4 for
+// variants 0..5), never more CTAs than tiles.
 static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
-  const int cap = variant == 1 ? 5 : variant == 3 ? 4 : 6;
+  const int cap = variant_cta_cap(variant);
   const int per = ctas_per_sm < 1 ? 1 : (ctas_per_sm > cap ? cap : ctas_per_sm);
   const long long c = (long long)device_sm_count() * per;
   return (int)(c < tb.total_tiles ? c : tb.total_tiles);
