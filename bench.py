@@ -436,13 +436,25 @@ def summarize_phases(stats) -> dict:
     return out
 
 
-def pair_roofline(stats, peak: dict) -> dict:
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) per
+# algorithmic byte of the J p + J^T u pair (tangent, tile kernels, per-splat sums,
+# adjoint) on the 100k-Gaussian, 8-view case, by cache format. The pair's traffic
+# grows with its entries, pixels and splats, so a full launch's traffic is this
+# ratio times its algorithmic bytes.
+PAIR_DRAM_PER_ALG_BYTE = {0: 1.129, 1: 1.216}   # FP32, BF16
+
+
+def pair_roofline(stats, peak: dict, fmt: int = None) -> dict:
     t = sum(s.ms_phase[2] + s.ms_phase[3] + s.ms_phase[4] + s.ms_phase[5] for s in stats) / 1e3
     b = sum(s.pair_bytes for s in stats)
     n = sum(s.n_pairs for s in stats)
     gbs = b / t / 1e9 if t > 0 else 0.0
+    ratio = PAIR_DRAM_PER_ALG_BYTE.get(fmt)
     return {"bound": "hbm", "achieved": gbs, "peak": peak["hbm_gbs"], "unit": "GB/s",
-            "frac": gbs / peak["hbm_gbs"], "traffic": None,
+            "frac": gbs / peak["hbm_gbs"],
+            "traffic": ratio * b / max(n, 1) if ratio is not None else None,
+            "traffic_note": ("DRAM bytes per pair: ncu dram read + write per algorithmic byte on the 100k-Gaussian "
+                             "case, scaled by this pair's algorithmic bytes" if ratio is not None else None),
             "kernel": "J p + J^T u pair: tangent, apply_J, apply_JT, adjoint kernels",
             "algorithmic_bytes_per_pair": b / max(n, 1), "ms_per_pair": t * 1e3 / max(n, 1),
             "peak_source": peak["source"] + " (MEASURED_PEAKS.json hbm_gbs)" if peak["source"] == "measured"
@@ -644,7 +656,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(args, f"chosen: {ch['fmt']} cache, {pre}, batched subsets in one CUDA graph"),
                        cache_fmt=ch["fmt"]),
-        "roofline": pair_roofline(ch["prof"], peak),
+        "roofline": pair_roofline(ch["prof"], peak, g.CACHE_FMT[ch["fmt"]]),
         "e2e": result.get("e2e"),
         "clocks": ch["clocks"],
         "gpu_launches": ch["launches"] // max(args.steps, 1),
@@ -666,7 +678,7 @@ def run_ours(args):
     }
     if "plain" in result:
         pl = result["plain"]
-        line["plain_fp32"] = {"ms_per_step": pl["ms"], "roofline": pair_roofline(pl["stats"], peak),
+        line["plain_fp32"] = {"ms_per_step": pl["ms"], "roofline": pair_roofline(pl["stats"], peak, 0),
                               "autotune": pl["autotune"],
                               "phase_ms": summarize_phases(pl["stats"]),
                               "cache_gb": statistics.mean(s.cache_bytes for s in pl["stats"]) / 1e9}
