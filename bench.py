@@ -77,7 +77,7 @@ def parse_args(argv=None):
                     help="kernel mode: one cache of the first --apply-views cameras, then one J^T u and one J p "
                          "(for ncu captures); with --sweep, every kernel variant timed")
     ap.add_argument("--apply-views", type=int, default=8)
-    ap.add_argument("--apply-variant", type=int, default=3, help="1..6: forced apply kernel variant 0..5")
+    ap.add_argument("--apply-variant", type=int, default=3, help="1..8: forced apply kernel variant 0..7")
     ap.add_argument("--sweep", action="store_true")
     return ap.parse_args(argv)
 
@@ -656,7 +656,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(args, f"chosen: {ch['fmt']} cache, {pre}, batched subsets in one CUDA graph"),
                        cache_fmt=ch["fmt"]),
-        "roofline": pair_roofline(ch["prof"], peak, g.CACHE_FMT[ch["fmt"]]),
+        "roofline": pair_roofline(ch["prof"], peak, {"fp32": 0, "bf16": 1, "fp16s": 2}.get(ch["fmt"])),
         "e2e": result.get("e2e"),
         "clocks": ch["clocks"],
         "gpu_launches": ch["launches"] // max(args.steps, 1),
@@ -742,7 +742,7 @@ def run_apply_pass(args):
            "device_free_gb": free_b / 1e9, "device_total_gb": total_b / 1e9}
     if args.sweep:
         pay = 16 if args.cache_fmt == "fp32" else 8
-        for v in range(1, 7):
+        for v in range(1, 9):
             ctx.set_options(apply_variant=v)
             for name, call in (("J", lambda: ctx.apply_J(cache, p, uo)), ("JT", lambda: ctx.apply_JT(cache, u, gout))):
                 ts = []

@@ -493,7 +493,7 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
 
 // Candidates of the persistent tile kernels' autotuner: (variant, CTAs per SM),
 // each variant at the residency its registers allow and one CTA fewer.
-constexpr int kBatchCand = 12;
+constexpr int kBatchCand = 16;
 inline int cand_variant(int c) { return c / 2; }
 inline int cand_ctas(int c) {
   const int cap = variant_cta_cap(c / 2);
@@ -891,7 +891,7 @@ static gslm_status validate_opts(const gslm_options* o) {
   if (!(o->lambda_min > 0.f) || !(o->lambda_max >= o->lambda_min)) return GSLM_E_INVALID;
   if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
   if (o->batch_ctas < 0 || o->batch_ctas > 6) return GSLM_E_INVALID;
-  if (o->apply_variant < 0 || o->apply_variant > 6) return GSLM_E_INVALID;
+  if (o->apply_variant < 0 || o->apply_variant > 8) return GSLM_E_INVALID;
   if (o->line_search < 0 || o->line_search > 60) return GSLM_E_INVALID;
   if (o->objective != GSLM_OBJ_L2 && o->objective != GSLM_OBJ_L1_SSIM) return GSLM_E_INVALID;
   if (!(o->lambda_l1 >= 0.f) || !(o->lambda_ssim >= 0.f) || !(o->res_eps > 0.f) || !std::isfinite(o->lambda_l1) ||

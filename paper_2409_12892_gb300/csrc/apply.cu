@@ -688,7 +688,9 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
 // the minimum number of resident 256-thread blocks per SM the registers must
 // allow: 0 = (16, 2, 6), 1 = (16, 4, 5), 2 = (32, 2, 6), 3 = (32, 4, 4),
 // 4 = (8, 2, 6); 5 = J p with per-warp private tiles (32, 2, 4) and J^T u
-// (16, 4, 4).
+// (16, 4, 4); 6 = J p private tiles (32, 3, 4) and J^T u (32, 3, 4); 7 = J p
+// (32, 3, 6) and J^T u (16, 3, 6). U = 3 fills a 94-entry segment (the paper
+// workload's mean) with 96 lane slots at G = 32 or 2 x 48 at G = 16.
 template <int kFmt, int G, int U, int B, int kMode = 0>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
   k_apply_J<kFmt, G, U, B, kMode><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
@@ -725,6 +727,8 @@ cudaError_t apply_J_batch_variant(int variant, const TileBatch& tb, int ctas, cu
     case 2: return run_J_batch<kFmt, 32, 2, 6>(tb, ctas, st);
     case 3: return run_J_batch<kFmt, 32, 4, 4>(tb, ctas, st);
     case 5: return run_J_batch<kFmt, 32, 2, 4, 1>(tb, ctas, st);
+    case 6: return run_J_batch<kFmt, 32, 3, 4, 1>(tb, ctas, st);
+    case 7: return run_J_batch<kFmt, 32, 3, 6>(tb, ctas, st);
     default: return run_J_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -737,6 +741,8 @@ cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, c
     case 2: return run_JT_batch<kFmt, 32, 2, 6>(tb, ctas, st);
     case 3: return run_JT_batch<kFmt, 32, 4, 4>(tb, ctas, st);
     case 5: return run_JT_batch<kFmt, 16, 4, 4>(tb, ctas, st);
+    case 6: return run_JT_batch<kFmt, 32, 3, 4>(tb, ctas, st);
+    case 7: return run_JT_batch<kFmt, 16, 3, 6>(tb, ctas, st);
     default: return run_JT_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -750,6 +756,8 @@ cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot,
     case 2: return run_J<kFmt, 32, 2, 6>(cv, ydot, F_add, u, sq, st);
     case 3: return run_J<kFmt, 32, 4, 4>(cv, ydot, F_add, u, sq, st);
     case 5: return run_J<kFmt, 32, 2, 4, 1>(cv, ydot, F_add, u, sq, st);
+    case 6: return run_J<kFmt, 32, 3, 4, 1>(cv, ydot, F_add, u, sq, st);
+    case 7: return run_J<kFmt, 32, 3, 6>(cv, ydot, F_add, u, sq, st);
     default: return run_J<kFmt, 8, 2, 6>(cv, ydot, F_add, u, sq, st);
   }
 }
@@ -762,6 +770,8 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
     case 2: return run_JT<kFmt, 32, 2, 6>(cv, u, seg_ybar, st);
     case 3: return run_JT<kFmt, 32, 4, 4>(cv, u, seg_ybar, st);
     case 5: return run_JT<kFmt, 16, 4, 4>(cv, u, seg_ybar, st);
+    case 6: return run_JT<kFmt, 32, 3, 4>(cv, u, seg_ybar, st);
+    case 7: return run_JT<kFmt, 16, 3, 6>(cv, u, seg_ybar, st);
     default: return run_JT<kFmt, 8, 2, 6>(cv, u, seg_ybar, st);
   }
 }
@@ -770,7 +780,7 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
 
 int apply_J_partials(const CacheView& cv) { return cv.n_tiles; }
 
-int apply_variants() { return 6; }
+int apply_variants() { return 8; }
 
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add, float* u,
                            double* sq_partials, int variant, cudaStream_t st) {
@@ -798,8 +808,8 @@ int device_sm_count() {
 }
 
 // Resident CTAs of a persistent grid: never more than the kernel variant's
-// register and shared-memory budget lets share an SM (6, 5, 6, 4, 6, 4 for
-// variants 0..5), never more CTAs than tiles.
+// register and shared-memory budget lets share an SM (6, 5, 6, 4, 6, 4, 4, 6
+// for variants 0..7), never more CTAs than tiles.
 static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
   const int cap = variant_cta_cap(variant);
   const int per = ctas_per_sm < 1 ? 1 : (ctas_per_sm > cap ? cap : ctas_per_sm);
