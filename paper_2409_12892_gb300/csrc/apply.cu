@@ -531,6 +531,25 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
       group_sum16<G>(a, lane);
       // moment i: m0 = sum s, m1 = sum s dx, m2 = sum s dy, m3 = sum s dx^2,
       // m4 = sum s dx dy, m5 = sum s dy^2, m6..m8 = sum w u
+      if constexpr (G == 16) {
+        // lane o of the group holds moment o: output o needs moment o (6..8), its
+        // neighbour's (0..4) and moments 0 and 2 (three shuffles in all)
+        const float mo = a[0];
+        const float mn = __shfl_down_sync(kFull, mo, 1, 16);
+        const float m0 = __shfl_sync(kFull, mo, 0, 16);
+        const float m2 = __shfl_sync(kFull, mo, 2, 16);
+        if (has && gl < 9) {
+          float val = mo;
+          if (gl == 0) val = r.A * mn + r.B * m2;
+          else if (gl == 1) val = r.B * mo + r.C * mn;
+          else if (gl == 2) val = -0.5f * mn;
+          else if (gl == 3) val = -mn;
+          else if (gl == 4) val = -0.5f * mn;
+          else if (gl == 5) val = m0 * r.io;
+          seg_ybar[(size_t)S.pos[k] * 12 + gl] = val;
+        }
+        continue;
+      }
       float m[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) m[i] = group_moment<G>(a, i);
@@ -689,7 +708,7 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
 // allow: 0 = (16, 2, 6), 1 = (16, 4, 5), 2 = (32, 2, 6), 3 = (32, 4, 4),
 // 4 = (8, 2, 6); 5 = J p with per-warp private tiles (32, 2, 4) and J^T u
 // (16, 4, 4); 6 = J p private tiles (32, 3, 4) and J^T u (32, 3, 4); 7 = J p
-// (32, 3, 6) and J^T u (16, 3, 6). U = 3 fills a 94-entry segment (the paper
+// (32, 3, 6) and J^T u (16, 3, 5). U = 3 fills a 94-entry segment (the paper
 // workload's mean) with 96 lane slots at G = 32 or 2 x 48 at G = 16.
 template <int kFmt, int G, int U, int B, int kMode = 0>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
@@ -742,7 +761,7 @@ cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, c
     case 3: return run_JT_batch<kFmt, 32, 4, 4>(tb, ctas, st);
     case 5: return run_JT_batch<kFmt, 16, 4, 4>(tb, ctas, st);
     case 6: return run_JT_batch<kFmt, 32, 3, 4>(tb, ctas, st);
-    case 7: return run_JT_batch<kFmt, 16, 3, 6>(tb, ctas, st);
+    case 7: return run_JT_batch<kFmt, 16, 3, 5>(tb, ctas, st);
     default: return run_JT_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -771,7 +790,7 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
     case 3: return run_JT<kFmt, 32, 4, 4>(cv, u, seg_ybar, st);
     case 5: return run_JT<kFmt, 16, 4, 4>(cv, u, seg_ybar, st);
     case 6: return run_JT<kFmt, 32, 3, 4>(cv, u, seg_ybar, st);
-    case 7: return run_JT<kFmt, 16, 3, 6>(cv, u, seg_ybar, st);
+    case 7: return run_JT<kFmt, 16, 3, 5>(cv, u, seg_ybar, st);
     default: return run_JT<kFmt, 8, 2, 6>(cv, u, seg_ybar, st);
   }
 }
