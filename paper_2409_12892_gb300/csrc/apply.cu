@@ -441,7 +441,7 @@ __device__ __forceinline__ float group_moment(const float (&v)[16], int i) {
 }
 
 // J^T u over one tile into per-segment partials, stored at each segment's
-// slot-order position (so the adjoint kernel reads a splat's partials as one
+// splat-order position (so the adjoint kernel reads a splat's partials as one
 // contiguous range). The caller synchronises before. su4 / sxy are filled here.
 template <int kFmt, int G, int U>
 __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, const float* __restrict__ u,
