@@ -252,7 +252,10 @@ def run_steps(g, ctx, params, N, cams, targets, wl, steps: int, warmup: int, dis
 def run_e2e(g, ctx, P_host, N, ld, cams, targets, wl, steps: int, warmup: int, dist):
     """The same step through the C ABI from pinned host buffers: each step copies
     the parameters and the targets of its views (one copy per view) to the
-    device, runs the LM step and copies the parameters back."""
+    device, runs the LM step and copies the parameters back. The targets of step
+    s + 1 are copied on a second stream while step s runs (two device buffers,
+    ordered by events); the parameters go up before and come back after each
+    step on the step's own stream."""
     import numpy as np
     import torch
     import synth
@@ -262,29 +265,52 @@ def run_e2e(g, ctx, P_host, N, ld, cams, targets, wl, steps: int, warmup: int, d
     offs = np.cumsum([0] + [c.width * c.height for c in cams])
     d_params = torch.empty_like(h_params, device=dev)
     st = torch.cuda.current_stream()
+    cp = torch.cuda.Stream(device=dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lam, h2d, d2h = wl.lambda0, 0, 0
-    d_t = None
-    for s in range(warmup + steps):
+
+    def plan(s):
         subsets = synth.subset_views(wl, s)
         views = [v for sub in subsets for v in sub]
         remap = {v: i for i, v in enumerate(views)}
-        cc = [cams[v] for v in views]
-        subs = [[remap[v] for v in sub] for sub in subsets]
-        npx = int(sum(offs[v + 1] - offs[v] for v in views))
-        if d_t is None or d_t.shape[0] < npx:
-            d_t = torch.empty((npx, 3), dtype=torch.float32, device=dev)
+        return views, [cams[v] for v in views], [[remap[v] for v in sub] for sub in subsets], \
+            int(sum(offs[v + 1] - offs[v] for v in views))
+
+    plans = [plan(s) for s in range(warmup + steps)]
+    npx_max = max(p[3] for p in plans)
+    bufs = [torch.empty((npx_max, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+    free = [torch.cuda.Event(), torch.cuda.Event()]     # the step that read the buffer has finished
+    ready = [torch.cuda.Event(), torch.cuda.Event()]    # the buffer holds its step's targets
+
+    def upload(s):
+        views, _, _, _ = plans[s]
+        k = s % 2
+        with torch.cuda.stream(cp):
+            cp.wait_event(free[k])
+            o = 0
+            for v in views:
+                n = int(offs[v + 1] - offs[v])
+                bufs[k][o:o + n].copy_(h_targets[offs[v]:offs[v + 1]], non_blocking=True)
+                o += n
+            ready[k].record(cp)
+
+    for k in range(2):
+        free[k].record(st)
+    for s in range(warmup + steps):
         if s == warmup:
             barrier(dist)
             torch.cuda.synchronize()
             ev0.record(st)
+        if s == 0 or s == warmup:     # the timed region copies its own first targets
+            upload(s)
+        views, cc, subs, npx = plans[s]
+        k = s % 2
         d_params.copy_(h_params, non_blocking=True)
-        o = 0
-        for v in views:
-            n = int(offs[v + 1] - offs[v])
-            d_t[o:o + n].copy_(h_targets[offs[v]:offs[v + 1]], non_blocking=True)
-            o += n
-        state, _ = ctx.lm_step(d_params, N, cc, d_t[:npx], subs, lam, s)
+        st.wait_event(ready[k])
+        if s + 1 < warmup + steps and s + 1 != warmup:
+            upload(s + 1)
+        state, _ = ctx.lm_step(d_params, N, cc, bufs[k][:npx], subs, lam, s)
+        free[k].record(st)
         lam = state.lambda_
         h_params.copy_(d_params, non_blocking=True)
         if s >= warmup:
