@@ -1,0 +1,78 @@
+"""Precision of the cache formats at the paper scale (GPU only): the FP32, BF16
+and FP16-with-scale caches against the FP64 oracle on a 2k-Gaussian crop of
+the 1.5M-Gaussian scene (the 2,000 Gaussians of cluster 0 nearest its mean,
+seen by the first 4 views of LM step 0's first subset at 1264x832).
+
+Reported and bounded per format: J p and J^T u (relative L2 over pixels with no
+blending decision near a threshold; J^T u for a u supported on those pixels),
+diag(J^T J), and x after the 8 PCG iterations of the paper's setting (Jacobi,
+lambda = 1e-3). The J p / J^T u bounds are those of the tiny-case tests (FP32
+1e-4, BF16 2e-2, FP16 with scale 5e-3); PCG x for FP32 is held to the 1e-3
+PCG tolerance, for the 16-bit caches to 5e-2 (the solve amplifies the product
+errors: x0 = M^-1 b overshoots and r0 = b - A x0 cancels).
+"""
+import numpy as np
+import pytest
+
+import synth
+from common import N_PARAMS, pixel_mask, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+BOUNDS = {"fp32": (1e-4, 1e-3), "bf16": (2e-2, 5e-2), "fp16s": (5e-3, 5e-2)}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_12892_gb300 import build
+    build.build()
+    import paper_2409_12892_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def crop():
+    from oracle import jacobian as J, solver
+    wl = synth.WORKLOADS["paper"]
+    P = synth.make_gaussians(wl)
+    cams = synth.make_cameras(wl)
+    idx = synth.crop_2k(wl, P, 2000)
+    views = synth.subset_views(wl, 0)[0][:4]
+    Pc = P[idx]
+    cc = [cams[i] for i in views]
+    tgt = J.render(synth.perturbed_copy(wl, P)[idx].astype(np.float64), cc).astype(np.float32)
+    sys_ = solver.build_subset(Pc.astype(np.float64), cc, tgt.astype(np.float64))
+    x_ref, _ = solver.solve_subset(sys_, wl.lambda0, wl.pcg_iters)
+    return wl, Pc, cc, tgt, sys_, x_ref
+
+
+@pytest.mark.parametrize("fmt", ["fp32", "bf16", "fp16s"])
+def test_cache_format_precision_on_the_paper_crop(lib, crop, fmt):
+    from oracle import jacobian as J
+    wl, P, cams, tgt, sys_, x_ref = crop
+    N = P.shape[0]
+    n_res = J.n_residuals(cams)
+    mask = np.repeat(pixel_mask(sys_.lin), 3)
+    assert mask.mean() > 0.98
+    ctx = lib.Context(cache_fmt=fmt, n_iters=wl.pcg_iters, break_rel2=0.0)
+    cache = ctx.build_cache(lib.to_soa(P), N, cams, torch.from_numpy(tgt).cuda().view(-1, 3))
+    p = synth.random_vector(21, (N, N_PARAMS))
+    u = np.where(mask, synth.random_vector(22, n_res), 0.0).astype(np.float32)
+    Jp = ctx.apply_J(cache, lib.to_soa(p)).cpu().numpy().ravel()
+    JTu = lib.from_soa(ctx.apply_JT(cache, torch.from_numpy(u).cuda().view(-1, 3)), N)
+    e_J = rel_l2(Jp[mask], J.apply_J(sys_.lin, p.astype(np.float64), n_res)[mask])
+    e_JT = rel_l2(JTu, J.apply_JT(sys_.lin, u.astype(np.float64), N))
+    diag = ctx.jacobi_diag(cache)
+    e_d = rel_l2(lib.from_soa(diag, N), sys_.M)
+    x, st, _ = ctx.pcg_solve(cache, cache.b, diag, wl.lambda0)
+    e_x = rel_l2(lib.from_soa(x, N), x_ref)
+    print(f"{fmt}: entries {cache.info().entries}, J p {e_J:.2e}, J^T u {e_JT:.2e}, diag {e_d:.2e}, "
+          f"PCG x ({st.iters} iterations) {e_x:.2e}")
+    b_prod, b_x = BOUNDS[fmt]
+    assert e_J < b_prod and e_JT < b_prod and e_d < max(b_prod, 1e-4) * 2
+    assert st.iters == wl.pcg_iters and e_x < b_x
+    cache.free()
