@@ -58,3 +58,34 @@ def test_version_and_default_options_without_gpu(lib_path):
     lib.gslm_default_options(ctypes.byref(opt))
     assert opt.n_iters == 8 and abs(opt.break_rel2 - 0.01) < 1e-9 and opt.cache_fmt == 0
     assert abs(opt.lambda_min - 1e-4) < 1e-10 and abs(opt.lambda_max - 1e4) < 1e-3
+
+
+STRUCTS = {"gslm_options": "Options", "gslm_lm_stats": "LMStats", "gslm_cache_info": "CacheInfo",
+           "gslm_pcg_stats": "PcgStats", "gslm_camera": "Camera", "gslm_lm_state": "LMState"}
+
+
+def test_header_is_c99_and_struct_layouts_match_the_binding(tmp_path):
+    """The header compiles as plain C99, and every struct the binding mirrors has the
+    same size and field offsets in C and in ctypes (a mismatch would shift fields
+    silently across the ABI)."""
+    from paper_2409_12892_gb300 import gslm
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gslm.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS.items():
+        cls = getattr(gslm, pyname)
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, pyname in STRUCTS.items():
+        cls = getattr(gslm, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
