@@ -73,8 +73,8 @@ def test_header_is_c99_and_struct_layouts_match_the_binding(tmp_path):
     for cname, pyname in STRUCTS.items():
         cls = getattr(gslm, pyname)
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
-        for f in cls._fields_:
-            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+        for f in cls._fields_:   # a trailing underscore avoids a Python keyword (lambda)
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0].rstrip("_")}));')
     lines += ["  return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
