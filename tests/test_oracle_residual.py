@@ -190,3 +190,82 @@ def test_l1ssim_lm_step_pred_is_the_gauss_newton_model():
     E = lambda g: R.cost(J.render(P + g * res.delta, cams, smooth=True), tgt, cams, obj)
     h = 1e-6
     assert abs((E(h) - E(-h)) / (2 * h) - 2 * np.dot(sys_.F, u)) <= 1e-4 * abs(2 * np.dot(sys_.F, u))
+
+
+# ----------------------------------------------------------------------------- planted mistakes
+def _pins_fail(checks) -> bool:
+    """True if any of the given pin checks raises an AssertionError."""
+    for check in checks:
+        try:
+            check()
+        except AssertionError:
+            return True
+    return False
+
+
+def _centre_grad_pins():
+    for pix in [(0, 0, 0), (3, 7, 1), (8, 12, 2), (16, 22, 0), (10, 0, 2)]:
+        test_centre_gradient_matches_central_differences(pix)
+
+
+def _window_pins():
+    test_local_mean_of_a_constant_image_and_its_zero_padded_corner()
+    for pix in [(0, 0, 0), (0, 11, 1), (8, 12, 2), (16, 22, 0), (5, 1, 1)]:
+        test_ssim_map_matches_the_explicit_window(pix)
+
+
+def _mistaken_centre_grad(kind):
+    def grad(x, y):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        t = R.ssim_terms(x, y)
+        w0 = 1.0 if kind == "no_centre_weight" else R.window()[R.WINDOW // 2] ** 2
+        A1 = 2.0 * t.mu_x * t.mu_y + R.SSIM_C1
+        A2 = 2.0 * t.cov + R.SSIM_C2
+        B1 = t.mu_x ** 2 + t.mu_y ** 2 + R.SSIM_C1
+        B2 = t.var_x + t.var_y + R.SSIM_C2
+        dA1 = 2.0 * w0 * t.mu_y
+        dA2 = 2.0 * w0 * (y - t.mu_y)
+        dB1 = 2.0 * w0 * t.mu_x
+        dB2 = 2.0 * w0 * (x - t.mu_x) * (-1.0 if kind == "variance_sign" else 1.0)
+        if kind == "dropped_covariance":
+            dA2 = 0.0 * dA2
+        return (dA1 * A2 + A1 * dA2) / (B1 * B2) - t.ssim * (dB1 / B1 + dB2 / B2)
+    return grad
+
+
+@pytest.mark.parametrize("kind", ["no_centre_weight", "variance_sign", "dropped_covariance"])
+def test_planted_centre_gradient_mistakes_are_caught(monkeypatch, kind):
+    monkeypatch.setattr(R, "ssim_center_grad", _mistaken_centre_grad(kind))
+    assert _pins_fail([_centre_grad_pins, test_residual_derivatives_match_central_differences])
+
+
+@pytest.mark.parametrize("mode", ["reflect", "nearest"])
+def test_planted_padding_mistakes_are_caught(monkeypatch, mode):
+    from scipy import ndimage
+
+    def local_mean(img):
+        g = R.window()
+        out = ndimage.correlate1d(np.asarray(img, np.float64), g, axis=0, mode=mode)
+        return ndimage.correlate1d(out, g, axis=1, mode=mode)
+    monkeypatch.setattr(R, "local_mean", local_mean)
+    assert _pins_fail([_window_pins])
+
+
+def test_planted_residual_mistakes_are_caught(monkeypatch):
+    real = R.view_weights
+
+    def no_ssim_in_e(img, tgt, obj):
+        w = real(img, tgt, obj)
+        w.e = w.dr1 * w.r1               # the SSIM residual's share of J^T F dropped
+        return w
+    monkeypatch.setattr(R, "view_weights", no_ssim_in_e)
+    assert _pins_fail([test_residual_derivatives_match_central_differences])
+    monkeypatch.setattr(R, "view_weights", real)
+
+    def weights_not_squared(img, tgt, obj):
+        w = real(img, tgt, obj)
+        w.w = np.abs(w.dr1) + np.abs(w.dr2)   # sum of |dr/dc| instead of their squares
+        return w
+    monkeypatch.setattr(R, "view_weights", weights_not_squared)
+    assert _pins_fail([test_residual_derivatives_match_central_differences])
