@@ -117,10 +117,6 @@ __device__ __forceinline__ float4 decode(const typename Raw<kFmt>::T& r, float s
 // each lane keeping U entries in flight.
 constexpr int kStage = 256;
 
-struct Tangent {
-  float dmx, dmy, dA, dB, dC, od, dr, dg, db;
-};
-
 __device__ __forceinline__ SegRec rec_from(const uint4& a, const uint4& b, const uint4& c) {
   SegRec s;
   s.e0 = ((unsigned long long)a.y << 32) | a.x;
@@ -136,37 +132,76 @@ __device__ __forceinline__ SegRec rec_from(const uint4& a, const uint4& b, const
   return s;
 }
 
-// Shared staging area of one chunk of segments (records as three 16-byte
-// words each; splat tangents for J p).
-struct StageRec {
-  uint4 r0[kStage], r1[kStage], r2[kStage];
+// Both tile kernels take a pixel's position as its offset (x', y') from the
+// tile centre (7.5, 7.5) and fold the splat mean into per-segment constants,
+// so no entry spends instructions on the offset from the mean: with e = mean -
+// centre, the exponent tangent of J p is re-expanded in (x', y') and the
+// J^T u moments about the centre are shifted to the mean after the sums.
+constexpr float kTileCentre = 0.5f * (kTile - 1);
+
+// Shared staging of one chunk of segments for J p: what a lane reads, prepared
+// once per segment. The tangent of the blending exponent log(o G) is the
+// quadratic q = K0 + x' (K1 + K3 x' + K4 y') + y' (K2 + K5 y').
+struct StageJ {
+  uint4 w0[kStage];     // e0 (low, high word), entry count, FP16S scale
+  float4 w1[kStage];    // K0, K1, K2, K3
+  float4 w2[kStage];    // K4, K5, colour tangents dr, dg
+  float w3[kStage];     // colour tangent db
 };
-struct Stage : StageRec {
-  uint32_t pos[kStage];     // splat-order position of the segment (J^T u output)
-};
-struct StageT {             // the 9 floats of a splat tangent that J p reads
-  float4 t0[kStage], t1[kStage];
-  float t2[kStage];
+// For J^T u: the entry range read while streaming, and what the moments need
+// after the sums (read then, so it holds no registers during the stream).
+struct StageJT {
+  uint4 w0[kStage];     // e0 (low, high word), entry count, FP16S scale
+  float4 w1[kStage];    // e = mean - centre (x, y), conic A, B
+  float2 w2[kStage];    // conic C, 1 / opacity
+  uint32_t pos[kStage]; // splat-order position of the segment (output row)
 };
 
-// Stages segments [first, first + cnt) of the cache (and their tangents).
-template <bool kTangent>
-__device__ __forceinline__ void stage_chunk(const CacheView& cv, uint32_t first, int cnt, StageRec& S, StageT* T,
-                                            const float* __restrict__ ydot, uint32_t* pos) {
+__device__ __forceinline__ uint4 entry_word(const uint4& a, const uint4& c) {
+  return make_uint4(a.x, a.y, a.z - a.x, c.w);   // segments hold < 2^32 entries
+}
+
+// Stages segments [first, first + cnt) of the cache for J p; ydot holds the
+// splat tangents (12 floats per splat: dmx, dmy, dA, dB, dC, do, dr, dg, db).
+__device__ __forceinline__ void stage_chunk_J(const CacheView& cv, uint32_t first, int cnt, StageJ& S,
+                                              const float* __restrict__ ydot) {
   for (int t = threadIdx.x; t < cnt; t += kTilePix) {
     const uint4* q = reinterpret_cast<const uint4*>(cv.seg_rec + first + t);
     const uint4 a = q[0], b = q[1], c = q[2];
-    S.r0[t] = a;
-    S.r1[t] = b;
-    S.r2[t] = c;
-    if constexpr (!kTangent) pos[t] = cv.seg_pos[first + t];
-    if constexpr (kTangent) {
-      const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)b.x * 12);
-      T->t0[t] = yd[0];
-      T->t1[t] = yd[1];
-      T->t2[t] = ydot[(size_t)b.x * 12 + 8];
-    }
+    const SegRec r = rec_from(a, b, c);
+    const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)r.slot * 12);
+    const float4 y0 = yd[0], y1 = yd[1];
+    const float db = ydot[(size_t)r.slot * 12 + 8];
+    // q about the mean: k0 + dx (k1 + k3 dx + k4 dy) + dy (k2 + k5 dy)
+    const float k1 = r.A * y0.x + r.B * y0.y, k2 = r.B * y0.x + r.C * y0.y;
+    const float k3 = -0.5f * y0.z, k4 = -y0.w, k5 = -0.5f * y1.x, k0 = y1.y * r.io;
+    // with dx = x' - ex, dy = y' - ey
+    const float ex = r.mx - kTileCentre, ey = r.my - kTileCentre;
+    const float K1 = k1 - 2.f * k3 * ex - k4 * ey, K2 = k2 - 2.f * k5 * ey - k4 * ex;
+    const float K0 = k0 - ex * (k1 - k3 * ex - k4 * ey) - ey * (k2 - k5 * ey);
+    S.w0[t] = entry_word(a, c);
+    S.w1[t] = make_float4(K0, K1, K2, k3);
+    S.w2[t] = make_float4(k4, k5, y1.z, y1.w);
+    S.w3[t] = db;
   }
+}
+
+// Stages segments [first, first + cnt) of the cache for J^T u.
+__device__ __forceinline__ void stage_chunk_JT(const CacheView& cv, uint32_t first, int cnt, StageJT& S) {
+  for (int t = threadIdx.x; t < cnt; t += kTilePix) {
+    const uint4* q = reinterpret_cast<const uint4*>(cv.seg_rec + first + t);
+    const uint4 a = q[0], b = q[1], c = q[2];
+    const SegRec r = rec_from(a, b, c);
+    S.w0[t] = entry_word(a, c);
+    S.w1[t] = make_float4(r.mx - kTileCentre, r.my - kTileCentre, r.A, r.B);
+    S.w2[t] = make_float2(r.C, r.io);
+    S.pos[t] = cv.seg_pos[first + t];
+  }
+}
+
+// Pixel p's offset from the tile centre.
+__device__ __forceinline__ float2 centred_xy(int p) {
+  return make_float2((float)(p & (kTile - 1)) - kTileCentre, (float)(p / kTile) - kTileCentre);
 }
 
 // Largest value of v over the groups of G lanes of the warp (all lanes converged).
@@ -178,7 +213,8 @@ __device__ __forceinline__ uint32_t warp_max_groups(uint32_t v) {
 }
 
 // J p over one tile. su (u of the tile, padded planes) must be zero on entry;
-// sxy filled; the caller synchronises before.
+// sxy holds the pixels' offsets from the tile centre; the caller synchronises
+// before.
 // Epilogue of a J p tile: u = w (dc/dx) p with the residual-to-pixel weights
 // (1 without them); for the predicted decrease, per-tile sums of e.u (Fadd
 // holds e, or F for L2) and w.u^2, where u is the unweighted (dc/dx) p. The
@@ -255,7 +291,7 @@ template <int kFmt, int G, int U, int kMode>
 __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, const float* __restrict__ ydot,
                                              const float* __restrict__ Fadd, float* __restrict__ u,
                                              double* __restrict__ sq_partials, float* su, const float2* sxy,
-                                             double* dred, unsigned int* next_seg, StageRec& S, StageT& T) {
+                                             double* dred, unsigned int* next_seg, StageJ& S) {
   static_assert(G == 8 || G == 16 || G == 32, "group size");
   static_assert(kMode == 0 || G == 32, "private tiles need one segment per warp");
   constexpr int kGPW = 32 / G;
@@ -269,7 +305,7 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
   const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
   for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
     const int cnt = (int)min((uint32_t)kStage, n - c0);
-    stage_chunk<true>(cv, g0 + c0, cnt, S, &T, ydot, nullptr);
+    stage_chunk_J(cv, g0 + c0, cnt, S, ydot);
     if (threadIdx.x == 0) *next_seg = 0;
     __syncthreads();
     for (;;) {
@@ -279,31 +315,22 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
       if (kb >= (uint32_t)cnt) break;
       const uint32_t k = kb + grp;
       const bool has = k < (uint32_t)cnt;
-      SegRec r;
-      Tangent t;
-      uint32_t len = 0;
+      uint4 w0 = make_uint4(0u, 0u, 0u, 0u);
+      float4 w1 = make_float4(0.f, 0.f, 0.f, 0.f), w2 = w1;
+      float db = 0.f;
       if (has) {
-        r = rec_from(S.r0[k], S.r1[k], S.r2[k]);
-        const float4 y0 = T.t0[k], y1 = T.t1[k];
-        const float y2x = T.t2[k];
-        t.dmx = y0.x;
-        t.dmy = y0.y;
-        t.dA = y0.z;
-        t.dB = y0.w;
-        t.dC = y1.x;
-        t.od = y1.y * r.io;
-        t.dr = y1.z;
-        t.dg = y1.w;
-        t.db = y2x;
-        len = (uint32_t)(r.e1 - r.e0);
+        w0 = S.w0[k];
+        w1 = S.w1[k];
+        w2 = S.w2[k];
+        db = S.w3[k];
       }
+      const uint32_t len = w0.z;
+      const float scale = __uint_as_float(w0.w);
+      const unsigned long long e0 = ((unsigned long long)w0.y << 32) | w0.x;
+      const float K0 = w1.x, K1 = w1.y, K2 = w1.z, K3 = w1.w, K4 = w2.x, K5 = w2.y, dr = w2.z, dg = w2.w;
       const uint32_t mlen = warp_max_groups<G>(len);
-      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + (has ? r.e0 : 0);
-      const uint8_t* po = cv.pixoff + (has ? r.e0 : 0);
-      // the tangent of the blending exponent is a quadratic in (dx, dy) per
-      // segment: q = k0 + dx (k1 + k3 dx + k4 dy) + dy (k2 + k5 dy)
-      const float k1 = r.A * t.dmx + r.B * t.dmy, k2 = r.B * t.dmx + r.C * t.dmy;
-      const float k3 = -0.5f * t.dA, k4 = -t.dB, k5 = -0.5f * t.dC, k0 = t.od;
+      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + e0;
+      const uint8_t* po = cv.pixoff + e0;
       for (uint32_t base = 0; base < mlen; base += G * U) {
         typename Raw<kFmt>::T raw[U];
         int pp[U];
@@ -320,12 +347,11 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
           const uint32_t i = base + gl + G * j;
           if (i < len) {
             const int p = pp[j];
-            const float4 pe = decode<kFmt>(raw[j], r.scale);
+            const float4 pe = decode<kFmt>(raw[j], scale);
             const float2 c = sxy[p];
-            const float dx = c.x - r.mx, dy = c.y - r.my;
-            const float q = fmaf(dx, fmaf(k3, dx, fmaf(k4, dy, k1)), fmaf(dy, fmaf(k5, dy, k2), k0));
-            const float v0 = fmaf(pe.x, t.dr, pe.y * q), v1 = fmaf(pe.x, t.dg, pe.z * q);
-            const float v2 = fmaf(pe.x, t.db, pe.w * q);
+            const float q = fmaf(c.x, fmaf(K3, c.x, fmaf(K4, c.y, K1)), fmaf(c.y, fmaf(K5, c.y, K2), K0));
+            const float v0 = fmaf(pe.x, dr, pe.y * q), v1 = fmaf(pe.x, dg, pe.z * q);
+            const float v2 = fmaf(pe.x, db, pe.w * q);
             if constexpr (kMode == 1) {   // the warp's own unpadded planes [ch][p]
               float* sp = su + warp * (3 * kTilePix) + p;
               sp[0] += v0;
@@ -351,9 +377,8 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
   __shared__ float2 sxy[kTilePix];                       \
   __shared__ double dred[2 * kWarps];                    \
   __shared__ unsigned int next_seg;                      \
-  __shared__ StageRec S;                                 \
-  __shared__ StageT T;                                   \
-  sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
+  __shared__ StageJ S;                                   \
+  sxy[threadIdx.x] = centred_xy(threadIdx.x);
 
 template <int kFmt, int G, int U, int kMinBlocks, int kMode>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, const float* __restrict__ ydot,
@@ -364,7 +389,7 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, 
   APPLY_J_SHARED
   for (int i = threadIdx.x; i < (kMode ? kWarps * 3 * kTilePix : kPlane3); i += kTilePix) su[i] = 0.f;
   __syncthreads();
-  apply_J_tile<kFmt, G, U, kMode>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg, S, T);
+  apply_J_tile<kFmt, G, U, kMode>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg, S);
 }
 
 // Subset of a global tile index of a batch.
@@ -390,7 +415,7 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J_batch(const __
     const CacheView& cv = tb.v[b];
     if (cv.skip == nullptr || *cv.skip == 0)
       apply_J_tile<kFmt, G, U, kMode>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
-                               nullptr, su, sxy, dred, &next_seg, S, T);
+                               nullptr, su, sxy, dred, &next_seg, S);
     __syncthreads();
   }
 }
@@ -446,7 +471,7 @@ __device__ __forceinline__ float group_moment(const float (&v)[16], int i) {
 template <int kFmt, int G, int U>
 __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, const float* __restrict__ u,
                                               float* __restrict__ seg_ybar, float4* su4, float2* sxy,
-                                              unsigned int* next_seg, Stage& S) {
+                                              unsigned int* next_seg, StageJT& S) {
   static_assert(G == 8 || G == 16 || G == 32, "group size");
   constexpr int kGPW = 32 / G;
   const uint32_t g0 = cv.tile_seg_off[tile];
@@ -464,13 +489,13 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
       uv = make_float4(u[pix * 3 + 0], u[pix * 3 + 1], u[pix * 3 + 2], 0.f);
     }
     su4[threadIdx.x] = uv;
-    sxy[threadIdx.x] = make_float2((float)(threadIdx.x & (kTile - 1)), (float)(threadIdx.x / kTile));
+    sxy[threadIdx.x] = centred_xy(threadIdx.x);
   }
   const int lane = threadIdx.x & 31;
   const int gl = lane & (G - 1), grp = lane / G;
   for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
     const int cnt = (int)min((uint32_t)kStage, n - c0);
-    stage_chunk<false>(cv, g0 + c0, cnt, S, nullptr, nullptr, S.pos);
+    stage_chunk_JT(cv, g0 + c0, cnt, S);
     if (threadIdx.x == 0) *next_seg = 0;
     __syncthreads();
     for (;;) {
@@ -480,20 +505,19 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
       if (kb >= (uint32_t)cnt) break;
       const uint32_t k = kb + grp;
       const bool has = k < (uint32_t)cnt;
-      SegRec r;
-      uint32_t len = 0;
-      if (has) {
-        r = rec_from(S.r0[k], S.r1[k], S.r2[k]);
-        len = (uint32_t)(r.e1 - r.e0);
-      }
+      const uint4 w0 = has ? S.w0[k] : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t len = w0.z;
+      const float scale = __uint_as_float(w0.w);
+      const unsigned long long e0 = ((unsigned long long)w0.y << 32) | w0.x;
       const uint32_t mlen = warp_max_groups<G>(len);
-      // moments of s = h . u over the segment's pixels (tile-local offsets from
-      // the splat mean), and sums of w u; the conic is applied once per segment
+      // moments of s = h . u over the segment's pixels, taken about the tile
+      // centre, and sums of w u; the shift to the mean and the conic are
+      // applied once per segment
       float a[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) a[i] = 0.f;
-      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + (has ? r.e0 : 0);
-      const uint8_t* po = cv.pixoff + (has ? r.e0 : 0);
+      const typename Raw<kFmt>::T* pl = reinterpret_cast<const typename Raw<kFmt>::T*>(cv.payload) + e0;
+      const uint8_t* po = cv.pixoff + e0;
       for (uint32_t base = 0; base < mlen; base += G * U) {
         typename Raw<kFmt>::T raw[U];
         int pp[U];
@@ -510,18 +534,17 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
           const uint32_t i = base + gl + G * j;
           if (i < len) {
             const int p = pp[j];
-            const float4 pej = decode<kFmt>(raw[j], r.scale);
+            const float4 pej = decode<kFmt>(raw[j], scale);
             const float4 uv = su4[p];
             const float2 c = sxy[p];
-            const float dx = c.x - r.mx, dy = c.y - r.my;
             const float sv = pej.y * uv.x + pej.z * uv.y + pej.w * uv.z;
-            const float t1 = sv * dx, t2 = sv * dy;
+            const float t1 = sv * c.x, t2 = sv * c.y;
             a[0] += sv;
             a[1] += t1;
             a[2] += t2;
-            a[3] += t1 * dx;
-            a[4] += t1 * dy;
-            a[5] += t2 * dy;
+            a[3] += t1 * c.x;
+            a[4] += t1 * c.y;
+            a[5] += t2 * c.y;
             a[6] += pej.x * uv.x;
             a[7] += pej.x * uv.y;
             a[8] += pej.x * uv.z;
@@ -529,23 +552,31 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
         }
       }
       group_sum16<G>(a, lane);
-      // moment i: m0 = sum s, m1 = sum s dx, m2 = sum s dy, m3 = sum s dx^2,
-      // m4 = sum s dx dy, m5 = sum s dy^2, m6..m8 = sum w u
+      // sums about the centre: S0 = sum s, Sx = sum s x', Sy = sum s y', Sxx,
+      // Sxy, Syy, then the three sums of w u. With e = mean - centre the moments
+      // about the mean are m1 = Sx - ex S0, m2 = Sy - ey S0, m3 = sum s dx^2 =
+      // Sxx - ex (Sx + m1), m4 = sum s dx dy = Sxy - ey Sx - ex m2 and
+      // m5 = sum s dy^2 = Syy - ey (Sy + m2)
       if constexpr (G == 16) {
-        // lane o of the group holds moment o: output o needs moment o (6..8), its
-        // neighbour's (0..4) and moments 0 and 2 (three shuffles in all)
-        const float mo = a[0];
-        const float mn = __shfl_down_sync(kFull, mo, 1, 16);
-        const float m0 = __shfl_sync(kFull, mo, 0, 16);
-        const float m2 = __shfl_sync(kFull, mo, 2, 16);
+        // lane o of the group holds sum o: output o needs sum o (6..8), its
+        // neighbour's (2..4) and S0, Sx, Sy (four shuffles in all)
+        const float so = a[0];
+        const float sn = __shfl_down_sync(kFull, so, 1, 16);
+        const float s0 = __shfl_sync(kFull, so, 0, 16);
+        const float s1 = __shfl_sync(kFull, so, 1, 16);
+        const float s2 = __shfl_sync(kFull, so, 2, 16);
         if (has && gl < 9) {
-          float val = mo;
-          if (gl == 0) val = r.A * mn + r.B * m2;
-          else if (gl == 1) val = r.B * mo + r.C * mn;
-          else if (gl == 2) val = -0.5f * mn;
-          else if (gl == 3) val = -mn;
-          else if (gl == 4) val = -0.5f * mn;
-          else if (gl == 5) val = m0 * r.io;
+          const float4 w1 = S.w1[k];
+          const float2 w2 = S.w2[k];
+          const float ex = w1.x, ey = w1.y;
+          const float m1 = fmaf(-ex, s0, s1), m2 = fmaf(-ey, s0, s2);
+          float val = so;
+          if (gl == 0) val = w1.z * m1 + w1.w * m2;
+          else if (gl == 1) val = w1.w * m1 + w2.x * m2;
+          else if (gl == 2) val = -0.5f * fmaf(-ex, s1 + m1, sn);
+          else if (gl == 3) val = -fmaf(-ey, s1, fmaf(-ex, m2, sn));
+          else if (gl == 4) val = -0.5f * fmaf(-ey, s2 + m2, sn);
+          else if (gl == 5) val = s0 * w2.y;
           seg_ybar[(size_t)S.pos[k] * 12 + gl] = val;
         }
         continue;
@@ -554,15 +585,19 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
 #pragma unroll
       for (int i = 0; i < 9; ++i) m[i] = group_moment<G>(a, i);
       if (has) {
+        const float4 w1 = S.w1[k];
+        const float2 w2 = S.w2[k];
+        const float ex = w1.x, ey = w1.y;
+        const float m1 = fmaf(-ex, m[0], m[1]), m2 = fmaf(-ey, m[0], m[2]);
         // output o of the segment's 9 (G = 8: lane 0 also writes output 8)
         for (int o = gl; o < 9; o += G) {
           float val = m[o];
-          if (o == 0) val = r.A * m[1] + r.B * m[2];
-          else if (o == 1) val = r.B * m[1] + r.C * m[2];
-          else if (o == 2) val = -0.5f * m[3];
-          else if (o == 3) val = -m[4];
-          else if (o == 4) val = -0.5f * m[5];
-          else if (o == 5) val = m[0] * r.io;
+          if (o == 0) val = w1.z * m1 + w1.w * m2;
+          else if (o == 1) val = w1.w * m1 + w2.x * m2;
+          else if (o == 2) val = -0.5f * fmaf(-ex, m[1] + m1, m[3]);
+          else if (o == 3) val = -fmaf(-ey, m[1], fmaf(-ex, m2, m[4]));
+          else if (o == 4) val = -0.5f * fmaf(-ey, m[2] + m2, m[5]);
+          else if (o == 5) val = m[0] * w2.y;
           seg_ybar[(size_t)S.pos[k] * 12 + o] = val;
         }
       }
@@ -575,7 +610,7 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
   __shared__ float4 su4[kTilePix];        \
   __shared__ float2 sxy[kTilePix];        \
   __shared__ unsigned int next_seg;       \
-  __shared__ Stage S;
+  __shared__ StageJT S;
 
 template <int kFmt, int G, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv, const float* __restrict__ u,
