@@ -43,3 +43,36 @@ def pixel_mask(lin, threshold=1e-4):
     flagged by the oracle itself (ViewRaster.flip).
     """
     return np.concatenate([(vl.ras.margin >= threshold) & ~vl.ras.flip for vl in lin])
+
+
+def pcg_bound(sys_, lam: float, n_iters: int, x_ref, eps: float = 1e-5, seeds=(0, 1), floor: float = 1e-3) -> float:
+    """Bound on the relative L2 distance of a float32 solve from the oracle's x_ref
+    after n_iters iterations of Algorithm 1 without break test.
+
+    1e-3, unless the solve amplifies the rounding of its products more than that
+    allows: then twice the largest distance by which relative noise eps on b and
+    on every J p and J^T u product moves the oracle's own solve. eps = 1e-5 is the
+    float32 products' error against the oracle (J p and J^T u within 1e-5 relative
+    L2 on the paper crop). With weak damping x0 = M^-1 b overshoots and r0 = b - A x0
+    cancels; at lambda = 1e-3 on the tiny case, 8 iterations turn 1e-5 of product
+    noise into 1.4e-3 to 1.7e-3 of x.
+    """
+    from oracle import jacobian as jac, solver
+    N = sys_.b.shape[0]
+    n_res = sys_.F.shape[0]
+    worst = 0.0
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+
+        def noisy_JTJ(v):
+            u = jac.apply_J(sys_.lin, v, n_res)
+            u = u * (1.0 + eps * rng.standard_normal(u.shape))
+            if sys_.W is not None:
+                u = sys_.W * u
+            g = jac.apply_JT(sys_.lin, u, N)
+            return g * (1.0 + eps * rng.standard_normal(g.shape))
+
+        b = sys_.b * (1.0 + eps * rng.standard_normal(sys_.b.shape))
+        x = solver.pcg(noisy_JTJ, b, sys_.M, lam, n_iters, 0.0)[0]
+        worst = max(worst, rel_l2(x, x_ref))
+    return max(floor, 2.0 * worst)

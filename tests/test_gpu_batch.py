@@ -9,14 +9,16 @@ iterations, and the spread between two runs varies from one run to the next
 (5e-5 to 4e-4 seen). Batched and per-subset solves are therefore held to the
 PCG tolerance of 1e-3 (relative L2; a subset that got another subset's data
 would be off by orders of magnitude more), the spread of the per-subset
-solve is printed beside it, and the batched solve is held to the oracle's
-1e-3 at lambda = 1e-3.
+solve is printed beside it, and the batched solve is held to the oracle at
+lambda = 1e-3 within the PCG bound of `common.pcg_bound` (1e-3 where the solve
+allows it; on the tiny case 8 iterations amplify 1e-5 of product noise about
+150 times).
 """
 import numpy as np
 import pytest
 
 import synth
-from common import rel_l2, tiny_case
+from common import pcg_bound, rel_l2, tiny_case
 
 pytestmark = pytest.mark.gpu
 
@@ -90,19 +92,22 @@ def test_batched_solve_matches_the_oracle(lib):
     lam = 1e-3
     ctx = lib.Context(n_iters=8, break_rel2=0.0)
     params = lib.to_soa(P)
-    caches, diags, refs = [], [], []
+    caches, diags, refs, bounds = [], [], [], []
     for vs in subsets:
         t = _subset_targets(cams, tgt, vs)
         sys_ = solver.build_subset(P.astype(np.float64), [cams[v] for v in vs], t.astype(np.float64))
         refs.append(solver.solve_subset(sys_, lam, n_iters=8, break_rel2=0.0)[0])
+        bounds.append(pcg_bound(sys_, lam, 8, refs[-1]))
         c = ctx.build_cache(params, N, [cams[v] for v in vs], torch.from_numpy(t).cuda().view(-1, 3))
         caches.append(c)
         diags.append(ctx.jacobi_diag(c))
     for rep in range(2):
         xs, stats, _ = ctx.pcg_solve_batch(caches, [c.b for c in caches], diags, lam)
-        for x, r, st in zip(xs, refs, stats):
+        for x, r, st, bound in zip(xs, refs, stats, bounds):
             assert st.iters == 8
-            assert rel_l2(lib.from_soa(x, N), r) < 1e-3
+            err = rel_l2(lib.from_soa(x, N), r)
+            print(f"call {rep}: batched vs oracle {err:.2e} (bound {bound:.2e})")
+            assert err < bound
 
 
 def test_batched_solve_stops_each_subset_at_its_own_break_test(lib):
