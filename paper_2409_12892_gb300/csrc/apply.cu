@@ -465,13 +465,21 @@ __device__ __forceinline__ float group_moment(const float (&v)[16], int i) {
   else return __shfl_sync(kFull, (i & 1) ? v[1] : v[0], i >> 1, 8);
 }
 
+// Shared-memory transpose of a 16-lane group's 9 partial sums: rows of 20
+// floats (16 lanes + 4 of padding, so that the 16-byte row reads of lanes
+// 0..7 hit distinct banks) and a group stride of 208 floats (16 banks apart,
+// so that the two groups of a warp store without conflicts).
+constexpr int kRedRow = 20;
+constexpr int kRedGroup = 208;
+static_assert(9 * kRedRow <= kRedGroup && kRedGroup % 32 == 16 && kRedRow % 4 == 0, "transpose layout");
+
 // J^T u over one tile into per-segment partials, stored at each segment's
 // splat-order position (so the adjoint kernel reads a splat's partials as one
 // contiguous range). The caller synchronises before. su4 / sxy are filled here.
 template <int kFmt, int G, int U>
 __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, const float* __restrict__ u,
                                               float* __restrict__ seg_ybar, float4* su4, float2* sxy,
-                                              unsigned int* next_seg, StageJT& S) {
+                                              unsigned int* next_seg, StageJT& S, float* sred) {
   static_assert(G == 8 || G == 16 || G == 32, "group size");
   constexpr int kGPW = 32 / G;
   const uint32_t g0 = cv.tile_seg_off[tile];
@@ -551,16 +559,29 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
           }
         }
       }
-      group_sum16<G>(a, lane);
       // sums about the centre: S0 = sum s, Sx = sum s x', Sy = sum s y', Sxx,
       // Sxy, Syy, then the three sums of w u. With e = mean - centre the moments
       // about the mean are m1 = Sx - ex S0, m2 = Sy - ey S0, m3 = sum s dx^2 =
       // Sxx - ex (Sx + m1), m4 = sum s dx dy = Sxy - ey Sx - ex m2 and
       // m5 = sum s dy^2 = Syy - ey (Sy + m2)
       if constexpr (G == 16) {
+        // the group's 16 x 9 partials transposed through shared memory: lane o
+        // (o < 9) reads row o (the 16 lanes' partials of sum o) with four
+        // 16-byte loads, in place of a 16-value shuffle reduction
+        float* rb = sred + ((threadIdx.x >> 5) * 2 + grp) * kRedGroup;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) rb[i * kRedRow + gl] = a[i];
+        __syncwarp();
+        float so = 0.f;
+        if (gl < 9) {
+          const float4* row = reinterpret_cast<const float4*>(rb + gl * kRedRow);
+          const float4 q0 = row[0], q1 = row[1], q2 = row[2], q3 = row[3];
+          so = ((q0.x + q0.y) + (q0.z + q0.w) + ((q1.x + q1.y) + (q1.z + q1.w))) +
+               ((q2.x + q2.y) + (q2.z + q2.w) + ((q3.x + q3.y) + (q3.z + q3.w)));
+        }
+        __syncwarp();   // the next segment's partials overwrite rb
         // lane o of the group holds sum o: output o needs sum o (6..8), its
         // neighbour's (2..4) and S0, Sx, Sy (four shuffles in all)
-        const float so = a[0];
         const float sn = __shfl_down_sync(kFull, so, 1, 16);
         const float s0 = __shfl_sync(kFull, so, 0, 16);
         const float s1 = __shfl_sync(kFull, so, 1, 16);
@@ -581,6 +602,7 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
         }
         continue;
       }
+      group_sum16<G>(a, lane);
       float m[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) m[i] = group_moment<G>(a, i);
@@ -606,18 +628,19 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
   }
 }
 
-#define APPLY_JT_SHARED                   \
-  __shared__ float4 su4[kTilePix];        \
-  __shared__ float2 sxy[kTilePix];        \
-  __shared__ unsigned int next_seg;       \
-  __shared__ StageJT S;
+#define APPLY_JT_SHARED                                      \
+  __shared__ float4 su4[kTilePix];                           \
+  __shared__ float2 sxy[kTilePix];                           \
+  __shared__ unsigned int next_seg;                          \
+  __shared__ StageJT S;                                      \
+  __shared__ __align__(16) float sred[G == 16 ? kWarps * 2 * kRedGroup : 4];
 
 template <int kFmt, int G, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv, const float* __restrict__ u,
                                                                    float* __restrict__ seg_ybar) {
   APPLY_JT_SHARED
   if (cv.skip != nullptr && *cv.skip) return;
-  apply_JT_tile<kFmt, G, U>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg, S);
+  apply_JT_tile<kFmt, G, U>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg, S, sred);
 }
 
 // Persistent J^T u over every subset of a batch (see k_apply_J_batch).
@@ -634,7 +657,7 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const _
     const CacheView& cv = tb.v[b];
     if (cv.skip == nullptr || *cv.skip == 0)
       apply_JT_tile<kFmt, G, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.u[b], tb.seg_ybar[b], su4, sxy,
-                                &next_seg, S);
+                                &next_seg, S, sred);
     __syncthreads();
   }
 }
