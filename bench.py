@@ -467,7 +467,7 @@ def summarize_phases(stats) -> dict:
 # adjoint) on the 100k-Gaussian, 8-view case, by cache format. The pair's traffic
 # grows with its entries, pixels and splats, so a full launch's traffic is this
 # ratio times its algorithmic bytes.
-PAIR_DRAM_PER_ALG_BYTE = {0: 1.129, 1: 1.216}   # FP32, BF16
+PAIR_DRAM_PER_ALG_BYTE = {0: 1.127, 1: 1.215}   # FP32, BF16
 
 
 def pair_roofline(stats, peak: dict, fmt: int = None) -> dict:
