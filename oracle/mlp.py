@@ -4,7 +4,7 @@ The paper uses the Jacobi preconditioner M^-1 = 1 / diag(J^T J) (Sec. 3.3,
 Algorithm 1). This module is the oracle for the learned replacement: a small
 per-Gaussian network whose softplus output gives a positive diagonal D, so that
 z = D r keeps PCG on a symmetric positive definite system. The paper has no
-such network; the reading below is this project's (stated in the design doc):
+such network; the reading below is this project's:
 
   features phi (64) per Gaussian, from one image subset's linear system:
       log(M_k + 1e-12), k = 0..58    the subset's diag(J^T J)

@@ -7,7 +7,7 @@
 * ``lm_step``: Eq. norm-eq for the direction, Eq. tr-update for rho and the
   damping update, with gamma = 1 (no line search).
 
-Readings where the paper is silent (stated again in the design doc):
+Readings where the paper is silent:
   - the loop "for i = 0 to n_iters" runs n_iters times after the initial product;
   - the LM update follows Ceres (Sec. 3.2), whose Levenberg-Marquardt strategy
     clamps the diagonal diag(J^T J) to [1e-6, 1e32] before using it; the
