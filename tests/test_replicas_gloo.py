@@ -4,8 +4,9 @@ The method shards by image subset, but every run here has one GPU, so
 `bench.py --gpus N` runs N independent replicas: a barrier around the timed
 region, the step time as the maximum over ranks, and no data-path collective.
 These tests run that host logic as two processes: rendezvous through the same
-environment torchrun sets, the max-over-ranks reduction, the barrier, and the
-reference arm, which only rank 0 runs (the other ranks return at once).
+environment torchrun sets, the max-over-ranks reduction, the barrier, the
+agreement to time the steps again when any rank's clocks void its number, and
+the reference arm, which only rank 0 runs (the other ranks return at once).
 """
 import os
 import socket
@@ -71,6 +72,28 @@ def test_reference_arm_runs_on_rank_0_only(tmp_path):
     mp.spawn(_reference_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
     assert open(tmp_path / "ref0.txt").read().strip() == "rank 0 reached the oracle"
     assert open(tmp_path / "ref1.txt").read().strip() == "returned 0"
+
+
+def _remeasure_rank_main(rank, ws, port, out_dir):
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(ws), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import bench
+    r, n, dist = bench.dist_init("gloo")
+    # only rank 1's GPU throttled: both ranks must time the steps again, or the
+    # rank that does would wait at the barrier alone
+    why = "slowdown: hw_thermal_slowdown" if rank == 1 else ""
+    first = bench.agree_remeasure(why, dist, "cpu")
+    second = bench.agree_remeasure("", dist, "cpu")
+    bench.barrier(dist)
+    with open(os.path.join(out_dir, f"re{rank}.txt"), "w") as f:
+        f.write(f"{int(first)} {int(second)}\n")
+    dist.destroy_process_group()
+
+
+def test_ranks_agree_to_measure_again(tmp_path):
+    port = _free_port()
+    mp.spawn(_remeasure_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    assert [open(tmp_path / f"re{r}.txt").read().split() for r in range(2)] == [["1", "0"], ["1", "0"]]
 
 
 def test_single_rank_needs_no_process_group(monkeypatch):
