@@ -478,6 +478,34 @@ def _mlp_case(seed=0, n=4):
     return mlp, net, phi, M, b, apply_A, A
 
 
+def test_mlp_features_layout_on_closed_form_values():
+    """phi = [log M (59), log-scale (3), sigmoid(opacity logit) (1), log(1 + entries) (1)]
+    for parameter rows whose other columns hold noise that must not leak in."""
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    P = rng.normal(size=(2, 59))
+    P[:, 3:6] = [[-3.0, -2.5, -4.0], [0.5, 0.0, -1.0]]
+    P[:, 10] = [math.log(3.0), 0.0]                       # opacities 3/4 and 1/2
+    M = np.exp(np.tile(np.linspace(-5.0, 5.0, 59), (2, 1)))
+    M[1, 7] = 0.0                                          # a parameter no entry touches
+    entries = np.array([math.e ** 2 - 1.0, 0.0])
+    phi = mlp.features(M, P, entries)
+    assert phi.shape == (2, 64)
+    assert np.allclose(phi[0, :59], np.linspace(-5.0, 5.0, 59), atol=1e-9)
+    assert phi[1, 7] == pytest.approx(math.log(1e-12)) and np.isfinite(phi).all()
+    assert np.array_equal(phi[:, 59:62], P[:, 3:6])
+    assert phi[:, 62] == pytest.approx([0.75, 0.5])
+    assert phi[:, 63] == pytest.approx([2.0, 0.0])
+
+
+def test_mlp_standardizer_is_the_population_moments_with_a_floor():
+    from oracle import mlp
+    phi = np.array([[1.0, 4.0], [2.0, 4.0], [3.0, 4.0]])
+    mu, sd = mlp.standardizer(phi)
+    assert mu == pytest.approx([2.0, 4.0])
+    assert sd == pytest.approx([math.sqrt(2.0 / 3.0), 1e-6])   # 1/n, not 1/(n - 1); a constant column floored
+
+
 def test_mlp_activations_closed_forms():
     from oracle import mlp
     assert abs(mlp.softplus(0.0) - math.log(2.0)) < 1e-15
