@@ -40,9 +40,6 @@ constexpr int kVecBlocks = 2432;   // 16 blocks of 256 threads per SM on 152 SMs
 __device__ __forceinline__ const float* subset_D(const float* D, unsigned d_mask, long long off) {
   return (D != nullptr && ((d_mask >> blockIdx.y) & 1u)) ? D + off : nullptr;
 }
-__device__ __forceinline__ float minv_at(const float* __restrict__ D, const float* __restrict__ M, long long o) {
-  return D != nullptr ? D[o] : 1.f / clamp_diag(M[o]);
-}
 
 // The vector kernels walk the 59 rows in the outer loop and, inside a row,
 // one float4 (four Gaussians) per thread, so the resident warps stream through
