@@ -140,8 +140,9 @@ __device__ __forceinline__ SegRec rec_from(const uint4& a, const uint4& b, const
 constexpr float kTileCentre = 0.5f * (kTile - 1);
 
 // Shared staging of one chunk of segments for J p: what a lane reads, prepared
-// once per segment. The tangent of the blending exponent log(o G) is the
-// quadratic q = K0 + x' (K1 + K3 x' + K4 y') + y' (K2 + K5 y').
+// once per segment. The tangent of log alpha (alpha = o exp(-d^T Sigma'^-1 d / 2),
+// the splat's blending weight at the pixel) is the quadratic
+// q = K0 + x' (K1 + K3 x' + K4 y') + y' (K2 + K5 y').
 struct StageJ {
   uint4 w0[kStage];     // e0 (low, high word), entry count, FP16S scale
   float4 w1[kStage];    // K0, K1, K2, K3
