@@ -45,17 +45,22 @@ def pixel_mask(lin, threshold=1e-4):
     return np.concatenate([(vl.ras.margin >= threshold) & ~vl.ras.flip for vl in lin])
 
 
-def pcg_bound(sys_, lam: float, n_iters: int, x_ref, eps: float = 1e-5, seeds=(0, 1), floor: float = 1e-3) -> float:
-    """Bound on the relative L2 distance of a float32 solve from the oracle's x_ref
-    after n_iters iterations of Algorithm 1 without break test.
+def pcg_noise_spread(sys_, lam: float, n_iters: int, x_ref, eps: float = 1e-5, seeds=(0, 1)) -> float:
+    """How far float32-level rounding can move a solve of this system: twice the
+    largest relative L2 distance from x_ref (the oracle's solve) of the oracle's
+    own Algorithm 1 run for n_iters iterations without break test with relative
+    noise eps on b and on every J p and J^T u product. eps = 1e-5 is the float32
+    products' error against the oracle (J p and J^T u within 1e-5 relative L2 on
+    the paper crop).
 
-    1e-3, unless the solve amplifies the rounding of its products more than that
-    allows: then twice the largest distance by which relative noise eps on b and
-    on every J p and J^T u product moves the oracle's own solve. eps = 1e-5 is the
-    float32 products' error against the oracle (J p and J^T u within 1e-5 relative
-    L2 on the paper crop). With weak damping x0 = M^-1 b overshoots and r0 = b - A x0
-    cancels; at lambda = 1e-3 on the tiny case, 8 iterations turn 1e-5 of product
-    noise into 1.4e-3 to 1.7e-3 of x.
+    Algorithm 1 starts from x0 = M^-1 b, which overshoots the solution (by about
+    4x in norm on these scenes), so the iterations cancel most of x0 and amplify
+    the products' rounding with every iteration, whatever the damping: on the
+    tiny case the spread is 1.3e-4 after 2 iterations, 2.7e-4 after 3 and 1.7e-3
+    after 8 (at lambda = 1e-3 and at lambda = 1 alike). The PCG parity tests
+    therefore hold x to the 1e-3 tolerance after an iteration count at which
+    this spread is at most 5e-4, and report the spread and the distance after
+    the paper's 8 iterations beside it.
     """
     from oracle import jacobian as jac, solver
     N = sys_.b.shape[0]
@@ -75,4 +80,10 @@ def pcg_bound(sys_, lam: float, n_iters: int, x_ref, eps: float = 1e-5, seeds=(0
         b = sys_.b * (1.0 + eps * rng.standard_normal(sys_.b.shape))
         x = solver.pcg(noisy_JTJ, b, sys_.M, lam, n_iters, 0.0)[0]
         worst = max(worst, rel_l2(x, x_ref))
-    return max(floor, 2.0 * worst)
+    return 2.0 * worst
+
+
+# PCG solutions are held to this relative L2 distance from the oracle's, on
+# systems whose noise spread (pcg_noise_spread) is at most PCG_SPREAD_MAX.
+PCG_TOL = 1e-3
+PCG_SPREAD_MAX = 5e-4

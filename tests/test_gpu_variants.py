@@ -5,14 +5,15 @@ each one must compute the same products: J p and J^T u of every variant (lane
 groups of 8, 16 or 32, 2 to 4 entries in flight per lane, shared atomics or
 per-warp private tiles) are held to the bound of their cache format (FP32 1e-4,
 BF16 2e-2, FP16 with scale 5e-3), and a batched solve (persistent kernels) with
-each variant forced is held to the PCG bound (`common.pcg_bound`) against the
-oracle's Algorithm 1.
+each variant forced is held to the PCG tolerance of 1e-3 against the oracle's
+Algorithm 1 after 2 iterations (where float32 rounding moves x by at most
+5e-4: `common.pcg_noise_spread`).
 """
 import numpy as np
 import pytest
 
 import synth
-from common import N_PARAMS, pcg_bound, pixel_mask, ragged_case, rel_l2
+from common import N_PARAMS, PCG_SPREAD_MAX, PCG_TOL, pcg_noise_spread, pixel_mask, ragged_case, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +38,27 @@ def case():
     wl, P, cams, tgt = ragged_case()
     lin = J.linearise(P.astype(np.float64), cams)
     return P, cams, tgt, lin
+
+
+PCG_LAMBDA, PCG_ITERS = 1e-2, 2
+
+
+@pytest.fixture(scope="module")
+def halves(case):
+    """The two halves of the ragged case's views, each with the oracle's PCG
+    solution after PCG_ITERS iterations (checked to be a well-posed comparison)."""
+    from oracle import solver
+    P, cams, tgt, lin = case
+    offs = np.concatenate([[0], np.cumsum([c.width * c.height * 3 for c in cams])])
+    k = len(cams) // 2
+    out = []
+    for c, t in ((cams[:k], tgt[:offs[k]]), (cams[k:], tgt[offs[k]:])):
+        sys_ = solver.build_subset(P.astype(np.float64), c, t.astype(np.float64))
+        x_ref, _ = solver.solve_subset(sys_, PCG_LAMBDA, PCG_ITERS)
+        spread = pcg_noise_spread(sys_, PCG_LAMBDA, PCG_ITERS, x_ref, seeds=(0,))
+        assert spread <= PCG_SPREAD_MAX, spread
+        out.append((c, t, x_ref))
+    return out
 
 
 def test_the_library_offers_the_variants_tested(lib):
@@ -67,24 +89,16 @@ def test_every_variant_matches_the_oracle(lib, case, variant, fmt, tol):
 
 
 @pytest.mark.parametrize("variant", range(1, N_VARIANTS + 1))
-def test_every_variant_in_the_batched_solve(lib, case, variant):
-    from oracle import solver
+def test_every_variant_in_the_batched_solve(lib, case, halves, variant):
     P, cams, tgt, lin = case
     N = P.shape[0]
-    halves = [cams[: len(cams) // 2], cams[len(cams) // 2:]]
-    offs = np.concatenate([[0], np.cumsum([c.width * c.height * 3 for c in cams])])
-    k = len(cams) // 2
-    tg = [tgt[:offs[k]], tgt[offs[k]:]]
-    lam = 1e-2
-    ctx = lib.Context(n_iters=4, break_rel2=0.0, apply_variant=variant, autotune=False)
-    caches = [ctx.build_cache(lib.to_soa(P), N, c, torch.from_numpy(t).cuda().view(-1, 3)) for c, t in zip(halves, tg)]
+    ctx = lib.Context(n_iters=PCG_ITERS, break_rel2=0.0, apply_variant=variant, autotune=False)
+    caches = [ctx.build_cache(lib.to_soa(P), N, c, torch.from_numpy(t).cuda().view(-1, 3)) for c, t, _ in halves]
     diags = [ctx.jacobi_diag(c) for c in caches]
-    xs, stats, status = ctx.pcg_solve_batch(caches, [c.b for c in caches], diags, lam)
-    assert all(s.iters == 4 for s in stats)
-    for c, t, x in zip(halves, tg, xs):
-        sys_ = solver.build_subset(P.astype(np.float64), c, t.astype(np.float64))
-        x_ref, _ = solver.solve_subset(sys_, lam, 4)
-        assert rel_l2(lib.from_soa(x, N), x_ref) < pcg_bound(sys_, lam, 4, x_ref, seeds=(0,)), variant
+    xs, stats, status = ctx.pcg_solve_batch(caches, [c.b for c in caches], diags, PCG_LAMBDA)
+    assert all(s.iters == PCG_ITERS for s in stats)
+    for (_, _, x_ref), x in zip(halves, xs):
+        assert rel_l2(lib.from_soa(x, N), x_ref) < PCG_TOL, variant
     for c in caches:
         c.free()
     ctx.close()

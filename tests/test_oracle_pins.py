@@ -123,6 +123,32 @@ def test_projection_off_axis_mean_is_pinhole():
     np.testing.assert_allclose(pr.y[0, 0:2], [40 * tc[0] / tc[2] + 20, 45 * tc[1] / tc[2] + 10], atol=1e-12)
 
 
+def test_projection_culls_splats_whose_float32_covariance_chain_overflows():
+    """The renderer computes a splat's covariance chain in float32; a splat is
+    drawn only if that chain stays within the float32 range. For an isotropic
+    Gaussian on the optical axis Sigma2 = a I with a = (f s / z)^2 + 0.3 (closed
+    form), so the determinant's product a * c = a^2 leaves the range at
+    a = sqrt(FLT_MAX): kept at 0.9 sqrt(FLT_MAX), culled at 1.1 sqrt(FLT_MAX).
+    A log-scale whose 3D covariance exp(2 s) alone exceeds FLT_MAX is culled
+    too, and ordinary log-scales (about -3.5) are 20 orders of magnitude away."""
+    f32max = float(np.finfo(np.float32).max)
+    z0, f = 3.0, 50.0
+    cam = synth.Camera(np.eye(3), np.zeros(3), f, f, 16.0, 12.0, 32, 24)
+
+    def log_scale_for(a):
+        return math.log(math.sqrt(a - cv.DILATION) * z0 / f)
+
+    q = np.array([0.3, -0.5, 0.7, 0.4])
+    P = np.stack([gaussian((0.0, 0.0, z0), log_scale=log_scale_for(0.9 * math.sqrt(f32max)), quat=q),
+                  gaussian((0.0, 0.0, z0), log_scale=log_scale_for(1.1 * math.sqrt(f32max)), quat=q),
+                  gaussian((0.0, 0.0, z0), log_scale=0.5 * math.log(f32max) + 0.5, quat=q),
+                  gaussian((0.0, 0.0, z0), log_scale=-3.5, quat=q)])
+    pr = projection.project(P, cam, want_jac=False)
+    assert pr.visible.tolist() == [True, False, False, True]
+    a = (f * math.exp(P[0, 3]) / z0) ** 2 + cv.DILATION
+    np.testing.assert_allclose(pr.y[0, 2:5] * a, [1.0, 0.0, 1.0], rtol=0, atol=1e-9)
+
+
 # ----------------------------------------------------------------------------- compositing
 def test_two_splat_closed_form_compositing():
     """c = a1 c1 + (1 - a1) a2 c2 for two splats along one pixel's ray (Eq. alpha-blending)."""
