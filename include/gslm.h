@@ -166,7 +166,8 @@ typedef struct {
    * kernels, [7] rho evaluation (J Delta and the trial render). */
   double ms_phase[8];
   int32_t n_pairs;       /* J p + J^T u pairs executed (initial product + PCG iterations) */
-  int32_t pad;
+  int32_t trial_overflows; /* trial renders (line search and rho) whose splats needed more than
+                              2^32 tile keys; each counted one as cost +inf */
   /* Algorithmic bytes of those pairs: per pair on a cache with E entries of B_e
    * payload bytes, P pixels, N Gaussians and S active splats:
    * 2 E (B_e + 1) + 24 P + 472 N + 192 S. */
@@ -226,14 +227,19 @@ gslm_status gslm_apply_JT(gslm_ctx* ctx, const gslm_cache* cache, const float* u
  * memory once running (a service whose memory another allocator reserved up
  * front, or a thread that may not call cudaMalloc). The paper has no
  * counterpart. The per-segment partial sums live in one fixed 24 MiB
- * __device__ array inside the library (held by every GPU that loads it, until
- * exit) instead of a context buffer; the call allocates nothing.
+ * __device__ array inside the library instead of a context buffer; the call
+ * allocates nothing. gslm_create looks up the array's address on the
+ * context's device, which places the array there: every device on which a
+ * context was created holds it until the process exits.
  * Limits and rules: caches with more than 2^19 (tile, splat) segments
- * (gslm_cache_info.segments) are rejected with GSLM_E_INVALID. The first call
- * on a device looks up the array's device address for that device, so make it
- * with that device current and before any stream capture. All calls share the
- * array: calls whose work overlaps on the GPU (other streams, other contexts)
- * race; calls on one stream are ordered and need no clearing in between. */
+ * (gslm_cache_info.segments) are rejected with GSLM_E_INVALID, and so is a call
+ * made while another device than the context's is current. It runs the same
+ * apply_JT kernel variant as gslm_apply_JT on that context. With CUDA's lazy
+ * module loading the first launch of a kernel in a process loads its code,
+ * which takes device memory: make one call (or one gslm_apply_JT call) during
+ * set-up, or set CUDA_MODULE_LOADING=EAGER. All calls share the array: calls
+ * whose work overlaps on the GPU (other streams, other contexts) race; calls
+ * on one stream are ordered and need no clearing in between. */
 gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* cache, const float* u, float* g);
 
 /* M = diag(J^T J) [Eq. diag-jtj]. diag: [59][ld]. */

@@ -96,6 +96,7 @@ struct gslm_ctx {
   int bctas_JT[3] = {0, 0, 0};
   cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};   // start + first chunk, full chunk, last chunk
   cudaStream_t cap_st = nullptr;    // private stream the batched solve is captured on
+  void* noalloc_scratch = nullptr;  // gslm_apply_JT_noalloc's array on this device (looked up at creation)
   ~gslm_ctx() {
     for (auto ge : graph_exec)
       if (ge != nullptr) cudaGraphExecDestroy(ge);
@@ -799,8 +800,11 @@ bool cache_parts(const gslm_cache* c, CacheParts* out) {
 bool context_parts(const gslm_ctx* c, int cache_fmt, ContextParts* out) {
   if (c == nullptr || out == nullptr || cache_fmt < 0 || cache_fmt > 2) return false;
   out->st = c->st;
-  out->variant_JT = c->var_JT[cache_fmt] >= 0 ? c->var_JT[cache_fmt] : kDefaultVariant;
+  // the variant do_apply_JT would run: forced by the options, else tuned, else the default
+  if (c->opt.apply_variant > 0) out->variant_JT = c->opt.apply_variant - 1;
+  else out->variant_JT = c->var_JT[cache_fmt] >= 0 ? c->var_JT[cache_fmt] : kDefaultVariant;
   out->device = c->device;
+  out->noalloc_scratch = c->noalloc_scratch;
   return true;
 }
 
@@ -925,6 +929,13 @@ gslm_status gslm_create(const gslm_options* opt, void* stream, gslm_ctx** out) {
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
+  cudaGetLastError();
+  // Look up gslm_apply_JT_noalloc's fixed array here, with the context's device
+  // current: the lookup loads the array's module (24 MiB of device memory), so
+  // that the allocation-free call itself never does. A failure leaves the
+  // address null and that call returns GSLM_E_CUDA.
+  void* scratch = nullptr;
+  if (noalloc_scratch_address(&scratch) == cudaSuccess) c->noalloc_scratch = scratch;
   cudaGetLastError();
   *out = c;
   return GSLM_OK;
@@ -1512,6 +1523,8 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   }
   // the trial render of params + g Delta over the first nv[i] views of every
   // subset i; +inf when the trial splats exceed the renderer's tile-key capacity
+  // (counted in trial_overflows)
+  int trial_overflows = 0;
   auto trial_cost = [&](double g, const std::vector<int>& nv, double* out) -> gslm_status {
     CK(launch_axpy_params((int)N, ld, params, (float)g, ctx->lm_delta.as<float>(), ctx->lm_trial.as<float>(), st));
     double e = 0.0;
@@ -1525,6 +1538,8 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
       const gslm_status rs = gslm_render(ctx, ctx->lm_trial.as<float>(), N, ld, scams[i].data(), nv[i],
                                          ctx->lm_img.as<float>(), ctx->lm_tgt.as<float>(), &ci);
       if (rs == GSLM_E_CACHE_OVERFLOW) {
+        ++trial_overflows;
+        ctx->err.clear();
         *out = INFINITY;
         return GSLM_OK;
       }
@@ -1600,7 +1615,7 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
     for (int k = 0; k < 8; ++k) stats->ms_phase[k] = 0.0;
     ctx->timer.collect(stats->ms_phase, 8);
     stats->n_pairs = n_pairs;
-    stats->pad = 0;
+    stats->trial_overflows = trial_overflows;
     stats->pair_bytes = pair_bytes;
     stats->cache_segments = segs;
     stats->active_splats = actives;

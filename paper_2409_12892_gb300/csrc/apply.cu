@@ -61,12 +61,10 @@ __device__ __forceinline__ unsigned group_mask() {
 }
 
 // ---------------------------------------------------------------------------
-// Work distribution of both tile kernels: the warps of a tile's CTA take the
-// tile's segments one at a time from a shared counter (long and short segments
-// balance), read a segment's 48-byte record with one broadcast load, and stream
-// its entries with every lane keeping U loads in flight. The record (and for
-// J p the splat tangent) of the segment after next is fetched while the
-// current one streams, so the record latency stays off the critical path.
+// Work distribution of both tile kernels: the tile's segment records are staged
+// in shared memory first (below), then the warps of the tile's CTA take the
+// staged segments from a shared counter (long and short segments balance) and
+// stream each segment's entries with every lane keeping U loads in flight.
 constexpr int kWarps = kTilePix / 32;
 
 // Shared-memory index of pixel p of colour plane ch, padded by one word every

@@ -219,8 +219,9 @@ struct CacheParts {
 };
 struct ContextParts {
   cudaStream_t st;
-  int variant_JT;   // apply_JT kernel variant for the cache format asked about
+  int variant_JT;   // apply_JT kernel variant for the cache format asked about (forced, tuned or default)
   int device;
+  void* noalloc_scratch;   // device address of the allocation-free J^T u's array on the context's device, or null
 };
 bool cache_parts(const gslm_cache* c, CacheParts* out);
 // out = (J^T J + lambda clamp(M)) v through the cache (api.cu).
@@ -230,6 +231,9 @@ cudaStream_t context_stream(const gslm_ctx* c);
 gslm_status precond_for_cache(gslm_precond* pc, gslm_ctx* ctx, const gslm_cache* c, const float* M, float* D);
 bool context_parts(const gslm_ctx* c, int cache_fmt, ContextParts* out);
 void set_context_error(gslm_ctx* c, const char* msg);
+// Device address, on the current device, of the fixed array gslm_apply_JT_noalloc
+// uses (noalloc.cu); looking it up loads the array's module on that device.
+cudaError_t noalloc_scratch_address(void** out);
 
 // ----------------------------------------------------------------------------
 // Launchers (each defined in the .cu file that holds the kernel).
@@ -329,6 +333,7 @@ cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const ui
                                 float* seg_scale, uint8_t* pixoff,
                                 unsigned long long* seg_entry_off, uint32_t* seg_slot, SegRec* seg_rec,
                                 uint8_t* slot_active, int* err, cudaStream_t st);
+
 
 // apply.cu. `variant` selects one of apply_variants() kernel configurations
 // (entries in flight per lane and register budget); all compute the same result.

@@ -7,22 +7,28 @@
 // gslm_apply_JT keeps its per-segment partial sums in a context-owned buffer
 // that grows with cudaMallocAsync; this variant keeps them in the fixed array
 // below instead and calls no allocating routine.
-#include <mutex>
-
+//
+// Set-up happens in gslm_create, not here: with the context's device current,
+// it looks up the array's device address (the array's name is only a host-side
+// stand-in for it), which loads this file's module and so places the array on
+// that device. Every device on which a context was created holds the array
+// until the process exits; the call itself only reads the stored address.
 #include "internal.cuh"
 
 // Largest cache (in non-empty tile/splat segments) the variant accepts.
 static constexpr long long kNoAllocMaxSegments = 1ll << 19;
 
-// 2^19 segments x 12 floats = 24 MiB of per-segment J^T u partials. Every GPU
-// that loads the library holds this array until the process exits.
+// 2^19 segments x 12 floats = 24 MiB of per-segment J^T u partials.
 static __device__ __align__(256) float g_noalloc_seg_ybar[kNoAllocMaxSegments * 12];
 
-namespace {
-constexpr int kMaxDevices = 256;
-std::mutex g_setup_mu;
-void* g_setup_addr[kMaxDevices] = {};   // device address of the array, per device, set up once
-}  // namespace
+namespace gslm {
+cudaError_t noalloc_scratch_address(void** out) {
+  *out = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(out, g_noalloc_seg_ybar);
+  if (e != cudaSuccess) *out = nullptr;
+  return e;
+}
+}  // namespace gslm
 
 extern "C" gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* cache, const float* u, float* g) {
   gslm::CacheParts cp;
@@ -37,32 +43,19 @@ extern "C" gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* ca
                                  "the most this allocation-free variant holds; use gslm_apply_JT");
     return GSLM_E_INVALID;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != xp.device) {
     cudaGetLastError();
-    gslm::set_context_error(ctx, "apply_JT_noalloc: no usable current CUDA device");
-    return GSLM_E_CUDA;
+    gslm::set_context_error(ctx, "apply_JT_noalloc: the current CUDA device is not the context's device");
+    return GSLM_E_INVALID;
   }
-  void* scratch = nullptr;
-  {
-    // Set-up, once per device, with that device current: the array's name is
-    // only a host-side stand-in, its device address has to be looked up.
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (g_setup_addr[dev] == nullptr) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_seg_ybar);
-      if (e != cudaSuccess || p == nullptr) {
-        cudaGetLastError();
-        gslm::set_context_error(ctx, "apply_JT_noalloc: cudaGetSymbolAddress failed");
-        return GSLM_E_CUDA;
-      }
-      g_setup_addr[dev] = p;
-    }
-    scratch = g_setup_addr[dev];
+  if (xp.noalloc_scratch == nullptr) {
+    gslm::set_context_error(ctx, "apply_JT_noalloc: the fixed array could not be set up when the context was created");
+    return GSLM_E_CUDA;
   }
   // Every segment slot read below is written first in this call, so nothing in
   // the shared array needs clearing.
-  float* seg_ybar = static_cast<float*>(scratch);
+  float* seg_ybar = static_cast<float*>(xp.noalloc_scratch);
   cudaError_t e = gslm::launch_apply_JT(cp.view, u, seg_ybar, xp.variant_JT, xp.st);
   if (e == cudaSuccess)
     e = gslm::launch_vjp(cp.params, cp.N, cp.ld, cp.cams, cp.V, cp.smooth, cp.view.slot_seg_start,

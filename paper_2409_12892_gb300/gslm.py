@@ -72,7 +72,7 @@ class LMStats(ctypes.Structure):
     _fields_ = [("cost", c_double), ("cost_new", c_double), ("predicted", c_double), ("rho", c_double),
                 ("accepted", c_int32), ("pcg_iters", c_int32), ("cache_entries", c_int64),
                 ("cache_bytes", c_int64), ("ms_total", c_double), ("ms_phase", c_double * 8),
-                ("n_pairs", c_int32), ("pad", c_int32), ("pair_bytes", c_double), ("cache_segments", c_int64),
+                ("n_pairs", c_int32), ("trial_overflows", c_int32), ("pair_bytes", c_double), ("cache_segments", c_int64),
                 ("active_splats", c_int64), ("gamma", c_double), ("ls_evals", c_int32), ("seq_groups", c_int32)]
 
 
