@@ -39,6 +39,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "LM-step ms and J*p+J^T*u HBM GB/s at 1.5M Gaussians, chosen vs plain FP32"
+CHOSEN_FORM = "chosen: 16-bit cache, batched subsets in CUDA graphs, preconditioner judged at 1e-3"
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -65,8 +66,10 @@ def parse_args(argv=None):
     ap.add_argument("--train-systems", type=int, default=2, help="subset systems of step 0 trained on")
     ap.add_argument("--skip-equal", action="store_true", help="skip the equal-residual comparison")
     ap.add_argument("--equal-cap", type=int, default=1000, help="PCG iteration cap of the equal-residual step")
-    ap.add_argument("--equal-lambda", type=float, default=1.0,
-                    help="LM damping of the equal-residual step (both forms)")
+    ap.add_argument("--equal-lambdas", default="1e-3,1,1e4",
+                    help="LM dampings of the equal-residual steps (both forms), comma-separated")
+    ap.add_argument("--cpu-views", type=int, default=1, help="views per subset of the CPU oracle sample")
+    ap.add_argument("--detail", default="", help="also write the full record of the run to this JSON file")
     ap.add_argument("--objective", choices=["l2", "l1ssim"], default="l2",
                     help="energy of the LM step: sum of squares (the timed configuration) or Eq. gn-loss")
     ap.add_argument("--line-search", type=int, default=0,
@@ -268,6 +271,8 @@ def run_steps(g, ctx, params, N, cams, targets, wl, steps: int, warmup: int, dis
         ctx.memory_usage(reset_peak=True)         # host-side read of the pool's counters
         state, lm = ctx.lm_step(params, N, cams, targets, subsets, lam, s)
         lm.mem_peak = ctx.memory_usage()["peak"]
+        lm.lam_in = lam
+        lm.n_pix = sum(cams[v].width * cams[v].height for sub in subsets for v in sub)
         lam = state.lambda_
         if s >= warmup:
             stats.append(lm)
@@ -354,43 +359,146 @@ def run_e2e(g, ctx, P_host, N, ld, cams, targets, wl, steps: int, warmup: int, d
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
-ORACLE_SAMPLE = ("FP64 oracle (numpy) build_cache + diag(J^T J) + Algorithm 1 (8 PCG iterations, break 0.01) "
-                 "on the 2,000 Gaussians of cluster 0 nearest its mean, seen by the first 4 views of "
-                 "step 0's first subset at 1264x832; scaled to one LM step by cache entries "
-                 "(E_step / E_sample); trial render and rho evaluation not in the sample")
+# Gaussians of the CPU sample: the trial render of the step at lambda0 draws
+# splats whose log-scales grew by tens, each over the whole view, and sets the
+# oracle's time; this many keep a sample step to a few seconds on 4 cores.
+ORACLE_SAMPLE_GAUSSIANS = 200
+ORACLE_SAMPLE = "oracle LM step: {ng} Gaussians nearest cluster 0's mean, step 0's 4 subsets x {vps} view"
 
 
-def oracle_sample_seconds(workload: str = "paper", reps: int = 1):
-    """Run the oracle sample `reps` times; returns ([seconds], entries of the sample)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample_inputs(workload: str = "paper", views_per_subset: int = 1, n_keep: int = ORACLE_SAMPLE_GAUSSIANS):
+    """The crop's parameters, its subsets' cameras and targets (oracle renders of the perturbed crop)."""
     import warnings
     import numpy as np
     import synth
-    from oracle import jacobian as J, solver
+    from oracle import jacobian as J
     warnings.filterwarnings("ignore")
     wl = synth.WORKLOADS[workload]
     P = synth.make_gaussians(wl)
     cams = synth.make_cameras(wl)
-    idx = synth.crop_2k(wl, P, 2000)
-    views = synth.subset_views(wl, 0)[0][:4]
+    idx = synth.crop_2k(wl, P, n_keep)
+    subsets = [[cams[v] for v in vs[:views_per_subset]] for vs in synth.subset_views(wl, 0)]
     Pc = P[idx].astype(np.float64)
-    cc = [cams[i] for i in views]
-    tgt = J.render(synth.perturbed_copy(wl, P)[idx].astype(np.float64), cc)
-    times, entries = [], 0
-    for _ in range(reps):
+    Pt = synth.perturbed_copy(wl, P)[idx].astype(np.float64)
+    return wl, Pc, subsets, [J.render(Pt, cc) for cc in subsets]
+
+
+def _oracle_subset_worker(conn):
+    """One image subset of an oracle LM step in its own process: build and solve
+    the subset's system, return (Delta_i, M_i, cost_i); then, given the combined
+    Delta, return the subset's predicted and trial costs."""
+    import os as _os
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        _os.environ[k] = "1"
+    import warnings
+    import numpy as np
+    from oracle import jacobian as J, solver
+    warnings.filterwarnings("ignore")
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            return
+        params, cams, tgt, lam, n_iters, brk = msg
+        sys_ = solver.build_subset(params, cams, tgt)
+        d, st = solver.solve_subset(sys_, lam, n_iters, brk)
+        conn.send((d, sys_.M, sys_.cost, sum(vl.a.shape[0] for vl in sys_.lin)))
+        delta = conn.recv()
+        u = J.apply_J(sys_.lin, delta, sys_.F.shape[0]) + sys_.F
+        cost1 = float(np.sum((J.render(params + delta, cams) - tgt) ** 2))
+        conn.send((float(np.dot(u, u)), cost1))
+
+
+def oracle_lm_step_timed(Pc, subsets, targets, lam, n_iters=8, brk=0.01, workers=1) -> dict:
+    """Wall time of one oracle LM step (gamma = 1). workers = 1: oracle.solver.lm_step in
+    this process; workers > 1: the subsets' independent parts (Eq. combine-pcg) run in
+    one process each, the combine and rho here."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import solver
+    if workers <= 1:
         t0 = time.perf_counter()
-        sys_ = solver.build_subset(Pc, cc, tgt)
-        solver.solve_subset(sys_, wl.lambda0, wl.pcg_iters, 0.01)
-        times.append(time.perf_counter() - t0)
-        entries = sum(vl.a.shape[0] for vl in sys_.lin)
-    return times, entries
+        r = solver.lm_step(Pc, subsets, targets, lam, n_iters=n_iters, break_rel2=brk)
+        return {"ms": (time.perf_counter() - t0) * 1e3, "accepted": bool(r.accepted), "rho": r.rho,
+                "cost": r.cost, "cost_new": r.cost_new}
+    ctx = mp.get_context("spawn")
+    procs, conns = [], []
+    for _ in range(len(subsets)):
+        a, b = ctx.Pipe()
+        pr = ctx.Process(target=_oracle_subset_worker, args=(b,), daemon=True)
+        pr.start()
+        procs.append(pr)
+        conns.append(a)
+    try:
+        for c in conns:             # workers up (imports done) before the clock starts
+            c.send((Pc[:1], subsets[0][:1], targets[0][:subsets[0][0].width * subsets[0][0].height * 3],
+                    lam, 0, 0.0))
+            c.recv()
+            c.send(np.zeros_like(Pc[:1]))
+            c.recv()
+        t0 = time.perf_counter()
+        for c, cams, tgt in zip(conns, subsets, targets):
+            c.send((Pc, cams, tgt, lam, n_iters, brk))
+        out = [c.recv() for c in conns]
+        delta = solver.combine([o[0] for o in out], [o[1] for o in out])
+        cost0 = sum(o[2] for o in out)
+        for c in conns:
+            c.send(delta)
+        pc_ = [c.recv() for c in conns]
+        pred = sum(p_ for p_, _ in pc_)
+        cost1 = sum(c_ for _, c_ in pc_)
+        ms = (time.perf_counter() - t0) * 1e3
+        den = cost0 - pred
+        rho = (cost0 - cost1) / den if den > 0 else -math.inf
+        return {"ms": ms, "accepted": bool(den > 0 and rho > 1e-5), "rho": rho, "cost": cost0, "cost_new": cost1,
+                "entries": sum(o[3] for o in out)}
+    finally:
+        for c in conns:
+            try:
+                c.send(None)
+            except (OSError, BrokenPipeError):
+                pass
+        for pr in procs:
+            pr.join(timeout=10)
 
 
-def oracle_subprocess(reps: int) -> dict:
-    """The oracle sample in a fresh single-threaded process (no GPU state inherited)."""
+def cpu_baseline(workload: str = "paper", views_per_subset: int = 1) -> dict:
+    """The oracle LM step on the crop sample, measured at 1 thread and at one process
+    per subset (bounded by the host's cores), with the host CPU recorded."""
+    wl, Pc, subsets, targets = oracle_sample_inputs(workload, views_per_subset)
+    nproc = os.cpu_count() or 1
+    one = oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=1)
+    par = oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=len(subsets))
+    w = min(nproc, len(subsets))
+    return {"value": one["ms"], "unit": "ms per oracle LM step of the sample", "cores": 1, "kind": "oracle",
+            "sample": ORACLE_SAMPLE.format(ng=ORACLE_SAMPLE_GAUSSIANS, vps=views_per_subset),
+            "cpu_model": cpu_model(), "host_cores": nproc,
+            "threads_1_ms": one["ms"], "threads_nproc_ms": par["ms"], "threads_nproc_cores": w}
+
+
+def cpu_baseline_subprocess(workload: str = "paper", views_per_subset: int = 1) -> dict:
+    """cpu_baseline in a fresh process with one BLAS / OpenMP thread (no GPU state inherited)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ("import json, bench; t, e = bench.oracle_sample_seconds('paper', %d); "
-            "print(json.dumps({'times': t, 'entries': e}))" % reps)
+    code = ("import json, bench; print(json.dumps(bench.cpu_baseline(%r, %d)))" % (workload, views_per_subset))
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
@@ -445,28 +553,38 @@ def oracle_step_entries_estimate(workload: str = "paper", n_views: int = 2, tile
 
 # ----------------------------------------------------------------------------- arms
 def run_reference(args):
-    import multiprocessing as mp  # noqa: F401  (no pool: the sample runs in this process)
+    """The oracle on the host cores, on a bounded sample of the workload: each step is
+    one oracle LM step on the crop sample (one process per image subset); the value
+    is scaled to one step of the whole workload by cache entries (an extrapolation,
+    labelled so; the measured sample time is reported beside it)."""
     rank, ws, dist = dist_init("gloo")
     if rank != 0:
         return 0
     t_est0 = time.perf_counter()
     E_step = oracle_step_entries_estimate(args.workload)
     t_est = time.perf_counter() - t_est0
-    res = oracle_subprocess(args.warmup + args.steps)
-    times = res["times"][args.warmup:]
-    scale = E_step / max(res["entries"], 1)
-    value = statistics.mean(times) * scale * 1000.0
+    wl, Pc, subsets, targets = oracle_sample_inputs(args.workload, args.cpu_views)
+    runs = [oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=len(subsets))
+            for _ in range(args.warmup + args.steps)][args.warmup:]
+    sample_ms = statistics.mean(r["ms"] for r in runs)
+    entries = runs[0]["entries"]
+    value = sample_ms * E_step / max(entries, 1)
+    nproc = os.cpu_count() or 1
+    cb = {"value": value, "unit": "ms", "cores": min(nproc, len(subsets)), "kind": "oracle",
+          "sample": ORACLE_SAMPLE.format(ng=ORACLE_SAMPLE_GAUSSIANS, vps=args.cpu_views), "cpu_model": cpu_model(), "host_cores": nproc,
+          "value_kind": "extrapolated: measured sample ms x (cache entries of one workload step, estimated by the "
+                        "oracle on a 5% tile sample of two views) / (cache entries of the sample)",
+          "measured_sample_ms": sample_ms, "sample_entries": entries, "step_entries_estimate": E_step,
+          "estimate_seconds": t_est}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, "oracle"),
-        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE,
-                         "sample_seconds": statistics.mean(times), "sample_entries": res["entries"],
-                         "step_entries_estimate": E_step, "estimate_seconds": t_est},
+        "config": dict(workload_config(args, CHOSEN_FORM), cache_fmt=args.cache_fmt),
+        "cpu_baseline": cb,
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(sig(line)), flush=True)
     return 0
 
 
@@ -480,7 +598,7 @@ def workload_config(args, form: str) -> dict:
                      + " views per LM step"),
         "form": form, "pcg_iters": wl.pcg_iters, "break_rel2": 0.01, "lambda0": wl.lambda0,
         "line_search": args.line_search, "objective": args.objective,
-        "l2_flush": "inputs larger than L2: the gradient caches of a step are tens of GB",
+        "l2_flush": "inputs larger than L2",
         "parallelism": f"{args.gpus} independent replicas" if args.gpus > 1 else "single GPU",
     }
 
@@ -510,12 +628,8 @@ def pair_roofline(stats, peak: dict, fmt: int = None) -> dict:
     return {"bound": "hbm", "achieved": gbs, "peak": peak["hbm_gbs"], "unit": "GB/s",
             "frac": gbs / peak["hbm_gbs"],
             "traffic": ratio * b / max(n, 1) if ratio is not None else None,
-            "traffic_note": ("DRAM bytes per pair: ncu dram read + write per algorithmic byte on the 100k-Gaussian "
-                             "case, scaled by this pair's algorithmic bytes" if ratio is not None else None),
-            "kernel": "J p + J^T u pair: tangent, apply_J, apply_JT, adjoint kernels",
-            "algorithmic_bytes_per_pair": b / max(n, 1), "ms_per_pair": t * 1e3 / max(n, 1),
-            "peak_source": peak["source"] + " (MEASURED_PEAKS.json hbm_gbs)" if peak["source"] == "measured"
-            else "fallback 6.8 TB/s"}
+            "bytes_per_pair": b / max(n, 1), "ms_per_pair": t * 1e3 / max(n, 1),
+            "peak_source": "measured" if peak["source"] == "measured" else "fallback 6.8 TB/s"}
 
 
 def subset_targets(targets, cams, views):
@@ -560,31 +674,30 @@ def train_precond(g, ctx, params, N, cams, targets, wl, args):
     return pc, rep
 
 
-def judge_precond(g, ctx, pc, params, N, cams, targets, wl, cap: int = 64) -> dict:
-    """Jacobi against the network on LM step 0's first subset system: PCG
-    iterations to the paper's break test (||r|| <= 0.1 ||b||) and the relative
-    residual after the paper's 8 iterations. The network is kept only if it
-    needs fewer iterations."""
-    import math as m
+def judge_precond(g, ctx, pc, params, N, cams, targets, wl, lambdas, cap: int = 200, rel: float = 1e-3) -> dict:
+    """The rule for keeping the learned preconditioner: on LM step 0's first subset
+    system, PCG iterations to ||r|| <= rel ||b|| with the network against Jacobi at
+    every damping in `lambdas` (the values the timed steps run at, from lambda0 up);
+    the network is kept only if it needs fewer iterations than Jacobi at each of them."""
     import synth
     vs = synth.subset_views(wl, 0)[0]
     cache = ctx.build_cache(params, N, [cams[v] for v in vs], subset_targets(targets, cams, vs), want_F=False)
     diag = ctx.jacobi_diag(cache)
     D = pc.apply(ctx.precond_features(cache, diag), diag)
-    out = {}
-    for name, pre in (("jacobi", None), ("learned", D)):
-        ctx.set_options(n_iters=cap, break_rel2=0.01)
-        _, st, _ = ctx.pcg_solve(cache, cache.b, diag, wl.lambda0, precond=pre)
-        ctx.set_options(n_iters=wl.pcg_iters, break_rel2=0.0)
-        _, st8, _ = ctx.pcg_solve(cache, cache.b, diag, wl.lambda0, precond=pre)
-        out[name] = {"iters_to_0.1": st.iters if st.rr < 0.01 * st.bb else None,
-                     "rel_residual_after_8": m.sqrt(st8.rr / st8.bb) if st8.bb > 0 else None}
+    rows = []
+    ctx.set_options(n_iters=cap, break_rel2=rel * rel)
+    for lam in lambdas:
+        row = {"lambda": lam}
+        for name, pre in (("jacobi", None), ("learned", D)):
+            _, st, _ = ctx.pcg_solve(cache, cache.b, diag, lam, precond=pre)
+            row[name] = st.iters if st.rr <= rel * rel * st.bb else None
+        rows.append(row)
     ctx.set_options(n_iters=wl.pcg_iters, break_rel2=0.01)
     cache.free()
-    ij, il = out["jacobi"]["iters_to_0.1"], out["learned"]["iters_to_0.1"]
-    out["keep_learned"] = il is not None and (ij is None or il < ij)
-    out["rule"] = "keep the network only if it reaches ||r|| <= 0.1 ||b|| in fewer PCG iterations than Jacobi"
-    return out
+    keep = all(r["learned"] is not None and (r["jacobi"] is None or r["learned"] < r["jacobi"]) for r in rows)
+    return {"iters_to_1e-3": rows, "cap": cap, "keep_learned": keep,
+            "rule": "keep the network only if it reaches ||r|| <= 1e-3 ||b|| in fewer PCG iterations than Jacobi "
+                    "at every damping the timed steps use"}
 
 
 def psnr_from_cost(cost: float, n_pix: int) -> float:
@@ -632,6 +745,42 @@ def profiled_step(g, ctx, params, N, cams, targets, wl, step: int):
     return lm
 
 
+def sig(x, n: int = 4):
+    """x rounded to n significant digits (recursively through lists and dicts), so
+    that the JSON line stays short."""
+    if isinstance(x, float):
+        if not math.isfinite(x) or x == 0.0:
+            return x
+        return float(f"{x:.{n}g}")
+    if isinstance(x, dict):
+        return {k: sig(v, n) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, n) for v in x]
+    return x
+
+
+def timed_lambdas(wl, steps: int, warmup: int) -> list:
+    """Dampings the judge checks: lambda0 and the first and last damping of the timed
+    steps when every step is rejected (lambda doubles per rejection), clamped."""
+    cl = lambda v: min(max(v, wl.lambda_min), wl.lambda_max)
+    return sorted({cl(wl.lambda0), cl(wl.lambda0 * 2.0 ** warmup), cl(wl.lambda0 * 2.0 ** (warmup + steps - 1))})
+
+
+def equal_forms(g, ctx, pc, P, N, ld, cams, targets, wl, dev, lambdas, cap, args, with_learned) -> dict:
+    """equal_residual_step at each damping: Jacobi, and the network capped at Jacobi's iterations."""
+    out = {}
+    for lam in lambdas:
+        ej = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap, lam=lam,
+                                 ls=args.equal_line_search, ls_timed=args.line_search)
+        row = {"jacobi": ej}
+        if with_learned and pc is not None:
+            cap_l = max(1, int(math.ceil(ej["pcg_iters_per_subset"])))
+            row["learned"] = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap_l, pc, lam=lam,
+                                                 ls=args.equal_line_search, ls_timed=args.line_search)
+        out[lam] = row
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2409_12892_gb300 as g
@@ -648,6 +797,7 @@ def run_ours(args):
     wl, P, cams, targets = build_workload(wl, dev)
     N = P.shape[0]
     ld = g.padded_ld(N)
+    eq_lams = [float(v) for v in args.equal_lambdas.split(",") if v.strip()]
     result = {}
     forms = [("chosen", args.cache_fmt)]
     if not args.skip_plain:
@@ -661,7 +811,8 @@ def run_ours(args):
         pc, train, judge = None, None, None
         if chosen and args.precond == "learned":
             pc, train = train_precond(g, ctx, params, N, cams, targets, wl, args)
-            judge = judge_precond(g, ctx, pc, params, N, cams, targets, wl)
+            judge = judge_precond(g, ctx, pc, params, N, cams, targets, wl,
+                                  timed_lambdas(wl, args.steps, args.warmup))
             if judge["keep_learned"]:
                 ctx.set_precond(pc)
         clocks = ClockSampler(local) if chosen else None
@@ -687,23 +838,9 @@ def run_ours(args):
         del params
         torch.cuda.empty_cache()
         if not args.skip_equal:
-            if chosen:
-                # the plain form runs later; the learned run is capped at the cap, Jacobi first
-                eq_j = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, args.equal_cap,
-                                           lam=args.equal_lambda, ls=args.equal_line_search,
-                                           ls_timed=args.line_search)
-                eq = {"jacobi": eq_j}
-                if pc is not None:
-                    cap_l = max(1, int(math.ceil(eq_j["pcg_iters_per_subset"])))
-                    eq["learned"] = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, cap_l, pc,
-                                                        lam=args.equal_lambda, ls=args.equal_line_search,
-                                                        ls_timed=args.line_search)
-                    eq["learned"]["cap"] = cap_l
-                result[form]["equal"] = eq
-            else:
-                result[form]["equal"] = equal_residual_step(g, ctx, P, N, ld, cams, targets, wl, dev, args.equal_cap,
-                                                            lam=args.equal_lambda, ls=args.equal_line_search,
-                                                            ls_timed=args.line_search)
+            ctx.set_precond(None)
+            result[form]["equal"] = equal_forms(g, ctx, pc, P, N, ld, cams, targets, wl, dev, eq_lams,
+                                                args.equal_cap, args, chosen)
         ctx.set_precond(None)
         if pc is not None:
             pc.free()
@@ -715,63 +852,80 @@ def run_ours(args):
     stats = ch["stats"]
     E_step = statistics.mean(s.cache_entries for s in stats)
     pre = "learned preconditioner" if ch["precond"] == "learned" else "Jacobi"
+    fmt_name = {"fp32": "f32", "bf16": "bf16-cache/f32-accumulate", "fp16s": "f16-scaled-cache/f32-accumulate"}
+    detail = {}
     line = {
         "metric": METRIC, "value": ch["ms"], "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ch["ms"], "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(args, f"chosen: {ch['fmt']} cache, {pre}, batched subsets in one CUDA graph"),
-                       cache_fmt=ch["fmt"]),
+        "vs_baseline": None, "dtype": fmt_name.get(ch["fmt"], ch["fmt"]), "data": "synthetic",
+        "gpu_launches": ch["launches"] // max(args.steps, 1),
+        "config": dict(workload_config(args, CHOSEN_FORM), cache_fmt=ch["fmt"]),
+        "precond": ch["precond"],
         "roofline": pair_roofline(ch["prof"], peak, {"fp32": 0, "bf16": 1, "fp16s": 2}.get(ch["fmt"])),
         "e2e": result.get("e2e"),
-        "clocks": ch["clocks"],
-        "clocks_remeasured": ch["remeasured"],
-        "gpu_launches": ch["launches"] // max(args.steps, 1),
-        "gpu_launches_total": ch["launches"],
-        "phase_ms": summarize_phases(ch["prof"]),
-        "phase_ms_note": "one extra LM step with per-phase CUDA events after the timed steps",
-        "autotune": ch["autotune"],
-        "precond_training": ch["train"],
-        "precond_judge": ch["judge"],
-        "lm": {"accepted": [int(s.accepted) for s in stats], "rho": [s.rho for s in stats],
-               "gamma": [s.gamma for s in stats], "line_search_evals": [s.ls_evals for s in stats],
-               "cost": [s.cost for s in stats], "cost_new": [s.cost_new for s in stats],
-               "predicted": [s.predicted for s in stats], "pcg_iters": [s.pcg_iters for s in stats],
+        "clocks": {k: v for k, v in (ch["clocks"] or {}).items() if k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "phase_ms": sig(summarize_phases(ch["prof"]), 3),
+        "lm": {"lambda": sig([s.lam_in for s in stats], 2),
+               "accepted": "".join(str(int(s.accepted)) for s in stats),
+               "rho": sig([s.rho for s in stats], 2), "pcg_iters": [s.pcg_iters for s in stats],
+               "trial_overflows": sum(s.trial_overflows for s in stats),
+               "psnr_first_last": [psnr_from_cost(stats[0].cost, stats[0].n_pix),
+                                   psnr_from_cost(stats[-1].cost_new if stats[-1].accepted else stats[-1].cost,
+                                                  stats[-1].n_pix)],
                "cache_entries": E_step, "cache_gb": statistics.mean(s.cache_bytes for s in stats) / 1e9,
-               "cache_segments": statistics.mean(s.cache_segments for s in stats),
-               "active_splats": statistics.mean(s.active_splats for s in stats),
-               "sequential_groups": [s.seq_groups for s in stats],
                "device_peak_gb": max(s.mem_peak for s in stats) / 1e9},
     }
+    detail["lm_ms"] = [s.ms_total for s in stats]
+    detail["clocks"] = ch["clocks"]
+    if ch["remeasured"] is not None:
+        line["clocks_remeasured"] = ch["remeasured"]
+    if ch["judge"] is not None:
+        line["precond_judge"] = {"keep": ch["judge"]["keep_learned"],
+                                 "iters_to_1e-3": [[r["lambda"], r["jacobi"], r["learned"]]
+                                                   for r in ch["judge"]["iters_to_1e-3"]]}
+        detail["precond_judge"] = ch["judge"]
+        detail["precond_training"] = ch["train"]
     if "plain" in result:
         pl = result["plain"]
-        line["plain_fp32"] = {"ms_per_step": pl["ms"], "roofline": pair_roofline(pl["stats"], peak, 0),
-                              "autotune": pl["autotune"],
-                              "phase_ms": summarize_phases(pl["stats"]),
-                              "cache_gb": statistics.mean(s.cache_bytes for s in pl["stats"]) / 1e9}
+        rf = pair_roofline(pl["stats"], peak, 0)
+        line["plain_fp32"] = {"ms": pl["ms"], "pair_frac": rf["frac"]}
         line["speedup_vs_plain"] = pl["ms"] / ch["ms"]
+        detail["plain_fp32"] = {"roofline": rf, "autotune": pl["autotune"], "phase_ms": summarize_phases(pl["stats"]),
+                                "cache_gb": statistics.mean(s.cache_bytes for s in pl["stats"]) / 1e9}
     if "equal" in ch:
-        eqc = ch["equal"]
-        cands = [e for e in (eqc.get("learned"), eqc["jacobi"]) if e is not None and e["reached"]]
-        best = min(cands, key=lambda e: e["ms"]) if cands else eqc["jacobi"]
-        eq = {"chosen": best, "chosen_jacobi": eqc["jacobi"], "chosen_learned": eqc.get("learned"),
-              "rel_residual": 1e-3, "pcg_iteration_cap": args.equal_cap,
-              "rule": "chosen = the faster of the BF16 batched form with Jacobi and with the network, among runs "
-                      "that reached 1e-3 (the network's run is capped at Jacobi's iterations per subset)",
-              "lambda": args.equal_lambda,
-              "note": "one LM step from the initial parameters, every subset solved to ||r|| <= 1e-3 ||b||"}
-        if "plain" in result and "equal" in result["plain"]:
-            pe = result["plain"]["equal"]
-            eq["plain_fp32_jacobi"] = pe
-            eq["speedup"] = pe["ms"] / best["ms"]
-            eq["pcg_iteration_ratio"] = best["pcg_iters_total"] / max(pe["pcg_iters_total"], 1)
-            eq["psnr_after_diff_db"] = best["psnr_after_db"] - pe["psnr_after_db"]
-        line["equal_residual"] = eq
+        eqs, short = {}, []
+        for lam, row in ch["equal"].items():
+            cands = [e for e in (row.get("learned"), row["jacobi"]) if e is not None and e["reached"]]
+            best = min(cands, key=lambda e: e["ms"]) if cands else row["jacobi"]
+            ent = {"chosen": best, "chosen_jacobi": row["jacobi"], "chosen_learned": row.get("learned")}
+            # per damping: ms [chosen, plain], iterations per subset, reached / accepted
+            # [chosen, plain], PSNR [before, after chosen, after plain], speedup
+            srow = {"lambda": lam, "ms": [best["ms"]], "its": best["pcg_iters_per_subset"],
+                    "reached": [int(best["reached"])], "accepted": [best["accepted"]],
+                    "psnr": [sig(best["psnr_before_db"], 6), sig(best["psnr_after_db"], 6)]}
+            if best["precond"] != "jacobi":
+                srow["precond"] = best["precond"]
+            pe = result.get("plain", {}).get("equal", {}).get(lam)
+            if pe is not None:
+                pj = pe["jacobi"]
+                ent["plain_fp32_jacobi"] = pj
+                srow["ms"].append(pj["ms"])
+                srow["reached"].append(int(pj["reached"]))
+                srow["accepted"].append(pj["accepted"])
+                srow["psnr"].append(sig(pj["psnr_after_db"], 6))
+                srow["speedup"] = pj["ms"] / best["ms"]
+            eqs[lam] = ent
+            short.append(srow)
+        line["equal_residual"] = {"cap": args.equal_cap, "steps": short}
+        detail["equal_residual"] = {str(k): v for k, v in eqs.items()}
     if not args.skip_cpu:
-        res = oracle_subprocess(1)
-        t = res["times"][0]
-        v = t * (E_step / max(res["entries"], 1)) * 1000.0
-        line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE,
-                                "sample_seconds": t, "sample_entries": res["entries"], "step_entries": E_step}
+        cb = cpu_baseline_subprocess(args.workload, args.cpu_views)
+        line["cpu_baseline"] = cb
+    detail["autotune"] = ch["autotune"]
+    line = sig(line)
+    if args.detail:
+        with open(args.detail, "w") as f:
+            json.dump(sig(dict(detail, line=line), 6), f, indent=1)
     print(json.dumps(line), flush=True)
     return 0
 

@@ -65,7 +65,7 @@ def test_pair_roofline_arithmetic():
     r = bench.pair_roofline([st, st], peak, 1)
     assert r["achieved"] == pytest.approx(18e9 / 20e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 5000.0)
-    assert r["algorithmic_bytes_per_pair"] == pytest.approx(1e9)
+    assert r["bytes_per_pair"] == pytest.approx(1e9)
     assert r["ms_per_pair"] == pytest.approx(20.0 / 18)
     assert r["traffic"] == pytest.approx(bench.PAIR_DRAM_PER_ALG_BYTE[1] * 1e9)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
