@@ -70,6 +70,8 @@ def parse_args(argv=None):
                     help="LM dampings of the equal-residual steps (both forms), comma-separated")
     ap.add_argument("--cpu-views", type=int, default=1, help="views per subset of the CPU oracle sample")
     ap.add_argument("--detail", default="", help="also write the full record of the run to this JSON file")
+    ap.add_argument("--cpu-suite", default="",
+                    help="only time the oracle on the host (comma list of tiny, crop, medium_subset) and print it")
     ap.add_argument("--objective", choices=["l2", "l1ssim"], default="l2",
                     help="energy of the LM step: sum of squares (the timed configuration) or Eq. gn-loss")
     ap.add_argument("--line-search", type=int, default=0,
@@ -82,6 +84,9 @@ def parse_args(argv=None):
     ap.add_argument("--apply-views", type=int, default=8)
     ap.add_argument("--apply-variant", type=int, default=3, help="1..8: forced apply kernel variant 0..7")
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--formats", default="",
+                    help="with --apply-pass: cache formats to compare (e.g. fp32,bf16,thin): bytes and the times "
+                         "of J p, J^T u and diag(J^T J) on the same views")
     return ap.parse_args(argv)
 
 
@@ -492,6 +497,55 @@ def cpu_baseline(workload: str = "paper", views_per_subset: int = 1) -> dict:
             "sample": ORACLE_SAMPLE.format(ng=ORACLE_SAMPLE_GAUSSIANS, vps=views_per_subset),
             "cpu_model": cpu_model(), "host_cores": nproc,
             "threads_1_ms": one["ms"], "threads_nproc_ms": par["ms"], "threads_nproc_cores": w}
+
+
+def cpu_suite(items=("tiny", "crop", "medium_subset")) -> dict:
+    """The oracle timed outright on the host cores, for the record (not run by the
+    default bench): the tiny workload's 5 LM steps (one subset, so one thread);
+    the paper crop's LM step (2,000 Gaussians, step 0's 4 subsets x 1 view) at one
+    thread and one process per subset; one 8-view subset of the medium workload
+    (cache, diag and 8-iteration PCG) at one thread."""
+    import warnings
+    import numpy as np
+    import synth
+    from oracle import jacobian as J, solver
+    warnings.filterwarnings("ignore")
+    out = {"cpu_model": cpu_model(), "host_cores": os.cpu_count()}
+    if "tiny" in items:
+        wl = synth.WORKLOADS["tiny"]
+        P = synth.make_gaussians(wl).astype(np.float64)
+        cams = synth.make_cameras(wl)
+        tgt = J.render(synth.perturbed_copy(wl, P).astype(np.float64), cams) + synth.pixel_noise(wl, sum(
+            c.width * c.height * 3 for c in cams))
+        lam, steps, t0 = wl.lambda0, [], time.perf_counter()
+        for s in range(5):
+            t1 = time.perf_counter()
+            r = solver.lm_step(P, [cams], [tgt], lam, n_iters=wl.pcg_iters, break_rel2=0.01)
+            steps.append({"ms": (time.perf_counter() - t1) * 1e3, "accepted": int(r.accepted), "lambda": lam})
+            P, lam = r.params, r.lam
+        out["tiny_5_lm_steps"] = {"ms": (time.perf_counter() - t0) * 1e3, "cores": 1, "steps": steps}
+    if "crop" in items:
+        wl, Pc, subsets, targets = oracle_sample_inputs("paper", 1, 2000)
+        one = oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=1)
+        par = oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=len(subsets))
+        out["paper_crop_2k_lm_step"] = {"threads_1_ms": one["ms"], "procs_4_ms": par["ms"],
+                                        "sample": "2,000 Gaussians nearest cluster 0's mean, 4 subsets x 1 view"}
+    if "medium_subset" in items:
+        wl = synth.WORKLOADS["medium"]
+        P = synth.make_gaussians(wl).astype(np.float64)
+        cams = synth.make_cameras(wl)
+        vs = synth.subset_views(wl, 0)[0]
+        cc = [cams[v] for v in vs]
+        tgt = J.render(synth.perturbed_copy(wl, P).astype(np.float64), cc)
+        t0 = time.perf_counter()
+        sys_ = solver.build_subset(P, cc, tgt)
+        t1 = time.perf_counter()
+        solver.solve_subset(sys_, wl.lambda0, wl.pcg_iters, 0.01)
+        t2 = time.perf_counter()
+        out["medium_one_subset"] = {"build_ms": (t1 - t0) * 1e3, "pcg_ms": (t2 - t1) * 1e3, "cores": 1,
+                                    "entries": int(sum(vl.a.shape[0] for vl in sys_.lin)),
+                                    "views": len(cc)}
+    return out
 
 
 def cpu_baseline_subprocess(workload: str = "paper", views_per_subset: int = 1) -> dict:
@@ -983,8 +1037,70 @@ def run_apply_pass(args):
     return 0
 
 
+def run_format_pass(args):
+    """Per cache format, one cache of the first --apply-views cameras: device bytes,
+    build time and the median of 5 timed J p (with the tangent), J^T u (with the
+    per-splat sums and the adjoint) and diag(J^T J) calls (CUDA events), one JSON line."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2409_12892_gb300 as g
+    from paper_2409_12892_gb300 import build as b
+    b.build()
+    wl = workload(args)
+    P = synth.make_gaussians(wl)
+    cams = synth.make_cameras(wl)[:args.apply_views]
+    N = P.shape[0]
+    params = g.to_soa(P)
+    tg = torch.empty((g.n_pixels(cams), 3), device="cuda")
+    g.Context().render(g.to_soa(synth.perturbed_copy(wl, P)), N, cams, img=tg)
+    u = torch.from_numpy(synth.random_vector(5, (g.n_pixels(cams), 3)).astype(np.float32)).cuda()
+    out = {"mode": "format-pass", "workload": wl.name, "views": len(cams)}
+
+    def timed(call, reps=6):
+        ts = []
+        for r in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            call()
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for fmt in args.formats.split(","):
+        ctx = g.Context(cache_fmt=fmt)
+        torch.cuda.synchronize()
+        cache = ctx.build_cache(params, N, cams, tg)
+        cache.free()
+        t_build = timed(lambda: ctx.build_cache(params, N, cams, tg).free(), reps=3)
+        cache = ctx.build_cache(params, N, cams, tg)
+        info = cache.info()
+        p = torch.from_numpy(synth.random_vector(3, (59, cache.ld)).astype(np.float32)).cuda()
+        uo = ctx.apply_J(cache, p)
+        go = ctx.apply_JT(cache, u)
+        dg = ctx.jacobi_diag(cache)
+        out[fmt] = {"entries": info.entries, "segments": info.segments, "bytes": info.bytes,
+                    "build_ms": t_build, "J_ms": timed(lambda: ctx.apply_J(cache, p, uo)),
+                    "JT_ms": timed(lambda: ctx.apply_JT(cache, u, go)),
+                    "diag_ms": timed(lambda: ctx.jacobi_diag(cache, dg))}
+        cache.free()
+        ctx.close()
+        torch.cuda.empty_cache()
+    print(json.dumps(sig(out)), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.cpu_suite:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(k, "1")
+        print(json.dumps(sig(cpu_suite(tuple(args.cpu_suite.split(","))))), flush=True)
+        return 0
+    if args.apply_pass and args.formats:
+        return run_format_pass(args)
     if args.apply_pass:
         return run_apply_pass(args)
     if args.impl == "reference":

@@ -67,7 +67,19 @@ typedef enum {
   GSLM_W_PCG_BREAKDOWN = 1    /* PCG stopped early: p^T g <= 0 or not finite */
 } gslm_status;
 
-typedef enum { GSLM_CACHE_FP32 = 0, GSLM_CACHE_BF16 = 1, GSLM_CACHE_FP16S = 2 } gslm_cache_fmt;
+/* Cache formats. FP32, BF16 and FP16S store one entry per contributing
+ * (pixel, splat) pair: its weight alpha T and alpha dc/dalpha, in float32, in
+ * bfloat16, or in float16 scaled per (tile, splat) segment.
+ * GSLM_CACHE_THIN stores no entries: the cache keeps, per (tile, splat)
+ * segment, the projected splat; per pixel, its final colour and how many of its
+ * tile's segments reach it before blending stops; and a checkpoint of the
+ * pixel's transmittance and colour prefix before every 32nd segment of its tile
+ * (the memory-saving thinning the paper's limitations section proposes). J p,
+ * J^T u and diag(J^T J) then blend each pixel's splats again, J^T u and the
+ * diagonal window by window from those checkpoints. It takes several times
+ * less memory and more time per product; gslm_pcg_solve_batch and the batched
+ * gslm_lm_step solve thin caches one subset after another. */
+typedef enum { GSLM_CACHE_FP32 = 0, GSLM_CACHE_BF16 = 1, GSLM_CACHE_FP16S = 2, GSLM_CACHE_THIN = 3 } gslm_cache_fmt;
 
 /* The energy the LM step minimises.
  * GSLM_OBJ_L2: residual c - C per pixel channel, E = ||c - C||^2.

@@ -120,6 +120,9 @@ struct gslm_cache {
   Buf cams, rec, slot_active, tile_seg_off, seg_entry_off, seg_slot, seg_rec, payload, seg_scale, pixoff;
   Buf slot_seg_start, slot_seg_end, slot_seg_list, seg_pos, F, own_params, vmask, act_off;
   Buf W;   // residual-to-pixel weights [n_pix][3] (L1 + SSIM objective only)
+  // thin caches (GSLM_CACHE_THIN) only
+  Buf thin_rec, img, n_live, win_off, win_tile, ckpt;
+  long long n_win = 0;
 
   CacheView view() const {
     CacheView cv;
@@ -149,6 +152,13 @@ struct gslm_cache {
     cv.fmt = fmt;
     cv.skip = nullptr;
     cv.wres = W.as<float>();
+    cv.thin_rec = thin_rec.as<SplatRec>();
+    cv.img = img.as<float>();
+    cv.n_live = n_live.as<uint32_t>();
+    cv.win_off = win_off.as<uint32_t>();
+    cv.win_tile = win_tile.as<uint32_t>();
+    cv.ckpt = ckpt.as<float4>();
+    cv.n_win = n_win;
     return cv;
   }
   // splat tangents the tangent kernel writes: one per active splat (compact
@@ -158,7 +168,18 @@ struct gslm_cache {
     return cams.bytes + rec.bytes + slot_active.bytes + tile_seg_off.bytes + seg_entry_off.bytes + seg_slot.bytes +
            seg_rec.bytes +
            payload.bytes + seg_scale.bytes + pixoff.bytes + slot_seg_start.bytes + slot_seg_end.bytes +
-           slot_seg_list.bytes + seg_pos.bytes + F.bytes + own_params.bytes + vmask.bytes + act_off.bytes + W.bytes;
+           slot_seg_list.bytes + seg_pos.bytes + F.bytes + own_params.bytes + vmask.bytes + act_off.bytes + W.bytes +
+           thin_rec.bytes + img.bytes + n_live.bytes + win_off.bytes + win_tile.bytes + ckpt.bytes;
+  }
+  // Algorithmic bytes of one J p + J^T u pair through this cache (N Gaussians):
+  // entries (payload and pixel offset), or for a thin cache the segment
+  // records, checkpoints and per-pixel counts the kernels read; u written and
+  // read, p read and g written, and the per-splat tangent and adjoint records.
+  double pair_bytes(int N_) const {
+    const double stream = fmt == GSLM_CACHE_THIN
+                              ? (double)n_seg * 96.0 + (double)n_win * kTilePix * 16.0 + (double)n_tiles * kTilePix * 8.0
+                              : (double)n_entries * (double)((fmt == GSLM_CACHE_FP32 ? 16 : 8) + 1);
+    return 2.0 * stream + 24.0 * (double)n_pix + 472.0 * (double)N_ + 192.0 * (double)n_active;
   }
 };
 
@@ -193,7 +214,7 @@ int bits_for(unsigned long long n) {
   return b;
 }
 
-size_t payload_bytes(int fmt) { return fmt == GSLM_CACHE_FP32 ? 16 : 8; }
+size_t payload_bytes(int fmt) { return fmt == GSLM_CACHE_FP32 ? 16 : fmt == GSLM_CACHE_THIN ? 0 : 8; }
 
 // Cameras of a call with their tile/pixel offsets.
 gslm_status make_cams(gslm_ctx* ctx, const gslm_camera* cams, int V, std::vector<DevCam>& out, int& n_tiles,
@@ -392,6 +413,11 @@ gslm_status do_apply_J(gslm_ctx* ctx, const gslm_cache* c, const float* p, float
   cv.skip = sc != nullptr ? &sc->done : nullptr;
   ctx->timer.end(t);
   t = ctx->timer.begin(PH_APPLY_J);
+  if (c->fmt == GSLM_CACHE_THIN) {   // blends the tile's segments again; no kernel variants
+    CK(launch_thin_apply_J(cv, ctx->ydot.as<float>(), Fadd, u, sq_partials, st));
+    ctx->timer.end(t);
+    return GSLM_OK;
+  }
   int& var = ctx->var_J[c->fmt];
   if (ctx->opt.apply_variant > 0) {
     CK(launch_apply_J(cv, ctx->ydot.as<float>(), Fadd, u, sq_partials, ctx->opt.apply_variant - 1, st));
@@ -413,9 +439,12 @@ gslm_status do_apply_JT(gslm_ctx* ctx, const gslm_cache* c, const float* u, floa
   CacheView cv = c->view();
   cv.skip = sc != nullptr ? &sc->done : nullptr;
   bool t = ctx->timer.begin(PH_APPLY_JT);
-  int& var = ctx->var_JT[c->fmt];
   float* sy = ctx->seg_ybar.as<float>();
-  if (ctx->opt.apply_variant > 0) {
+  int var_dummy = 0;
+  int& var = c->fmt == GSLM_CACHE_THIN ? var_dummy : ctx->var_JT[c->fmt];
+  if (c->fmt == GSLM_CACHE_THIN) {   // window by window from the checkpoints
+    CK(launch_thin_apply_JT(cv, u, sy, st));
+  } else if (ctx->opt.apply_variant > 0) {
     CK(launch_apply_JT(cv, u, sy, ctx->opt.apply_variant - 1, st));
   } else if (var < 0 && ctx->opt.autotune) {
     CKS(tune_variant(ctx, [&](int v) { return launch_apply_JT(cv, u, sy, v, st); }, &var, &ctx->ms_JT[c->fmt]));
@@ -798,10 +827,12 @@ bool cache_parts(const gslm_cache* c, CacheParts* out) {
 }
 
 bool context_parts(const gslm_ctx* c, int cache_fmt, ContextParts* out) {
-  if (c == nullptr || out == nullptr || cache_fmt < 0 || cache_fmt > 2) return false;
+  if (c == nullptr || out == nullptr || cache_fmt < 0 || cache_fmt > 3) return false;
   out->st = c->st;
-  // the variant do_apply_JT would run: forced by the options, else tuned, else the default
-  if (c->opt.apply_variant > 0) out->variant_JT = c->opt.apply_variant - 1;
+  // the variant do_apply_JT would run: forced by the options, else tuned, else
+  // the default (thin caches have one kernel)
+  if (cache_fmt == GSLM_CACHE_THIN) out->variant_JT = 0;
+  else if (c->opt.apply_variant > 0) out->variant_JT = c->opt.apply_variant - 1;
   else out->variant_JT = c->var_JT[cache_fmt] >= 0 ? c->var_JT[cache_fmt] : kDefaultVariant;
   out->device = c->device;
   out->noalloc_scratch = c->noalloc_scratch;
@@ -890,7 +921,7 @@ void gslm_default_options(gslm_options* o) {
 }
 
 static gslm_status validate_opts(const gslm_options* o) {
-  if (o->cache_fmt < 0 || o->cache_fmt > 2) return GSLM_E_INVALID;
+  if (o->cache_fmt < 0 || o->cache_fmt > 3) return GSLM_E_INVALID;
   if (o->n_iters < 0 || o->n_iters > 100000) return GSLM_E_INVALID;
   if (!(o->lambda_min > 0.f) || !(o->lambda_max >= o->lambda_min)) return GSLM_E_INVALID;
   if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
@@ -1013,6 +1044,8 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
   c->V = V;
   c->smooth = ctx->opt.smooth;
   c->fmt = ctx->opt.cache_fmt;
+  const bool thin = c->fmt == GSLM_CACHE_THIN;
+  if (thin && c->smooth) return fail(ctx, GSLM_E_INVALID, "build_cache: thin caches are built in the default mode only");
   CKS(make_cams(ctx, cams, V, c->hcams, c->n_tiles, c->n_pix));
   if (copy_params) {
     CK(c->own_params.alloc(sizeof(float) * kNP * (size_t)ld, st));
@@ -1045,9 +1078,18 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
                         B.scan_tmp.p, st));
   CK(exclusive_scan_u32(tile_segs.as<uint32_t>(), c->tile_seg_off.as<uint32_t>(), n_tiles, B.scan_tmp.p, st));
   unsigned long long E = 0;
-  uint32_t nseg = 0;
+  uint32_t nseg = 0, nwin = 0;
   CK(cudaMemcpyAsync(&E, tile_entry_off.as<unsigned long long>() + n_tiles, sizeof(E), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&nseg, c->tile_seg_off.as<uint32_t>() + n_tiles, sizeof(nseg), cudaMemcpyDeviceToHost, st));
+  if (thin) {
+    // checkpoint windows: ceil(segments / 32) per tile
+    Buf wcount;
+    CK(wcount.alloc(sizeof(uint32_t) * (n_tiles + 1), st));
+    CK(c->win_off.alloc(sizeof(uint32_t) * (n_tiles + 1), st));
+    CK(launch_thin_window_counts(c->tile_seg_off.as<uint32_t>(), n_tiles, wcount.as<uint32_t>(), st));
+    CK(exclusive_scan_u32(wcount.as<uint32_t>(), c->win_off.as<uint32_t>(), n_tiles, B.scan_tmp.p, st));
+    CK(cudaMemcpyAsync(&nwin, c->win_off.as<uint32_t>() + n_tiles, sizeof(nwin), cudaMemcpyDeviceToHost, st));
+  }
   CKS(reduce_to_host(ctx, cost_part.as<double>(), n_tiles, &c->cost));
   if (ctx->opt.objective == GSLM_OBJ_L1_SSIM) {
     // Eq. gn-loss: F becomes e = sum (dr/dc) r, the weights w = sum (dr/dc)^2 are kept
@@ -1059,8 +1101,11 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
   }
   c->n_entries = (long long)E;
   c->n_seg = nseg;
-  const size_t need = E * (payload_bytes(c->fmt) + 1) + (size_t)nseg * (8 + 4 + 4 + 48 + 4 * (c->fmt == 2)) +
-                      (size_t)S * (sizeof(SplatRec) + 1 + 8);
+  c->n_win = nwin;
+  const size_t need = (thin ? (size_t)nseg * sizeof(SplatRec) + (size_t)nwin * kTilePix * 16 +
+                                  (size_t)n_tiles * kTilePix * 4 + 12 * (size_t)c->n_pix
+                            : E * (payload_bytes(c->fmt) + 1)) +
+                      (size_t)nseg * (8 + 4 + 4 + 48 + 4 * (c->fmt == 2)) + (size_t)S * (sizeof(SplatRec) + 1 + 8);
   if (ctx->opt.mem_budget != 0 && need > ctx->opt.mem_budget) {
     char msg[160];
     std::snprintf(msg, sizeof(msg), "cache needs %zu bytes (%llu entries), budget %zu", need, E,
@@ -1068,8 +1113,21 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
     return fail(ctx, GSLM_E_CACHE_OVERFLOW, msg);
   }
   const long long ns = std::max<long long>(nseg, 1);
-  CK(c->payload.alloc(payload_bytes(c->fmt) * std::max<unsigned long long>(E, 1), st));
-  CK(c->pixoff.alloc(std::max<unsigned long long>(E, 1), st));
+  ThinOut tout{};
+  if (thin) {
+    // no entries: the segments' splats, per-pixel live counts and checkpoints
+    CK(c->thin_rec.alloc(sizeof(SplatRec) * ns, st));
+    CK(c->ckpt.alloc((size_t)std::max<uint32_t>(nwin, 1) * kTilePix * sizeof(float4), st));
+    CK(c->n_live.alloc((size_t)std::max(n_tiles, 1) * kTilePix * sizeof(uint32_t), st));
+    CK(c->win_tile.alloc(sizeof(uint32_t) * std::max<uint32_t>(nwin, 1), st));
+    CK(launch_thin_window_tiles(c->win_off.as<uint32_t>(), n_tiles, c->win_tile.as<uint32_t>(), st));
+    tout.rec = c->thin_rec.as<SplatRec>();
+    tout.ckpt = c->ckpt.as<float4>();
+    tout.win_off = c->win_off.as<uint32_t>();
+    tout.n_live = c->n_live.as<uint32_t>();
+  }
+  CK(c->payload.alloc(thin ? 16 : payload_bytes(c->fmt) * std::max<unsigned long long>(E, 1), st));
+  CK(c->pixoff.alloc(thin ? 16 : std::max<unsigned long long>(E, 1), st));
   CK(c->seg_entry_off.alloc(sizeof(unsigned long long) * (ns + 1), st));
   CK(c->seg_slot.alloc(sizeof(uint32_t) * ns, st));
   CK(c->seg_rec.alloc(sizeof(SegRec) * ns, st));
@@ -1084,7 +1142,7 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
                          tile_entry_off.as<unsigned long long>(), c->tile_seg_off.as<uint32_t>(), c->fmt,
                          c->payload.p, c->seg_scale.as<float>(), c->pixoff.as<uint8_t>(),
                          c->seg_entry_off.as<unsigned long long>(), c->seg_slot.as<uint32_t>(),
-                         c->seg_rec.as<SegRec>(), c->slot_active.as<uint8_t>(), errflag.as<int>(), st));
+                         c->seg_rec.as<SegRec>(), c->slot_active.as<uint8_t>(), errflag.as<int>(), tout, st));
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1152,6 +1210,13 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
   c->cams.bytes = B.cams.bytes;
   c->cams.st = st;
   B.cams.p = nullptr;
+  if (thin) {   // a thin cache keeps the rendered image (each pixel's final colour)
+    c->img.p = img.p;
+    c->img.bytes = img.bytes;
+    c->img.st = img.st;
+    img.p = nullptr;
+    img.bytes = 0;
+  }
   // b = -J^T F
   if (b != nullptr) CKS(do_apply_JT(ctx, c, c->F.as<float>(), b, -1.f, nullptr, nullptr, 0.f, nullptr, nullptr));
   if (F != nullptr)
@@ -1207,7 +1272,8 @@ gslm_status gslm_jacobi_diag(gslm_ctx* ctx, const gslm_cache* c, float* diag) {
   if (ctx == nullptr || c == nullptr || diag == nullptr) return fail(ctx, GSLM_E_INVALID, "jacobi_diag: null");
   cudaStream_t st = ctx->st;
   CK(ctx->seg_q.ensure(sizeof(float) * kDiagBlock * std::max<long long>(c->n_seg, 1), st));
-  CK(launch_diag_entries(c->view(), ctx->seg_q.as<float>(), st));
+  if (c->fmt == GSLM_CACHE_THIN) CK(launch_thin_diag(c->view(), ctx->seg_q.as<float>(), st));
+  else CK(launch_diag_entries(c->view(), ctx->seg_q.as<float>(), st));
   // with compact splat keys, one block per splat first (segments summed in splat order)
   float* splat_q = nullptr;
   Buf sq;
@@ -1255,6 +1321,27 @@ gslm_status gslm_pcg_solve_batch(gslm_ctx* ctx, const gslm_cache* const* caches,
       return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: null entry");
   cudaStream_t st = ctx->st;
   bool breakdown = false;
+  if (caches[0]->fmt == GSLM_CACHE_THIN) {
+    // thin caches: the subsets one after another, with the arithmetic of gslm_pcg_solve
+    for (int i = 0; i < n_b; ++i) {
+      if (caches[i]->fmt != GSLM_CACHE_THIN) return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: mixed cache formats");
+      for (const void* v : {(const void*)b[i], (const void*)diag[i], (const void*)x[i]})
+        if ((reinterpret_cast<uintptr_t>(v) & 15u) != 0)
+          return fail(ctx, GSLM_E_INVALID, "pcg_solve_batch: vector not 16-byte aligned");
+      CKS(pcg_enqueue(ctx, caches[i], b[i], diag[i], D != nullptr ? D[i] : nullptr, lambda, x[i]));
+      PcgScalars h;
+      CK(cudaMemcpyAsync(&h, ctx->scalars.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      breakdown |= h.breakdown != 0;
+      if (stats != nullptr) {
+        stats[i].iters = h.iters;
+        stats[i].breakdown = h.breakdown;
+        stats[i].rr = h.rr;
+        stats[i].bb = h.bb;
+      }
+    }
+    return breakdown ? GSLM_W_PCG_BREAKDOWN : GSLM_OK;
+  }
   for (int g0 = 0; g0 < n_b; g0 += kMaxBatch) {
     const int gn = std::min(kMaxBatch, n_b - g0);
     BatchLayout L;
@@ -1346,7 +1433,8 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
   CK(ctx->lm_den.ensure(vb, st));
   CK(ctx->lm_delta.ensure(vb, st));
   CK(ctx->lm_trial.ensure(vb, st));
-  const bool batched = ctx->opt.batch != 0;
+  // thin caches have no persistent batched tile kernels: their subsets are solved one after another
+  const bool batched = ctx->opt.batch != 0 && ctx->opt.cache_fmt != GSLM_CACHE_THIN;
   if (!batched) {
     CK(ctx->lm_x.ensure(vb, st));
     CK(ctx->lm_b.ensure(vb, st));
@@ -1456,8 +1544,7 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
       pcg_iters += h.iters;
       const gslm_cache* c = caches[i];
       n_pairs += 1 + h.iters;
-      pair_bytes += (1.0 + h.iters) * (2.0 * (double)c->n_entries * (double)(payload_bytes(c->fmt) + 1) +
-                                       24.0 * (double)c->n_pix + 472.0 * (double)N + 192.0 * (double)c->n_active);
+      pair_bytes += (1.0 + h.iters) * c->pair_bytes((int)N);
     }
     if (!batched) continue;
     BatchLayout L;
@@ -1494,8 +1581,7 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld, co
       const gslm_cache* c = caches[g0 + k];
       pcg_iters += h[k].iters;
       n_pairs += 1 + h[k].iters;
-      pair_bytes += (1.0 + h[k].iters) * (2.0 * (double)c->n_entries * (double)(payload_bytes(c->fmt) + 1) +
-                                          24.0 * (double)c->n_pix + 472.0 * (double)N + 192.0 * (double)c->n_active);
+      pair_bytes += (1.0 + h[k].iters) * c->pair_bytes((int)N);
     }
     // back to the pool (which keeps them for the next step): the trial renders
     // below need room beside the caches

@@ -161,6 +161,23 @@ struct CacheView {
   int fmt;
   const int* skip;                 // if non-null and *skip != 0 the kernels do nothing (PCG finished)
   const float* wres;               // [n_pix][3] residual-to-pixel weights (dr/dc)^2, or null (L2: 1)
+  // GSLM_CACHE_THIN only (null otherwise): no entries; the kernels blend again
+  const SplatRec* thin_rec;        // [n_seg] the projected splat of each segment, as the blending read it
+  const float* img;                // [n_pix][3] final colour of each pixel
+  const uint32_t* n_live;          // [n_tiles * 256] segments of its tile a pixel takes before it stops
+  const uint32_t* win_off;         // [n_tiles + 1] first window of each tile (32 segments per window)
+  const uint32_t* win_tile;        // [n_win] tile of each window
+  const float4* ckpt;              // [n_win * 256] (T, colour prefix) of each pixel before the window
+  long long n_win;
+};
+
+// Thin-cache outputs of the cache-writing pass (GSLM_CACHE_THIN).
+constexpr int kThinWindow = 32;    // segments per checkpoint window
+struct ThinOut {
+  SplatRec* rec;                   // [n_seg]
+  float4* ckpt;                    // [n_win * 256]
+  const uint32_t* win_off;         // [n_tiles + 1]
+  uint32_t* n_live;                // [n_tiles * 256]
 };
 
 // Counts kernel launches of this library (reported by gslm_kernel_launches).
@@ -325,6 +342,7 @@ cudaError_t launch_raster_count(const DevCam* cams, int V, int n_tiles, const ui
                                 const SplatRec* rec, int smooth, const float* targets,
                                 float* img, float* F, double* cost_partials, uint32_t* tile_entries,
                                 uint32_t* tile_segs, cudaStream_t st);
+// fmt GSLM_CACHE_THIN: no payload or pixel offsets; writes thin instead.
 cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const uint32_t* tile_start,
                                 const uint32_t* tile_end, const uint32_t* tile_vals,
                                 const SplatRec* rec, int smooth, const float* img,
@@ -332,8 +350,18 @@ cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const ui
                                 const uint32_t* tile_seg_off, int fmt, void* payload,
                                 float* seg_scale, uint8_t* pixoff,
                                 unsigned long long* seg_entry_off, uint32_t* seg_slot, SegRec* seg_rec,
-                                uint8_t* slot_active, int* err, cudaStream_t st);
+                                uint8_t* slot_active, int* err, const ThinOut& thin, cudaStream_t st);
 
+// thin.cu: the thin cache's windows and its J p, J^T u and diag(J^T J) blocks
+// (same outputs as launch_apply_J / launch_apply_JT / launch_diag_entries).
+// win_count: [n_tiles] windows per tile (ceil(segments / 32)).
+cudaError_t launch_thin_window_counts(const uint32_t* tile_seg_off, int n_tiles, uint32_t* win_count,
+                                      cudaStream_t st);
+cudaError_t launch_thin_window_tiles(const uint32_t* win_off, int n_tiles, uint32_t* win_tile, cudaStream_t st);
+cudaError_t launch_thin_apply_J(const CacheView& cv, const float* ydot, const float* F_add, float* u,
+                                double* sq_partials, cudaStream_t st);
+cudaError_t launch_thin_apply_JT(const CacheView& cv, const float* u, float* seg_ybar, cudaStream_t st);
+cudaError_t launch_thin_diag(const CacheView& cv, float* seg_q, cudaStream_t st);
 
 // apply.cu. `variant` selects one of apply_variants() kernel configurations
 // (entries in flight per lane and register budget); all compute the same result.

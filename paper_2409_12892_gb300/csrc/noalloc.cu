@@ -56,7 +56,8 @@ extern "C" gslm_status gslm_apply_JT_noalloc(gslm_ctx* ctx, const gslm_cache* ca
   // Every segment slot read below is written first in this call, so nothing in
   // the shared array needs clearing.
   float* seg_ybar = static_cast<float*>(xp.noalloc_scratch);
-  cudaError_t e = gslm::launch_apply_JT(cp.view, u, seg_ybar, xp.variant_JT, xp.st);
+  cudaError_t e = cp.view.fmt == GSLM_CACHE_THIN ? gslm::launch_thin_apply_JT(cp.view, u, seg_ybar, xp.st)
+                                                 : gslm::launch_apply_JT(cp.view, u, seg_ybar, xp.variant_JT, xp.st);
   if (e == cudaSuccess)
     e = gslm::launch_vjp(cp.params, cp.N, cp.ld, cp.cams, cp.V, cp.smooth, cp.view.slot_seg_start,
                          cp.view.slot_seg_end, cp.view.vmask, cp.view.act_off, seg_ybar, nullptr, 1.f, g, nullptr,

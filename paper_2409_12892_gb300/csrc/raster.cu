@@ -230,6 +230,12 @@ __device__ __forceinline__ void store_entry(void* payload, unsigned long long po
   }
 }
 
+// kFmt GSLM_CACHE_THIN writes no entries: per segment the projected splat
+// (thin.rec), per pixel the number of its tile's segments it takes before it
+// stops (thin.n_live) and, before every kThinWindow-th segment of the tile, the
+// pixel's transmittance and colour prefix (thin.ckpt). Segment records and
+// entry offsets are written as for the other formats (the entry offsets count
+// the entries a full cache would hold).
 template <int kFmt>
 __global__ void __launch_bounds__(kTilePix) k_raster_write(
     const DevCam* __restrict__ cams, int V, const uint32_t* __restrict__ tstart,
@@ -238,7 +244,9 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
     const uint32_t* __restrict__ tile_seg_off, void* __restrict__ payload, float* __restrict__ seg_scale,
     uint8_t* __restrict__ pixoff, unsigned long long* __restrict__ seg_entry_off,
     uint32_t* __restrict__ seg_slot, SegRec* __restrict__ seg_rec, uint8_t* __restrict__ slot_active,
-    int* __restrict__ err) {
+    int* __restrict__ err, const ThinOut thin) {
+  constexpr bool kThin = kFmt == GSLM_CACHE_THIN;
+  __shared__ unsigned nzs;                // sub-batch splats that are segments (bit j)
   __shared__ float4 sA[kTilePix];
   __shared__ float2 sB[kTilePix];
   __shared__ float4 sC[kTilePix];
@@ -268,6 +276,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
   uint32_t erun = 0, srun = 0;
   float T = 1.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
   bool done = !ts.inside;
+  uint32_t nlive = done ? 0u : 0xffffffffu;   // thin: set where the pixel stops
   for (uint32_t b = s0; b < s1; b += kTilePix) {
     if (__syncthreads_count(done) == kTilePix) break;
     const uint32_t i = b + threadIdx.x;
@@ -287,6 +296,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
       uint32_t mask = 0;
       float Tl = T;
       bool dl = done;
+      int jstop = -1;
       for (int j = 0; j < m; ++j) {
         if (dl) break;
         const Blend bl = blend_weight(ts.px, ts.py, sA[sub + j], sB[sub + j], smooth);
@@ -294,6 +304,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
           const float test = transmit(Tl, bl.alpha);
           if (!smooth && test < kTMin) {
             dl = true;
+            jstop = j;
           } else {
             mask |= 1u << j;
             Tl = test;
@@ -348,6 +359,13 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
             r.io = 1.f / bb.y;
             r.scale = 1.f;
             seg_rec[sidx] = r;
+            if (kThin) {
+              SplatRec t;
+              t.a = a;
+              t.b = make_float4(bb.x, bb.y, 0.f, 0.f);
+              t.c = sC[sub + j];
+              thin.rec[sidx] = t;
+            }
           } else {
             atomicOr(err, 2);
           }
@@ -357,9 +375,35 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
         if (lane == 31) {
           add_e = inc;
           add_s = __popc(nz);
+          nzs = nz;
         }
       }
       __syncthreads();
+      if (kThin) {
+        // checkpoints before the window-opening segments, the pixel's state
+        // advanced over its own contributions; where the pixel stopped
+        const uint32_t wbase = thin.win_off[tile];
+        for (int j = 0; j < m; ++j) {
+          const int sj = segidx[j];
+          if (sj >= 0 && ((uint32_t)(sj - (int)sbase) % kThinWindow) == 0u)
+            thin.ckpt[(size_t)(wbase + (uint32_t)(sj - (int)sbase) / kThinWindow) * kTilePix + threadIdx.x] =
+                make_float4(T, p0, p1, p2);
+          if (!((mask >> j) & 1u)) continue;
+          const float araw = sAraw[j][threadIdx.x];
+          const float alpha = smooth ? araw : fminf(kAlphaMax, araw);
+          const float4 c = sC[sub + j];
+          const float w = __fmul_rn(alpha, T);
+          p0 = __fmaf_rn(c.x, w, p0);
+          p1 = __fmaf_rn(c.y, w, p1);
+          p2 = __fmaf_rn(c.z, w, p2);
+          T = transmit(T, alpha);
+        }
+        if (jstop >= 0) nlive = srun + (uint32_t)__popc(nzs & ((1u << jstop) - 1u));
+        done = dl;
+        erun += add_e;
+        srun += add_s;
+        continue;
+      }
       // D: entries. FP16S first needs every segment's largest magnitude.
       if (kFmt == GSLM_CACHE_FP16S) {
         float Tq = T, q0 = p0, q1 = p1, q2 = p2;
@@ -421,6 +465,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
       srun += add_s;
     }
   }
+  if (kThin) thin.n_live[(size_t)tile * kTilePix + threadIdx.x] = nlive == 0xffffffffu ? srun : nlive;
   if (threadIdx.x == 0 && (ebase + erun != eend || sbase + srun != send)) atomicOr(err, 4);
 }
 
@@ -455,17 +500,19 @@ cudaError_t launch_raster_write(const DevCam* cams, int V, int n_tiles, const ui
                                 int smooth, const float* img, const unsigned long long* tile_entry_off,
                                 const uint32_t* tile_seg_off, int fmt, void* payload, float* seg_scale,
                                 uint8_t* pixoff, unsigned long long* seg_entry_off, uint32_t* seg_slot,
-                                SegRec* seg_rec, uint8_t* slot_active, int* err, cudaStream_t st) {
+                                SegRec* seg_rec, uint8_t* slot_active, int* err, const ThinOut& thin,
+                                cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
 #define GSLM_WRITE(F)                                                                                         \
   do {                                                                                                        \
     k_raster_write<F><<<n_tiles, kTilePix, 0, st>>>(cams, V, tile_start, tile_end, tile_vals, rec, smooth, img, \
                                                     tile_entry_off, tile_seg_off, payload, seg_scale, pixoff,   \
-                                                    seg_entry_off, seg_slot, seg_rec, slot_active, err);        \
+                                                    seg_entry_off, seg_slot, seg_rec, slot_active, err, thin);  \
     note_launch();                                                                                            \
   } while (0)
   if (fmt == GSLM_CACHE_FP32) GSLM_WRITE(GSLM_CACHE_FP32);
   else if (fmt == GSLM_CACHE_BF16) GSLM_WRITE(GSLM_CACHE_BF16);
+  else if (fmt == GSLM_CACHE_THIN) GSLM_WRITE(GSLM_CACHE_THIN);
   else GSLM_WRITE(GSLM_CACHE_FP16S);
 #undef GSLM_WRITE
   return cudaGetLastError();

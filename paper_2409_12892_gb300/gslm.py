@@ -30,7 +30,7 @@ c_float, c_double, c_int32, c_int64, c_void_p, c_size_t = (
 
 STATUS = {0: "GSLM_OK", -1: "GSLM_E_INVALID", -2: "GSLM_E_OOM", -3: "GSLM_E_CUDA",
           -4: "GSLM_E_CACHE_OVERFLOW", -5: "GSLM_E_TIMEOUT", -6: "GSLM_E_NUMERIC", 1: "GSLM_W_PCG_BREAKDOWN"}
-CACHE_FMT = {"fp32": 0, "bf16": 1, "fp16s": 2}
+CACHE_FMT = {"fp32": 0, "bf16": 1, "fp16s": 2, "thin": 3}
 OBJECTIVE = {"l2": 0, "l1ssim": 1}
 
 

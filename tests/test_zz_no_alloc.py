@@ -98,6 +98,18 @@ def test_noalloc_apply_JT_runs_the_forced_variant(g, variant):
     ctx.close()
 
 
+def test_noalloc_apply_JT_on_a_thin_cache(g):
+    ctx = g.Context(cache_fmt="thin")
+    P, cache, us = _ragged(g, ctx)
+    ref = ctx.apply_JT(cache, us[0]).clone()
+    out = torch.full_like(ref, float("nan"))
+    assert _noalloc(g, ctx, cache, us[0], out) == 0
+    torch.cuda.synchronize()
+    assert rel_l2(g.from_soa(out, P.shape[0]), g.from_soa(ref, P.shape[0])) < 1e-4
+    cache.free()
+    ctx.close()
+
+
 def test_noalloc_apply_JT_on_a_cache_without_segments_gives_zeros(g):
     """Every Gaussian behind the only camera: no segment, so J^T u = 0."""
     wl = synth.small_workload("edge", 41, 200, 1, 40, 24, cam_radius=4.0, log_scale_mean=-2.0)
