@@ -60,10 +60,11 @@ def parse_args(argv=None):
     ap.add_argument("--views", type=int, default=0, help="override: views per subset (profiling-sized cases)")
     ap.add_argument("--precond", choices=["learned", "jacobi"], default="learned",
                     help="preconditioner of the chosen form")
-    ap.add_argument("--train-steps", type=int, default=24, help="Adam steps of the learned preconditioner")
+    ap.add_argument("--train-steps", type=int, default=12, help="Adam steps of the learned preconditioner")
     ap.add_argument("--train-K", type=int, default=8, help="unrolled PCG iterations of the training loss")
     ap.add_argument("--train-lr", type=float, default=3e-3)
-    ap.add_argument("--train-systems", type=int, default=2, help="subset systems of step 0 trained on")
+    ap.add_argument("--train-systems", type=int, default=5,
+                    help="train on the first subset system of each of LM steps 1..n")
     ap.add_argument("--skip-equal", action="store_true", help="skip the equal-residual comparison")
     ap.add_argument("--equal-cap", type=int, default=1000, help="PCG iteration cap of the equal-residual step")
     ap.add_argument("--equal-lambdas", default="1e-3,1,1e4",
@@ -697,35 +698,52 @@ def subset_targets(targets, cams, views):
 
 
 def train_precond(g, ctx, params, N, cams, targets, wl, args):
-    """The learned preconditioner, trained on the GPU on the subset systems of LM
-    step 0 (Adam on the unrolled-PCG residual). Returns (network, report)."""
+    """The learned preconditioner, trained on the GPU (Adam on the unrolled-PCG
+    residual) on the first subset system of each of LM steps 1..train_systems, at
+    the damping each of those steps runs at when the steps before it are rejected
+    (lambda0 2^s). Returns (network, report)."""
     import torch
     import synth
     t0 = time.perf_counter()
-    subsets = synth.subset_views(wl, 0)[:max(1, args.train_systems)]
+    steps = list(range(1, max(1, args.train_systems) + 1))
     systems = []
-    for vs in subsets:
+    for s in steps:
+        vs = synth.subset_views(wl, s)[0]
         cc = [cams[v] for v in vs]
         cache = ctx.build_cache(params, N, cc, subset_targets(targets, cams, vs), want_F=False)
         diag = ctx.jacobi_diag(cache)
-        systems.append((cache, diag, ctx.precond_features(cache, diag)))
+        lam = min(max(wl.lambda0 * 2.0 ** s, wl.lambda_min), wl.lambda_max)
+        systems.append((cache, diag, ctx.precond_features(cache, diag), lam))
     pc = g.Precond(ctx, seed=0)
-    pc.fit_standardizer(torch.cat([phi for _, _, phi in systems]))
+    pc.fit_standardizer(torch.cat([phi for _, _, phi, _ in systems]))
     losses = []
     for _ in range(args.train_steps):
         L = 0.0
-        for cache, diag, phi in systems:
-            L += pc.accumulate(cache, phi, cache.b, diag, wl.lambda0, args.train_K, 1.0 / len(systems))
+        for cache, diag, phi, lam in systems:
+            L += pc.accumulate(cache, phi, cache.b, diag, lam, args.train_K, 1.0 / len(systems))
         losses.append(L / len(systems))
         pc.adam(args.train_lr)
-    for cache, _, _ in systems:
+    # cost of using the network on one subset: features and inference
+    cache, diag, _, _ = systems[0]
+    st = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(st)
+    phi = ctx.precond_features(cache, diag)
+    e1.record(st)
+    pc.apply(phi, diag)
+    e2.record(st)
+    torch.cuda.synchronize()
+    for cache, _, _, _ in systems:
         cache.free()
-    del systems
+    del systems, phi
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    rep = {"systems": len(subsets), "adam_steps": args.train_steps, "K": args.train_K, "lr": args.train_lr,
+    rep = {"systems": [f"step {s}, first subset, lambda {min(max(wl.lambda0 * 2.0 ** s, wl.lambda_min), wl.lambda_max):g}"
+                       for s in steps],
+           "adam_steps": args.train_steps, "K": args.train_K, "lr": args.train_lr,
            "loss_first": losses[0] if losses else None, "loss_last": losses[-1] if losses else None,
-           "seconds": time.perf_counter() - t0,
+           "seconds": time.perf_counter() - t0, "features_ms": e0.elapsed_time(e1), "inference_ms": e1.elapsed_time(e2),
+           "weights": "bfloat16 weight matrices, float32 biases, float32 activations and sums",
            "loss": "1/2 log(||r_K||^2/||b||^2) after K iterations of Algorithm 1 with D"}
     return pc, rep
 
@@ -955,10 +973,12 @@ def run_ours(args):
             best = min(cands, key=lambda e: e["ms"]) if cands else row["jacobi"]
             ent = {"chosen": best, "chosen_jacobi": row["jacobi"], "chosen_learned": row.get("learned")}
             # per damping: ms [chosen, plain], iterations per subset, reached / accepted
-            # [chosen, plain], PSNR [before, after chosen, after plain], speedup
+            # [chosen, plain], speedup
+            # PSNR as the value before the step and the gains of the two forms (dB)
             srow = {"lambda": lam, "ms": [best["ms"]], "its": best["pcg_iters_per_subset"],
                     "reached": [int(best["reached"])], "accepted": [best["accepted"]],
-                    "psnr": [sig(best["psnr_before_db"], 6), sig(best["psnr_after_db"], 6)]}
+                    "psnr_before": best["psnr_before_db"],
+                    "psnr_gain": [best["psnr_after_db"] - best["psnr_before_db"]]}
             if best["precond"] != "jacobi":
                 srow["precond"] = best["precond"]
             pe = result.get("plain", {}).get("equal", {}).get(lam)
@@ -968,7 +988,8 @@ def run_ours(args):
                 srow["ms"].append(pj["ms"])
                 srow["reached"].append(int(pj["reached"]))
                 srow["accepted"].append(pj["accepted"])
-                srow["psnr"].append(sig(pj["psnr_after_db"], 6))
+                srow["psnr_gain"].append(pj["psnr_after_db"] - pj["psnr_before_db"])
+                srow["psnr_after_diff_db"] = best["psnr_after_db"] - pj["psnr_after_db"]
                 srow["speedup"] = pj["ms"] / best["ms"]
             eqs[lam] = ent
             short.append(srow)

@@ -324,6 +324,10 @@ gslm_status gslm_lm_step(gslm_ctx* ctx, float* params, int64_t N, int64_t ld,
  *   h1 = GELU(W1 phi + b1), h2 = GELU(W2 h1 + b2), o = W3 h2 + b3
  *     (64 -> 64 -> 64 -> 59, GELU(x) = x Phi(x));
  *   D_k = softplus(o_k) / clamp(M_k), used as D in gslm_pcg_solve.
+ * The network computes with its weight matrices W1, W2, W3 rounded to
+ * bfloat16 (round to nearest even) and float32 biases, activations and sums;
+ * the weights held, set, got and updated by Adam are float32, and the weight
+ * gradient is that of the rounded matrices.
  * Training minimises L = 1/2 log(||r_K||^2 / ||b||^2), the relative residual
  * after K iterations of Algorithm 1 run with D (x0 = D b, z = D r), by reverse
  * mode through those iterations and then through the network, with Adam.

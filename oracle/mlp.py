@@ -14,6 +14,11 @@ such network; the reading below is this project's:
   network  h1 = GELU(W1 phi + b1), h2 = GELU(W2 h1 + b2), o = W3 h2 + b3
            (64 -> 64 -> 64 -> 59, exact GELU x Phi(x))
   output   c = softplus(o), D_k = c_k / clamp(M_k)   (clamp as for Jacobi)
+  weights  the network computes with its weight matrices rounded to bfloat16
+           (round to nearest even from float32), its biases and everything else
+           in float64 here; the weights kept and updated are masters, and the
+           weight gradient is that of the rounded weights (bf16=False: exact).
+           The biases are not rounded, so the initial network is exactly Jacobi
   init     W3 = 0, b3 = log(e - 1): c = 1, i.e. D = the Jacobi preconditioner
   loss     L = 1/2 log(||r_K||^2 / ||b||^2): the relative residual after K
            iterations of Algorithm 1 run with D in place of M^-1 (x0 = D b,
@@ -111,8 +116,27 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-x))
 
 
-def forward(net: MLP, phi_hat: np.ndarray):
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """x rounded to the nearest bfloat16 (the upper 16 bits of its float32,
+    round half to even), as float64. bfloat16 keeps float32's sign and 8-bit
+    exponent and the top 7 of its 23 mantissa bits."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def effective(net: MLP, bf16: bool = True) -> MLP:
+    """The weights the network computes with: the matrices rounded to bfloat16
+    (biases exact), or all exact."""
+    if not bf16:
+        return net
+    return MLP(bf16_round(net.W1), net.b1, bf16_round(net.W2), net.b2, bf16_round(net.W3), net.b3)
+
+
+def forward(net: MLP, phi_hat: np.ndarray, bf16: bool = True):
     """Returns (a1, h1, a2, h2, o) for standardised features (N, 64)."""
+    net = effective(net, bf16)
     a1 = phi_hat @ net.W1.T + net.b1
     h1 = gelu(a1)
     a2 = h1 @ net.W2.T + net.b2
@@ -121,15 +145,17 @@ def forward(net: MLP, phi_hat: np.ndarray):
     return a1, h1, a2, h2, o
 
 
-def precond_diag(net: MLP, phi_hat: np.ndarray, M: np.ndarray) -> np.ndarray:
+def precond_diag(net: MLP, phi_hat: np.ndarray, M: np.ndarray, bf16: bool = True) -> np.ndarray:
     """D (N, 59) = softplus(o) / clamp(M)."""
-    o = forward(net, phi_hat)[-1]
+    o = forward(net, phi_hat, bf16)[-1]
     return softplus(o) / clamp_diag(M)
 
 
-def backward(net: MLP, phi_hat: np.ndarray, M: np.ndarray, dD: np.ndarray):
-    """Weight gradients (list matching net.params()) for an upstream gradient dL/dD (N, 59)."""
-    a1, h1, a2, h2, o = forward(net, phi_hat)
+def backward(net: MLP, phi_hat: np.ndarray, M: np.ndarray, dD: np.ndarray, bf16: bool = True):
+    """Weight gradients (list matching net.params()) for an upstream gradient dL/dD (N, 59),
+    taken at the weights the network computes with (see effective)."""
+    a1, h1, a2, h2, o = forward(net, phi_hat, bf16)
+    net = effective(net, bf16)
     do = dD / clamp_diag(M) * sigmoid(o)           # D = softplus(o) / clamp(M)
     gW3 = do.T @ h2
     gb3 = do.sum(axis=0)
@@ -229,11 +255,12 @@ def unrolled_loss_and_grad(apply_A, b: np.ndarray, d: np.ndarray, K: int):
     return L, dbar
 
 
-def loss_and_grad(net: MLP, phi_hat: np.ndarray, M: np.ndarray, apply_A, b: np.ndarray, K: int):
+def loss_and_grad(net: MLP, phi_hat: np.ndarray, M: np.ndarray, apply_A, b: np.ndarray, K: int,
+                  bf16: bool = True):
     """Unrolled-PCG loss of the network's D on one system and its weight gradients."""
-    D = precond_diag(net, phi_hat, M)
+    D = precond_diag(net, phi_hat, M, bf16)
     L, dD = unrolled_loss_and_grad(apply_A, b, D, K)
-    return L, backward(net, phi_hat, M, dD)
+    return L, backward(net, phi_hat, M, dD, bf16)
 
 
 @dataclass

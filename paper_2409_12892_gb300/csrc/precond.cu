@@ -101,6 +101,17 @@ __global__ void k_feature_stats(const double* __restrict__ sums, int N, float* _
 }
 
 // ---------------------------------------------------------------------------- network
+// The network computes with bfloat16 weight matrices and float32 biases,
+// activations and sums: W1, W2 and W3 (the float32 master copy that Adam
+// updates) are rounded to bfloat16 (round to nearest even) as they are staged
+// into shared memory, and the weight gradient is that of the rounded weights.
+// The biases stay float32, so the initial network (W3 = 0, b3 = log(e - 1)) is
+// exactly the Jacobi preconditioner.
+__device__ __forceinline__ float bf16_weight(int i, float w) {
+  const bool bias = (i >= kOffB1 && i < kOffW2) || (i >= kOffB2 && i < kOffW3) || i >= kOffB3;
+  return bias ? w : __bfloat162float(__float2bfloat16_rn(w));
+}
+
 // D = softplus(o) / clamp(M): one thread per Gaussian, weights in shared memory
 // (every lane of a warp reads the same weight: a broadcast).
 __global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ W, const float* __restrict__ mu,
@@ -110,7 +121,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ W, 
   extern __shared__ float sw[];
   float* smu = sw + kNW;
   float* srs = smu + kIn;
-  for (int i = threadIdx.x; i < kNW; i += blockDim.x) sw[i] = W[i];
+  for (int i = threadIdx.x; i < kNW; i += blockDim.x) sw[i] = bf16_weight(i, W[i]);
   if (threadIdx.x < kIn) {
     smu[threadIdx.x] = mu[threadIdx.x];
     srs[threadIdx.x] = 1.f / sd[threadIdx.x];
@@ -173,7 +184,7 @@ __global__ void __launch_bounds__(kGradThreads) k_mlp_backward(
   float* act = sw + kNW;
   float* smu = act + kChunk * kRow;
   float* srs = smu + kIn;
-  for (int i = threadIdx.x; i < kNW; i += blockDim.x) sw[i] = W[i];
+  for (int i = threadIdx.x; i < kNW; i += blockDim.x) sw[i] = bf16_weight(i, W[i]);
   if (threadIdx.x < kIn) {
     smu[threadIdx.x] = mu[threadIdx.x];
     srs[threadIdx.x] = 1.f / sd[threadIdx.x];

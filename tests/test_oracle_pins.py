@@ -600,12 +600,35 @@ def test_unrolled_pcg_adjoint_matches_central_differences(K):
         assert abs(fd - g[k]) <= 1e-5 * np.abs(g).max(), (k, fd, g[k])
 
 
+def test_bf16_rounding_of_the_network_weights():
+    """Round to nearest even on the top 16 bits of the float32 (bfloat16: 8-bit
+    exponent, 7 mantissa bits): exact halfway cases go to the even mantissa;
+    random values agree with torch's bfloat16 conversion; and the network with
+    rounded weights is the exact network evaluated at those weights."""
+    from oracle import mlp
+    torch = pytest.importorskip("torch")
+    one = 1.0
+    cases = [(one, one), (one + 2.0 ** -8, one), (one + 3 * 2.0 ** -8, one + 2.0 ** -6),
+             (one + 2.0 ** -8 + 2.0 ** -20, one + 2.0 ** -7), (-2.5, -2.5), (0.0, 0.0),
+             (3.0e38, float(torch.tensor(3.0e38).to(torch.bfloat16).float()))]
+    for x, want in cases:
+        assert mlp.bf16_round(np.array([x]))[0] == want, x
+    x = np.random.default_rng(1).standard_normal(5000) * np.exp(np.random.default_rng(2).normal(0, 8, 5000))
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).float().double().numpy()
+    np.testing.assert_array_equal(mlp.bf16_round(x), ref)
+    _, net, phi, M, _, _, _ = _mlp_case(0, 20)
+    rounded = mlp.MLP(mlp.bf16_round(net.W1), net.b1, mlp.bf16_round(net.W2), net.b2, mlp.bf16_round(net.W3),
+                      net.b3)
+    np.testing.assert_array_equal(mlp.precond_diag(net, phi, M), mlp.precond_diag(rounded, phi, M, bf16=False))
+    assert np.abs(mlp.precond_diag(net, phi, M) - mlp.precond_diag(net, phi, M, bf16=False)).max() > 0
+
+
 def test_mlp_backward_matches_central_differences():
     mlp, net, phi, M, b, _, _ = _mlp_case(0, 40)
     W = np.random.default_rng(9).standard_normal(M.shape)   # f(net) = sum W * D(net)
-    g = np.concatenate([x.ravel() for x in mlp.backward(net, phi, M, W)])
+    g = np.concatenate([x.ravel() for x in mlp.backward(net, phi, M, W, bf16=False)])
     v = net.flat()
-    f = lambda w: float(np.sum(W * mlp.precond_diag(mlp.MLP.from_flat(w), phi, M)))
+    f = lambda w: float(np.sum(W * mlp.precond_diag(mlp.MLP.from_flat(w), phi, M, bf16=False)))
     rng = np.random.default_rng(5)
     for i in rng.choice(v.size, 150, replace=False):
         h = 1e-6 * max(1.0, abs(v[i]))
@@ -618,7 +641,7 @@ def test_mlp_backward_matches_central_differences():
 
 def test_mlp_loss_gradient_matches_central_differences():
     mlp, net, phi, M, b, apply_A, _ = _mlp_case(1, 3)
-    L, grads = mlp.loss_and_grad(net, phi, M, apply_A, b, 5)
+    L, grads = mlp.loss_and_grad(net, phi, M, apply_A, b, 5, bf16=False)
     g = np.concatenate([x.ravel() for x in grads])
     v = net.flat()
     rng = np.random.default_rng(7)
@@ -627,8 +650,8 @@ def test_mlp_loss_gradient_matches_central_differences():
         vp, vm = v.copy(), v.copy()
         vp[i] += h
         vm[i] -= h
-        fd = (mlp.loss_and_grad(mlp.MLP.from_flat(vp), phi, M, apply_A, b, 5)[0]
-              - mlp.loss_and_grad(mlp.MLP.from_flat(vm), phi, M, apply_A, b, 5)[0]) / (2 * h)
+        fd = (mlp.loss_and_grad(mlp.MLP.from_flat(vp), phi, M, apply_A, b, 5, bf16=False)[0]
+              - mlp.loss_and_grad(mlp.MLP.from_flat(vm), phi, M, apply_A, b, 5, bf16=False)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-5 * max(1e-3, np.abs(g).max()), i
 
 
