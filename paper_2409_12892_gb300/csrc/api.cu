@@ -261,7 +261,7 @@ gslm_status check_vec_args(gslm_ctx* ctx, long long N, long long ld) {
 // and build_cache). Leaves the per-tile splat lists in (tile_start, tile_end,
 // tile_vals) and the splats in rec.
 struct Binning {
-  Buf cams, rec, ntiles, rect, depth, flags, pos, vis, keys_a, vals_a, keys_b, vals_b, sort_tmp, key_off;
+  Buf cams, rec, ntiles, rect, tmask, depth, flags, pos, vis, keys_a, vals_a, keys_b, vals_b, sort_tmp, key_off;
   Buf tile_start, tile_end, scan_tmp;
   uint32_t* tile_vals = nullptr;
   uint32_t* tile_keys = nullptr;
@@ -280,8 +280,9 @@ gslm_status bin_splats(gslm_ctx* ctx, const float* params, int N, long long ld, 
   CK(B.ntiles.alloc(sizeof(uint32_t) * S, st));
   CK(B.rect.alloc(sizeof(uint2) * S, st));
   CK(B.depth.alloc(sizeof(uint32_t) * S, st));
+  CK(B.tmask.alloc(sizeof(unsigned long long) * S, st));
   CK(launch_project(params, N, ld, B.cams.as<DevCam>(), V, smooth, B.rec.as<SplatRec>(), B.ntiles.as<uint32_t>(),
-                    B.rect.as<uint2>(), B.depth.as<uint32_t>(), st));
+                    B.rect.as<uint2>(), B.depth.as<uint32_t>(), B.tmask.as<unsigned long long>(), st));
   // visible splats, compacted in slot order
   CK(B.flags.alloc(sizeof(uint32_t) * S, st));
   CK(B.pos.alloc(sizeof(uint32_t) * (S + 1), st));
@@ -325,9 +326,10 @@ gslm_status bin_splats(gslm_ctx* ctx, const float* params, int N, long long ld, 
   for (Buf* b : {&B.keys_a, &B.keys_b, &B.vals_b, &B.vis, &B.ntiles, &B.depth, &B.flags, &B.pos}) b->release();
   CK(B.keys_a.alloc(sizeof(uint32_t) * nk, st));
   CK(B.vals_a.alloc(sizeof(uint32_t) * nk, st));
-  CK(launch_emit_keys(sorted_slots.as<uint32_t>(), B.n_vis, B.rect.as<uint2>(), B.cams.as<DevCam>(), V, N,
+  CK(launch_emit_keys(sorted_slots.as<uint32_t>(), B.n_vis, B.rect.as<uint2>(), B.tmask.as<unsigned long long>(),
+                      B.cams.as<DevCam>(), V, N,
                       B.key_off.as<unsigned long long>(), B.keys_a.as<uint32_t>(), B.vals_a.as<uint32_t>(), st));
-  for (Buf* b : {&sorted_slots, &B.rect, &B.key_off}) b->release();
+  for (Buf* b : {&sorted_slots, &B.rect, &B.tmask, &B.key_off}) b->release();
   CK(B.keys_b.alloc(sizeof(uint32_t) * nk, st));
   CK(B.vals_b.alloc(sizeof(uint32_t) * nk, st));
   CK(B.sort_tmp.ensure(radix_temp_bytes(nk), st));

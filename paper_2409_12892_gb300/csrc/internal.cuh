@@ -31,6 +31,40 @@ constexpr float kDiagMin = 1e-6f;
 constexpr float kDiagMax = 1e32f;
 __host__ __device__ __forceinline__ float clamp_diag(float m) { return fminf(fmaxf(m, kDiagMin), kDiagMax); }
 
+// Tile culling. A splat's tile rectangle (radius 3 sigma) holds tiles where its
+// alpha stays below 1/255 at every pixel, which blending skips pixel by pixel.
+// For rectangles of at most kCullMaxTiles tiles the projection tests each tile
+// and keeps a mask of the tiles the splat can reach; only those get a tile key.
+// The test is conservative (it keeps a tile unless the splat provably misses
+// every pixel centre in it), so blending sees the same contributions.
+constexpr int kCullMaxTiles = 64;
+// Whether alpha = o exp(-q/2), q = A dx^2 + 2 B dx dy + C dy^2 with (dx, dy) =
+// pixel centre - (mx, my), can reach 1/255 at a pixel centre of tile (tx, ty):
+// the least q over the box of the tile's pixel centres (0 if the mean is in the
+// box, else its least value on the four edges, each a 1-D quadratic) against
+// 2 ln(255 o), with margins far above float32 rounding.
+__device__ __forceinline__ bool tile_reachable(float mx, float my, float A, float B, float C, float o, int tx,
+                                               int ty) {
+  if (!(A > 0.f) || !(C > 0.f) || !(o > 0.f)) return true;
+  const float t = 2.f * logf(255.f * o);
+  const float x0 = (float)(tx * kTile) + 0.5f - mx, x1 = x0 + (float)(kTile - 1);
+  const float y0 = (float)(ty * kTile) + 0.5f - my, y1 = y0 + (float)(kTile - 1);
+  if (x0 <= 0.f && 0.f <= x1 && y0 <= 0.f && 0.f <= y1) return true;
+  float qmin = INFINITY, scale = 0.f;
+  auto at = [&](float x, float y) {
+    const float q = A * x * x + 2.f * B * x * y + C * y * y;
+    if (q < qmin) {
+      qmin = q;
+      scale = A * x * x + 2.f * fabsf(B * x * y) + C * y * y;
+    }
+  };
+  at(x0, fminf(fmaxf(-B * x0 / C, y0), y1));
+  at(x1, fminf(fmaxf(-B * x1 / C, y0), y1));
+  at(fminf(fmaxf(-B * y0 / A, x0), x1), y0);
+  at(fminf(fmaxf(-B * y1 / A, x0), x1), y1);
+  return !(qmin > t + 0.05f * (1.f + fabsf(t)) + 1e-3f * scale);
+}
+
 // Stream-ordered device buffer.
 struct Buf {
   void* p = nullptr;
@@ -257,9 +291,12 @@ cudaError_t noalloc_scratch_address(void** out);
 // All return cudaGetLastError() of the launch.
 
 // project.cu
+// tmask (may be null: no tile culling): per slot, the tiles of its rectangle
+// (row-major, bit (ty - y0) * width + (tx - x0)) the splat can reach, for
+// rectangles of at most kCullMaxTiles tiles; ntiles counts those tiles.
 cudaError_t launch_project(const float* params, int N, long long ld, const DevCam* cams, int V,
                            int smooth, SplatRec* rec, uint32_t* ntiles, uint2* rect,
-                           uint32_t* depth_key, cudaStream_t st);
+                           uint32_t* depth_key, unsigned long long* tmask, cudaStream_t st);
 cudaError_t launch_view_mask(const uint8_t* slot_active, int N, int V, unsigned long long* vmask,
                              cudaStream_t st);
 // vmask (per Gaussian, bit v = view v has cache entries) may be null, and must
@@ -333,9 +370,11 @@ cudaError_t launch_ranges(const uint32_t* sorted_keys, long long n, uint32_t* st
                           uint32_t* end, cudaStream_t st);
 
 // raster.cu
+// tmask as written by launch_project (may be null: every tile of the rectangle).
 cudaError_t launch_emit_keys(const uint32_t* sorted_slots, long long n_vis, const uint2* rect,
-                             const DevCam* cams, int V, int N, const unsigned long long* key_off,
-                             uint32_t* tile_keys, uint32_t* tile_vals, cudaStream_t st);
+                             const unsigned long long* tmask, const DevCam* cams, int V, int N,
+                             const unsigned long long* key_off, uint32_t* tile_keys, uint32_t* tile_vals,
+                             cudaStream_t st);
 // Blend every tile. mode 0: render only; mode 1: also count entries/segments.
 cudaError_t launch_raster_count(const DevCam* cams, int V, int n_tiles, const uint32_t* tile_start,
                                 const uint32_t* tile_end, const uint32_t* tile_vals,

@@ -288,7 +288,8 @@ __global__ void k_view_mask(const uint8_t* __restrict__ slot_active, int N, int 
 
 __global__ void k_project(const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams,
                           int V, int smooth, SplatRec* __restrict__ rec, uint32_t* __restrict__ ntiles,
-                          uint2* __restrict__ rect, uint32_t* __restrict__ depth_key) {
+                          uint2* __restrict__ rect, uint32_t* __restrict__ depth_key,
+                          unsigned long long* __restrict__ tmask) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_slots(N, V)) return;
   const int v = (int)(s / N);
@@ -318,6 +319,23 @@ __global__ void k_project(const float* __restrict__ P, int N, long long ld, cons
     y1 = (int)fminf(fmaxf(floorf((VG.my + r) * inv) + 1.f, 0.f), (float)cam.tiles_y);
   }
   if (x1 <= x0 || y1 <= y0) return;
+  // tiles of a small rectangle the splat can reach (all for a large one)
+  // (the key emission reads the mask of every rectangle of at most
+  // kCullMaxTiles tiles, so it is written for each of them: all bits in smooth mode)
+  uint32_t nt = (uint32_t)((x1 - x0) * (y1 - y0));
+  if (tmask != nullptr && nt <= (uint32_t)kCullMaxTiles) {
+    unsigned long long m = nt == 64u ? ~0ull : (1ull << nt) - 1ull;
+    if (!smooth) {
+      m = 0ull;
+      int bit = 0;
+      for (int ty = y0; ty < y1; ++ty)
+        for (int tx = x0; tx < x1; ++tx, ++bit)
+          if (tile_reachable(VG.mx, VG.my, VG.A, VG.B, VG.C, G.o, tx, ty)) m |= 1ull << bit;
+    }
+    nt = (uint32_t)__popcll(m);
+    tmask[s] = m;
+    if (nt == 0) return;   // the splat reaches no pixel
+  }
   float Y[16];
   sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
   float rgb[3];
@@ -334,7 +352,7 @@ __global__ void k_project(const float* __restrict__ P, int N, long long ld, cons
   R.b = make_float4(VG.C, G.o, VG.tc[2], 0.f);
   R.c = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
   rec[s] = R;
-  ntiles[s] = (uint32_t)((x1 - x0) * (y1 - y0));
+  ntiles[s] = nt;
   rect[s] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
   depth_key[s] = __float_as_uint(VG.tc[2]);
 }
@@ -883,12 +901,13 @@ __global__ void k_splat_sum_batch(const __grid_constant__ GaussBatch gb, const P
 }  // namespace
 
 cudaError_t launch_project(const float* params, int N, long long ld, const DevCam* cams, int V, int smooth,
-                           SplatRec* rec, uint32_t* ntiles, uint2* rect, uint32_t* depth_key, cudaStream_t st) {
+                           SplatRec* rec, uint32_t* ntiles, uint2* rect, uint32_t* depth_key,
+                           unsigned long long* tmask, cudaStream_t st) {
   const long long n = (long long)N * V;
   if (n == 0) return cudaSuccess;
   const int bs = 256;
   { k_project<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(params, N, ld, cams, V, smooth, rec, ntiles, rect,
-                                                          depth_key); note_launch(); }
+                                                          depth_key, tmask); note_launch(); }
   return cudaGetLastError();
 }
 

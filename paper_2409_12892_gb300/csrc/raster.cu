@@ -37,9 +37,9 @@ __device__ __forceinline__ int find_view(const DevCam* __restrict__ cams, int V,
 }
 
 __global__ void k_emit_keys(const uint32_t* __restrict__ sorted_slots, long long n_vis,
-                            const uint2* __restrict__ rect, const DevCam* __restrict__ cams, int N,
-                            const unsigned long long* __restrict__ key_off, uint32_t* __restrict__ keys,
-                            uint32_t* __restrict__ vals) {
+                            const uint2* __restrict__ rect, const unsigned long long* __restrict__ tmask,
+                            const DevCam* __restrict__ cams, int N, const unsigned long long* __restrict__ key_off,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_vis) return;
   const uint32_t slot = sorted_slots[i];
@@ -47,9 +47,14 @@ __global__ void k_emit_keys(const uint32_t* __restrict__ sorted_slots, long long
   const DevCam& cam = cams[v];
   const uint2 r = rect[slot];
   const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+  // the tiles the projection kept (key_off counts exactly those)
+  const bool masked = tmask != nullptr && (x1 - x0) * (y1 - y0) <= kCullMaxTiles;
+  const unsigned long long m = masked ? tmask[slot] : ~0ull;
   unsigned long long o = key_off[i];
+  int bit = 0;
   for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx) {
+    for (int tx = x0; tx < x1; ++tx, ++bit) {
+      if (masked && !((m >> bit) & 1ull)) continue;
       keys[o] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
       vals[o] = slot;
       ++o;
@@ -471,12 +476,13 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
 
 }  // namespace
 
-cudaError_t launch_emit_keys(const uint32_t* sorted_slots, long long n_vis, const uint2* rect, const DevCam* cams,
-                             int V, int N, const unsigned long long* key_off, uint32_t* tile_keys,
-                             uint32_t* tile_vals, cudaStream_t st) {
+cudaError_t launch_emit_keys(const uint32_t* sorted_slots, long long n_vis, const uint2* rect,
+                             const unsigned long long* tmask, const DevCam* cams, int V, int N,
+                             const unsigned long long* key_off, uint32_t* tile_keys, uint32_t* tile_vals,
+                             cudaStream_t st) {
   (void)V;
   if (n_vis <= 0) return cudaSuccess;
-  { k_emit_keys<<<(unsigned)((n_vis + 255) / 256), 256, 0, st>>>(sorted_slots, n_vis, rect, cams, N, key_off,
+  { k_emit_keys<<<(unsigned)((n_vis + 255) / 256), 256, 0, st>>>(sorted_slots, n_vis, rect, tmask, cams, N, key_off,
                                                                tile_keys, tile_vals); note_launch(); }
   return cudaGetLastError();
 }

@@ -57,6 +57,37 @@ def test_render_matches_oracle(lib, case):
     assert abs(cost - ref_cost) <= 1e-4 * ref_cost
 
 
+def test_tile_culling_drops_keys_but_no_contribution(lib):
+    """The projection keeps a tile key only for tiles where the splat can reach
+    alpha >= 1/255 at some pixel centre (conservatively). Anisotropic splats miss
+    corner tiles of their 3-sigma rectangles, so fewer keys are sorted than the
+    rectangles hold, while the image and every cache entry stay the oracle's."""
+    from oracle import jacobian as J, projection
+    wl = synth.small_workload("aniso", 515, 400, 3, 160, 96, cam_radius=3.0, log_scale_mean=-2.0)
+    P = synth.make_gaussians(wl)
+    P[:, 3] += 0.9          # stretch one axis: elongated splats at every orientation
+    P[:, 10] = -2.0         # faint splats: their 1/255 contour lies well inside 3 sigma
+    cams = synth.make_cameras(wl)
+    lin = J.linearise(P.astype(np.float64), cams)
+    rect_keys = 0
+    for cam in cams:
+        r = projection.project(P.astype(np.float64), cam, want_jac=False).rect
+        rect_keys += int(((r[:, 2] - r[:, 0]) * (r[:, 3] - r[:, 1])).sum())
+    tgt = np.concatenate([im.ravel() for im in synth.smooth_images(515, cams)]).astype(np.float32)
+    ctx = lib.Context()
+    cache = ctx.build_cache(lib.to_soa(P), P.shape[0], cams, torch.from_numpy(tgt).cuda().view(-1, 3))
+    info = cache.info()
+    print(f"tile keys {info.keys} of {rect_keys} in the rectangles")
+    assert info.keys < 0.9 * rect_keys
+    mask = pixel_mask(lin)
+    img = np.concatenate([vl.ras.image.ravel() for vl in lin]).reshape(-1, 3)
+    got = cache.F.cpu().numpy().reshape(-1, 3) + tgt.reshape(-1, 3)
+    assert np.abs(got - img)[mask].max() < 1e-5
+    n_rec = sum(vl.ras.rec_pix.shape[0] for vl in lin)
+    assert abs(info.entries - n_rec) <= max(2, 1e-4 * n_rec)
+    cache.free()
+
+
 def test_build_cache_b_and_residual(lib, case):
     from oracle import jacobian as J
     name, P, cams, tgt, lin = case
