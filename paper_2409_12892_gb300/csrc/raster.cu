@@ -251,17 +251,19 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
     uint32_t* __restrict__ seg_slot, SegRec* __restrict__ seg_rec, uint8_t* __restrict__ slot_active,
     int* __restrict__ err, const ThinOut thin) {
   constexpr bool kThin = kFmt == GSLM_CACHE_THIN;
-  __shared__ unsigned nzs;                // sub-batch splats that are segments (bit j)
   __shared__ float4 sA[kTilePix];
   __shared__ float2 sB[kTilePix];
   __shared__ float4 sC[kTilePix];
   __shared__ uint32_t sSlot[kTilePix];
-  __shared__ uint32_t bal[kTilePix / 32][32];
-  __shared__ uint32_t woff[kTilePix / 32][32];
-  __shared__ uint32_t segst[32];
-  __shared__ int segidx[32];
+  // Per sub-batch of 32 splats every warp works out the splats' entry and
+  // segment offsets itself (lane = splat) from all warps' ballots, so one
+  // barrier per sub-batch suffices; the ballots alternate between two buffers
+  // so that a warp already in the next sub-batch cannot overwrite ballots
+  // another warp still reads.
+  __shared__ uint32_t bal[2][kTilePix / 32][32];
+  __shared__ uint32_t wpos[kTilePix / 32][32];   // a warp's first entry position of each splat (own row)
+  __shared__ int wseg[kTilePix / 32][32];        // segment index of each splat or -1 (own row)
   __shared__ uint32_t segmax[32];
-  __shared__ uint32_t add_e, add_s;
   __shared__ float sAraw[32][kTilePix];   // o G of the sub-batch's splats at each pixel (phase A -> D)
   const int tile = blockIdx.x;
   const int v = find_view(cams, V, tile);
@@ -318,20 +320,24 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
         }
       }
       // B: per-warp ballots, one per splat
+      const int par = (sub >> 5) & 1;
 #pragma unroll 4
       for (int j = 0; j < 32; ++j) {
         const unsigned bj = __ballot_sync(kFull, (mask >> j) & 1u);
-        if (lane == j) bal[warp][j] = bj;
+        if (lane == j) bal[par][warp][j] = bj;
       }
       __syncthreads();
-      // C: segment and entry offsets of the m splats (warp 0, lane = splat)
-      if (warp == 0) {
+      // C: segment and entry offsets of the m splats, in every warp (lane =
+      // splat); warp 0 also writes the segment records
+      uint32_t add_e, add_s;
+      unsigned nzs;
+      {
         const int j = lane;
-        uint32_t cj = 0;
+        uint32_t cj = 0, own = 0;
 #pragma unroll
         for (int w = 0; w < kTilePix / 32; ++w) {
-          const uint32_t c = __popc(bal[w][j]);
-          woff[w][j] = cj;
+          const uint32_t c = __popc(bal[par][w][j]);
+          own += w < warp ? c : 0u;
           cj += c;
         }
         uint32_t inc = cj;
@@ -341,15 +347,18 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
         }
         const uint32_t excl = inc - cj;
         const unsigned nz = __ballot_sync(kFull, cj > 0);
-        segidx[j] = -1;
-        if (cj > 0) {
-          const uint32_t sidx = sbase + srun + __popc(nz & lt);
+        const uint32_t sidx = sbase + srun + __popc(nz & lt);
+        wpos[warp][j] = erun + excl + own;
+        wseg[warp][j] = cj > 0 && sidx < send ? (int)sidx : -1;
+        add_e = __shfl_sync(kFull, inc, 31);
+        add_s = (uint32_t)__popc(nz);
+        nzs = nz;
+        if (warp == 0 && cj > 0) {
           const uint32_t slot = sSlot[sub + j];
           if (sidx < send) {
             seg_slot[sidx] = slot;
             seg_entry_off[sidx] = ebase + erun + excl;
             slot_active[slot] = 1;
-            segidx[j] = (int)sidx;
             const float4 a = sA[sub + j];
             const float2 bb = sB[sub + j];
             SegRec r;
@@ -375,21 +384,15 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
             atomicOr(err, 2);
           }
         }
-        segst[j] = erun + excl;
-        if (kFmt == GSLM_CACHE_FP16S) segmax[j] = 0u;
-        if (lane == 31) {
-          add_e = inc;
-          add_s = __popc(nz);
-          nzs = nz;
-        }
+        if (kFmt == GSLM_CACHE_FP16S && warp == 0) segmax[j] = 0u;
       }
-      __syncthreads();
+      __syncwarp();
       if (kThin) {
         // checkpoints before the window-opening segments, the pixel's state
         // advanced over its own contributions; where the pixel stopped
         const uint32_t wbase = thin.win_off[tile];
         for (int j = 0; j < m; ++j) {
-          const int sj = segidx[j];
+          const int sj = wseg[warp][j];
           if (sj >= 0 && ((uint32_t)(sj - (int)sbase) % kThinWindow) == 0u)
             thin.ckpt[(size_t)(wbase + (uint32_t)(sj - (int)sbase) / kThinWindow) * kTilePix + threadIdx.x] =
                 make_float4(T, p0, p1, p2);
@@ -411,6 +414,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
       }
       // D: entries. FP16S first needs every segment's largest magnitude.
       if (kFmt == GSLM_CACHE_FP16S) {
+        __syncthreads();   // segmax cleared by warp 0
         float Tq = T, q0 = p0, q1 = p1, q2 = p2;
         for (int j = 0; j < m; ++j) {
           if (!((mask >> j) & 1u)) continue;
@@ -431,9 +435,9 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
           Tq = transmit(Tq, alpha);
         }
         __syncthreads();
-        if (threadIdx.x < 32 && segidx[threadIdx.x] >= 0) {
-          seg_scale[segidx[threadIdx.x]] = __uint_as_float(segmax[threadIdx.x]);
-          seg_rec[segidx[threadIdx.x]].scale = __uint_as_float(segmax[threadIdx.x]);
+        if (threadIdx.x < 32 && wseg[0][threadIdx.x] >= 0) {
+          seg_scale[wseg[0][threadIdx.x]] = __uint_as_float(segmax[threadIdx.x]);
+          seg_rec[wseg[0][threadIdx.x]].scale = __uint_as_float(segmax[threadIdx.x]);
         }
       }
       for (int j = 0; j < m; ++j) {
@@ -450,8 +454,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
         const float h0 = clamped ? 0.f : alpha * (T * c.x - (Cf0 - p0) * inv1m);
         const float h1 = clamped ? 0.f : alpha * (T * c.y - (Cf1 - p1) * inv1m);
         const float h2 = clamped ? 0.f : alpha * (T * c.z - (Cf2 - p2) * inv1m);
-        const unsigned long long pos =
-            ebase + segst[j] + woff[warp][j] + (uint32_t)__popc(bal[warp][j] & lt);
+        const unsigned long long pos = ebase + wpos[warp][j] + (uint32_t)__popc(bal[par][warp][j] & lt);
         float inv_scale = 1.f;
         if (kFmt == GSLM_CACHE_FP16S) {
           const float s = __uint_as_float(segmax[j]);
