@@ -83,7 +83,7 @@ def parse_args(argv=None):
                     help="kernel mode: one cache of the first --apply-views cameras, then one J^T u and one J p "
                          "(for ncu captures); with --sweep, every kernel variant timed")
     ap.add_argument("--apply-views", type=int, default=8)
-    ap.add_argument("--apply-variant", type=int, default=3, help="1..8: forced apply kernel variant 0..7")
+    ap.add_argument("--apply-variant", type=int, default=3, help="1..10: forced apply kernel variant 0..9")
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--formats", default="",
                     help="with --apply-pass: cache formats to compare (e.g. fp32,bf16,thin): bytes and the times "
@@ -1039,7 +1039,7 @@ def run_apply_pass(args):
            "device_free_gb": free_b / 1e9, "device_total_gb": total_b / 1e9}
     if args.sweep:
         pay = 16 if args.cache_fmt == "fp32" else 8
-        for v in range(1, 9):
+        for v in range(1, 11):
             ctx.set_options(apply_variant=v)
             for name, call in (("J", lambda: ctx.apply_J(cache, p, uo)), ("JT", lambda: ctx.apply_JT(cache, u, gout))):
                 ts = []

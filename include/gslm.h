@@ -121,7 +121,7 @@ typedef struct {
   int32_t graph;       /* 1 (default): a batched solve is captured into one CUDA graph and launched
                           once (after the first batched solve of a context, which also autotunes) */
   int32_t batch_ctas;  /* resident CTAs per SM of the persistent batched tile kernels; 0 = autotune */
-  int32_t apply_variant; /* 0: autotuned (or default) apply kernel variant; 1..8: always variant 0..7 */
+  int32_t apply_variant; /* 0: autotuned (or default) apply kernel variant; 1..10: always variant 0..9 */
   int32_t line_search; /* gslm_lm_step: 0 = full step (gamma = 1); n > 0 = Eq. line-search over
                           gamma = 1, 1/2, ..., 2^(1-n) on the first 30% of the step's views,
                           stopping at the first cost increase (default 8) */

@@ -525,7 +525,7 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
 
 // Candidates of the persistent tile kernels' autotuner: (variant, CTAs per SM),
 // each variant at the residency its registers allow and one CTA fewer.
-constexpr int kBatchCand = 16;
+constexpr int kBatchCand = 20;   // 2 x apply_variants()
 inline int cand_variant(int c) { return c / 2; }
 inline int cand_ctas(int c) {
   const int cap = variant_cta_cap(c / 2);
@@ -928,7 +928,7 @@ static gslm_status validate_opts(const gslm_options* o) {
   if (!(o->lambda_min > 0.f) || !(o->lambda_max >= o->lambda_min)) return GSLM_E_INVALID;
   if (o->group != 0 && o->group != 8 && o->group != 16 && o->group != 32) return GSLM_E_INVALID;
   if (o->batch_ctas < 0 || o->batch_ctas > 6) return GSLM_E_INVALID;
-  if (o->apply_variant < 0 || o->apply_variant > 8) return GSLM_E_INVALID;
+  if (o->apply_variant < 0 || o->apply_variant > 10) return GSLM_E_INVALID;
   if (o->line_search < 0 || o->line_search > 60) return GSLM_E_INVALID;
   if (o->objective != GSLM_OBJ_L2 && o->objective != GSLM_OBJ_L1_SSIM) return GSLM_E_INVALID;
   if (!(o->lambda_l1 >= 0.f) || !(o->lambda_ssim >= 0.f) || !(o->res_eps > 0.f) || !std::isfinite(o->lambda_l1) ||
@@ -1128,8 +1128,10 @@ static gslm_status build_cache_impl(gslm_ctx* ctx, const float* params, int64_t 
     tout.win_off = c->win_off.as<uint32_t>();
     tout.n_live = c->n_live.as<uint32_t>();
   }
-  CK(c->payload.alloc(thin ? 16 : payload_bytes(c->fmt) * std::max<unsigned long long>(E, 1), st));
-  CK(c->pixoff.alloc(thin ? 16 : std::max<unsigned long long>(E, 1), st));
+  // 32 bytes of slack: the tile kernels' L2 prefetches cover whole 16-byte
+  // blocks around a segment's entries, up to 15 bytes past the last entry
+  CK(c->payload.alloc(thin ? 16 : payload_bytes(c->fmt) * std::max<unsigned long long>(E, 1) + 32, st));
+  CK(c->pixoff.alloc(thin ? 16 : std::max<unsigned long long>(E, 1) + 32, st));
   CK(c->seg_entry_off.alloc(sizeof(unsigned long long) * (ns + 1), st));
   CK(c->seg_slot.alloc(sizeof(uint32_t) * ns, st));
   CK(c->seg_rec.alloc(sizeof(SegRec) * ns, st));

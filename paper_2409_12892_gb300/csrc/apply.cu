@@ -160,13 +160,35 @@ __device__ __forceinline__ uint4 entry_word(const uint4& a, const uint4& c) {
   return make_uint4(a.x, a.y, a.z - a.x, c.w);   // segments hold < 2^32 entries
 }
 
+// Variants 8 and 9 ask L2 to fetch a segment's entries (payload and pixel
+// offsets: two bulk prefetches, no completion to wait for, no registers held)
+// kPf segments before a lane group takes it, so that its loads hit L2 instead
+// of waiting on DRAM. The prefetched ranges are widened to 16-byte
+// boundaries; the cache's payload and pixel-offset arrays are allocated 32
+// bytes long for this.
+template <int kFmt>
+__device__ __forceinline__ void prefetch_segment_l2(const CacheView& cv, const uint4& w0) {
+  constexpr unsigned long long B = kFmt == GSLM_CACHE_FP32 ? 16 : 8;
+  const unsigned long long e0 = ((unsigned long long)w0.y << 32) | w0.x, e1 = e0 + w0.z;
+  const unsigned long long p0 = (e0 * B) & ~15ull, p1 = (e1 * B + 15ull) & ~15ull;
+  const unsigned long long x0 = e0 & ~15ull, x1 = (e1 + 15ull) & ~15ull;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const unsigned char*>(cv.payload) + p0),
+               "r"((uint32_t)(p1 - p0))
+               : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(cv.pixoff + x0), "r"((uint32_t)(x1 - x0))
+               : "memory");
+}
+
 // Stages segments [first, first + cnt) of the cache for J p; ydot holds the
 // splat tangents (12 floats per splat: dmx, dmy, dA, dB, dC, do, dr, dg, db).
+// With kPf > 0 the first kPf segments' entries are prefetched to L2.
+template <int kFmt, int kPf>
 __device__ __forceinline__ void stage_chunk_J(const CacheView& cv, uint32_t first, int cnt, StageJ& S,
                                               const float* __restrict__ ydot) {
   for (int t = threadIdx.x; t < cnt; t += kTilePix) {
     const uint4* q = reinterpret_cast<const uint4*>(cv.seg_rec + first + t);
     const uint4 a = q[0], b = q[1], c = q[2];
+    if (kPf > 0 && t < kPf) prefetch_segment_l2<kFmt>(cv, entry_word(a, c));
     const SegRec r = rec_from(a, b, c);
     const float4* yd = reinterpret_cast<const float4*>(ydot + (size_t)r.slot * 12);
     const float4 y0 = yd[0], y1 = yd[1];
@@ -185,11 +207,13 @@ __device__ __forceinline__ void stage_chunk_J(const CacheView& cv, uint32_t firs
   }
 }
 
-// Stages segments [first, first + cnt) of the cache for J^T u.
+// Stages segments [first, first + cnt) of the cache for J^T u (kPf as for J p).
+template <int kFmt, int kPf>
 __device__ __forceinline__ void stage_chunk_JT(const CacheView& cv, uint32_t first, int cnt, StageJT& S) {
   for (int t = threadIdx.x; t < cnt; t += kTilePix) {
     const uint4* q = reinterpret_cast<const uint4*>(cv.seg_rec + first + t);
     const uint4 a = q[0], b = q[1], c = q[2];
+    if (kPf > 0 && t < kPf) prefetch_segment_l2<kFmt>(cv, entry_word(a, c));
     const SegRec r = rec_from(a, b, c);
     S.w0[t] = entry_word(a, c);
     S.w1[t] = make_float4(r.mx - kTileCentre, r.my - kTileCentre, r.A, r.B);
@@ -230,7 +254,17 @@ __device__ __forceinline__ void apply_J_epilogue(const CacheView& cv, int tile, 
     const long long pix = cam.pix_off + (long long)y * cam.W + x;
     const int p = threadIdx.x;
     float u0, u1, u2;
-    if constexpr (kMode == 1) {
+    if constexpr (kMode == 2) {
+      u0 = u1 = u2 = 0.f;
+      const float4* s4 = reinterpret_cast<const float4*>(su);
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const float4 t = s4[w * kTilePix + p];
+        u0 += t.x;
+        u1 += t.y;
+        u2 += t.z;
+      }
+    } else if constexpr (kMode == 1) {
       u0 = u1 = u2 = 0.f;
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) {
@@ -285,8 +319,10 @@ __device__ __forceinline__ void apply_J_epilogue(const CacheView& cv, int tile, 
 // kMode 0: one tile of u accumulated with shared-memory atomics. kMode 1 (G =
 // 32 only): a warp works on one segment at a time, whose entries are distinct
 // pixels, so each warp adds into its own copy of the tile with plain
-// read-modify-writes and the copies are summed in the epilogue.
-template <int kFmt, int G, int U, int kMode>
+// read-modify-writes and the copies are summed in the epilogue. kMode 2: as 1
+// with the copy's three channels of a pixel in one float4 (one 16-byte load
+// and one store per entry instead of three of each).
+template <int kFmt, int G, int U, int kMode, int kPf>
 __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, const float* __restrict__ ydot,
                                              const float* __restrict__ Fadd, float* __restrict__ u,
                                              double* __restrict__ sq_partials, float* su, const float2* sxy,
@@ -304,7 +340,7 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
   const uint32_t n = cv.tile_seg_off[tile + 1] - g0;
   for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
     const int cnt = (int)min((uint32_t)kStage, n - c0);
-    stage_chunk_J(cv, g0 + c0, cnt, S, ydot);
+    stage_chunk_J<kFmt, kPf>(cv, g0 + c0, cnt, S, ydot);
     if (threadIdx.x == 0) *next_seg = 0;
     __syncthreads();
     for (;;) {
@@ -314,6 +350,9 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
       if (kb >= (uint32_t)cnt) break;
       const uint32_t k = kb + grp;
       const bool has = k < (uint32_t)cnt;
+      if constexpr (kPf > 0) {
+        if (gl == 0 && k + kPf < (uint32_t)cnt) prefetch_segment_l2<kFmt>(cv, S.w0[k + kPf]);
+      }
       uint4 w0 = make_uint4(0u, 0u, 0u, 0u);
       float4 w1 = make_float4(0.f, 0.f, 0.f, 0.f), w2 = w1;
       float db = 0.f;
@@ -351,7 +390,14 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
             const float q = fmaf(c.x, fmaf(K3, c.x, fmaf(K4, c.y, K1)), fmaf(c.y, fmaf(K5, c.y, K2), K0));
             const float v0 = fmaf(pe.x, dr, pe.y * q), v1 = fmaf(pe.x, dg, pe.z * q);
             const float v2 = fmaf(pe.x, db, pe.w * q);
-            if constexpr (kMode == 1) {   // the warp's own unpadded planes [ch][p]
+            if constexpr (kMode == 2) {   // the warp's own tile of float4 [p]
+              float4* sp = reinterpret_cast<float4*>(su) + warp * kTilePix + p;
+              float4 t = *sp;
+              t.x += v0;
+              t.y += v1;
+              t.z += v2;
+              *sp = t;
+            } else if constexpr (kMode == 1) {   // the warp's own unpadded planes [ch][p]
               float* sp = su + warp * (3 * kTilePix) + p;
               sp[0] += v0;
               sp[kTilePix] += v1;
@@ -371,24 +417,27 @@ __device__ __forceinline__ void apply_J_tile(const CacheView& cv, int tile, cons
   apply_J_epilogue<kMode>(cv, tile, cam, tx, ty, su, Fadd, u, sq_partials, dred);
 }
 
+// Floats of the J p accumulation tile(s) of each mode.
+constexpr int su_floats(int mode) { return mode == 2 ? kWarps * 4 * kTilePix : mode == 1 ? kWarps * 3 * kTilePix : kPlane3; }
+
 #define APPLY_J_SHARED                                   \
-  __shared__ float su[kMode ? kWarps * 3 * kTilePix : kPlane3];   \
+  __shared__ __align__(16) float su[su_floats(kMode)];   \
   __shared__ float2 sxy[kTilePix];                       \
   __shared__ double dred[2 * kWarps];                    \
   __shared__ unsigned int next_seg;                      \
   __shared__ StageJ S;                                   \
   sxy[threadIdx.x] = centred_xy(threadIdx.x);
 
-template <int kFmt, int G, int U, int kMinBlocks, int kMode>
+template <int kFmt, int G, int U, int kMinBlocks, int kMode, int kPf>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J(CacheView cv, const float* __restrict__ ydot,
                                                                   const float* __restrict__ Fadd,
                                                                   float* __restrict__ u,
                                                                   double* __restrict__ sq_partials) {
   if (cv.skip != nullptr && *cv.skip) return;
   APPLY_J_SHARED
-  for (int i = threadIdx.x; i < (kMode ? kWarps * 3 * kTilePix : kPlane3); i += kTilePix) su[i] = 0.f;
+  for (int i = threadIdx.x; i < su_floats(kMode); i += kTilePix) su[i] = 0.f;
   __syncthreads();
-  apply_J_tile<kFmt, G, U, kMode>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg, S);
+  apply_J_tile<kFmt, G, U, kMode, kPf>(cv, blockIdx.x, ydot, Fadd, u, sq_partials, su, sxy, dred, &next_seg, S);
 }
 
 // Subset of a global tile index of a batch.
@@ -400,12 +449,12 @@ __device__ __forceinline__ int batch_subset(const TileBatch& tb, long long gt) {
 
 // Persistent J p over every subset of a batch: each CTA takes tiles from the
 // batch's queue until all are done (tiles of finished solves are skipped).
-template <int kFmt, int G, int U, int kMinBlocks, int kMode>
+template <int kFmt, int G, int U, int kMinBlocks, int kMode, int kPf>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J_batch(const __grid_constant__ TileBatch tb) {
   APPLY_J_SHARED
   __shared__ long long s_tile;
   for (;;) {
-    for (int i = threadIdx.x; i < (kMode ? kWarps * 3 * kTilePix : kPlane3); i += kTilePix) su[i] = 0.f;
+    for (int i = threadIdx.x; i < su_floats(kMode); i += kTilePix) su[i] = 0.f;
     if (threadIdx.x == 0) s_tile = (long long)atomicAdd(tb.queue, 1u);
     __syncthreads();
     const long long gt = s_tile;
@@ -413,7 +462,7 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_J_batch(const __
     const int b = batch_subset(tb, gt);
     const CacheView& cv = tb.v[b];
     if (cv.skip == nullptr || *cv.skip == 0)
-      apply_J_tile<kFmt, G, U, kMode>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
+      apply_J_tile<kFmt, G, U, kMode, kPf>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.ydot[b], nullptr, tb.u[b],
                                nullptr, su, sxy, dred, &next_seg, S);
     __syncthreads();
   }
@@ -475,7 +524,7 @@ static_assert(9 * kRedRow <= kRedGroup && kRedGroup % 32 == 16 && kRedRow % 4 ==
 // J^T u over one tile into per-segment partials, stored at each segment's
 // splat-order position (so the adjoint kernel reads a splat's partials as one
 // contiguous range). The caller synchronises before. su4 / sxy are filled here.
-template <int kFmt, int G, int U>
+template <int kFmt, int G, int U, int kPf>
 __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, const float* __restrict__ u,
                                               float* __restrict__ seg_ybar, float4* su4, float2* sxy,
                                               unsigned int* next_seg, StageJT& S, float* sred) {
@@ -502,7 +551,7 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
   const int gl = lane & (G - 1), grp = lane / G;
   for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
     const int cnt = (int)min((uint32_t)kStage, n - c0);
-    stage_chunk_JT(cv, g0 + c0, cnt, S);
+    stage_chunk_JT<kFmt, kPf>(cv, g0 + c0, cnt, S);
     if (threadIdx.x == 0) *next_seg = 0;
     __syncthreads();
     for (;;) {
@@ -512,6 +561,9 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
       if (kb >= (uint32_t)cnt) break;
       const uint32_t k = kb + grp;
       const bool has = k < (uint32_t)cnt;
+      if constexpr (kPf > 0) {
+        if (gl == 0 && k + kPf < (uint32_t)cnt) prefetch_segment_l2<kFmt>(cv, S.w0[k + kPf]);
+      }
       const uint4 w0 = has ? S.w0[k] : make_uint4(0u, 0u, 0u, 0u);
       const uint32_t len = w0.z;
       const float scale = __uint_as_float(w0.w);
@@ -634,16 +686,16 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
   __shared__ StageJT S;                                      \
   __shared__ __align__(16) float sred[G == 16 ? kWarps * 2 * kRedGroup : 4];
 
-template <int kFmt, int G, int U, int kMinBlocks>
+template <int kFmt, int G, int U, int kMinBlocks, int kPf>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv, const float* __restrict__ u,
                                                                    float* __restrict__ seg_ybar) {
   APPLY_JT_SHARED
   if (cv.skip != nullptr && *cv.skip) return;
-  apply_JT_tile<kFmt, G, U>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg, S, sred);
+  apply_JT_tile<kFmt, G, U, kPf>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg, S, sred);
 }
 
 // Persistent J^T u over every subset of a batch (see k_apply_J_batch).
-template <int kFmt, int G, int U, int kMinBlocks>
+template <int kFmt, int G, int U, int kMinBlocks, int kPf>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const __grid_constant__ TileBatch tb) {
   APPLY_JT_SHARED
   __shared__ long long s_tile;
@@ -655,7 +707,7 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const _
     const int b = batch_subset(tb, gt);
     const CacheView& cv = tb.v[b];
     if (cv.skip == nullptr || *cv.skip == 0)
-      apply_JT_tile<kFmt, G, U>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.u[b], tb.seg_ybar[b], su4, sxy,
+      apply_JT_tile<kFmt, G, U, kPf>(cv, (int)(gt - (b > 0 ? tb.tile_end[b - 1] : 0)), tb.u[b], tb.seg_ybar[b], su4, sxy,
                                 &next_seg, S, sred);
     __syncthreads();
   }
@@ -767,30 +819,33 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
 // (16, 4, 4); 6 = J p private tiles (32, 3, 4) and J^T u (32, 3, 4); 7 = J p
 // (32, 3, 6) and J^T u (16, 3, 5). U = 3 fills a 94-entry segment (the paper
 // workload's mean) with 96 lane slots at G = 32 or 2 x 48 at G = 16.
-template <int kFmt, int G, int U, int B, int kMode = 0>
+// With L2 prefetch of the segment kPf ahead: 8 = J p private tiles (32, 3, 4)
+// and J^T u (16, 2, 6), both kPf = 16; 9 = J p float4 private tiles (32, 3, 4),
+// kPf = 16, and J^T u (16, 4, 5), kPf = 32.
+template <int kFmt, int G, int U, int B, int kMode = 0, int kPf = 0>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
-  k_apply_J<kFmt, G, U, B, kMode><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
+  k_apply_J<kFmt, G, U, B, kMode, kPf><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int kFmt, int G, int U, int B>
+template <int kFmt, int G, int U, int B, int kPf = 0>
 cudaError_t run_JT(const CacheView& cv, const float* u, float* seg_ybar, cudaStream_t st) {
-  k_apply_JT<kFmt, G, U, B><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar);
+  k_apply_JT<kFmt, G, U, B, kPf><<<cv.n_tiles, kTilePix, 0, st>>>(cv, u, seg_ybar);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int kFmt, int G, int U, int B, int kMode = 0>
+template <int kFmt, int G, int U, int B, int kMode = 0, int kPf = 0>
 cudaError_t run_J_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
-  k_apply_J_batch<kFmt, G, U, B, kMode><<<ctas, kTilePix, 0, st>>>(tb);
+  k_apply_J_batch<kFmt, G, U, B, kMode, kPf><<<ctas, kTilePix, 0, st>>>(tb);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int kFmt, int G, int U, int B>
+template <int kFmt, int G, int U, int B, int kPf = 0>
 cudaError_t run_JT_batch(const TileBatch& tb, int ctas, cudaStream_t st) {
-  k_apply_JT_batch<kFmt, G, U, B><<<ctas, kTilePix, 0, st>>>(tb);
+  k_apply_JT_batch<kFmt, G, U, B, kPf><<<ctas, kTilePix, 0, st>>>(tb);
   note_launch();
   return cudaGetLastError();
 }
@@ -805,6 +860,8 @@ cudaError_t apply_J_batch_variant(int variant, const TileBatch& tb, int ctas, cu
     case 5: return run_J_batch<kFmt, 32, 2, 4, 1>(tb, ctas, st);
     case 6: return run_J_batch<kFmt, 32, 3, 4, 1>(tb, ctas, st);
     case 7: return run_J_batch<kFmt, 32, 3, 6>(tb, ctas, st);
+    case 8: return run_J_batch<kFmt, 32, 3, 4, 1, 16>(tb, ctas, st);
+    case 9: return run_J_batch<kFmt, 32, 3, 4, 2, 16>(tb, ctas, st);
     default: return run_J_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -819,6 +876,8 @@ cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, c
     case 5: return run_JT_batch<kFmt, 16, 4, 4>(tb, ctas, st);
     case 6: return run_JT_batch<kFmt, 32, 3, 4>(tb, ctas, st);
     case 7: return run_JT_batch<kFmt, 16, 3, 5>(tb, ctas, st);
+    case 8: return run_JT_batch<kFmt, 16, 2, 6, 16>(tb, ctas, st);
+    case 9: return run_JT_batch<kFmt, 16, 4, 5, 32>(tb, ctas, st);
     default: return run_JT_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -834,6 +893,8 @@ cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot,
     case 5: return run_J<kFmt, 32, 2, 4, 1>(cv, ydot, F_add, u, sq, st);
     case 6: return run_J<kFmt, 32, 3, 4, 1>(cv, ydot, F_add, u, sq, st);
     case 7: return run_J<kFmt, 32, 3, 6>(cv, ydot, F_add, u, sq, st);
+    case 8: return run_J<kFmt, 32, 3, 4, 1, 16>(cv, ydot, F_add, u, sq, st);
+    case 9: return run_J<kFmt, 32, 3, 4, 2, 16>(cv, ydot, F_add, u, sq, st);
     default: return run_J<kFmt, 8, 2, 6>(cv, ydot, F_add, u, sq, st);
   }
 }
@@ -848,6 +909,8 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
     case 5: return run_JT<kFmt, 16, 4, 4>(cv, u, seg_ybar, st);
     case 6: return run_JT<kFmt, 32, 3, 4>(cv, u, seg_ybar, st);
     case 7: return run_JT<kFmt, 16, 3, 5>(cv, u, seg_ybar, st);
+    case 8: return run_JT<kFmt, 16, 2, 6, 16>(cv, u, seg_ybar, st);
+    case 9: return run_JT<kFmt, 16, 4, 5, 32>(cv, u, seg_ybar, st);
     default: return run_JT<kFmt, 8, 2, 6>(cv, u, seg_ybar, st);
   }
 }
@@ -856,7 +919,7 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
 
 int apply_J_partials(const CacheView& cv) { return cv.n_tiles; }
 
-int apply_variants() { return 8; }
+int apply_variants() { return 10; }
 
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add, float* u,
                            double* sq_partials, int variant, cudaStream_t st) {
@@ -884,8 +947,8 @@ int device_sm_count() {
 }
 
 // Resident CTAs of a persistent grid: never more than the kernel variant's
-// register and shared-memory budget lets share an SM (6, 5, 6, 4, 6, 4, 4, 6
-// for variants 0..7), never more CTAs than tiles.
+// register and shared-memory budget lets share an SM (6, 5, 6, 4, 6, 4, 4, 6,
+// 4, 4 for variants 0..9), never more CTAs than tiles.
 static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
   const int cap = variant_cta_cap(variant);
   const int per = ctas_per_sm < 1 ? 1 : (ctas_per_sm > cap ? cap : ctas_per_sm);

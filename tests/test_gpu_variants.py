@@ -3,7 +3,8 @@
 The autotuner keeps whichever variant runs fastest on the caller's cache, so
 each one must compute the same products: J p and J^T u of every variant (lane
 groups of 8, 16 or 32, 2 to 4 entries in flight per lane, shared atomics or
-per-warp private tiles) are held to the bound of their cache format (FP32 1e-4,
+per-warp private tiles of three planes or of float4, with or without L2
+prefetch of the segments ahead) are held to the bound of their cache format (FP32 1e-4,
 BF16 2e-2, FP16 with scale 5e-3), and a batched solve (persistent kernels) with
 each variant forced is held to the PCG tolerance of 1e-3 against the oracle's
 Algorithm 1 after 2 iterations (where float32 rounding moves x by at most
@@ -19,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-N_VARIANTS = 8
+N_VARIANTS = 10
 
 
 @pytest.fixture(scope="module")

@@ -85,7 +85,7 @@ def test_noalloc_apply_JT_allocates_no_device_memory(g):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 6, 8])
+@pytest.mark.parametrize("variant", [1, 2, 6, 8, 9, 10])
 def test_noalloc_apply_JT_runs_the_forced_variant(g, variant):
     ctx = g.Context(autotune=False, apply_variant=variant)
     P, cache, us = _ragged(g, ctx)
