@@ -160,16 +160,16 @@ __device__ __forceinline__ uint4 entry_word(const uint4& a, const uint4& c) {
   return make_uint4(a.x, a.y, a.z - a.x, c.w);   // segments hold < 2^32 entries
 }
 
-// Variants 8 and 9 ask L2 to fetch a segment's entries (payload and pixel
-// offsets: two bulk prefetches, no completion to wait for, no registers held)
-// kPf segments before a lane group takes it, so that its loads hit L2 instead
-// of waiting on DRAM. The prefetched ranges are widened to 16-byte
+// The tile kernels' variants 8 and 9 ask L2 to fetch a segment's entries
+// (payload and pixel offsets: two bulk prefetches, no completion to wait for,
+// no registers held) kPf segments before a lane group takes it, so that its
+// loads hit L2 instead of waiting on DRAM; the diagonal kernel asks for a
+// group's next segment while it works on the current one. The prefetched ranges are widened to 16-byte
 // boundaries; the cache's payload and pixel-offset arrays are allocated 32
 // bytes long for this.
 template <int kFmt>
-__device__ __forceinline__ void prefetch_segment_l2(const CacheView& cv, const uint4& w0) {
+__device__ __forceinline__ void prefetch_range_l2(const CacheView& cv, unsigned long long e0, unsigned long long e1) {
   constexpr unsigned long long B = kFmt == GSLM_CACHE_FP32 ? 16 : 8;
-  const unsigned long long e0 = ((unsigned long long)w0.y << 32) | w0.x, e1 = e0 + w0.z;
   const unsigned long long p0 = (e0 * B) & ~15ull, p1 = (e1 * B + 15ull) & ~15ull;
   const unsigned long long x0 = e0 & ~15ull, x1 = (e1 + 15ull) & ~15ull;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const unsigned char*>(cv.payload) + p0),
@@ -177,6 +177,12 @@ __device__ __forceinline__ void prefetch_segment_l2(const CacheView& cv, const u
                : "memory");
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(cv.pixoff + x0), "r"((uint32_t)(x1 - x0))
                : "memory");
+}
+
+template <int kFmt>
+__device__ __forceinline__ void prefetch_segment_l2(const CacheView& cv, const uint4& w0) {
+  const unsigned long long e0 = ((unsigned long long)w0.y << 32) | w0.x;
+  prefetch_range_l2<kFmt>(cv, e0, e0 + w0.z);
 }
 
 // Stages segments [first, first + cnt) of the cache for J p; ydot holds the
@@ -761,9 +767,14 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
       const SegRec r = rec_from(rq[0], rq[1], rq[2]);   // tile-local mean, conic, 1/o, FP16 scale
       const float mx = r.mx, my = r.my, A = r.A, B = r.B, C = r.C, io = r.io;
       const float scale = kFmt == GSLM_CACHE_FP16S ? r.scale : 1.f;
-      for (unsigned long long e = r.e0 + gl; e < r.e1; e += kDiagG) {
-        const float4 pe = load_entry<kFmt>(cv.payload, e, scale);
-        const int p = cv.pixoff[e];
+      // the entry range of the group's next segment, asked of L2 after this one's entries
+      const uint32_t nseg = seg + kWarps * kGPW;
+      unsigned long long ne0 = 0, ne1 = 0;
+      if (gl == 0 && nseg < g1) {
+        ne0 = cv.seg_entry_off[nseg];
+        ne1 = cv.seg_entry_off[nseg + 1];
+      }
+      auto add_entry = [&](const float4& pe, int p) {
         float wr = 1.f, wg = 1.f, wb = 1.f;
         if constexpr (kWeighted) {
           wr = sw[0][p];
@@ -789,7 +800,18 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
         q[39] += wr * aa;
         q[40] += wg * aa;
         q[41] += wb * aa;
+      };
+      // two entries per lane in flight
+      unsigned long long e = r.e0 + gl;
+      for (; e + kDiagG < r.e1; e += 2 * kDiagG) {
+        const float4 pa = load_entry<kFmt>(cv.payload, e, scale);
+        const float4 pb = load_entry<kFmt>(cv.payload, e + kDiagG, scale);
+        const int xa = cv.pixoff[e], xb = cv.pixoff[e + kDiagG];
+        add_entry(pa, xa);
+        add_entry(pb, xb);
       }
+      if (e < r.e1) add_entry(load_entry<kFmt>(cv.payload, e, scale), cv.pixoff[e]);
+      if (gl == 0 && nseg < g1) prefetch_range_l2<kFmt>(cv, ne0, ne1);
     }
     // three recursive-halving reductions of 16 values over the group: lane gl
     // then holds sum gl of each block
