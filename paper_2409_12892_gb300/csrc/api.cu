@@ -527,14 +527,14 @@ gslm_status pcg_enqueue(gslm_ctx* ctx, const gslm_cache* c, const float* b, cons
 // each variant at the residency its registers allow and one CTA fewer.
 constexpr int kBatchCand = 20;   // 2 x apply_variants()
 inline int cand_variant(int c) { return c / 2; }
-inline int cand_ctas(int c) {
-  const int cap = variant_cta_cap(c / 2);
+inline int cand_ctas(int c, bool jt) {
+  const int cap = variant_cta_cap(c / 2, jt);
   return (c & 1) ? cap - 1 : cap;
 }
 
 // Times every candidate once (each computes the same result) and keeps the fastest.
 template <class F>
-gslm_status tune_batch(gslm_ctx* ctx, F&& launch, int* var, int* ctas) {
+gslm_status tune_batch(gslm_ctx* ctx, F&& launch, bool jt, int* var, int* ctas) {
   cudaStream_t st = ctx->st;
   std::vector<cudaEvent_t> ev(kBatchCand + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
@@ -546,7 +546,7 @@ gslm_status tune_batch(gslm_ctx* ctx, F&& launch, int* var, int* ctas) {
   } evg{ev};
   CK(cudaEventRecord(ev[0], st));
   for (int c = 0; c < kBatchCand; ++c) {
-    CKS(launch(cand_variant(c), cand_ctas(c)));
+    CKS(launch(cand_variant(c), cand_ctas(c, jt)));
     CK(cudaEventRecord(ev[c + 1], st));
   }
   CK(cudaEventSynchronize(ev[kBatchCand]));
@@ -561,7 +561,7 @@ gslm_status tune_batch(gslm_ctx* ctx, F&& launch, int* var, int* ctas) {
     }
   }
   *var = cand_variant(best);
-  *ctas = cand_ctas(best);
+  *ctas = cand_ctas(best, jt);
   return GSLM_OK;
 }
 
@@ -679,14 +679,14 @@ gslm_status pcg_batch_enqueue(gslm_ctx* ctx, const gslm_cache* const* cs, const 
       return GSLM_OK;
     }
     if (vJ < 0 && tune) {
-      CKS(tune_batch(ctx, runJ, &vJ, &cJ));
+      CKS(tune_batch(ctx, runJ, false, &vJ, &cJ));
     } else {
       CKS(runJ(vJ < 0 ? kDefaultVariant : vJ, ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : (cJ > 0 ? cJ : 4)));
     }
     ctx->timer.end(t);
     t = ctx->timer.begin(PH_APPLY_JT);
     if (vJT < 0 && tune) {
-      CKS(tune_batch(ctx, runJT, &vJT, &cJT));
+      CKS(tune_batch(ctx, runJT, true, &vJT, &cJT));
     } else {
       CKS(runJT(vJT < 0 ? kDefaultVariant : vJT,
                 ctx->opt.batch_ctas > 0 ? ctx->opt.batch_ctas : (cJT > 0 ? cJT : 4)));

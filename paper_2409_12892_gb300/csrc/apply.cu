@@ -154,7 +154,41 @@ struct StageJT {
   float4 w1[kStage];    // e = mean - centre (x, y), conic A, B
   float2 w2[kStage];    // conic C, 1 / opacity
   uint32_t pos[kStage]; // splat-order position of the segment (output row)
+  uint16_t order[kStage];   // processing order (groups of G < 32 lanes): by passes, most first
+  uint32_t bcount[16];      // pass-count buckets (zero between stages)
 };
+
+// Groups of G < 32 lanes work on 32 / G segments per warp in lock step, each
+// pass as long as the longest: the staged segments are taken in the order of
+// their pass counts (ceil(entries / P), P = G U; most passes first, a counting
+// sort in shared memory), so the segments a warp takes together need the same
+// number of passes. Which group takes which segment does not change any
+// result. Thread t holds staged segment t (cnt <= kStage = the CTA's threads).
+template <int P>
+__device__ __forceinline__ void order_by_passes(StageJT& S, int cnt) {
+  constexpr int kB = kTilePix / P;
+  static_assert(kB >= 1 && kB <= 16, "buckets");
+  const int t = threadIdx.x;
+  int bk = 0;
+  if (t < cnt) {
+    bk = kB - 1 - (int)min((S.w0[t].z - 1u) / (uint32_t)P, (uint32_t)(kB - 1));
+    atomicAdd(&S.bcount[bk], 1u);
+  }
+  __syncthreads();
+  if (t < 32) {   // bucket starts: exclusive scan of the counts
+    const uint32_t c = t < kB ? S.bcount[t] : 0u;
+    uint32_t inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(kFull, inc, o);
+      if (t >= o) inc += x;
+    }
+    if (t < kB) S.bcount[t] = inc - c;
+  }
+  __syncthreads();
+  if (t < cnt) S.order[atomicAdd(&S.bcount[bk], 1u)] = (uint16_t)t;
+  __syncthreads();
+  if (t < kB) S.bcount[t] = 0u;
+}
 
 __device__ __forceinline__ uint4 entry_word(const uint4& a, const uint4& c) {
   return make_uint4(a.x, a.y, a.z - a.x, c.w);   // segments hold < 2^32 entries
@@ -559,16 +593,18 @@ __device__ __forceinline__ void apply_JT_tile(const CacheView& cv, int tile, con
     const int cnt = (int)min((uint32_t)kStage, n - c0);
     stage_chunk_JT<kFmt, kPf>(cv, g0 + c0, cnt, S);
     if (threadIdx.x == 0) *next_seg = 0;
-    __syncthreads();
+    if constexpr (G < 32) order_by_passes<G * U>(S, cnt);
+    else __syncthreads();
     for (;;) {
       uint32_t kb = 0;
       if (lane == 0) kb = atomicAdd(next_seg, (unsigned)kGPW);
       kb = __shfl_sync(kFull, kb, 0);
       if (kb >= (uint32_t)cnt) break;
-      const uint32_t k = kb + grp;
-      const bool has = k < (uint32_t)cnt;
+      const bool has = kb + grp < (uint32_t)cnt;
+      const uint32_t k = !has ? 0u : G < 32 ? (uint32_t)S.order[kb + grp] : kb + grp;   // staged index
       if constexpr (kPf > 0) {
-        if (gl == 0 && k + kPf < (uint32_t)cnt) prefetch_segment_l2<kFmt>(cv, S.w0[k + kPf]);
+        const uint32_t kp = kb + grp + kPf;
+        if (gl == 0 && kp < (uint32_t)cnt) prefetch_segment_l2<kFmt>(cv, S.w0[G < 32 ? (uint32_t)S.order[kp] : kp]);
       }
       const uint4 w0 = has ? S.w0[k] : make_uint4(0u, 0u, 0u, 0u);
       const uint32_t len = w0.z;
@@ -697,6 +733,8 @@ __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT(CacheView cv,
                                                                    float* __restrict__ seg_ybar) {
   APPLY_JT_SHARED
   if (cv.skip != nullptr && *cv.skip) return;
+  if (threadIdx.x < 16) S.bcount[threadIdx.x] = 0u;
+  __syncthreads();
   apply_JT_tile<kFmt, G, U, kPf>(cv, blockIdx.x, u, seg_ybar, su4, sxy, &next_seg, S, sred);
 }
 
@@ -705,6 +743,7 @@ template <int kFmt, int G, int U, int kMinBlocks, int kPf>
 __global__ void __launch_bounds__(kTilePix, kMinBlocks) k_apply_JT_batch(const __grid_constant__ TileBatch tb) {
   APPLY_JT_SHARED
   __shared__ long long s_tile;
+  if (threadIdx.x < 16) S.bcount[threadIdx.x] = 0u;   // the loop's first barrier orders it
   for (;;) {
     if (threadIdx.x == 0) s_tile = (long long)atomicAdd(tb.queue, 1u);
     __syncthreads();
@@ -841,9 +880,9 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
 // (16, 4, 4); 6 = J p private tiles (32, 3, 4) and J^T u (32, 3, 4); 7 = J p
 // (32, 3, 6) and J^T u (16, 3, 5). U = 3 fills a 94-entry segment (the paper
 // workload's mean) with 96 lane slots at G = 32 or 2 x 48 at G = 16.
-// With L2 prefetch of the segment kPf ahead: 8 = J p private tiles (32, 3, 4)
-// and J^T u (16, 2, 6), both kPf = 16; 9 = J p float4 private tiles (32, 3, 4),
-// kPf = 16, and J^T u (16, 4, 5), kPf = 32.
+// With L2 prefetch of the segment 16 ahead: 8 = J p private tiles (32, 3, 4)
+// and J^T u (8, 2, 6); 9 = J p float4 private tiles (32, 3, 4) and J^T u
+// (8, 4, 5).
 template <int kFmt, int G, int U, int B, int kMode = 0, int kPf = 0>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
   k_apply_J<kFmt, G, U, B, kMode, kPf><<<cv.n_tiles, kTilePix, 0, st>>>(cv, ydot, F_add, u, sq);
@@ -898,8 +937,8 @@ cudaError_t apply_JT_batch_variant(int variant, const TileBatch& tb, int ctas, c
     case 5: return run_JT_batch<kFmt, 16, 4, 4>(tb, ctas, st);
     case 6: return run_JT_batch<kFmt, 32, 3, 4>(tb, ctas, st);
     case 7: return run_JT_batch<kFmt, 16, 3, 5>(tb, ctas, st);
-    case 8: return run_JT_batch<kFmt, 16, 2, 6, 16>(tb, ctas, st);
-    case 9: return run_JT_batch<kFmt, 16, 4, 5, 32>(tb, ctas, st);
+    case 8: return run_JT_batch<kFmt, 8, 2, 6, 16>(tb, ctas, st);
+    case 9: return run_JT_batch<kFmt, 8, 4, 5, 16>(tb, ctas, st);
     default: return run_JT_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -931,8 +970,8 @@ cudaError_t apply_JT_variant(int variant, const CacheView& cv, const float* u, f
     case 5: return run_JT<kFmt, 16, 4, 4>(cv, u, seg_ybar, st);
     case 6: return run_JT<kFmt, 32, 3, 4>(cv, u, seg_ybar, st);
     case 7: return run_JT<kFmt, 16, 3, 5>(cv, u, seg_ybar, st);
-    case 8: return run_JT<kFmt, 16, 2, 6, 16>(cv, u, seg_ybar, st);
-    case 9: return run_JT<kFmt, 16, 4, 5, 32>(cv, u, seg_ybar, st);
+    case 8: return run_JT<kFmt, 8, 2, 6, 16>(cv, u, seg_ybar, st);
+    case 9: return run_JT<kFmt, 8, 4, 5, 16>(cv, u, seg_ybar, st);
     default: return run_JT<kFmt, 8, 2, 6>(cv, u, seg_ybar, st);
   }
 }
@@ -969,10 +1008,10 @@ int device_sm_count() {
 }
 
 // Resident CTAs of a persistent grid: never more than the kernel variant's
-// register and shared-memory budget lets share an SM (6, 5, 6, 4, 6, 4, 4, 6,
-// 4, 4 for variants 0..9), never more CTAs than tiles.
-static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
-  const int cap = variant_cta_cap(variant);
+// register and shared-memory budget lets share an SM (variant_cta_cap), never
+// more CTAs than tiles.
+static int batch_ctas(const TileBatch& tb, int variant, bool jt, int ctas_per_sm) {
+  const int cap = variant_cta_cap(variant, jt);
   const int per = ctas_per_sm < 1 ? 1 : (ctas_per_sm > cap ? cap : ctas_per_sm);
   const long long c = (long long)device_sm_count() * per;
   return (int)(c < tb.total_tiles ? c : tb.total_tiles);
@@ -980,7 +1019,7 @@ static int batch_ctas(const TileBatch& tb, int variant, int ctas_per_sm) {
 
 cudaError_t launch_apply_J_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st) {
   if (tb.n <= 0 || tb.total_tiles <= 0) return cudaSuccess;
-  const int ctas = batch_ctas(tb, variant, ctas_per_sm);
+  const int ctas = batch_ctas(tb, variant, false, ctas_per_sm);
   if (tb.fmt == GSLM_CACHE_FP32) return apply_J_batch_variant<GSLM_CACHE_FP32>(variant, tb, ctas, st);
   if (tb.fmt == GSLM_CACHE_BF16) return apply_J_batch_variant<GSLM_CACHE_BF16>(variant, tb, ctas, st);
   return apply_J_batch_variant<GSLM_CACHE_FP16S>(variant, tb, ctas, st);
@@ -988,7 +1027,7 @@ cudaError_t launch_apply_J_batch(const TileBatch& tb, int variant, int ctas_per_
 
 cudaError_t launch_apply_JT_batch(const TileBatch& tb, int variant, int ctas_per_sm, cudaStream_t st) {
   if (tb.n <= 0 || tb.total_tiles <= 0) return cudaSuccess;
-  const int ctas = batch_ctas(tb, variant, ctas_per_sm);
+  const int ctas = batch_ctas(tb, variant, true, ctas_per_sm);
   if (tb.fmt == GSLM_CACHE_FP32) return apply_JT_batch_variant<GSLM_CACHE_FP32>(variant, tb, ctas, st);
   if (tb.fmt == GSLM_CACHE_BF16) return apply_JT_batch_variant<GSLM_CACHE_BF16>(variant, tb, ctas, st);
   return apply_JT_batch_variant<GSLM_CACHE_FP16S>(variant, tb, ctas, st);

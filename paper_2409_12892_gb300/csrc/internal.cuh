@@ -405,8 +405,12 @@ cudaError_t launch_thin_diag(const CacheView& cv, float* seg_q, cudaStream_t st)
 // apply.cu. `variant` selects one of apply_variants() kernel configurations
 // (entries in flight per lane and register budget); all compute the same result.
 int apply_variants();
-// Most 256-thread CTAs of a variant that fit one SM (registers, shared memory).
-inline int variant_cta_cap(int v) { return v == 1 ? 5 : (v == 3 || v == 5 || v == 6 || v == 8 || v == 9) ? 4 : 6; }
+// Most 256-thread CTAs of a variant's J p (jt false) or J^T u kernel that fit
+// one SM (registers, shared memory).
+inline int variant_cta_cap(int v, bool jt) {
+  if (jt) return (v == 1 || v == 7 || v == 9) ? 5 : (v == 3 || v == 5 || v == 6) ? 4 : 6;
+  return v == 1 ? 5 : (v == 3 || v == 5 || v == 6 || v == 8 || v == 9) ? 4 : 6;
+}
 // sq_partials (may be null): [2][n_tiles] per-tile sums of ||u + F_add||^2 and ||u||^2.
 cudaError_t launch_apply_J(const CacheView& cv, const float* ydot, const float* F_add,
                            float* u, double* sq_partials, int variant, cudaStream_t st);

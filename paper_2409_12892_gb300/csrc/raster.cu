@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_count(
   __shared__ float4 sA[kTilePix];
   __shared__ float2 sB[kTilePix];
   __shared__ float4 sC[kTilePix];
-  __shared__ int flag[kTilePix];
+  __shared__ unsigned flag[kTilePix / 32];   // bit j of word b: splat 32 b + j of the batch contributes
   __shared__ double dred[kTilePix / 32];
   __shared__ uint32_t ured[kTilePix / 32];
   const int tile = blockIdx.x;
@@ -136,12 +136,17 @@ __global__ void __launch_bounds__(kTilePix) k_raster_count(
       sB[threadIdx.x] = make_float2(r.b.x, r.b.y);
       sC[threadIdx.x] = r.c;
     }
-    if (kCount) flag[threadIdx.x] = 0;
+    if (kCount && threadIdx.x < kTilePix / 32) flag[threadIdx.x] = 0u;
     __syncthreads();
     const int cnt = (int)min((uint32_t)kTilePix, s1 - b);
-    for (int j = 0; j < cnt; ++j) {
-      bool contrib = false;
-      if (!done) {
+    // 32 splats at a time; a warp whose pixels are all done leaves the batch
+    for (int jb = 0; jb < cnt; jb += 32) {
+      if (__all_sync(kFull, done)) break;
+      const int jn = min(32, cnt - jb);
+      unsigned mine = 0u;   // this pixel's contributions among the 32
+      for (int jj = 0; jj < jn; ++jj) {
+        if (done) break;
+        const int j = jb + jj;
         const Blend bl = blend_weight(ts.px, ts.py, sA[j], sB[j], smooth);
         const float alpha = bl.alpha;
         if (bl.valid) {
@@ -156,17 +161,19 @@ __global__ void __launch_bounds__(kTilePix) k_raster_count(
             c2 = __fmaf_rn(c.z, w, c2);
             T = test;
             ++n;
-            contrib = true;
+            mine |= 1u << jj;
           }
         }
       }
       if (kCount) {
-        if (__any_sync(kFull, contrib) && lane == 0) flag[j] = 1;
+        const unsigned any = __reduce_or_sync(kFull, mine);
+        if (lane == 0 && any != 0u) atomicOr(&flag[jb >> 5], any);
       }
     }
     if (kCount) {
       __syncthreads();
-      nseg += (uint32_t)__syncthreads_count(threadIdx.x < (unsigned)cnt && flag[threadIdx.x] != 0);
+      nseg += (uint32_t)__syncthreads_count(threadIdx.x < (unsigned)cnt &&
+                                            ((flag[threadIdx.x >> 5] >> (threadIdx.x & 31)) & 1u));
     }
   }
   double local = 0.0;
@@ -416,8 +423,8 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
       if (kFmt == GSLM_CACHE_FP16S) {
         __syncthreads();   // segmax cleared by warp 0
         float Tq = T, q0 = p0, q1 = p1, q2 = p2;
-        for (int j = 0; j < m; ++j) {
-          if (!((mask >> j) & 1u)) continue;
+        for (unsigned mm = mask; mm != 0u; mm &= mm - 1u) {
+          const int j = __ffs(mm) - 1;
           const float araw = sAraw[j][threadIdx.x];
           const float alpha = smooth ? araw : fminf(kAlphaMax, araw);
           const float4 c = sC[sub + j];
@@ -425,7 +432,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
           q0 = __fmaf_rn(c.x, w, q0);
           q1 = __fmaf_rn(c.y, w, q1);
           q2 = __fmaf_rn(c.z, w, q2);
-          const float inv1m = 1.f / (1.f - alpha);
+          const float inv1m = __fdividef(1.f, 1.f - alpha);
           const bool clamped = !smooth && araw > kAlphaMax;
           const float h0 = clamped ? 0.f : alpha * (Tq * c.x - (Cf0 - q0) * inv1m);
           const float h1 = clamped ? 0.f : alpha * (Tq * c.y - (Cf1 - q1) * inv1m);
@@ -440,8 +447,9 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
           seg_rec[wseg[0][threadIdx.x]].scale = __uint_as_float(segmax[threadIdx.x]);
         }
       }
-      for (int j = 0; j < m; ++j) {
-        if (!((mask >> j) & 1u)) continue;
+      // the pixel's own contributions in splat order (set bits of its mask)
+      for (unsigned mm = mask; mm != 0u; mm &= mm - 1u) {
+        const int j = __ffs(mm) - 1;
         const float araw = sAraw[j][threadIdx.x];   // as blend_weight computed it in phase A
         const float alpha = smooth ? araw : fminf(kAlphaMax, araw);
         const float4 c = sC[sub + j];
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
         p0 = __fmaf_rn(c.x, w, p0);
         p1 = __fmaf_rn(c.y, w, p1);
         p2 = __fmaf_rn(c.z, w, p2);
-        const float inv1m = 1.f / (1.f - alpha);
+        const float inv1m = __fdividef(1.f, 1.f - alpha);   // 0 < 1 - alpha <= 1
         const bool clamped = !smooth && araw > kAlphaMax;
         const float h0 = clamped ? 0.f : alpha * (T * c.x - (Cf0 - p0) * inv1m);
         const float h1 = clamped ? 0.f : alpha * (T * c.y - (Cf1 - p1) * inv1m);

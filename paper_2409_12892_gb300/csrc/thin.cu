@@ -98,7 +98,7 @@ __device__ __forceinline__ Entry entry_of(const Weight& bl, float T, const float
   p0 = __fmaf_rn(c.x, e.w, p0);
   p1 = __fmaf_rn(c.y, e.w, p1);
   p2 = __fmaf_rn(c.z, e.w, p2);
-  const float inv1m = 1.f / (1.f - bl.alpha);
+  const float inv1m = __fdividef(1.f, 1.f - bl.alpha);   // as the cache-writing pass
   const bool clamped = !smooth && bl.araw > kAlphaMax;
   e.h0 = clamped ? 0.f : bl.alpha * (T * c.x - (Cf.x - p0) * inv1m);
   e.h1 = clamped ? 0.f : bl.alpha * (T * c.y - (Cf.y - p1) * inv1m);
