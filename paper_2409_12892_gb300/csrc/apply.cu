@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
 // (32, 3, 6) and J^T u (16, 3, 5). U = 3 fills a 94-entry segment (the paper
 // workload's mean) with 96 lane slots at G = 32 or 2 x 48 at G = 16.
 // With L2 prefetch of the segment 16 ahead: 8 = J p private tiles (32, 3, 4)
-// and J^T u (8, 2, 6); 9 = J p float4 private tiles (32, 3, 4) and J^T u
+// and J^T u (8, 2, 6); 9 = J p float4 private tiles (32, 4, 4) and J^T u
 // (8, 4, 5).
 template <int kFmt, int G, int U, int B, int kMode = 0, int kPf = 0>
 cudaError_t run_J(const CacheView& cv, const float* ydot, const float* F_add, float* u, double* sq, cudaStream_t st) {
@@ -922,7 +922,7 @@ cudaError_t apply_J_batch_variant(int variant, const TileBatch& tb, int ctas, cu
     case 6: return run_J_batch<kFmt, 32, 3, 4, 1>(tb, ctas, st);
     case 7: return run_J_batch<kFmt, 32, 3, 6>(tb, ctas, st);
     case 8: return run_J_batch<kFmt, 32, 3, 4, 1, 16>(tb, ctas, st);
-    case 9: return run_J_batch<kFmt, 32, 3, 4, 2, 16>(tb, ctas, st);
+    case 9: return run_J_batch<kFmt, 32, 4, 4, 2, 16>(tb, ctas, st);
     default: return run_J_batch<kFmt, 8, 2, 6>(tb, ctas, st);
   }
 }
@@ -955,7 +955,7 @@ cudaError_t apply_J_variant(int variant, const CacheView& cv, const float* ydot,
     case 6: return run_J<kFmt, 32, 3, 4, 1>(cv, ydot, F_add, u, sq, st);
     case 7: return run_J<kFmt, 32, 3, 6>(cv, ydot, F_add, u, sq, st);
     case 8: return run_J<kFmt, 32, 3, 4, 1, 16>(cv, ydot, F_add, u, sq, st);
-    case 9: return run_J<kFmt, 32, 3, 4, 2, 16>(cv, ydot, F_add, u, sq, st);
+    case 9: return run_J<kFmt, 32, 4, 4, 2, 16>(cv, ydot, F_add, u, sq, st);
     default: return run_J<kFmt, 8, 2, 6>(cv, ydot, F_add, u, sq, st);
   }
 }

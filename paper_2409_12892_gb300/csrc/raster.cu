@@ -83,6 +83,33 @@ __device__ __forceinline__ Blend blend_weight(float px, float py, float4 a, floa
 
 __device__ __forceinline__ float transmit(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.f, alpha)); }
 
+// Row reach of a splat: the largest |py - mean y| at which some pixel of the
+// row can take alpha >= 1/255 (blend_weight's test). With the conic
+// Q = [[A, B], [B, C]] (A = a.z, B = a.w, C = b.x) the blend is valid where
+// Q(d) <= L = 2 ln(255 o), and the least Q over a row at offset dy is
+// dy^2 det(Q) / A, so rows with |dy| > sqrt(L A / det(Q)) hold no valid pixel.
+// Widened by 0.1% and 0.01 pixel, far beyond float32 rounding of the blend's
+// own arithmetic; -1 where the splat is never valid (o <= 1/255), +inf where
+// nothing is skipped (smooth mode, a degenerate conic, NaN). A warp (two rows
+// of the tile) skips a splat whose reach misses both rows: every decision the
+// blend would take there is "not valid", so nothing changes but the work.
+__device__ __forceinline__ float row_reach(const SplatRec& r, int smooth) {
+  if (smooth) return INFINITY;
+  const float A = r.a.z, B = r.a.w, C = r.b.x, o = r.b.y;
+  const float L = 2.f * logf(255.f * o);
+  if (!(L > 0.f)) return -1.f;
+  const float det = A * C - B * B;
+  if (!(A > 0.f) || !(det > 0.f)) return INFINITY;
+  const float y = sqrtf(L * A / det);
+  return y == y ? y * 1.001f + 0.01f : INFINITY;
+}
+
+// True when a splat with mean y `my` and row reach `reach` misses both rows of
+// a warp whose first row's pixel centres lie at yc0 (NaN: false).
+__device__ __forceinline__ bool misses_rows(float my, float reach, float yc0) {
+  return yc0 - my > reach || my - (yc0 + 1.f) > reach;
+}
+
 struct TileSetup {
   int x, y;
   bool inside;
@@ -115,6 +142,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_count(
   __shared__ float4 sA[kTilePix];
   __shared__ float2 sB[kTilePix];
   __shared__ float4 sC[kTilePix];
+  __shared__ float sY[kTilePix];             // row reach of each splat
   __shared__ unsigned flag[kTilePix / 32];   // bit j of word b: splat 32 b + j of the batch contributes
   __shared__ double dred[kTilePix / 32];
   __shared__ uint32_t ured[kTilePix / 32];
@@ -123,6 +151,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_count(
   const DevCam& cam = cams[v];
   const TileSetup ts = tile_setup(cam, tile);
   const int lane = threadIdx.x & 31;
+  const float yc0 = (float)(ts.y0 + 2 * (int)(threadIdx.x >> 5)) + 0.5f;   // the warp's first row
   const uint32_t s0 = tstart[tile], s1 = tend[tile];
   float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
   uint32_t n = 0, nseg = 0;
@@ -135,6 +164,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_count(
       sA[threadIdx.x] = r.a;
       sB[threadIdx.x] = make_float2(r.b.x, r.b.y);
       sC[threadIdx.x] = r.c;
+      sY[threadIdx.x] = row_reach(r, smooth);
     }
     if (kCount && threadIdx.x < kTilePix / 32) flag[threadIdx.x] = 0u;
     __syncthreads();
@@ -143,9 +173,11 @@ __global__ void __launch_bounds__(kTilePix) k_raster_count(
     for (int jb = 0; jb < cnt; jb += 32) {
       if (__all_sync(kFull, done)) break;
       const int jn = min(32, cnt - jb);
+      const unsigned wskip = __ballot_sync(kFull, lane < jn && misses_rows(sA[jb + lane].y, sY[jb + lane], yc0));
       unsigned mine = 0u;   // this pixel's contributions among the 32
       for (int jj = 0; jj < jn; ++jj) {
         if (done) break;
+        if ((wskip >> jj) & 1u) continue;
         const int j = jb + jj;
         const Blend bl = blend_weight(ts.px, ts.py, sA[j], sB[j], smooth);
         const float alpha = bl.alpha;
@@ -261,6 +293,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
   __shared__ float4 sA[kTilePix];
   __shared__ float2 sB[kTilePix];
   __shared__ float4 sC[kTilePix];
+  __shared__ float sY[kTilePix];   // row reach of each splat
   __shared__ uint32_t sSlot[kTilePix];
   // Per sub-batch of 32 splats every warp works out the splats' entry and
   // segment offsets itself (lane = splat) from all warps' ballots, so one
@@ -278,6 +311,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
   const TileSetup ts = tile_setup(cam, tile);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
+  const float yc0 = (float)(ts.y0 + 2 * warp) + 0.5f;   // the warp's first row
   const uint32_t s0 = tstart[tile], s1 = tend[tile];
   float Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f;
   if (ts.inside) {
@@ -300,6 +334,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
       sA[threadIdx.x] = r.a;
       sB[threadIdx.x] = make_float2(r.b.x, r.b.y);
       sC[threadIdx.x] = r.c;
+      sY[threadIdx.x] = row_reach(r, smooth);
       sSlot[threadIdx.x] = slot;
     }
     __syncthreads();
@@ -311,8 +346,10 @@ __global__ void __launch_bounds__(kTilePix) k_raster_write(
       float Tl = T;
       bool dl = done;
       int jstop = -1;
+      const unsigned wskip = __ballot_sync(kFull, lane < m && misses_rows(sA[sub + lane].y, sY[sub + lane], yc0));
       for (int j = 0; j < m; ++j) {
         if (dl) break;
+        if ((wskip >> j) & 1u) continue;
         const Blend bl = blend_weight(ts.px, ts.py, sA[sub + j], sB[sub + j], smooth);
         if (bl.valid) {
           const float test = transmit(Tl, bl.alpha);
