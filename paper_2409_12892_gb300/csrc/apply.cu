@@ -771,7 +771,11 @@ constexpr int kDiagG = 16;
 template <int kFmt, bool kWeighted>
 __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* __restrict__ seg_q) {
   constexpr int kGPW = 32 / kDiagG;
+  constexpr int kPass = 2 * kDiagG;   // entries per pass of a group (two per lane)
+  constexpr int kBk = kTilePix / kPass;
   __shared__ float sw[3][kWeighted ? kTilePix : 1];   // residual-to-pixel weights of the tile's pixels
+  __shared__ uint16_t sorder[kTilePix];               // a chunk's segments by pass count, most first
+  __shared__ uint32_t sbc[kBk];
   const int tile = blockIdx.x;
   const uint32_t g0 = cv.tile_seg_off[tile], g1 = cv.tile_seg_off[tile + 1];
   if (g0 == g1) return;
@@ -792,84 +796,114 @@ __global__ void __launch_bounds__(kTilePix) k_diag_entries(CacheView cv, float* 
     sw[0][threadIdx.x] = w0;
     sw[1][threadIdx.x] = w1;
     sw[2][threadIdx.x] = w2;
-    __syncthreads();
   }
-  // every lane of a warp runs the same number of rounds (the reductions shuffle over the warp)
-  for (uint32_t base = g0 + warp * kGPW; base < g1; base += kWarps * kGPW) {
-    const uint32_t seg = base + grp;
-    const bool has = seg < g1;
-    float q[42];
-#pragma unroll
-    for (int i = 0; i < 42; ++i) q[i] = 0.f;
-    if (has) {
-      const uint4* rq = reinterpret_cast<const uint4*>(cv.seg_rec + seg);
-      const SegRec r = rec_from(rq[0], rq[1], rq[2]);   // tile-local mean, conic, 1/o, FP16 scale
-      const float mx = r.mx, my = r.my, A = r.A, B = r.B, C = r.C, io = r.io;
-      const float scale = kFmt == GSLM_CACHE_FP16S ? r.scale : 1.f;
-      // the entry range of the group's next segment, asked of L2 after this one's entries
-      const uint32_t nseg = seg + kWarps * kGPW;
-      unsigned long long ne0 = 0, ne1 = 0;
-      if (gl == 0 && nseg < g1) {
-        ne0 = cv.seg_entry_off[nseg];
-        ne1 = cv.seg_entry_off[nseg + 1];
+  if (threadIdx.x < kBk) sbc[threadIdx.x] = 0u;
+  __syncthreads();
+  // The tile's segments in chunks of 256, each taken in the order of its
+  // segments' pass counts (as the J^T u kernel does), so that the two
+  // segments a warp works on together need the same number of passes.
+  for (uint32_t c0 = g0; c0 < g1; c0 += kTilePix) {
+    const int cnt = (int)min((uint32_t)kTilePix, g1 - c0);
+    int bk = 0;
+    if ((int)threadIdx.x < cnt) {
+      const uint32_t len = (uint32_t)(cv.seg_entry_off[c0 + threadIdx.x + 1] - cv.seg_entry_off[c0 + threadIdx.x]);
+      bk = kBk - 1 - (int)min((len - 1u) / (uint32_t)kPass, (uint32_t)(kBk - 1));
+      atomicAdd(&sbc[bk], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const uint32_t c = threadIdx.x < kBk ? sbc[threadIdx.x] : 0u;
+      uint32_t inc = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(kFull, inc, o);
+        if ((int)threadIdx.x >= o) inc += x;
       }
-      auto add_entry = [&](const float4& pe, int p) {
-        float wr = 1.f, wg = 1.f, wb = 1.f;
-        if constexpr (kWeighted) {
-          wr = sw[0][p];
-          wg = sw[1][p];
-          wb = sw[2][p];
+      if (threadIdx.x < kBk) sbc[threadIdx.x] = inc - c;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) sorder[atomicAdd(&sbc[bk], 1u)] = (uint16_t)threadIdx.x;
+    __syncthreads();
+    if (threadIdx.x < kBk) sbc[threadIdx.x] = 0u;
+    // every lane of a warp runs the same number of rounds (the reductions shuffle over the warp)
+    for (int qb = warp * kGPW; qb < cnt; qb += kWarps * kGPW) {
+      const bool has = qb + grp < cnt;
+      const uint32_t seg = c0 + (has ? (uint32_t)sorder[qb + grp] : 0u);
+      float q[42];
+  #pragma unroll
+      for (int i = 0; i < 42; ++i) q[i] = 0.f;
+      if (has) {
+        const uint4* rq = reinterpret_cast<const uint4*>(cv.seg_rec + seg);
+        const SegRec r = rec_from(rq[0], rq[1], rq[2]);   // tile-local mean, conic, 1/o, FP16 scale
+        const float mx = r.mx, my = r.my, A = r.A, B = r.B, C = r.C, io = r.io;
+        const float scale = kFmt == GSLM_CACHE_FP16S ? r.scale : 1.f;
+        // the entry range of the group's next segment, asked of L2 after this one's entries
+        const int nq = qb + grp + kWarps * kGPW;
+        const bool pf = gl == 0 && nq < cnt;
+        unsigned long long ne0 = 0, ne1 = 0;
+        if (pf) {
+          const uint32_t nseg = c0 + sorder[nq];
+          ne0 = cv.seg_entry_off[nseg];
+          ne1 = cv.seg_entry_off[nseg + 1];
         }
-        const float dx = (float)(p & (kTile - 1)) - mx, dy = (float)(p / kTile) - my;
-        float gam[6] = {A * dx + B * dy, B * dx + C * dy, -0.5f * dx * dx, -dx * dy, -0.5f * dy * dy, io};
-        const float H2 = wr * pe.y * pe.y + wg * pe.z * pe.z + wb * pe.w * pe.w;
-        int k = 0;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = i; j < 6; ++j) q[k++] += H2 * gam[i] * gam[j];
-        const float xr = wr * pe.x * pe.y, xg = wg * pe.x * pe.z, xb = wb * pe.x * pe.w;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          q[21 + 3 * i + 0] += xr * gam[i];
-          q[21 + 3 * i + 1] += xg * gam[i];
-          q[21 + 3 * i + 2] += xb * gam[i];
+        auto add_entry = [&](const float4& pe, int p) {
+          float wr = 1.f, wg = 1.f, wb = 1.f;
+          if constexpr (kWeighted) {
+            wr = sw[0][p];
+            wg = sw[1][p];
+            wb = sw[2][p];
+          }
+          const float dx = (float)(p & (kTile - 1)) - mx, dy = (float)(p / kTile) - my;
+          float gam[6] = {A * dx + B * dy, B * dx + C * dy, -0.5f * dx * dx, -dx * dy, -0.5f * dy * dy, io};
+          const float H2 = wr * pe.y * pe.y + wg * pe.z * pe.z + wb * pe.w * pe.w;
+          int k = 0;
+  #pragma unroll
+          for (int i = 0; i < 6; ++i)
+  #pragma unroll
+            for (int j = i; j < 6; ++j) q[k++] += H2 * gam[i] * gam[j];
+          const float xr = wr * pe.x * pe.y, xg = wg * pe.x * pe.z, xb = wb * pe.x * pe.w;
+  #pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            q[21 + 3 * i + 0] += xr * gam[i];
+            q[21 + 3 * i + 1] += xg * gam[i];
+            q[21 + 3 * i + 2] += xb * gam[i];
+          }
+          const float aa = pe.x * pe.x;
+          q[39] += wr * aa;
+          q[40] += wg * aa;
+          q[41] += wb * aa;
+        };
+        // two entries per lane in flight
+        unsigned long long e = r.e0 + gl;
+        for (; e + kDiagG < r.e1; e += 2 * kDiagG) {
+          const float4 pa = load_entry<kFmt>(cv.payload, e, scale);
+          const float4 pb = load_entry<kFmt>(cv.payload, e + kDiagG, scale);
+          const int xa = cv.pixoff[e], xb = cv.pixoff[e + kDiagG];
+          add_entry(pa, xa);
+          add_entry(pb, xb);
         }
-        const float aa = pe.x * pe.x;
-        q[39] += wr * aa;
-        q[40] += wg * aa;
-        q[41] += wb * aa;
-      };
-      // two entries per lane in flight
-      unsigned long long e = r.e0 + gl;
-      for (; e + kDiagG < r.e1; e += 2 * kDiagG) {
-        const float4 pa = load_entry<kFmt>(cv.payload, e, scale);
-        const float4 pb = load_entry<kFmt>(cv.payload, e + kDiagG, scale);
-        const int xa = cv.pixoff[e], xb = cv.pixoff[e + kDiagG];
-        add_entry(pa, xa);
-        add_entry(pb, xb);
+        if (e < r.e1) add_entry(load_entry<kFmt>(cv.payload, e, scale), cv.pixoff[e]);
+        if (pf) prefetch_range_l2<kFmt>(cv, ne0, ne1);
       }
-      if (e < r.e1) add_entry(load_entry<kFmt>(cv.payload, e, scale), cv.pixoff[e]);
-      if (gl == 0 && nseg < g1) prefetch_range_l2<kFmt>(cv, ne0, ne1);
+      // three recursive-halving reductions of 16 values over the group: lane gl
+      // then holds sum gl of each block
+      float b0[16], b1[16], b2[16];
+  #pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        b0[i] = q[i];
+        b1[i] = q[16 + i];
+        b2[i] = i < 10 ? q[32 + i] : 0.f;
+      }
+      group_sum16<kDiagG>(b0, lane);
+      group_sum16<kDiagG>(b1, lane);
+      group_sum16<kDiagG>(b2, lane);
+      if (has) {
+        float* out = seg_q + (size_t)cv.seg_pos[seg] * kDiagBlock;
+        out[gl] = b0[0];
+        out[16 + gl] = b1[0];
+        if (gl < kDiagBlock - 32) out[32 + gl] = b2[0];   // the last two are zero padding
+      }
     }
-    // three recursive-halving reductions of 16 values over the group: lane gl
-    // then holds sum gl of each block
-    float b0[16], b1[16], b2[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      b0[i] = q[i];
-      b1[i] = q[16 + i];
-      b2[i] = i < 10 ? q[32 + i] : 0.f;
-    }
-    group_sum16<kDiagG>(b0, lane);
-    group_sum16<kDiagG>(b1, lane);
-    group_sum16<kDiagG>(b2, lane);
-    if (has) {
-      float* out = seg_q + (size_t)cv.seg_pos[seg] * kDiagBlock;
-      out[gl] = b0[0];
-      out[16 + gl] = b1[0];
-      if (gl < kDiagBlock - 32) out[32 + gl] = b2[0];   // the last two are zero padding
-    }
+    __syncthreads();   // sorder is rewritten by the next chunk
   }
 }
 
