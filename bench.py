@@ -668,12 +668,13 @@ def summarize_phases(stats) -> dict:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu
 # captures) per algorithmic byte of the J p + J^T u pair (tangent, tile kernels,
-# per-splat sums, adjoint): BF16 from every pair kernel of one LM step of the
-# 1.5M-Gaussian workload (4 subsets x 9 pairs: 1325 GB for 36 pairs of 29.72 GB);
-# FP32 from the 100k-Gaussian, 8-view case. The pair's traffic grows with its
-# entries, pixels and splats, so a launch's traffic is this ratio times its
-# algorithmic bytes.
-PAIR_DRAM_PER_ALG_BYTE = {0: 1.127, 1: 1.238}   # FP32, BF16
+# per-splat sums, adjoint), tile-kernel variant 9: BF16 from every pair kernel of
+# one LM step of the 1.5M-Gaussian workload (4 subsets x 9 pairs: 1343.6 GB for
+# 36 pairs of 29.38 GB); FP32 from one pair of a 25-view subset of the same
+# workload (63.18 GB for 55.21 GB). The pair's traffic grows with its entries,
+# pixels and splats, so a launch's traffic is this ratio times its algorithmic
+# bytes.
+PAIR_DRAM_PER_ALG_BYTE = {0: 1.144, 1: 1.270}   # FP32, BF16
 
 
 def pair_roofline(stats, peak: dict, fmt: int = None) -> dict:
