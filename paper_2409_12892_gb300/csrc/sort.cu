@@ -13,12 +13,11 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;   // 2048 items per block
 
+// Radix passes of 8-bit digits over 4096-item blocks (16 rounds of 32 items per
+// warp), or of 9-bit digits over 2048-item blocks where that takes fewer passes
+// (the tile keys: 17 bits, two passes instead of three).
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 16;                         // 32-item rounds per warp
-constexpr int kSortTile = kSortThreads * kSortRounds;   // 4096 items per block
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
 
 template <typename T>
 __device__ __forceinline__ unsigned long long as_u64(T v) {
@@ -129,13 +128,15 @@ cudaError_t scan_impl(const Tin* in, Tout* out, long long n, unsigned long long*
 }
 
 // ---------------------------------------------------------------------------- radix sort
+template <int kBits, int kRounds>
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, long long n, int shift, int nblocks,
                              uint32_t* __restrict__ hist) {
+  constexpr int kRadix = 1 << kBits, kSortTile = kSortThreads * kRounds;
   __shared__ uint32_t h[kRadix];
   for (int d = threadIdx.x; d < kRadix; d += kSortThreads) h[d] = 0;
   __syncthreads();
   const long long base = (long long)blockIdx.x * kSortTile;
-  for (int k = 0; k < kSortRounds; ++k) {
+  for (int k = 0; k < kRounds; ++k) {
     const long long i = base + threadIdx.x + (long long)k * kSortThreads;
     if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
   }
@@ -143,13 +144,17 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, long long n, int
   for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[(long long)d * nblocks + blockIdx.x] = h[d];
 }
 
-// Stable scatter of one 4096-item block. Items are ranked per digit with warp
-// match (stable within a warp), then per warp prefix (stable across warps); the
-// block is first reordered by digit in shared memory and then written out, so
-// each digit's run goes to global memory with coalesced stores.
+// Stable scatter of one block. Items are ranked per digit with warp match
+// (stable within a warp), then per warp prefix (stable across warps); the block
+// is first reordered by digit in shared memory and then written out, so each
+// digit's run goes to global memory with coalesced stores. Thread t owns the
+// kDPT consecutive digits from t kDPT for the counts' prefix sums.
+template <int kBits, int kRounds>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, long long n, int shift, int nblocks,
     const uint32_t* __restrict__ offs, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+  constexpr int kRadix = 1 << kBits, kSortTile = kSortThreads * kRounds, kDPT = kRadix / kSortThreads;
+  static_assert(kDPT == 1 || kDPT == 2, "digits per thread");
   __shared__ uint32_t wcnt[kSortWarps][kRadix];
   __shared__ uint32_t goff[kRadix];
   __shared__ uint32_t lstart[kRadix];
@@ -165,10 +170,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
   const long long bbase = (long long)blockIdx.x * kSortTile;
-  const long long wbase = bbase + (long long)warp * (kSortRounds * 32);
-  uint32_t kk[kSortRounds], vv[kSortRounds], rk[kSortRounds];
+  const long long wbase = bbase + (long long)warp * (kRounds * 32);
+  uint32_t kk[kRounds], vv[kRounds], rk[kRounds];
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
+  for (int r = 0; r < kRounds; ++r) {
     const long long i = wbase + r * 32 + lane;
     const bool ok = i < n;
     const unsigned okmask = __ballot_sync(0xffffffffu, ok);
@@ -187,9 +192,11 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
   __syncthreads();
   // per digit: warp prefixes, and the block's count of the digit
+  uint32_t dc[kDPT];
   uint32_t cnt = 0;
-  {
-    const int d = threadIdx.x;   // kSortThreads == kRadix
+#pragma unroll
+  for (int q = 0; q < kDPT; ++q) {
+    const int d = threadIdx.x * kDPT + q;
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
@@ -197,9 +204,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
       wcnt[w][d] = run;
       run += c;
     }
-    cnt = run;
+    dc[q] = run;
+    cnt += run;
   }
-  // exclusive scan of the digit counts over the block (digit = thread)
+  // exclusive scan of the digit counts over the block (digits in thread order)
   uint32_t inc = cnt;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
@@ -209,11 +217,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   __syncthreads();
   uint32_t woff = 0;
   for (int w = 0; w < warp; ++w) woff += wsum[w];
-  lstart[threadIdx.x] = woff + inc - cnt;
+  {
+    uint32_t st = woff + inc - cnt;
+#pragma unroll
+    for (int q = 0; q < kDPT; ++q) {
+      lstart[threadIdx.x * kDPT + q] = st;
+      st += dc[q];
+    }
+  }
   __syncthreads();
   // reorder by digit in shared memory
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
+  for (int r = 0; r < kRounds; ++r) {
     const long long i = wbase + r * 32 + lane;
     if (i < n) {
       const uint32_t d = (kk[r] >> shift) & (kRadix - 1);
@@ -286,30 +301,33 @@ cudaError_t exclusive_scan_u64(const uint32_t* in, unsigned long long* out, long
   return scan_impl<uint32_t, unsigned long long>(in, out, n, static_cast<unsigned long long*>(temp), st);
 }
 
+// Histogram words of the larger (9-bit) configuration, which holds the other.
 size_t radix_temp_bytes(long long n) {
-  const long long nb = div_up(n > 0 ? n : 1, kSortTile);
-  const long long h = nb * kRadix;
+  const long long nb = div_up(n > 0 ? n : 1, kSortThreads * 8);
+  const long long h = nb * 512;
   return (size_t)(2 * h + 1) * sizeof(uint32_t) + scan_temp_bytes(h) + 256;
 }
 
-cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp, long long n,
-                             int bits, void* temp, uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st) {
-  *keys_out = keys;
-  *vals_out = vals;
-  if (n <= 1 || bits <= 0) return cudaSuccess;
-  const int nblocks = (int)div_up(n, kSortTile);
+template <int kBits, int kRounds>
+cudaError_t radix_passes(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp, long long n,
+                         int bits, void* temp, uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st) {
+  constexpr int kRadix = 1 << kBits;
+  const int nblocks = (int)div_up(n, kSortThreads * kRounds);
   const long long h = (long long)nblocks * kRadix;
   uint32_t* hist = static_cast<uint32_t*>(temp);
   uint32_t* offs = hist + h;
   void* scan_tmp = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(offs + h + 1 + 64) & ~uintptr_t(63));
   uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
-  for (int shift = 0; shift < bits; shift += kRadixBits) {
-    { k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(ki, n, shift, nblocks, hist); note_launch(); }
+  for (int shift = 0; shift < bits; shift += kBits) {
+    { k_radix_hist<kBits, kRounds><<<nblocks, kSortThreads, 0, st>>>(ki, n, shift, nblocks, hist); note_launch(); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = exclusive_scan_u32(hist, offs, h, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    { k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(ki, vi, n, shift, nblocks, offs, ko, vo); note_launch(); }
+    {
+      k_radix_scatter<kBits, kRounds><<<nblocks, kSortThreads, 0, st>>>(ki, vi, n, shift, nblocks, offs, ko, vo);
+      note_launch();
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t* t = ki; ki = ko; ko = t;
@@ -318,6 +336,16 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
   *keys_out = ki;
   *vals_out = vi;
   return cudaSuccess;
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp, long long n,
+                             int bits, void* temp, uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st) {
+  *keys_out = keys;
+  *vals_out = vals;
+  if (n <= 1 || bits <= 0) return cudaSuccess;
+  if ((bits + 8) / 9 < (bits + 7) / 8)
+    return radix_passes<9, 8>(keys, vals, keys_tmp, vals_tmp, n, bits, temp, keys_out, vals_out, st);
+  return radix_passes<8, 16>(keys, vals, keys_tmp, vals_tmp, n, bits, temp, keys_out, vals_out, st);
 }
 
 cudaError_t launch_compact_flags(const uint32_t* counts, const uint32_t* pos, long long n, uint32_t* list,
