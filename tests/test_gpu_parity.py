@@ -223,14 +223,23 @@ def test_pcg_break_test_stops_early(lib):
     cache.free()
 
 
-@pytest.mark.parametrize("name,ls", [("tiny", 0), ("tiny", 8), ("ragged", 8)])
-def test_lm_step_matches_oracle(lib, name, ls):
+# The tiny case's step is compared after 3 PCG iterations, where float32
+# rounding moves Algorithm 1's x by at most 5e-4 (after 8 it can move it by
+# 1.7e-3: `common.pcg_noise_spread`), so that Delta is held to 1e-3; the ragged
+# case compares only the decisions and the quantities smooth in Delta, after
+# the paper's 8.
+@pytest.mark.parametrize("name,ls,its", [("tiny", 0, 3), ("tiny", 8, 3), ("ragged", 8, 8)])
+def test_lm_step_matches_oracle(lib, name, ls, its):
     import warnings
     from oracle import solver
     warnings.filterwarnings("ignore")
     wl, P, cams, tgt = CASES[name]()
-    res = solver.lm_step(P.astype(np.float64), [cams], [tgt.astype(np.float64)], 1e-3, n_iters=8, ls_steps=ls)
-    ctx = lib.Context(n_iters=8, break_rel2=0.0, line_search=ls)
+    res = solver.lm_step(P.astype(np.float64), [cams], [tgt.astype(np.float64)], 1e-3, n_iters=its, ls_steps=ls)
+    if name == "tiny":
+        sys_ = solver.build_subset(P.astype(np.float64), cams, tgt.astype(np.float64))
+        assert pcg_noise_spread(sys_, 1e-3, its, solver.solve_subset(sys_, 1e-3, n_iters=its, break_rel2=0.0)[0],
+                                seeds=(0,)) <= PCG_SPREAD_MAX
+    ctx = lib.Context(n_iters=its, break_rel2=0.0, line_search=ls)
     params = lib.to_soa(P)
     state, stats = ctx.lm_step(params, P.shape[0], cams, torch.from_numpy(tgt).cuda().view(-1, 3),
                                [list(range(len(cams)))], 1e-3)
