@@ -369,7 +369,7 @@ def run_e2e(g, ctx, P_host, N, ld, cams, targets, wl, steps: int, warmup: int, d
 # splats whose log-scales grew by tens, each over the whole view, and sets the
 # oracle's time; this many keep a sample step to a few seconds on 4 cores.
 ORACLE_SAMPLE_GAUSSIANS = 200
-ORACLE_SAMPLE = "oracle LM step: {ng} Gaussians nearest cluster 0's mean, step 0's 4 subsets x {vps} view"
+ORACLE_SAMPLE = "oracle LM step: {ng} Gaussians nearest cluster 0's mean, 4 subsets x {vps} view"
 
 
 def cpu_model() -> str:
@@ -494,7 +494,7 @@ def cpu_baseline(workload: str = "paper", views_per_subset: int = 1) -> dict:
     one = oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=1)
     par = oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=len(subsets))
     w = min(nproc, len(subsets))
-    return {"value": one["ms"], "unit": "ms per oracle LM step of the sample", "cores": 1, "kind": "oracle",
+    return {"value": one["ms"], "unit": "ms per sample LM step", "cores": 1, "kind": "oracle",
             "sample": ORACLE_SAMPLE.format(ng=ORACLE_SAMPLE_GAUSSIANS, vps=views_per_subset),
             "cpu_model": cpu_model(), "host_cores": nproc,
             "threads_1_ms": one["ms"], "threads_nproc_ms": par["ms"], "threads_nproc_cores": w}
@@ -646,9 +646,9 @@ def run_reference(args):
 def workload_config(args, form: str) -> dict:
     wl = workload(args)
     return {
-        "workload": (f"{wl.name}: {wl.n_gaussians} Gaussians ({wl.n_clusters} clusters), {wl.n_cameras} cameras "
-                     f"{'/'.join(f'{w}x{h}' for w, h in wl.resolutions)}, {len(wl.subset_sizes)} subsets of "
-                     + (f"{wl.subset_sizes[0]}" if len(set(wl.subset_sizes)) == 1
+        "workload": (f"{wl.name}: {wl.n_gaussians / 1e6:g}M Gaussians ({wl.n_clusters} clusters), "
+                     f"{wl.n_cameras} cameras {'/'.join(f'{w}x{h}' for w, h in wl.resolutions)}, "
+                     + (f"{len(wl.subset_sizes)}x{wl.subset_sizes[0]}" if len(set(wl.subset_sizes)) == 1
                         else "+".join(str(v) for v in wl.subset_sizes))
                      + " views per LM step"),
         "form": form, "pcg_iters": wl.pcg_iters, "break_rel2": 0.01, "lambda0": wl.lambda0,
@@ -822,9 +822,13 @@ def profiled_step(g, ctx, params, N, cams, targets, wl, step: int):
 
 def sig(x, n: int = 4):
     """x rounded to n significant digits (recursively through lists and dicts), so
-    that the JSON line stays short."""
+    that the JSON line stays short; a non-finite float becomes null (strict JSON:
+    e.g. rho of a step whose trial render overflowed or whose model predicts no
+    decrease)."""
     if isinstance(x, float):
-        if not math.isfinite(x) or x == 0.0:
+        if not math.isfinite(x):
+            return None
+        if x == 0.0:
             return x
         return float(f"{x:.{n}g}")
     if isinstance(x, dict):
