@@ -824,13 +824,14 @@ def sig(x, n: int = 4):
     """x rounded to n significant digits (recursively through lists and dicts), so
     that the JSON line stays short; a non-finite float becomes null (strict JSON:
     e.g. rho of a step whose trial render overflowed or whose model predicts no
-    decrease)."""
+    decrease), and a float that rounds to a whole number prints without its ".0"."""
     if isinstance(x, float):
         if not math.isfinite(x):
             return None
         if x == 0.0:
-            return x
-        return float(f"{x:.{n}g}")
+            return 0
+        r = float(f"{x:.{n}g}")
+        return int(r) if r.is_integer() and abs(r) < 1e15 else r
     if isinstance(x, dict):
         return {k: sig(v, n) for k, v in x.items()}
     if isinstance(x, (list, tuple)):
@@ -979,11 +980,11 @@ def run_ours(args):
             ent = {"chosen": best, "chosen_jacobi": row["jacobi"], "chosen_learned": row.get("learned")}
             # per damping: ms [chosen, plain], iterations per subset, reached / accepted
             # [chosen, plain], speedup
-            # PSNR as the value before the step and the gains of the two forms (dB)
+            # PSNR gains of the two forms (dB); the PSNR before the step once, beside the steps
             srow = {"lambda": lam, "ms": [best["ms"]], "its": best["pcg_iters_per_subset"],
                     "reached": [int(best["reached"])], "accepted": [best["accepted"]],
-                    "psnr_before": best["psnr_before_db"],
                     "psnr_gain": [best["psnr_after_db"] - best["psnr_before_db"]]}
+            psnr_before = best["psnr_before_db"]   # the same initial parameters at every damping
             if best["precond"] != "jacobi":
                 srow["precond"] = best["precond"]
             pe = result.get("plain", {}).get("equal", {}).get(lam)
@@ -998,7 +999,7 @@ def run_ours(args):
                 srow["speedup"] = pj["ms"] / best["ms"]
             eqs[lam] = ent
             short.append(srow)
-        line["equal_residual"] = {"cap": args.equal_cap, "steps": short}
+        line["equal_residual"] = {"cap": args.equal_cap, "psnr_before": psnr_before, "steps": short}
         detail["equal_residual"] = {str(k): v for k, v in eqs.items()}
     if not args.skip_cpu:
         cb = cpu_baseline_subprocess(args.workload, args.cpu_views)
