@@ -742,16 +742,23 @@ __global__ void __launch_bounds__(128, 4) k_vjp_batch(const float* __restrict__ 
 // column k of dy/dx and Q (per splat) is the sum over its cache entries and
 // channels of (dc/dy)^T (dc/dy), weighted by the residual-to-pixel weights,
 // stored as 21 geo-geo + 18 geo-rgb + 3 rgb values (and 2 of padding).
-__global__ void __launch_bounds__(128) k_diag(
+constexpr int kDiagThreads = 128;
+// 3 blocks per SM (168 registers, a few spilled) ran the paper subset's
+// diagonal faster than 2 blocks at 255 registers
+__global__ void __launch_bounds__(kDiagThreads, 3) k_diag(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
     const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
     const float* __restrict__ seg_q, const float* __restrict__ splat_q, float* __restrict__ dout) {
+  // the thread's 59 sums, one column of shared memory per thread (no thread
+  // reads another's, so no barrier): as a register array indexed by the
+  // geometric column loop they would live in local memory
+  __shared__ float sd[kNP][kDiagThreads];
+  float* d = &sd[0][threadIdx.x];   // d[k * kDiagThreads] is sum k
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
-  float d[kNP];
 #pragma unroll
-  for (int k = 0; k < kNP; ++k) d[k] = 0.f;
+  for (int k = 0; k < kNP; ++k) d[k * kDiagThreads] = 0.f;
   bool any = false;
   GaussGeo G;
   const bool use_mask = vmask != nullptr;
@@ -810,23 +817,28 @@ __global__ void __launch_bounds__(128) k_diag(
     for (int k = 0; k < 16; ++k)
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch)
-        if (live[ch]) d[11 + 3 * k + ch] += D[ch] * Y[k] * Y[k];
+        if (live[ch]) d[(11 + 3 * k + ch) * kDiagThreads] += D[ch] * Y[k] * Y[k];
     // the 11 geometric parameters: unit tangents
 #pragma unroll 1
     for (int k = 0; k < 11; ++k) {
-      float mud[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
-      float od = 0.f;
-      if (k < 3) mud[k] = 1.f;
-      else if (k < 6) ds[k - 3] = 1.f;
-      else if (k < 10) dq[k - 6] = 1.f;
-      else od = G.o * (1.f - G.o);
+      // unit tangent of parameter k, built with selects (k is not a
+      // compile-time index here, and arrays indexed by it would go to local memory)
+      float mud[3], ds[3], dq[4];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        mud[i] = k == i ? 1.f : 0.f;
+        ds[i] = k == 3 + i ? 1.f : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dq[i] = k == 6 + i ? 1.f : 0.f;
+      const float od = k == 10 ? G.o * (1.f - G.o) : 0.f;
       float Sd[6];
       sigma_tangent(G, ds, dq, Sd);
       float yv[9];
       geo_tangent(VG, cam, mud, Sd, yv);
       yv[5] = od;
       if (k < 3) {
-        const float md = VG.dir[k];
+        const float md = k == 0 ? VG.dir[0] : k == 1 ? VG.dir[1] : VG.dir[2];
         float dd[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) dd[i] = ((i == k ? 1.f : 0.f) - VG.dir[i] * md) * VG.inv_dlen;
@@ -851,11 +863,11 @@ __global__ void __launch_bounds__(128) k_diag(
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc += 2.f * Q[21 + i * 3 + c] * yv[i] * yv[6 + c];
       acc += D[0] * yv[6] * yv[6] + D[1] * yv[7] * yv[7] + D[2] * yv[8] * yv[8];
-      d[k] += acc;
+      d[k * kDiagThreads] += acc;
     }
   }
 #pragma unroll
-  for (int k = 0; k < kNP; ++k) dout[k * ld + g] = d[k];
+  for (int k = 0; k < kNP; ++k) dout[k * ld + g] = d[k * kDiagThreads];
 }
 
 // Per compact splat: the sum of its segments' J^T u partials. The segments of
@@ -1001,8 +1013,9 @@ cudaError_t launch_diag(const float* params, int N, long long ld, const DevCam* 
                         const uint32_t* act_off, const float* seg_q, const float* splat_q, float* diag,
                         cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  { k_diag<<<(N + 127) / 128, 128, 0, st>>>(params, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_q,
-                                            splat_q, diag); note_launch(); }
+  { k_diag<<<(N + kDiagThreads - 1) / kDiagThreads, kDiagThreads, 0, st>>>(params, N, ld, cams, V, smooth, s_start,
+                                                                          s_end, vmask, act_off, seg_q, splat_q,
+                                                                          diag); note_launch(); }
   return cudaGetLastError();
 }
 
