@@ -3,11 +3,14 @@
 // (k_tangent: ydot = (dy/dx) p, used by J p) and its adjoint (k_vjp:
 // (dy/dx)^T ybar, used by J^T u), plus the diag(J^T J) finalisation (k_diag).
 //
-// The per-Gaussian kernels keep one thread per Gaussian and loop over the views
-// of the cache, so each Gaussian's 59 parameters and 59 vector entries are read
-// once per call (coalesced, structure-of-arrays) and the per-view results are
-// summed in registers: this is the paper's applyJT_p2/p3 and the "sortX" it
+// The per-Gaussian kernels keep one lane per Gaussian for everything read or
+// written per Gaussian, so each Gaussian's 59 parameters and 59 vector entries
+// are read once per call (coalesced, structure-of-arrays), and sum its views'
+// results per Gaussian: this is the paper's applyJT_p2/p3 and the "sortX" it
 // needs before applyJ (Sec. A), replaced by one pass in the [59][ld] layout.
+// The per-view work itself is dealt out: a warp spreads the (Gaussian, view)
+// pairs of its 32 Gaussians over its 32 lanes (WarpDeal), since most Gaussians
+// have no view in a given image subset and the others 1 to 64.
 //
 // Splat attributes y (9): mean (mx, my), conic (A, B, C) = inverse of the 2D
 // covariance [[a, b], [b, c]], opacity o, colour (r, g, b).
@@ -368,93 +371,385 @@ constexpr int kGPB = 32;   // Gaussians per block
 __device__ __forceinline__ int role_rows(int role) { return role == 0 ? 11 : 16; }
 __device__ __forceinline__ int role_row(int role, int i) { return role == 0 ? i : 11 + 3 * i + (role - 1); }
 
+// (Gaussian, view) pairs of a warp's 32 Gaussians, dealt to its lanes. Lane l
+// owns Gaussian g0 + l with view mask m_l (ascending set bits = its active
+// views) and compact splat index base b_l; pair t of the warp (t < total) is
+// view number r of owner o, where o is the last lane whose exclusive prefix of
+// the mask popcounts is <= t and r = t - prefix_o. Whatever the owners' view
+// counts, every lane of the warp takes ceil(total / 32) pairs, where a loop
+// over each lane's own views would run as long as the busiest lane's.
+struct WarpDeal {
+  unsigned long long mask[kGPB];
+  uint32_t base[kGPB];
+  uint32_t off[kGPB];   // exclusive prefix of the popcounts
+};
+
+// Position of the r-th (from 0) set bit of m; r < popc(m).
+__device__ __forceinline__ int nth_set_bit(unsigned long long m, uint32_t r) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 32; w >= 1; w >>= 1) {
+    const unsigned long long low = m & ((1ull << w) - 1ull);
+    const uint32_t c = (uint32_t)__popcll(low);
+    if (r >= c) {
+      r -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = low;
+    }
+  }
+  return pos;
+}
+
+// Fills the warp's deal table (all 32 lanes call it) and returns the number of
+// pairs.
+__device__ __forceinline__ uint32_t deal_setup(WarpDeal& D, unsigned long long m, uint32_t base, int lane) {
+  const uint32_t c = (uint32_t)__popcll(m);
+  uint32_t inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  D.mask[lane] = m;
+  D.base[lane] = base;
+  D.off[lane] = inc - c;
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+// Owner lane, view and compact splat index of pair t.
+__device__ __forceinline__ void deal_pair(const WarpDeal& D, uint32_t t, int& o, int& v, long long& key) {
+  o = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1)
+    if (D.off[o + step] <= t) o += step;
+  const uint32_t r = t - D.off[o];
+  v = nth_set_bit(D.mask[o], r);
+  key = (long long)D.base[o] + r;
+}
+
+// Per-warp staging of the tangent's per-Gaussian inputs, [field][lane]: the
+// geometry warp keeps mu (3), Sigma (6), the mean tangent (3), the covariance
+// tangent (6) and the opacity tangent; a colour warp the channel's 16 SH
+// coefficients, their 16 tangents, mu (3) and the mean tangent (3).
+constexpr int kTanFields = 38;
+struct TangentShared {
+  float f[4][kTanFields][kGPB];
+  WarpDeal deal[4];
+};
+
 // ydot[slot] = (dy/dx) p for every active slot of Gaussian g. With z_beta
 // given, first p = z + beta p (Algorithm 1's last vector update, fused), and
 // the new p is written back to p_out. Roles: see above; the geometry warp
-// writes floats 0..5 of the slot's 12, warp 1 + c float 6 + c.
+// writes floats 0..5 of the slot's 12, warp 1 + c float 6 + c. With view masks
+// each warp deals its Gaussians' (Gaussian, view) pairs to all its lanes
+// (WarpDeal); without them (more than 64 views) each lane walks its own views.
+// All 32 lanes of a warp call this (g >= N on the lanes past the last Gaussian).
 __device__ __forceinline__ void tangent_body(
     int g, int role, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V,
     int smooth, const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
     const uint32_t* __restrict__ act_off, const float* __restrict__ pin, float* __restrict__ ydot,
-    const float* __restrict__ zb, float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
-  if (g >= N) return;
-  if (sc != nullptr && sc->done) return;
+    const float* __restrict__ zb, float* __restrict__ pout, const PcgScalars* __restrict__ sc, TangentShared& S) {
+  if (sc != nullptr && sc->done) return;   // the same for the whole block
+  const bool valid = g < N;
+  const int lane = threadIdx.x & 31;
   const float beta = zb != nullptr ? (float)sc->beta : 0.f;
   auto pval = [&](int row) -> float {
     const long long o = (long long)row * ld + g;
     return zb != nullptr ? zb[o] + beta * pin[o] : pin[o];
   };
   // own rows (updated and written back when fused), and the mean rows
-  float pm[3];
+  float pm[3] = {0.f, 0.f, 0.f};
+  if (valid) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) pm[i] = pval(i);
+    for (int i = 0; i < 3; ++i) pm[i] = pval(i);
+  }
   const bool use_mask = vmask != nullptr;
-  unsigned long long mm = use_mask ? vmask[g] : 0ull;
+  const unsigned long long m0 = (use_mask && valid) ? vmask[g] : 0ull;
+  float (*F)[kGPB] = S.f[role];
   if (role == 0) {
     float pg[11];
+    if (valid) {
 #pragma unroll
-    for (int i = 0; i < 11; ++i) {
-      pg[i] = i < 3 ? pm[i] : pval(i);
-      if (pout != nullptr) pout[(long long)i * ld + g] = pg[i];
+      for (int i = 0; i < 11; ++i) {
+        pg[i] = i < 3 ? pm[i] : pval(i);
+        if (pout != nullptr) pout[(long long)i * ld + g] = pg[i];
+      }
     }
-    if (use_mask && mm == 0) return;
-    GaussGeo G;
-    gauss_geo(P, ld, g, G);
-    float Sd[6];
-    sigma_tangent(G, pg + 3, pg + 6, Sd);
-    const float od = G.o * (1.f - G.o) * pg[10];
-    long long ti = act_off != nullptr ? (long long)act_off[g] : 0;   // compact splat index
-    for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
-      const long long slot = (long long)v * N + g;
-      if (!use_mask && !slot_active[slot]) continue;   // the mask holds exactly the active views
+    if (!use_mask) {
+      if (!valid) return;
+      GaussGeo G;
+      gauss_geo(P, ld, g, G);
+      float Sd[6];
+      sigma_tangent(G, pg + 3, pg + 6, Sd);
+      const float od = G.o * (1.f - G.o) * pg[10];
+      for (int v = 0; v < V; ++v) {
+        const long long slot = (long long)v * N + g;
+        if (!slot_active[slot]) continue;
+        const DevCam& cam = cams[v];
+        ViewGeo VG;
+        view_geo(G, cam, VG);
+        float yd[5];
+        geo_tangent(VG, cam, pm, Sd, yd);
+        float* out = ydot + slot * 12;
+        reinterpret_cast<float4*>(out)[0] = make_float4(yd[0], yd[1], yd[2], yd[3]);
+        reinterpret_cast<float2*>(out)[2] = make_float2(yd[4], od);
+      }
+      return;
+    }
+    if (m0 != 0ull) {
+      GaussGeo G;
+      gauss_geo(P, ld, g, G);
+      float Sd[6];
+      sigma_tangent(G, pg + 3, pg + 6, Sd);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) F[i][lane] = G.mu[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) F[3 + i][lane] = G.Sig[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) F[9 + i][lane] = pm[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) F[12 + i][lane] = Sd[i];
+      F[18][lane] = G.o * (1.f - G.o) * pg[10];
+    }
+    const uint32_t total = deal_setup(S.deal[0], m0, m0 != 0ull ? act_off[g] : 0u, lane);
+    for (uint32_t t = lane; t < total; t += 32) {
+      int o, v;
+      long long ti;
+      deal_pair(S.deal[0], t, o, v, ti);
+      GaussGeo G;   // view_geo reads mu and Sigma only
+#pragma unroll
+      for (int i = 0; i < 3; ++i) G.mu[i] = F[i][o];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) G.Sig[i] = F[3 + i][o];
+      float pmo[3], Sd[6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) pmo[i] = F[9 + i][o];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) Sd[i] = F[12 + i][o];
       const DevCam& cam = cams[v];
       ViewGeo VG;
       view_geo(G, cam, VG);
       float yd[5];
-      geo_tangent(VG, cam, pm, Sd, yd);
-      float* out = ydot + (act_off != nullptr ? ti++ : slot) * 12;
+      geo_tangent(VG, cam, pmo, Sd, yd);
+      float* out = ydot + ti * 12;
       reinterpret_cast<float4*>(out)[0] = make_float4(yd[0], yd[1], yd[2], yd[3]);
-      reinterpret_cast<float2*>(out)[2] = make_float2(yd[4], od);
+      reinterpret_cast<float2*>(out)[2] = make_float2(yd[4], F[18][o]);
     }
   } else {
     const int ch = role - 1;
     float ps[16], w[16];
+    if (valid) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int row = 11 + 3 * k + ch;
-      ps[k] = pval(row);
-      if (pout != nullptr) pout[(long long)row * ld + g] = ps[k];
+      for (int k = 0; k < 16; ++k) {
+        const int row = 11 + 3 * k + ch;
+        ps[k] = pval(row);
+        if (pout != nullptr) pout[(long long)row * ld + g] = ps[k];
+      }
     }
-    if (use_mask && mm == 0) return;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) w[k] = P[(11 + 3 * k + ch) * ld + g];
-    const float mu0 = P[g], mu1 = P[ld + g], mu2 = P[2 * ld + g];
-    long long ti = act_off != nullptr ? (long long)act_off[g] : 0;   // compact splat index
-    for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
-      const long long slot = (long long)v * N + g;
-      if (!use_mask && !slot_active[slot]) continue;   // the mask holds exactly the active views
-      const long long yi = act_off != nullptr ? ti++ : slot;
-      const DevCam& cam = cams[v];
-      const float d0 = mu0 - cam.campos[0], d1 = mu1 - cam.campos[1], d2 = mu2 - cam.campos[2];
+    // view v of Gaussian gg: the colour tangent of channel ch
+    auto colour = [&](const float (&wv)[16], const float (&psv)[16], const float (&mu)[3], const float (&pmv)[3],
+                      const DevCam& cam) -> float {
+      const float d0 = mu[0] - cam.campos[0], d1 = mu[1] - cam.campos[1], d2 = mu[2] - cam.campos[2];
       const float inv_dlen = 1.f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
       const float dir[3] = {d0 * inv_dlen, d1 * inv_dlen, d2 * inv_dlen};
       float Y[16];
       sh_basis(dir[0], dir[1], dir[2], Y);
-      const float mdot = dir[0] * pm[0] + dir[1] * pm[1] + dir[2] * pm[2];
+      const float mdot = dir[0] * pmv[0] + dir[1] * pmv[1] + dir[2] * pmv[2];
       float raw = kShOffset, acc = 0.f;
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        raw += Y[k] * w[k];
-        acc += Y[k] * ps[k];
+        raw += Y[k] * wv[k];
+        acc += Y[k] * psv[k];
       }
       float gr[3];
-      sh_grad(dir[0], dir[1], dir[2], w, gr);
+      sh_grad(dir[0], dir[1], dir[2], wv, gr);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) acc += gr[i] * (pm[i] - dir[i] * mdot) * inv_dlen;
-      ydot[yi * 12 + 6 + ch] = (!smooth && raw < 0.f) ? 0.f : acc;
+      for (int i = 0; i < 3; ++i) acc += gr[i] * (pmv[i] - dir[i] * mdot) * inv_dlen;
+      return (!smooth && raw < 0.f) ? 0.f : acc;
+    };
+    if (!use_mask) {
+      if (!valid) return;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) w[k] = P[(11 + 3 * k + ch) * ld + g];
+      const float mu[3] = {P[g], P[ld + g], P[2 * ld + g]};
+      for (int v = 0; v < V; ++v) {
+        const long long slot = (long long)v * N + g;
+        if (!slot_active[slot]) continue;
+        ydot[slot * 12 + 6 + ch] = colour(w, ps, mu, pm, cams[v]);
+      }
+      return;
+    }
+    if (m0 != 0ull) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        F[k][lane] = P[(11 + 3 * k + ch) * ld + g];
+        F[16 + k][lane] = ps[k];
+      }
+      F[32][lane] = P[g];
+      F[33][lane] = P[ld + g];
+      F[34][lane] = P[2 * ld + g];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) F[35 + i][lane] = pm[i];
+    }
+    const uint32_t total = deal_setup(S.deal[role], m0, m0 != 0ull ? act_off[g] : 0u, lane);
+    for (uint32_t t = lane; t < total; t += 32) {
+      int o, v;
+      long long ti;
+      deal_pair(S.deal[role], t, o, v, ti);
+      float wo[16], pso[16], mu[3], pmo[3];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        wo[k] = F[k][o];
+        pso[k] = F[16 + k][o];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        mu[i] = F[32 + i][o];
+        pmo[i] = F[35 + i][o];
+      }
+      ydot[ti * 12 + 6 + ch] = colour(wo, pso, mu, pmo, cams[v]);
     }
   }
 }
+
+// Per-view terms of the adjoint. Geometry: for the splat's ybar (mean 2,
+// conic 3, opacity) the view's terms of the 3D covariance gradient GS (6,
+// symmetric), of the opacity sum and of the mean gradient (3).
+__device__ __forceinline__ void vjp_geo_terms(const GaussGeo& G, const DevCam& cam, const float yb[6], float GS[6],
+                                              float& ob, float mub[3]) {
+  ViewGeo VG;
+  view_geo(G, cam, VG);
+  ob += yb[5];
+  // conic -> 2D covariance
+  const float A = VG.A, B = VG.B, C = VG.C;
+  const float ab = -(A * A * yb[2] + A * B * yb[3] + B * B * yb[4]);
+  const float bb = -(2.f * A * B * yb[2] + (A * C + B * B) * yb[3] + 2.f * B * C * yb[4]);
+  const float cb = -(B * B * yb[2] + B * C * yb[3] + C * C * yb[4]);
+  // 2D covariance -> 3D covariance (symmetric full-matrix gradient) and T
+  {
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        GS[k++] += ab * VG.T0[i] * VG.T0[j] + 0.5f * bb * (VG.T0[i] * VG.T1[j] + VG.T1[i] * VG.T0[j]) +
+                   cb * VG.T1[i] * VG.T1[j];
+      }
+  }
+  float T0b[3], T1b[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T0b[i] = 2.f * ab * VG.ST0[i] + bb * VG.ST1[i];
+    T1b[i] = bb * VG.ST0[i] + 2.f * cb * VG.ST1[i];
+  }
+  const float* W = cam.R;
+  const float J00b = T0b[0] * W[0] + T0b[1] * W[1] + T0b[2] * W[2];
+  const float J02b = T0b[0] * W[6] + T0b[1] * W[7] + T0b[2] * W[8];
+  const float J11b = T1b[0] * W[3] + T1b[1] * W[4] + T1b[2] * W[5];
+  const float J12b = T1b[0] * W[6] + T1b[1] * W[7] + T1b[2] * W[8];
+  const float iz = VG.iz, iz2 = iz * iz, iz3 = iz2 * iz;
+  const float tx = VG.tc[0], ty = VG.tc[1];
+  float tb[3];
+  tb[0] = -cam.fx * iz2 * J02b + cam.fx * iz * yb[0];
+  tb[1] = -cam.fy * iz2 * J12b + cam.fy * iz * yb[1];
+  tb[2] = -cam.fx * iz2 * J00b + 2.f * cam.fx * tx * iz3 * J02b - cam.fy * iz2 * J11b +
+          2.f * cam.fy * ty * iz3 * J12b - cam.fx * tx * iz2 * yb[0] - cam.fy * ty * iz2 * yb[1];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) mub[i] += W[0 * 3 + i] * tb[0] + W[1 * 3 + i] * tb[1] + W[2 * 3 + i] * tb[2];
+}
+
+// Colour channel: for the splat's colour ybar yc, the view's terms of the
+// channel's 16 SH coefficient gradients and of the mean gradient (3).
+__device__ __forceinline__ void vjp_colour_terms(const float w[16], const float mu[3], const DevCam& cam, float yc,
+                                                 int smooth, float out[16], float mub[3]) {
+  const float d0 = mu[0] - cam.campos[0], d1 = mu[1] - cam.campos[1], d2 = mu[2] - cam.campos[2];
+  const float inv_dlen = 1.f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  const float dir[3] = {d0 * inv_dlen, d1 * inv_dlen, d2 * inv_dlen};
+  float Y[16];
+  sh_basis(dir[0], dir[1], dir[2], Y);
+  float raw = kShOffset;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) raw += Y[k] * w[k];
+  const float rb = (!smooth && raw < 0.f) ? 0.f : yc;
+  float wsum[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    out[k] += Y[k] * rb;
+    wsum[k] = rb * w[k];
+  }
+  float db[3];
+  sh_grad(dir[0], dir[1], dir[2], wsum, db);
+  const float dd = dir[0] * db[0] + dir[1] * db[1] + dir[2] * db[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) mub[i] += (db[i] - dir[i] * dd) * inv_dlen;
+}
+
+// The splat's ybar: its record (one per Gaussian and view), or the sum of its
+// segments' partials. Returns false for a splat without segments.
+__device__ __forceinline__ bool splat_ybar6(const float* __restrict__ splat_ybar, const float* __restrict__ seg_ybar,
+                                            const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
+                                            long long sk, float yb[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) yb[i] = 0.f;
+  if (splat_ybar != nullptr) {
+    const float* sy = splat_ybar + (size_t)sk * 12;
+    const float4 u0 = *reinterpret_cast<const float4*>(sy);
+    const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
+    yb[0] = u0.x; yb[1] = u0.y; yb[2] = u0.z; yb[3] = u0.w; yb[4] = u1.x; yb[5] = u1.y;
+    return true;
+  }
+  const uint32_t a = s_start[sk], b = s_end[sk];
+  for (uint32_t j = a; j < b; ++j) {
+    const float* sy = seg_ybar + (size_t)j * 12;
+    const float4 u0 = *reinterpret_cast<const float4*>(sy);
+    const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
+    yb[0] += u0.x; yb[1] += u0.y; yb[2] += u0.z; yb[3] += u0.w; yb[4] += u1.x; yb[5] += u1.y;
+  }
+  return a != b;
+}
+
+__device__ __forceinline__ bool splat_ybar_colour(const float* __restrict__ splat_ybar,
+                                                  const float* __restrict__ seg_ybar,
+                                                  const uint32_t* __restrict__ s_start,
+                                                  const uint32_t* __restrict__ s_end, long long sk, int ch,
+                                                  float& yc) {
+  yc = 0.f;
+  if (splat_ybar != nullptr) {
+    yc = splat_ybar[(size_t)sk * 12 + 6 + ch];
+    return true;
+  }
+  const uint32_t a = s_start[sk], b = s_end[sk];
+  for (uint32_t j = a; j < b; ++j) yc += seg_ybar[(size_t)j * 12 + 6 + ch];
+  return a != b;
+}
+
+// Shared staging of the adjoint with view masks: each warp deals its
+// Gaussians' (Gaussian, view) pairs to its lanes in chunks of kVjpChunk; a
+// pair's terms go to the chunk's rows, and each owner lane then adds its own
+// rows in view order (the order a lane walking its own views adds them in).
+constexpr int kVjpChunk = 32;
+constexpr int kGeoTerms = 10, kGeoRow = 11;     // GS (6), ob, mub (3); odd row stride
+constexpr int kColTerms = 19, kColRow = 19;     // out (16), mub (3)
+struct VjpShared {
+  float gin[9][kGPB];                           // geometry warp: mu (3), Sigma (6)
+  float gt[kVjpChunk * kGeoRow];
+  float cin[3][19][kGPB];                       // colour warp c: w (16), mu (3)
+  float ct[3][kVjpChunk * kColRow];
+  WarpDeal deal[4];
+  float mub[4][kGPB][3];                        // the warps' mean-gradient sums
+  float ep[4][16][kGPB], em[4][16][kGPB];       // the epilogue's p and M rows, copied ahead (cp.async)
+};
+
+// 4-byte asynchronous copy global -> shared (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // g = scale * (dy/dx)^T ybar summed over the views; ybar of a slot is the sum
 // of its segments' partial sums, which the tile kernel stores in splat order:
@@ -464,7 +759,10 @@ __device__ __forceinline__ void tangent_body(
 // one contiguous run; else by its slot v * N + g.
 // Epilogue (M != null): g += lambda M p and a per-block float64 partial of
 // p^T g. Roles as for the tangent; the colour warps hand their view-direction
-// terms of the mean gradient to the geometry warp through shared memory.
+// terms of the mean gradient to the geometry warp through shared memory. With
+// view masks each warp deals its Gaussians' (Gaussian, view) pairs to all its
+// lanes (as the tangent does) and every owner adds its pairs' terms in view
+// order; without them each lane walks its own views.
 // All 128 threads of the block call this with the same g0.
 __device__ __forceinline__ void vjp_body(
     int g0, const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
@@ -472,13 +770,27 @@ __device__ __forceinline__ void vjp_body(
     const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
     const float* __restrict__ seg_ybar, const float* __restrict__ splat_ybar, float scale,
     float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
-    float (*s_mub)[kGPB][3], double& local) {
+    VjpShared& S, double& local) {
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
   const int g = g0 + lane;
   const bool valid = g < N;
   const bool use_mask = vmask != nullptr;
-  unsigned long long mm = (use_mask && valid) ? vmask[g] : 0ull;
-  long long key = (use_mask && valid) ? (long long)act_off[g] : 0;   // compact splat index
+  const unsigned long long m0 = (use_mask && valid) ? vmask[g] : 0ull;
+  const uint32_t base = m0 != 0ull ? act_off[g] : 0u;   // compact splat index of the first active view
+  // the epilogue's rows of p and M start moving now and land while the views
+  // are worked on (each lane later reads only its own copies)
+  const bool epi = valid && Mdiag != nullptr;
+  if (epi) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (i < role_rows(role)) {
+        const long long o = (long long)role_row(role, i) * ld + g;
+        cp_async4(&S.ep[role][i][lane], p + o);
+        cp_async4(&S.em[role][i][lane], Mdiag + o);
+      }
+    }
+    cp_async_commit();
+  }
   float mub[3] = {0.f, 0.f, 0.f};
   float out[16];
 #pragma unroll
@@ -488,68 +800,62 @@ __device__ __forceinline__ void vjp_body(
     float ob = 0.f;
     bool any = false;
     GaussGeo G;
-    for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
-      const long long sk = use_mask ? key++ : (long long)v * N + g;
-      float yb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (splat_ybar != nullptr) {   // the splat's sum, one record per (Gaussian, view)
-        const float* sy = splat_ybar + (size_t)sk * 12;
-        const float4 u0 = *reinterpret_cast<const float4*>(sy);
-        const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
-        yb[0] = u0.x; yb[1] = u0.y; yb[2] = u0.z; yb[3] = u0.w; yb[4] = u1.x; yb[5] = u1.y;
-      } else {
-        const uint32_t a = s_start[sk], b = s_end[sk];
-        if (a == b) continue;
-        for (uint32_t j = a; j < b; ++j) {
-          const float* sy = seg_ybar + (size_t)j * 12;
-          const float4 u0 = *reinterpret_cast<const float4*>(sy);
-          const float2 u1 = *reinterpret_cast<const float2*>(sy + 4);
-          yb[0] += u0.x; yb[1] += u0.y; yb[2] += u0.z; yb[3] += u0.w; yb[4] += u1.x; yb[5] += u1.y;
+    if (!use_mask) {
+      for (int v = 0; valid && v < V; ++v) {
+        float yb[6];
+        if (!splat_ybar6(nullptr, seg_ybar, s_start, s_end, (long long)v * N + g, yb)) continue;
+        if (!any) {
+          gauss_geo(P, ld, g, G);
+          any = true;
         }
+        vjp_geo_terms(G, cams[v], yb, GS, ob, mub);
       }
-      if (!any) {
+    } else {
+      if (m0 != 0ull) {
         gauss_geo(P, ld, g, G);
         any = true;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) S.gin[i][lane] = G.mu[i];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) S.gin[3 + i][lane] = G.Sig[i];
       }
-      const DevCam& cam = cams[v];
-      ViewGeo VG;
-      view_geo(G, cam, VG);
-      ob += yb[5];
-      // conic -> 2D covariance
-      const float A = VG.A, B = VG.B, C = VG.C;
-      const float ab = -(A * A * yb[2] + A * B * yb[3] + B * B * yb[4]);
-      const float bb = -(2.f * A * B * yb[2] + (A * C + B * B) * yb[3] + 2.f * B * C * yb[4]);
-      const float cb = -(B * B * yb[2] + B * C * yb[3] + C * C * yb[4]);
-      // 2D covariance -> 3D covariance (symmetric full-matrix gradient) and T
-      {
-        int k = 0;
+      WarpDeal& D = S.deal[0];
+      const uint32_t total = deal_setup(D, m0, base, lane);
+      const uint32_t my0 = D.off[lane], my1 = my0 + (uint32_t)__popcll(m0);
+      for (uint32_t cb = 0; cb < total; cb += kVjpChunk) {
+        const uint32_t ce = min(total, cb + (uint32_t)kVjpChunk);
+        for (uint32_t t = cb + lane; t < ce; t += 32) {
+          int o, v;
+          long long sk;
+          deal_pair(D, t, o, v, sk);
+          float tGS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, tob = 0.f, tmub[3] = {0.f, 0.f, 0.f};
+          float yb[6];
+          if (splat_ybar6(splat_ybar, seg_ybar, s_start, s_end, sk, yb)) {
+            GaussGeo Go;   // view_geo reads mu and Sigma only
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i) Go.mu[i] = S.gin[i][o];
 #pragma unroll
-          for (int j = i; j < 3; ++j) {
-            GS[k++] += ab * VG.T0[i] * VG.T0[j] + 0.5f * bb * (VG.T0[i] * VG.T1[j] + VG.T1[i] * VG.T0[j]) +
-                       cb * VG.T1[i] * VG.T1[j];
+            for (int i = 0; i < 6; ++i) Go.Sig[i] = S.gin[3 + i][o];
+            vjp_geo_terms(Go, cams[v], yb, tGS, tob, tmub);
           }
-      }
-      float T0b[3], T1b[3];
+          float* row = S.gt + (t - cb) * kGeoRow;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        T0b[i] = 2.f * ab * VG.ST0[i] + bb * VG.ST1[i];
-        T1b[i] = bb * VG.ST0[i] + 2.f * cb * VG.ST1[i];
-      }
-      const float* W = cam.R;
-      const float J00b = T0b[0] * W[0] + T0b[1] * W[1] + T0b[2] * W[2];
-      const float J02b = T0b[0] * W[6] + T0b[1] * W[7] + T0b[2] * W[8];
-      const float J11b = T1b[0] * W[3] + T1b[1] * W[4] + T1b[2] * W[5];
-      const float J12b = T1b[0] * W[6] + T1b[1] * W[7] + T1b[2] * W[8];
-      const float iz = VG.iz, iz2 = iz * iz, iz3 = iz2 * iz;
-      const float tx = VG.tc[0], ty = VG.tc[1];
-      float tb[3];
-      tb[0] = -cam.fx * iz2 * J02b + cam.fx * iz * yb[0];
-      tb[1] = -cam.fy * iz2 * J12b + cam.fy * iz * yb[1];
-      tb[2] = -cam.fx * iz2 * J00b + 2.f * cam.fx * tx * iz3 * J02b - cam.fy * iz2 * J11b +
-              2.f * cam.fy * ty * iz3 * J12b - cam.fx * tx * iz2 * yb[0] - cam.fy * ty * iz2 * yb[1];
+          for (int i = 0; i < 6; ++i) row[i] = tGS[i];
+          row[6] = tob;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) mub[i] += W[0 * 3 + i] * tb[0] + W[1 * 3 + i] * tb[1] + W[2 * 3 + i] * tb[2];
+          for (int i = 0; i < 3; ++i) row[7 + i] = tmub[i];
+        }
+        __syncwarp();
+        for (uint32_t t = max(my0, cb); t < min(my1, ce); ++t) {
+          const float* row = S.gt + (t - cb) * kGeoRow;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) GS[i] += row[i];
+          ob += row[6];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) mub[i] += row[7 + i];
+        }
+        __syncwarp();   // the next chunk rewrites the rows
+      }
     }
     if (any) {
       // 3D covariance -> M = R diag(S): Mb = 2 GS M
@@ -585,57 +891,77 @@ __device__ __forceinline__ void vjp_body(
   } else {
     // colour channel ch: SH coefficient gradients and the view-direction term of the mean
     const int ch = role - 1;
-    float w[16];
-    float mu0 = 0.f, mu1 = 0.f, mu2 = 0.f;
-    if (valid && (!use_mask || mm != 0)) {
+    if (!use_mask) {
+      if (valid) {
+        float w[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) w[k] = P[(11 + 3 * k + ch) * ld + g];
-      mu0 = P[g];
-      mu1 = P[ld + g];
-      mu2 = P[2 * ld + g];
-    }
-    for (int v = valid ? next_view(use_mask, mm, -1, V) : V; v < V; v = next_view(use_mask, mm, v, V)) {
-      const long long sk = use_mask ? key++ : (long long)v * N + g;
-      float yc = 0.f;
-      if (splat_ybar != nullptr) {
-        yc = splat_ybar[(size_t)sk * 12 + 6 + ch];
-      } else {
-        const uint32_t a = s_start[sk], b = s_end[sk];
-        if (a == b) continue;
-        for (uint32_t j = a; j < b; ++j) yc += seg_ybar[(size_t)j * 12 + 6 + ch];
+        for (int k = 0; k < 16; ++k) w[k] = P[(11 + 3 * k + ch) * ld + g];
+        const float mu[3] = {P[g], P[ld + g], P[2 * ld + g]};
+        for (int v = 0; v < V; ++v) {
+          float yc;
+          if (!splat_ybar_colour(nullptr, seg_ybar, s_start, s_end, (long long)v * N + g, ch, yc)) continue;
+          vjp_colour_terms(w, mu, cams[v], yc, smooth, out, mub);
+        }
       }
-      const DevCam& cam = cams[v];
-      const float d0 = mu0 - cam.campos[0], d1 = mu1 - cam.campos[1], d2 = mu2 - cam.campos[2];
-      const float inv_dlen = 1.f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-      const float dir[3] = {d0 * inv_dlen, d1 * inv_dlen, d2 * inv_dlen};
-      float Y[16];
-      sh_basis(dir[0], dir[1], dir[2], Y);
-      float raw = kShOffset;
+    } else {
+      float (*cin)[kGPB] = S.cin[ch];
+      float* ct = S.ct[ch];
+      if (m0 != 0ull) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) raw += Y[k] * w[k];
-      const float rb = (!smooth && raw < 0.f) ? 0.f : yc;
-      float wsum[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        out[k] += Y[k] * rb;
-        wsum[k] = rb * w[k];
+        for (int k = 0; k < 16; ++k) cin[k][lane] = P[(11 + 3 * k + ch) * ld + g];
+        cin[16][lane] = P[g];
+        cin[17][lane] = P[ld + g];
+        cin[18][lane] = P[2 * ld + g];
       }
-      float db[3];
-      sh_grad(dir[0], dir[1], dir[2], wsum, db);
-      const float dd = dir[0] * db[0] + dir[1] * db[1] + dir[2] * db[2];
+      WarpDeal& D = S.deal[role];
+      const uint32_t total = deal_setup(D, m0, base, lane);
+      const uint32_t my0 = D.off[lane], my1 = my0 + (uint32_t)__popcll(m0);
+      for (uint32_t cb = 0; cb < total; cb += kVjpChunk) {
+        const uint32_t ce = min(total, cb + (uint32_t)kVjpChunk);
+        for (uint32_t t = cb + lane; t < ce; t += 32) {
+          int o, v;
+          long long sk;
+          deal_pair(D, t, o, v, sk);
+          float tout[16], tmub[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-      for (int i = 0; i < 3; ++i) mub[i] += (db[i] - dir[i] * dd) * inv_dlen;
+          for (int k = 0; k < 16; ++k) tout[k] = 0.f;
+          float yc;
+          if (splat_ybar_colour(splat_ybar, seg_ybar, s_start, s_end, sk, ch, yc)) {
+            float w[16], mu[3];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) w[k] = cin[k][o];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) mu[i] = cin[16 + i][o];
+            vjp_colour_terms(w, mu, cams[v], yc, smooth, tout, tmub);
+          }
+          float* row = ct + (t - cb) * kColRow;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) row[k] = tout[k];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) row[16 + i] = tmub[i];
+        }
+        __syncwarp();
+        for (uint32_t t = max(my0, cb); t < min(my1, ce); ++t) {
+          const float* row = ct + (t - cb) * kColRow;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) out[k] += row[k];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) mub[i] += row[16 + i];
+        }
+        __syncwarp();   // the next chunk rewrites the rows
+      }
     }
   }
-  s_mub[role][lane][0] = mub[0];
-  s_mub[role][lane][1] = mub[1];
-  s_mub[role][lane][2] = mub[2];
+  S.mub[role][lane][0] = mub[0];
+  S.mub[role][lane][1] = mub[1];
+  S.mub[role][lane][2] = mub[2];
   __syncthreads();
   if (role == 0) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out[i] = s_mub[0][lane][i] + s_mub[1][lane][i] + s_mub[2][lane][i] + s_mub[3][lane][i];
+    for (int i = 0; i < 3; ++i) out[i] = S.mub[0][lane][i] + S.mub[1][lane][i] + S.mub[2][lane][i] + S.mub[3][lane][i];
   }
   if (valid) {
+    if (epi) cp_async_wait_all();
     const int nr = role_rows(role);
     float lf = 0.f;   // this role's rows of p^T g in float32; the sum over Gaussians in float64
 #pragma unroll
@@ -643,8 +969,8 @@ __device__ __forceinline__ void vjp_body(
       if (i < nr) {
         const long long o = (long long)role_row(role, i) * ld + g;
         if (Mdiag != nullptr) {
-          const float pk = p[o];
-          const float gk = scale * out[i] + lambda * clamp_diag(Mdiag[o]) * pk;
+          const float pk = S.ep[role][i][lane];
+          const float gk = scale * out[i] + lambda * clamp_diag(S.em[role][i][lane]) * pk;
           gout[o] = gk;
           lf = fmaf(pk, gk, lf);
         } else {
@@ -654,7 +980,7 @@ __device__ __forceinline__ void vjp_body(
     }
     local += (double)lf;
   }
-  __syncthreads();   // s_mub is reused by the next group of Gaussians
+  __syncthreads();   // S is reused by the next group of Gaussians
 }
 
 // Block reduction of the float64 partial dot into partials[blockIdx.x].
@@ -671,8 +997,9 @@ __global__ void __launch_bounds__(128) k_tangent(
     const uint8_t* __restrict__ slot_active, const unsigned long long* __restrict__ vmask,
     const uint32_t* __restrict__ act_off, const float* __restrict__ pin, float* __restrict__ ydot,
     const float* __restrict__ zb, float* __restrict__ pout, const PcgScalars* __restrict__ sc) {
+  __shared__ TangentShared S;
   tangent_body(blockIdx.x * kGPB + (threadIdx.x & 31), threadIdx.x >> 5, P, N, ld, cams, V, smooth, slot_active,
-               vmask, act_off, pin, ydot, zb, pout, sc);
+               vmask, act_off, pin, ydot, zb, pout, sc, S);
 }
 
 // Batched: blockIdx.y is the subset; its p, z and pout sit at offset
@@ -685,9 +1012,10 @@ __global__ void __launch_bounds__(128) k_tangent_batch(const float* __restrict__
   const int b = blockIdx.y;
   const SubsetRefs& s = gb.s[b];
   const long long off = (long long)b * vs;
+  __shared__ TangentShared S;
   tangent_body(blockIdx.x * kGPB + (threadIdx.x & 31), threadIdx.x >> 5, P, N, ld, s.cams, s.V, smooth,
                s.slot_active, s.vmask, s.act_off, pin + off, s.ydot, zb != nullptr ? zb + off : nullptr,
-               pout != nullptr ? pout + off : nullptr, sc != nullptr ? sc + b : nullptr);
+               pout != nullptr ? pout + off : nullptr, sc != nullptr ? sc + b : nullptr, S);
 }
 
 // Each block loops over groups of 32 Gaussians (bounded grid: at most
@@ -701,12 +1029,12 @@ __device__ __forceinline__ void vjp_blocks_loop(
     const float* __restrict__ seg_ybar, const float* __restrict__ splat_ybar, float scale,
     float* __restrict__ gout, const float* __restrict__ p, const float* __restrict__ Mdiag, float lambda,
     double* __restrict__ partials, const PcgScalars* __restrict__ sc) {
-  __shared__ float s_mub[4][kGPB][3];
+  __shared__ VjpShared S;
   double local = 0.0;
   if (sc == nullptr || !sc->done) {
     for (int g0 = blockIdx.x * kGPB; g0 < N; g0 += gridDim.x * kGPB)
       vjp_body(g0, P, N, ld, cams, V, smooth, s_start, s_end, vmask, act_off, seg_ybar, splat_ybar, scale, gout, p,
-               Mdiag, lambda, s_mub, local);
+               Mdiag, lambda, S, local);
   }
   if (partials != nullptr) write_dot_partial(local, partials);
 }
@@ -742,129 +1070,184 @@ __global__ void __launch_bounds__(128, 4) k_vjp_batch(const float* __restrict__ 
 // column k of dy/dx and Q (per splat) is the sum over its cache entries and
 // channels of (dc/dy)^T (dc/dy), weighted by the residual-to-pixel weights,
 // stored as 21 geo-geo + 18 geo-rgb + 3 rgb values (and 2 of padding).
-constexpr int kDiagThreads = 128;
-// 3 blocks per SM (168 registers, a few spilled) ran the paper subset's
-// diagonal faster than 2 blocks at 255 registers
-__global__ void __launch_bounds__(kDiagThreads, 3) k_diag(
+
+// One view's 59 terms of Gaussian g (geometry G, splat block Q), added to
+// acc[k * stride].
+__device__ __forceinline__ void diag_view_terms(const GaussGeo& G, const float (&Q)[kDiagBlock], const DevCam& cam,
+                                                const float* __restrict__ P, long long ld, int g, int smooth,
+                                                float* acc, int stride) {
+  ViewGeo VG;
+  view_geo(G, cam, VG);
+  float Y[16];
+  sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
+  bool live[3];
+  float grad[3][3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float w[16];
+    float raw = kShOffset;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      w[k] = P[(11 + 3 * k + ch) * ld + g];
+      raw += Y[k] * w[k];
+    }
+    live[ch] = smooth || raw >= 0.f;
+    sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], w, grad[ch]);
+  }
+  const float D[3] = {Q[39], Q[40], Q[41]};   // per channel: the weights differ between channels
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+      if (live[ch]) acc[(11 + 3 * k + ch) * stride] += D[ch] * Y[k] * Y[k];
+  // the 11 geometric parameters: unit tangents
+#pragma unroll 1
+  for (int k = 0; k < 11; ++k) {
+    // unit tangent of parameter k, built with selects (k is not a
+    // compile-time index here, and arrays indexed by it would go to local memory)
+    float mud[3], ds[3], dq[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      mud[i] = k == i ? 1.f : 0.f;
+      ds[i] = k == 3 + i ? 1.f : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dq[i] = k == 6 + i ? 1.f : 0.f;
+    const float od = k == 10 ? G.o * (1.f - G.o) : 0.f;
+    float Sd[6];
+    sigma_tangent(G, ds, dq, Sd);
+    float yv[9];
+    geo_tangent(VG, cam, mud, Sd, yv);
+    yv[5] = od;
+    if (k < 3) {
+      const float md = k == 0 ? VG.dir[0] : k == 1 ? VG.dir[1] : VG.dir[2];
+      float dd[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dd[i] = ((i == k ? 1.f : 0.f) - VG.dir[i] * md) * VG.inv_dlen;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch)
+        yv[6 + ch] = live[ch] ? grad[ch][0] * dd[0] + grad[ch][1] * dd[1] + grad[ch][2] * dd[2] : 0.f;
+    } else {
+      yv[6] = yv[7] = yv[8] = 0.f;
+    }
+    // v^T Q v with Q = [[Qgg, X], [X^T, diag(D)]]
+    float a = 0.f;
+    int idx = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i; j < 6; ++j) {
+        const float q = Q[idx++];
+        a += (i == j ? 1.f : 2.f) * q * yv[i] * yv[j];
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a += 2.f * Q[21 + i * 3 + c] * yv[i] * yv[6 + c];
+    a += D[0] * yv[6] * yv[6] + D[1] * yv[7] * yv[7] + D[2] * yv[8] * yv[8];
+    acc[k * stride] += a;
+  }
+}
+
+// The splat's block Q: its precomputed sum (splat_q), or the sum of its
+// segments' blocks. Returns false for a splat without segments.
+__device__ __forceinline__ bool splat_block(const float* __restrict__ splat_q, const float* __restrict__ seg_q,
+                                            const uint32_t* __restrict__ s_start,
+                                            const uint32_t* __restrict__ s_end, long long sk,
+                                            float (&Q)[kDiagBlock]) {
+#pragma unroll
+  for (int i = 0; i < kDiagBlock; ++i) Q[i] = 0.f;
+  if (splat_q != nullptr) {
+    const float4* q4 = reinterpret_cast<const float4*>(splat_q + (size_t)sk * kDiagBlock);
+#pragma unroll
+    for (int i = 0; i < kDiagBlock / 4; ++i) {
+      const float4 t = q4[i];
+      Q[4 * i + 0] = t.x; Q[4 * i + 1] = t.y; Q[4 * i + 2] = t.z; Q[4 * i + 3] = t.w;
+    }
+    return true;
+  }
+  const uint32_t a = s_start[sk], b = s_end[sk];
+  for (uint32_t j = a; j < b; ++j) {
+    const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * kDiagBlock);   // splat order
+#pragma unroll
+    for (int i = 0; i < kDiagBlock / 4; ++i) {
+      const float4 t = q4[i];
+      Q[4 * i + 0] += t.x; Q[4 * i + 1] += t.y; Q[4 * i + 2] += t.z; Q[4 * i + 3] += t.w;
+    }
+  }
+  return a != b;
+}
+
+// Two warps of 32 Gaussians (lane = Gaussian). Each thread's 59 sums sit in
+// its own column of shared memory (as a register array indexed by the rolled
+// column loop they would live in local memory). With view masks a warp deals
+// its Gaussians' (Gaussian, view) pairs to its lanes, 32 at a time: a pair's
+// 59 terms go to its row of the warp's chunk, and each owner adds its rows in
+// view order (the order of a lane walking its own views). Without masks (more
+// than 64 views) each lane walks its own views.
+constexpr int kDiagThreads = 64;
+struct DiagShared {
+  float sd[kNP][kDiagThreads];
+  float rows[kDiagThreads / 32][32 * kNP];   // row stride 59 (odd): no bank conflicts
+  WarpDeal deal[kDiagThreads / 32];
+};
+__global__ void __launch_bounds__(kDiagThreads, 6) k_diag(
     const float* __restrict__ P, int N, long long ld, const DevCam* __restrict__ cams, int V, int smooth,
     const uint32_t* __restrict__ s_start, const uint32_t* __restrict__ s_end,
     const unsigned long long* __restrict__ vmask, const uint32_t* __restrict__ act_off,
     const float* __restrict__ seg_q, const float* __restrict__ splat_q, float* __restrict__ dout) {
-  // the thread's 59 sums, one column of shared memory per thread (no thread
-  // reads another's, so no barrier): as a register array indexed by the
-  // geometric column loop they would live in local memory
-  __shared__ float sd[kNP][kDiagThreads];
-  float* d = &sd[0][threadIdx.x];   // d[k * kDiagThreads] is sum k
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= N) return;
+  __shared__ DiagShared S;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * kDiagThreads + threadIdx.x;
+  const bool valid = g < N;
+  float* d = &S.sd[0][threadIdx.x];   // d[k * kDiagThreads] is sum k
 #pragma unroll
   for (int k = 0; k < kNP; ++k) d[k * kDiagThreads] = 0.f;
-  bool any = false;
-  GaussGeo G;
-  const bool use_mask = vmask != nullptr;
-  unsigned long long mm = use_mask ? vmask[g] : 0ull;
-  long long key = use_mask ? (long long)act_off[g] : 0;   // splat key as in vjp_body
-  for (int v = next_view(use_mask, mm, -1, V); v < V; v = next_view(use_mask, mm, v, V)) {
-    const long long sk = use_mask ? key++ : (long long)v * N + g;
-    float Q[kDiagBlock];
-#pragma unroll
-    for (int i = 0; i < kDiagBlock; ++i) Q[i] = 0.f;
-    // the splat's block: summed over its segments beforehand (splat_q), or here
-    const uint32_t a = splat_q != nullptr ? 0u : s_start[sk], b = splat_q != nullptr ? 0u : s_end[sk];
-    if (splat_q != nullptr) {
-      const float4* q4 = reinterpret_cast<const float4*>(splat_q + (size_t)sk * kDiagBlock);
-#pragma unroll
-      for (int i = 0; i < kDiagBlock / 4; ++i) {
-        const float4 t = q4[i];
-        Q[4 * i + 0] = t.x; Q[4 * i + 1] = t.y; Q[4 * i + 2] = t.z; Q[4 * i + 3] = t.w;
+  if (vmask == nullptr) {
+    if (!valid) return;
+    GaussGeo G;
+    bool any = false;
+    for (int v = 0; v < V; ++v) {
+      float Q[kDiagBlock];
+      if (!splat_block(splat_q, seg_q, s_start, s_end, (long long)v * N + g, Q)) continue;
+      if (!any) {
+        gauss_geo(P, ld, g, G);
+        any = true;
       }
-    } else if (a == b) {
-      continue;
+      diag_view_terms(G, Q, cams[v], P, ld, g, smooth, d, kDiagThreads);
     }
-    if (!any) {
-      gauss_geo(P, ld, g, G);
-      any = true;
-    }
-    for (uint32_t j = a; j < b; ++j) {
-      const float4* q4 = reinterpret_cast<const float4*>(seg_q + (size_t)j * kDiagBlock);   // splat order
+  } else {
+    const unsigned long long m0 = valid ? vmask[g] : 0ull;
+    WarpDeal& D = S.deal[warp];
+    const uint32_t total = deal_setup(D, m0, m0 != 0ull ? act_off[g] : 0u, lane);
+    const uint32_t my0 = D.off[lane], my1 = my0 + (uint32_t)__popcll(m0);
+    const int gw = blockIdx.x * kDiagThreads + warp * 32;   // the warp's first Gaussian
+    float* rows = S.rows[warp];
+    for (uint32_t cb = 0; cb < total; cb += 32) {
+      const uint32_t t = cb + lane;
+      if (t < total) {
+        float* row = rows + lane * kNP;
 #pragma unroll
-      for (int i = 0; i < kDiagBlock / 4; ++i) {
-        const float4 t = q4[i];
-        Q[4 * i + 0] += t.x; Q[4 * i + 1] += t.y; Q[4 * i + 2] += t.z; Q[4 * i + 3] += t.w;
-      }
-    }
-    const DevCam& cam = cams[v];
-    ViewGeo VG;
-    view_geo(G, cam, VG);
-    float Y[16];
-    sh_basis(VG.dir[0], VG.dir[1], VG.dir[2], Y);
-    bool live[3];
-    float grad[3][3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float w[16];
-      float raw = kShOffset;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        w[k] = P[(11 + 3 * k + ch) * ld + g];
-        raw += Y[k] * w[k];
-      }
-      live[ch] = smooth || raw >= 0.f;
-      sh_grad(VG.dir[0], VG.dir[1], VG.dir[2], w, grad[ch]);
-    }
-    const float D[3] = {Q[39], Q[40], Q[41]};   // per channel: the weights differ between channels
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch)
-        if (live[ch]) d[(11 + 3 * k + ch) * kDiagThreads] += D[ch] * Y[k] * Y[k];
-    // the 11 geometric parameters: unit tangents
-#pragma unroll 1
-    for (int k = 0; k < 11; ++k) {
-      // unit tangent of parameter k, built with selects (k is not a
-      // compile-time index here, and arrays indexed by it would go to local memory)
-      float mud[3], ds[3], dq[4];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        mud[i] = k == i ? 1.f : 0.f;
-        ds[i] = k == 3 + i ? 1.f : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) dq[i] = k == 6 + i ? 1.f : 0.f;
-      const float od = k == 10 ? G.o * (1.f - G.o) : 0.f;
-      float Sd[6];
-      sigma_tangent(G, ds, dq, Sd);
-      float yv[9];
-      geo_tangent(VG, cam, mud, Sd, yv);
-      yv[5] = od;
-      if (k < 3) {
-        const float md = k == 0 ? VG.dir[0] : k == 1 ? VG.dir[1] : VG.dir[2];
-        float dd[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) dd[i] = ((i == k ? 1.f : 0.f) - VG.dir[i] * md) * VG.inv_dlen;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch)
-          yv[6 + ch] = live[ch] ? grad[ch][0] * dd[0] + grad[ch][1] * dd[1] + grad[ch][2] * dd[2] : 0.f;
-      } else {
-        yv[6] = yv[7] = yv[8] = 0.f;
-      }
-      // v^T Q v with Q = [[Qgg, X], [X^T, diag(D)]]
-      float acc = 0.f;
-      int idx = 0;
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = i; j < 6; ++j) {
-          const float q = Q[idx++];
-          acc += (i == j ? 1.f : 2.f) * q * yv[i] * yv[j];
+        for (int k = 0; k < kNP; ++k) row[k] = 0.f;
+        int o, v;
+        long long sk;
+        deal_pair(D, t, o, v, sk);
+        float Q[kDiagBlock];
+        if (splat_block(splat_q, seg_q, s_start, s_end, sk, Q)) {
+          GaussGeo G;
+          gauss_geo(P, ld, gw + o, G);
+          diag_view_terms(G, Q, cams[v], P, ld, gw + o, smooth, row, 1);
         }
+      }
+      __syncwarp();
+      for (uint32_t tt = max(my0, cb); tt < min(my1, cb + 32u); ++tt) {
+        const float* row = rows + (tt - cb) * kNP;
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc += 2.f * Q[21 + i * 3 + c] * yv[i] * yv[6 + c];
-      acc += D[0] * yv[6] * yv[6] + D[1] * yv[7] * yv[7] + D[2] * yv[8] * yv[8];
-      d[k * kDiagThreads] += acc;
+        for (int k = 0; k < kNP; ++k) d[k * kDiagThreads] += row[k];
+      }
+      __syncwarp();   // the next chunk rewrites the rows
     }
+    if (!valid) return;
   }
 #pragma unroll
   for (int k = 0; k < kNP; ++k) dout[k * ld + g] = d[k * kDiagThreads];

@@ -1,5 +1,6 @@
 """Edge cases of the CUDA path (GPU only): an empty scene, a single Gaussian,
-views of 1x1 and 17x3 pixels, and invalid arguments.
+views of 1x1 and 17x3 pixels, a cache of more than 64 views, and invalid
+arguments.
 
 The empty scene has every Gaussian behind the camera: no splat, no tile key,
 no cache entry. Everything must still run and give the defined results: a
@@ -98,6 +99,42 @@ def test_small_cases_match_the_oracle(lib, n, W, H):
     d_ref = J.jacobi_diag(lin, N)
     if np.linalg.norm(d_ref) > 0 and mask.all():
         assert rel_l2(d, d_ref) < 1e-4
+    cache.free()
+
+
+def test_more_than_64_views_match_the_oracle(lib):
+    """A cache of 70 views has no 64-bit view masks, so the per-Gaussian kernels
+    (tangent, adjoint, diagonal) walk each Gaussian's views themselves instead of
+    dealing the (Gaussian, view) pairs of a warp to its lanes."""
+    from oracle import jacobian as J
+    wl = synth.small_workload("manyviews", 43, 200, 70, 32, 24, cam_radius=4.0, log_scale_mean=-3.2)
+    P = synth.make_gaussians(wl)
+    cams = synth.make_cameras(wl)
+    tgt = np.concatenate([im.ravel() for im in synth.smooth_images(43, cams)]).astype(np.float32)
+    N = P.shape[0]
+    lin = J.linearise(P.astype(np.float64), cams)
+    mask = np.concatenate([(vl.ras.margin >= 1e-4) & ~vl.ras.flip for vl in lin])
+    n_res = J.n_residuals(cams)
+    ctx = lib.Context()
+    cache = ctx.build_cache(lib.to_soa(P), N, cams, torch.from_numpy(tgt).cuda().view(-1, 3))
+    assert cache.info().views == 70 and cache.info().entries > 0
+    p = synth.random_vector(2, (N, N_PARAMS))
+    u = ctx.apply_J(cache, lib.to_soa(p)).cpu().numpy()
+    u_ref = J.apply_J(lin, p.astype(np.float64), n_res).reshape(-1, 3)
+    assert rel_l2(u[mask], u_ref[mask]) < 1e-4
+    uu = np.where(np.repeat(mask, 3).reshape(-1, 3), synth.random_vector(3, (n_res // 3, 3)), 0.0).astype(np.float32)
+    g = lib.from_soa(ctx.apply_JT(cache, torch.from_numpy(uu).cuda()), N)
+    assert rel_l2(g, J.apply_JT(lin, uu.astype(np.float64).ravel(), N)) < 1e-4
+    # the diagonal of every Gaussian none of whose records sits at a pixel with a
+    # near-threshold blending decision (the diagonal sums over all pixels)
+    flagged = np.zeros(N, bool)
+    for vl in lin:
+        bad = ~mask[vl.pix_off // 3 + vl.ras.rec_pix]
+        flagged[vl.gauss[bad]] = True
+    assert (~flagged).sum() > N // 2
+    d = lib.from_soa(ctx.jacobi_diag(cache), N)
+    d_ref = J.jacobi_diag(lin, N)
+    assert rel_l2(d[~flagged], d_ref[~flagged]) < 1e-4
     cache.free()
 
 
