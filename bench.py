@@ -609,9 +609,10 @@ def oracle_step_entries_estimate(workload: str = "paper", n_views: int = 2, tile
 # ----------------------------------------------------------------------------- arms
 def run_reference(args):
     """The oracle on the host cores, on a bounded sample of the workload: each step is
-    one oracle LM step on the crop sample (one process per image subset); the value
-    is scaled to one step of the whole workload by cache entries (an extrapolation,
-    labelled so; the measured sample time is reported beside it)."""
+    one oracle LM step on the crop sample (one process per image subset), and the
+    value is that measured step's time, so that the steps fit the run's own clock.
+    The same time scaled to one step of the whole workload by cache entries is
+    reported beside it as an extrapolation, labelled so."""
     rank, ws, dist = dist_init("gloo")
     if rank != 0:
         return 0
@@ -621,16 +622,16 @@ def run_reference(args):
     wl, Pc, subsets, targets = oracle_sample_inputs(args.workload, args.cpu_views)
     runs = [oracle_lm_step_timed(Pc, subsets, targets, wl.lambda0, wl.pcg_iters, 0.01, workers=len(subsets))
             for _ in range(args.warmup + args.steps)][args.warmup:]
-    sample_ms = statistics.mean(r["ms"] for r in runs)
+    value = statistics.mean(r["ms"] for r in runs)
     entries = runs[0]["entries"]
-    value = sample_ms * E_step / max(entries, 1)
     nproc = os.cpu_count() or 1
-    cb = {"value": value, "unit": "ms", "cores": min(nproc, len(subsets)), "kind": "oracle",
-          "sample": ORACLE_SAMPLE.format(ng=ORACLE_SAMPLE_GAUSSIANS, vps=args.cpu_views), "cpu_model": cpu_model(), "host_cores": nproc,
-          "value_kind": "extrapolated: measured sample ms x (cache entries of one workload step, estimated by the "
-                        "oracle on a 5% tile sample of two views) / (cache entries of the sample)",
-          "measured_sample_ms": sample_ms, "sample_entries": entries, "step_entries_estimate": E_step,
-          "estimate_seconds": t_est}
+    cb = {"value": value, "unit": "ms per sample LM step", "cores": min(nproc, len(subsets)), "kind": "oracle",
+          "sample": ORACLE_SAMPLE.format(ng=ORACLE_SAMPLE_GAUSSIANS, vps=args.cpu_views), "cpu_model": cpu_model(),
+          "host_cores": nproc, "value_kind": "measured: one oracle LM step of the sample, mean over the timed steps",
+          "extrapolated_full_step_ms": value * E_step / max(entries, 1),
+          "extrapolation": "the sample's ms x (cache entries of one workload step, estimated by the oracle on a "
+                           "5% tile sample of two views) / (cache entries of the sample)",
+          "sample_entries": entries, "step_entries_estimate": E_step, "estimate_seconds": t_est}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
